@@ -1,0 +1,161 @@
+/*
+ * pfc.h - C ABI of the GB300 (sm_103a) semi-implicit Fourier pseudo-spectral
+ * phase-field-crystal (PFC) library, libpfc.so.
+ *
+ * The method (paper: "Multi-GPU fast Fourier transforms in MATLAB for large-scale phase-field
+ * crystal simulations"): a periodic field psi on an equispaced grid evolves by the conserved
+ * PFC dynamics of Eq. (6), d_t psi = lap((eps + L) psi + psi^3), discretised pseudo-spectrally
+ * (Eqs. (1)-(4)) with semi-implicit time integration (the update of Listing 1):
+ *
+ *     psi_hat <- (psi_hat - dt k^2 FFT(psi^3)) / (1 + dt k^2 Lk(k)),
+ *
+ * Lk(k) = eps + L(k). One-mode: Lk = r + (1 - k^2)^2. Two-mode (tenth-order PDE, the paper's
+ * FCC operator of Eq. (5) when R1 = 0 and q2^2 = 4/3): Lk = r + (1 - k^2)^2 (R1 + (q2^2 - k^2)^2).
+ *
+ * Conventions shared by every call:
+ *   - dims are given slowest first, like a C array or a torch/numpy shape: 2D (ny, nx),
+ *     3D (nz, ny, nx); x is contiguous. Every extent must be a power of two in [8, 4096]
+ *     (ny, nz >= 8 also), otherwise PFC_ERR_UNSUPPORTED.
+ *   - Box length per axis is n dx; k = 2 pi m / (n dx) with m in FFT order.
+ *   - Real arrays hold nfields fields back to back, each nz*ny*nx values; complex arrays
+ *     are interleaved (re, im) with the half-spectrum shape (nz, ny, nx/2 + 1).
+ *   - Element type: double for PFC_FP64, float for PFC_FP32_MIXED (complex: double2 / float2).
+ *   - All array pointers are DEVICE pointers (16-byte aligned) owned by the caller, unless a
+ *     parameter says "host". The plan owns its scratch, tables, status word and graphs.
+ *   - Calls are asynchronous and stream-ordered on the plan's stream, except pfc_mass,
+ *     pfc_energy and pfc_sync, which synchronise that stream.
+ *   - A plan is not thread-safe. Out-parameters are written only on PFC_OK.
+ *   - No C++ exception crosses the ABI. After a non-OK status, pfc_last_error() returns a
+ *     one-line description (thread-local, valid until the next call on the same thread).
+ */
+#ifndef PFC_H
+#define PFC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PFC_OK = 0,
+    PFC_ERR_INVALID_ARG = 1,        /* null pointer, bad count, non-positive dx or dt, ... */
+    PFC_ERR_UNSUPPORTED = 2,        /* a size or option this build does not implement */
+    PFC_ERR_UNSTABLE_OPERATOR = 3,  /* min_k (1 + dt k^2 Lk) <= 0 (or a coupled det <= 0) */
+    PFC_ERR_OUT_OF_MEMORY = 4,      /* device allocation failed */
+    PFC_ERR_CUDA = 5,               /* a CUDA runtime call failed */
+    PFC_ERR_NONFINITE = 6,          /* a reduction met NaN or Inf in the state */
+    PFC_ERR_TIMEOUT = 7             /* a bounded device-side wait gave up */
+} pfc_status;
+
+typedef enum { PFC_FP64 = 0, PFC_FP32_MIXED = 1 } pfc_precision;
+
+typedef enum { PFC_ONE_MODE = 0, PFC_TWO_MODE = 1 } pfc_op_kind;
+
+/* Linear PFC symbol Lk(k) (Eq. (5)-(6)); kind is a pfc_op_kind. R1 and q2 are read only for
+ * PFC_TWO_MODE. */
+typedef struct {
+    int kind;
+    double r;
+    double R1;
+    double q2;
+} pfc_op;
+
+typedef struct pfc_plan pfc_plan;
+
+/* Create a plan for nfields coupled fields on one grid.
+ *   ndim      2 or 3; dims[ndim] slowest first.
+ *   dx, dt    grid spacing and time step, > 0.
+ *   ops       nfields operators (host array).
+ *   nfields   1, or 2 for the density/composition pair. With 2 fields both are conserved
+ *             and the linear coupling alpha psi c enters both chemical potentials; the
+ *             per-mode 2x2 implicit system is solved exactly.
+ *   coupling  host nfields*nfields symmetric matrix, only the off-diagonal read; NULL = 0.
+ *   precision PFC_FP64 (all FP64) or PFC_FP32_MIXED (FP32 data and butterflies, twiddles
+ *             generated in FP64 and rounded, FP64 reductions, the k = 0 mode carried in FP64).
+ *   stream    cudaStream_t the plan issues all its work on (NULL = legacy default stream).
+ * Allocates the plan's device scratch (about 2 * nfields half-spectra) with cudaMalloc.
+ * Errors: INVALID_ARG, UNSUPPORTED, UNSTABLE_OPERATOR, OUT_OF_MEMORY, CUDA. */
+pfc_status pfc_plan_create(pfc_plan **out, int ndim, const int64_t *dims, double dx, double dt,
+                           const pfc_op *ops, int nfields, const double *coupling,
+                           int precision, void *stream);
+
+/* Release the plan and its device memory (synchronises its stream first). NULL is a no-op. */
+pfc_status pfc_plan_destroy(pfc_plan *plan);
+
+/* Advance state (device, real, nfields fields) by nsteps >= 0 semi-implicit steps, in place.
+ * One step is psi -> IFFT[(FFT psi - dt k^2 FFT psi^3) / (1 + dt k^2 Lk)] (Listing 1 update,
+ * Eq. (6)). The mean of each field (mass, the k = 0 mode) is held in FP64 across the call and
+ * is conserved exactly. nsteps = 0 leaves state untouched. */
+pfc_status pfc_step(pfc_plan *plan, void *state, int64_t nsteps);
+
+/* Forward real-to-complex transform of each field, unnormalised (Eq. (4), MATLAB fft):
+ * in_real (device, real) -> out_half (device, complex half spectrum). in_real is not modified;
+ * the arrays must not overlap. */
+pfc_status pfc_fft_r2c(pfc_plan *plan, const void *in_real, void *out_half);
+
+/* Inverse complex-to-real transform with the 1/N factor (MATLAB ifft); the imaginary parts
+ * of the kx = 0 and kx = nx/2 bins are ignored. in_half is not modified. */
+pfc_status pfc_fft_c2r(pfc_plan *plan, const void *in_half, void *out_real);
+
+/* Mass: the mean density of each field, out_host[nfields] (host), FP64 accumulation.
+ * Synchronises. Errors: NONFINITE if the state holds NaN or Inf. */
+pfc_status pfc_mass(pfc_plan *plan, const void *state, double *out_host);
+
+/* Energy density F/|Omega| of Eq. (5), summed over the plan's fields, out_host (host, one
+ * double): mean over points of psi Lk psi / 2 + psi^4 / 4 (+ alpha psi c for two fields),
+ * the quadratic part evaluated in Fourier space by Parseval, FP64 accumulation. Synchronises. */
+pfc_status pfc_energy(pfc_plan *plan, const void *state, double *out_host);
+
+/* Adjoint of one step (single-field plans). With psi_{n+1} = A psi_n - B psi_n^3,
+ * A = IFFT (1/D) FFT, B = IFFT (dt k^2/D) FFT, D = 1 + dt k^2 Lk:
+ *     lam_out = A lam_next - 3 psi_n^2 (B lam_next)
+ *     *dr_accum_dev += < lam_next, d psi_{n+1} / d r >,  d psi_{n+1}/dr = IFFT(-(dt k^2/D) psi_hat_{n+1})
+ * psi_n, lam_next, lam_out: device real arrays (lam_out may alias lam_next).
+ * dr_accum_dev: one device double, accumulated in FP64 (stream ordered, not synchronised). */
+pfc_status pfc_step_adjoint(pfc_plan *plan, const void *psi_n, const void *lam_next,
+                            void *lam_out, double *dr_accum_dev);
+
+/* Change r of field `field` (0-based); re-checks operator stability. */
+pfc_status pfc_set_r(pfc_plan *plan, int field, double r);
+
+/* Synchronise the plan's stream and return the latched device status (TIMEOUT, NONFINITE),
+ * clearing it. */
+pfc_status pfc_sync(pfc_plan *plan);
+
+/* Tile choice and memory of a plan (host out-params).
+ *   tiles[8] = {Py, Pz, Qy, Qz, W, row_groups_per_cta, threads_row, threads_line}
+ *   scratch_bytes = device bytes the plan owns. */
+pfc_status pfc_plan_info(pfc_plan *plan, int32_t *tiles, int64_t *scratch_bytes);
+
+/* Names of a status code and of the last error on this thread. Never NULL. */
+const char *pfc_status_string(pfc_status status);
+const char *pfc_last_error(void);
+
+/* ---------------------------------------------------------------------------------- */
+/* Batched ensemble: many independent 2D one-mode domains of uneven sizes stepped by one */
+/* launch per pass (a work list over all domains), the whole nsteps loop captured once  */
+/* in a CUDA graph.                                                                      */
+/* ---------------------------------------------------------------------------------- */
+typedef struct pfc_batch pfc_batch;
+
+/* ndomains >= 1 domains; dims_host[2*d] = ny, dims_host[2*d+1] = nx of domain d (powers of two
+ * in [8, 512]); r_host[d] its one-mode r. All share dx, dt and the precision. The packed state
+ * holds the domains back to back in index order, domain d at element offset
+ * sum_{e<d} ny_e nx_e. */
+pfc_status pfc_batch_create(pfc_batch **out, int ndomains, const int64_t *dims_host,
+                            const double *r_host, double dx, double dt, int precision,
+                            void *stream);
+pfc_status pfc_batch_destroy(pfc_batch *batch);
+
+/* Advance every domain of the packed device state by nsteps. */
+pfc_status pfc_batch_step(pfc_batch *batch, void *packed_state, int64_t nsteps);
+
+/* Per-domain mass (mean), out_host[ndomains]. Synchronises. */
+pfc_status pfc_batch_mass(pfc_batch *batch, const void *packed_state, double *out_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFC_H */

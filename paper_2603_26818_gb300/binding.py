@@ -1,0 +1,229 @@
+"""ctypes binding of libpfc.so (include/pfc.h): argument marshalling only.
+
+Every number is computed by the library's CUDA kernels. Device memory and streams come from
+PyTorch: arrays are CUDA tensors, the stream is torch's current stream at plan creation. If
+the library has not been built this module raises on first use; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpfc.so")
+
+PFC_OK = 0
+STATUS_NAMES = {0: "PFC_OK", 1: "PFC_ERR_INVALID_ARG", 2: "PFC_ERR_UNSUPPORTED",
+                3: "PFC_ERR_UNSTABLE_OPERATOR", 4: "PFC_ERR_OUT_OF_MEMORY", 5: "PFC_ERR_CUDA",
+                6: "PFC_ERR_NONFINITE", 7: "PFC_ERR_TIMEOUT"}
+PFC_FP64, PFC_FP32_MIXED = 0, 1
+PFC_ONE_MODE, PFC_TWO_MODE = 0, 1
+
+# every extern "C" symbol of include/pfc.h
+EXPORTS = ["pfc_plan_create", "pfc_plan_destroy", "pfc_step", "pfc_fft_r2c", "pfc_fft_c2r",
+           "pfc_mass", "pfc_energy", "pfc_step_adjoint", "pfc_set_r", "pfc_sync", "pfc_plan_info",
+           "pfc_status_string", "pfc_last_error", "pfc_batch_create", "pfc_batch_destroy",
+           "pfc_batch_step", "pfc_batch_mass"]
+
+
+class PfcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        self.name = STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{self.name}: {message}")
+
+
+class pfc_op(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("r", ctypes.c_double), ("R1", ctypes.c_double),
+                ("q2", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpfc.so and declare its signatures. Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it first (python -c 'import __graft_entry__ as g;"
+                           " g.build()'); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    vp, i64, dbl, cint = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    P = ctypes.POINTER
+    sig = {
+        "pfc_plan_create": [P(vp), cint, P(i64), dbl, dbl, P(pfc_op), cint, P(dbl), cint, vp],
+        "pfc_plan_destroy": [vp],
+        "pfc_step": [vp, vp, i64],
+        "pfc_fft_r2c": [vp, vp, vp],
+        "pfc_fft_c2r": [vp, vp, vp],
+        "pfc_mass": [vp, vp, P(dbl)],
+        "pfc_energy": [vp, vp, P(dbl)],
+        "pfc_step_adjoint": [vp, vp, vp, vp, vp],
+        "pfc_set_r": [vp, cint, dbl],
+        "pfc_sync": [vp],
+        "pfc_plan_info": [vp, P(ctypes.c_int32), P(i64)],
+        "pfc_batch_create": [P(vp), cint, P(i64), P(dbl), dbl, dbl, cint, vp],
+        "pfc_batch_destroy": [vp],
+        "pfc_batch_step": [vp, vp, i64],
+        "pfc_batch_mass": [vp, vp, P(dbl)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = cint
+    lib.pfc_status_string.argtypes = [cint]
+    lib.pfc_status_string.restype = ctypes.c_char_p
+    lib.pfc_last_error.argtypes = []
+    lib.pfc_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def check(status: int):
+    if status != PFC_OK:
+        msg = load_library().pfc_last_error().decode()
+        raise PfcError(status, msg)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dev_ptr(t: torch.Tensor, dtype, name: str) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise PfcError(1, f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise PfcError(1, f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise PfcError(1, f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def make_op(kind=PFC_ONE_MODE, r=-0.25, R1=0.0, q2=0.0) -> pfc_op:
+    return pfc_op(int(kind), float(r), float(R1), float(q2))
+
+
+class Plan:
+    """A pfc_plan: one grid (2D or 3D), nfields fields, one precision, one stream."""
+
+    def __init__(self, dims, dx, dt, ops, precision="fp64", coupling=None, stream=None):
+        lib = load_library()
+        if isinstance(ops, pfc_op):
+            ops = [ops]
+        ops = [o if isinstance(o, pfc_op) else make_op(*o) for o in ops]
+        self.dims = tuple(int(d) for d in dims)
+        self.ndim = len(self.dims)
+        self.nfields = len(ops)
+        self.precision = precision
+        self.real_dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.complex_dtype = torch.complex128 if precision == "fp64" else torch.complex64
+        prec = PFC_FP64 if precision == "fp64" else PFC_FP32_MIXED
+        dims_arr = (ctypes.c_int64 * self.ndim)(*self.dims)
+        ops_arr = (pfc_op * self.nfields)(*ops)
+        coup = None
+        if coupling is not None:
+            coup = (ctypes.c_double * 4)(0.0, float(coupling), float(coupling), 0.0)
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        check(lib.pfc_plan_create(ctypes.byref(h), self.ndim, dims_arr, float(dx), float(dt),
+                                  ops_arr, self.nfields, coup, prec,
+                                  ctypes.c_void_p(_stream_handle(self._stream))))
+        self._h = h
+        self.dx, self.dt = float(dx), float(dt)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def real_shape(self):
+        return ((self.nfields,) if self.nfields > 1 else ()) + self.dims
+
+    def half_shape(self):
+        return ((self.nfields,) if self.nfields > 1 else ()) + self.dims[:-1] + (self.dims[-1] // 2 + 1,)
+
+    def _check_real(self, t, name):
+        if tuple(t.shape) != self.real_shape():
+            raise PfcError(1, f"{name} has shape {tuple(t.shape)}, expected {self.real_shape()}")
+        return _dev_ptr(t, self.real_dtype, name)
+
+    def step(self, state: torch.Tensor, nsteps: int = 1) -> torch.Tensor:
+        p = self._check_real(state, "state")
+        check(load_library().pfc_step(self._h, ctypes.c_void_p(p), int(nsteps)))
+        return state
+
+    def fft_r2c(self, x: torch.Tensor, out: torch.Tensor = None) -> torch.Tensor:
+        p = self._check_real(x, "x")
+        if out is None:
+            out = torch.empty(self.half_shape(), dtype=self.complex_dtype, device=x.device)
+        q = _dev_ptr(out, self.complex_dtype, "out")
+        check(load_library().pfc_fft_r2c(self._h, ctypes.c_void_p(p), ctypes.c_void_p(q)))
+        return out
+
+    def fft_c2r(self, xh: torch.Tensor, out: torch.Tensor = None) -> torch.Tensor:
+        if tuple(xh.shape) != self.half_shape():
+            raise PfcError(1, f"xh has shape {tuple(xh.shape)}, expected {self.half_shape()}")
+        p = _dev_ptr(xh, self.complex_dtype, "xh")
+        if out is None:
+            out = torch.empty(self.real_shape(), dtype=self.real_dtype, device=xh.device)
+        q = self._check_real(out, "out")
+        check(load_library().pfc_fft_c2r(self._h, ctypes.c_void_p(p), ctypes.c_void_p(q)))
+        return out
+
+    def mass(self, state: torch.Tensor):
+        p = self._check_real(state, "state")
+        out = (ctypes.c_double * self.nfields)()
+        check(load_library().pfc_mass(self._h, ctypes.c_void_p(p), out))
+        return list(out)
+
+    def energy(self, state: torch.Tensor) -> float:
+        p = self._check_real(state, "state")
+        out = ctypes.c_double()
+        check(load_library().pfc_energy(self._h, ctypes.c_void_p(p), ctypes.byref(out)))
+        return out.value
+
+    def step_adjoint(self, psi_n, lam_next, lam_out, dr_accum: torch.Tensor):
+        a = self._check_real(psi_n, "psi_n")
+        b = self._check_real(lam_next, "lam_next")
+        c = self._check_real(lam_out, "lam_out")
+        d = _dev_ptr(dr_accum, torch.float64, "dr_accum")
+        check(load_library().pfc_step_adjoint(self._h, ctypes.c_void_p(a), ctypes.c_void_p(b),
+                                              ctypes.c_void_p(c), ctypes.c_void_p(d)))
+        return lam_out
+
+    def set_r(self, r: float, field: int = 0):
+        check(load_library().pfc_set_r(self._h, int(field), float(r)))
+
+    def sync(self):
+        check(load_library().pfc_sync(self._h))
+
+    def info(self):
+        tiles = (ctypes.c_int32 * 8)()
+        sb = ctypes.c_int64()
+        check(load_library().pfc_plan_info(self._h, tiles, ctypes.byref(sb)))
+        keys = ["Py", "Pz", "Qy", "Qz", "W", "gpc", "threads_row", "threads_line"]
+        d = dict(zip(keys, list(tiles)))
+        d["scratch_bytes"] = sb.value
+        return d
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            check(load_library().pfc_plan_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,633 @@
+// Host side of libpfc.so: plans, tile planning, launches, CUDA graphs and the C ABI of pfc.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pfc.h"
+#include "pfc_reduce.cuh"
+
+using namespace pfc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+pfc_status fail(pfc_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+#define PFC_CUDA(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? PFC_ERR_OUT_OF_MEMORY : PFC_ERR_CUDA, \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+    } while (0)
+
+int ilog2(int64_t v) {
+    int l = 0;
+    while ((int64_t(1) << l) < v) ++l;
+    return l;
+}
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// exp(-2 pi i t / n) in FP64 with the angle reduced to the first octant, so every entry is
+// the correctly rounded cosine/sine of a small argument (or an exact symmetry of one).
+void unit_root_fwd(int64_t t, int64_t n, double *re, double *im) {
+    t %= n;
+    const int64_t q = (4 * t) / n, rr = 4 * t - q * n;   // angle = (pi/2)(q + rr/n)
+    double c, s;
+    if (2 * rr <= n) {
+        const double phi = (M_PI / 2) * (double)rr / (double)n;
+        c = std::cos(phi);
+        s = std::sin(phi);
+    } else {
+        const double phi = (M_PI / 2) * (double)(n - rr) / (double)n;
+        c = std::sin(phi);
+        s = std::cos(phi);
+    }
+    double cc, ss;   // rotate by q quarter turns
+    switch (q) {
+        case 0: cc = c; ss = s; break;
+        case 1: cc = -s; ss = c; break;
+        case 2: cc = -c; ss = -s; break;
+        default: cc = s; ss = -c; break;
+    }
+    *re = cc;
+    *im = -ss;
+}
+
+double lin_symbol_host(const pfc_op &op, double k2) {
+    const double a = 1.0 - k2;
+    if (op.kind == PFC_ONE_MODE) return op.r + a * a;
+    const double b = op.q2 * op.q2 - k2;
+    return op.r + a * a * (op.R1 + b * b);
+}
+
+// min over k^2 in [0, k2max] of the implicit matrix's smallest eigenvalue (sampled densely).
+double min_implicit(const pfc_op *ops, int nfields, double alpha, double dt, double k2max) {
+    double mn = 1e300;
+    const int ns = 200000;
+    for (int i = 0; i <= ns; ++i) {
+        const double k2 = k2max * (double)i / ns;
+        const double m11 = 1.0 + dt * k2 * lin_symbol_host(ops[0], k2);
+        if (nfields == 1) {
+            mn = std::min(mn, m11);
+        } else {
+            const double m22 = 1.0 + dt * k2 * lin_symbol_host(ops[1], k2);
+            const double m12 = dt * k2 * alpha;
+            const double tr = m11 + m22, det = m11 * m22 - m12 * m12;
+            const double disc = std::sqrt(std::max(0.0, tr * tr / 4 - det));
+            mn = std::min(mn, tr / 2 - disc);
+        }
+    }
+    return mn;
+}
+
+OpDev to_dev(const pfc_op &o) { return OpDev{o.kind, o.r, o.R1, o.q2}; }
+
+struct Tiles {
+    Geom g;
+    int nt_row, nt_line;
+    size_t smem_row, smem_line;
+};
+
+// Choose the split of the y/z transforms between the passes and the tile widths.
+//   row pass:  gpc groups of P = Py Pz rows of padded length row_pad(M) + 1
+//   line pass: ntile tiles of Q W complex values (Q = ny nz / P), W columns each
+// Preference: wide line-pass rows (W * sizeof(V) up to 128 B), then the smallest P.
+bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, size_t smem_max) {
+    Geom g{};
+    g.nx = nx; g.ny = ny; g.nz = nz; g.M = nx / 2;
+    g.lnx = ilog2(nx); g.lny = ilog2(ny); g.lnz = ilog2(nz); g.lM = g.lnx - 1;
+    g.ltab = std::max(g.lnx, std::max(g.lny, g.lnz));
+    g.tpsh = 4;
+    g.rs = (int)round_up(row_pad(g.M) + 1, 2);
+    const size_t row_bytes = (size_t)g.rs * vb;
+    int best_score = -1;
+    Geom best{};
+    for (int Py = 1; Py <= 8; Py *= 2) {
+        if (Py > 1 && ny / Py < 8) continue;
+        if (ny % Py) continue;
+        for (int Pz = 1; Pz <= 8; Pz *= 2) {
+            if (nz == 1 && Pz > 1) continue;
+            if (Pz > 1 && nz / Pz < 8) continue;
+            if (nz % Pz) continue;
+            const int Qy = ny / Py, Qz = nz / Pz;
+            if (Qy < 8 && Qy != 1) continue;
+            if (Qz < 8 && Qz != 1) continue;
+            const int P = Py * Pz, Q = Qy * Qz;
+            if ((size_t)P * row_bytes > smem_max) continue;
+            for (int W = 16; W >= 1; W /= 2) {
+                if ((size_t)W * vb > 128) continue;
+                if (W > g.M + 1 && W > 1) continue;
+                const int64_t QW = (int64_t)Q * W;
+                if (QW < 8) continue;
+                const size_t tile = (size_t)(QW + (QW >> g.tpsh) + 1);
+                if ((size_t)ntile * tile * vb > smem_max) continue;
+                const int wb = (int)(W * vb);
+                const int score = wb * 64 - P;   // wide rows first, then small P
+                if (score > best_score) {
+                    best_score = score;
+                    best = g;
+                    best.Py = Py; best.Pz = Pz; best.Qy = Qy; best.Qz = Qz;
+                    best.W = W;
+                }
+                break;   // largest fitting W for this split
+            }
+        }
+    }
+    if (best_score < 0) return false;
+    g = best;
+    g.lPy = ilog2(g.Py); g.lPz = ilog2(g.Pz); g.lQy = ilog2(g.Qy); g.lQz = ilog2(g.Qz);
+    g.P = g.Py * g.Pz; g.Q = g.Qy * g.Qz; g.lQ = ilog2(g.Q);
+    g.lW = ilog2(g.W);
+    g.xs = (int)round_up(g.M + 1, std::max(g.W, 2));
+    g.ncg = g.xs / g.W;
+    // row groups per CTA: enough rows for >= 256 threads, within smem and dividing Q
+    const int Tr = g.M / 8;
+    int gpc = 1;
+    while (gpc * 2 <= g.Q && (size_t)(gpc * 2) * g.P * row_bytes <= smem_max &&
+           gpc * g.P * Tr < 256)
+        gpc *= 2;
+    g.gpc = gpc;
+    g.nreal = (int64_t)nx * ny * nz;
+    g.nhalf = (int64_t)g.P * g.Q * g.xs;
+    g.nstd = (int64_t)ny * nz * (g.M + 1);
+    t.g = g;
+    const int rows = gpc * g.P;
+    t.nt_row = std::min(512, std::max(Tr, rows * Tr));
+    if (t.nt_row < 64) t.nt_row = std::max(Tr, 64 / Tr * Tr);
+    t.smem_row = (size_t)rows * row_bytes;
+    const int64_t QW = (int64_t)g.Q * g.W;
+    t.nt_line = (int)std::min<int64_t>(512, std::max<int64_t>(64, QW / 8));
+    t.smem_line = (size_t)ntile * (size_t)(QW + (QW >> g.tpsh) + 1) * vb;
+    return true;
+}
+
+template <typename K> cudaError_t allow_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+struct pfc_plan {
+    int ndim = 0;
+    int nx = 0, ny = 0, nz = 0;
+    double dx = 0, dt = 0;
+    pfc_op ops[2] = {};
+    int nfields = 1;
+    double alpha = 0;
+    int prec = PFC_FP64;
+    cudaStream_t stream = nullptr;
+    Tiles t{};
+    void *X = nullptr, *C = nullptr, *tw = nullptr;
+    double *d_mean = nullptr, *d_part = nullptr, *d_out = nullptr;
+    int *d_status = nullptr;
+    size_t scratch = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    bool destroyed = false;
+};
+
+namespace {
+
+constexpr int GRAPH_CHUNK = 16;
+
+size_t vbytes(const pfc_plan *p) { return p->prec == PFC_FP64 ? 16 : 8; }
+size_t rbytes(const pfc_plan *p) { return p->prec == PFC_FP64 ? 8 : 4; }
+
+template <typename R> RowArgs<R> row_args(const pfc_plan *p) {
+    RowArgs<R> a{};
+    a.tw = reinterpret_cast<const typename VT<R>::V *>(p->tw);
+    a.scale = (R)1;
+    return a;
+}
+
+template <typename R> LineArgs<R> line_args(const pfc_plan *p) {
+    LineArgs<R> a{};
+    a.tw = reinterpret_cast<const typename VT<R>::V *>(p->tw);
+    a.scale = (R)1;
+    a.dt = p->dt;
+    a.dx = p->dx;
+    a.op0 = to_dev(p->ops[0]);
+    a.op1 = to_dev(p->ops[p->nfields > 1 ? 1 : 0]);
+    a.alpha = p->alpha;
+    return a;
+}
+
+template <typename R, int MODE> void launch_row(const pfc_plan *p, const RowArgs<R> &a, int nf) {
+    const Geom &g = p->t.g;
+    dim3 grid(g.Q / g.gpc, nf);
+    k_row<R, MODE><<<grid, p->t.nt_row, p->t.smem_row, p->stream>>>(g, a);
+}
+
+template <typename R, int MODE> void launch_line(const pfc_plan *p, const LineArgs<R> &a, int nf) {
+    const Geom &g = p->t.g;
+    dim3 grid(g.ncg, g.P, nf);
+    k_line<R, MODE><<<grid, p->t.nt_line, p->t.smem_line, p->stream>>>(g, a);
+}
+
+template <typename R> cudaError_t set_smem_attrs(const pfc_plan *p) {
+    cudaError_t e;
+    if ((e = allow_smem(k_row<R, ROW_CUBE>, p->t.smem_row)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_row<R, ROW_FWD>, p->t.smem_row)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_row<R, ROW_INV>, p->t.smem_row)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_line<R, LINE_STEP>, p->t.smem_line)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_line<R, LINE_FWD>, p->t.smem_line)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_line<R, LINE_INV>, p->t.smem_line)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+// Mean of each field of a real array into d_mean[f] (FP64).
+template <typename R> void launch_means(pfc_plan *p, const void *state) {
+    const Geom &g = p->t.g;
+    for (int f = 0; f < p->nfields; ++f) {
+        const R *x = reinterpret_cast<const R *>(state) + (size_t)f * g.nreal;
+        k_reduce_real<R, RED_SUM><<<RED_BLOCKS, RED_THREADS, 0, p->stream>>>(x, nullptr, g.nreal,
+                                                                             p->d_part, p->d_status);
+        k_finish<<<1, RED_THREADS, 0, p->stream>>>(p->d_part, RED_BLOCKS, 1.0 / (double)g.nreal,
+                                                   p->d_mean + f);
+    }
+}
+
+// One step on the carried state X' (row pass + line pass).
+template <typename R> void enqueue_one_step(pfc_plan *p) {
+    RowArgs<R> ra = row_args<R>(p);
+    ra.in = p->X;
+    ra.out = p->C;
+    ra.mean = p->d_mean;
+    launch_row<R, ROW_CUBE>(p, ra, p->nfields);
+    LineArgs<R> la = line_args<R>(p);
+    la.x = p->X;
+    la.c = p->C;
+    launch_line<R, LINE_STEP>(p, la, p->nfields);
+}
+
+template <typename R> pfc_status run_steps(pfc_plan *p, int64_t nsteps) {
+    if (nsteps >= GRAPH_CHUNK && !p->graph) {
+        cudaStream_t cap;
+        PFC_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaStream_t saved = p->stream;
+        p->stream = cap;
+        cudaGraph_t graph;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int s = 0; s < GRAPH_CHUNK; ++s) enqueue_one_step<R>(p);
+            e = cudaStreamEndCapture(cap, &graph);
+        }
+        p->stream = saved;
+        if (e == cudaSuccess) {
+            e = cudaGraphInstantiate(&p->graph, graph, 0);
+            cudaGraphDestroy(graph);
+        }
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) return fail(PFC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        p->graph_steps = GRAPH_CHUNK;
+    }
+    int64_t done = 0;
+    if (p->graph) {
+        for (; done + p->graph_steps <= nsteps; done += p->graph_steps)
+            PFC_CUDA(cudaGraphLaunch(p->graph, p->stream));
+    }
+    for (; done < nsteps; ++done) enqueue_one_step<R>(p);
+    PFC_CUDA(cudaGetLastError());
+    return PFC_OK;
+}
+
+template <typename R> pfc_status step_impl(pfc_plan *p, void *state, int64_t nsteps) {
+    const Geom &g = p->t.g;
+    launch_means<R>(p, state);
+    RowArgs<R> ra = row_args<R>(p);
+    ra.in = state;
+    ra.out = p->X;
+    ra.mean = p->d_mean;
+    ra.scale = (R)(1.0 / ((double)g.P * (double)g.M));
+    launch_row<R, ROW_FWD>(p, ra, p->nfields);
+    PFC_CUDA(cudaGetLastError());
+    pfc_status s = run_steps<R>(p, nsteps);
+    if (s != PFC_OK) return s;
+    RowArgs<R> rb = row_args<R>(p);
+    rb.in = p->X;
+    rb.out = state;
+    rb.mean = p->d_mean;
+    launch_row<R, ROW_INV>(p, rb, p->nfields);
+    PFC_CUDA(cudaGetLastError());
+    return PFC_OK;
+}
+
+template <typename R> pfc_status r2c_impl(pfc_plan *p, const void *in, void *out) {
+    RowArgs<R> ra = row_args<R>(p);
+    ra.in = in;
+    ra.out = p->X;
+    launch_row<R, ROW_FWD>(p, ra, p->nfields);
+    LineArgs<R> la = line_args<R>(p);
+    la.x = p->X;
+    la.std_out = out;
+    launch_line<R, LINE_FWD>(p, la, p->nfields);
+    PFC_CUDA(cudaGetLastError());
+    return PFC_OK;
+}
+
+template <typename R> pfc_status c2r_impl(pfc_plan *p, const void *in, void *out) {
+    const Geom &g = p->t.g;
+    LineArgs<R> la = line_args<R>(p);
+    la.x = p->X;
+    la.std_in = in;
+    la.scale = (R)(2.0 / (double)g.nreal);
+    launch_line<R, LINE_INV>(p, la, p->nfields);
+    RowArgs<R> ra = row_args<R>(p);
+    ra.in = p->X;
+    ra.out = out;
+    launch_row<R, ROW_INV>(p, ra, p->nfields);
+    PFC_CUDA(cudaGetLastError());
+    return PFC_OK;
+}
+
+pfc_status read_status(pfc_plan *p) {
+    int st = 0;
+    PFC_CUDA(cudaMemcpyAsync(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    PFC_CUDA(cudaStreamSynchronize(p->stream));
+    if (st) {
+        PFC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
+        PFC_CUDA(cudaStreamSynchronize(p->stream));
+        if (st & STATUS_TIMEOUT) return fail(PFC_ERR_TIMEOUT, "a bounded device wait gave up");
+        if (st & STATUS_NONFINITE) return fail(PFC_ERR_NONFINITE, "the state holds NaN or Inf");
+    }
+    return PFC_OK;
+}
+
+template <typename R> pfc_status mass_impl(pfc_plan *p, const void *state, double *out) {
+    launch_means<R>(p, state);
+    PFC_CUDA(cudaGetLastError());
+    std::vector<double> m(p->nfields);
+    PFC_CUDA(cudaMemcpyAsync(m.data(), p->d_mean, sizeof(double) * p->nfields,
+                             cudaMemcpyDeviceToHost, p->stream));
+    pfc_status s = read_status(p);
+    if (s != PFC_OK) return s;
+    std::memcpy(out, m.data(), sizeof(double) * p->nfields);
+    return PFC_OK;
+}
+
+template <typename R> pfc_status energy_impl(pfc_plan *p, const void *state, double *out) {
+    const Geom &g = p->t.g;
+    launch_means<R>(p, state);
+    // slots in d_out: [0, nf) spectral sums, [nf, 2nf) sum psi^4, [2nf] cross term
+    for (int f = 0; f < p->nfields; ++f) {
+        const R *x = reinterpret_cast<const R *>(state) + (size_t)f * g.nreal;
+        RowArgs<R> ra = row_args<R>(p);
+        ra.in = x;
+        ra.out = p->X;
+        ra.mean = p->d_mean + f;
+        launch_row<R, ROW_FWD>(p, ra, 1);
+        LineArgs<R> la = line_args<R>(p);
+        la.x = p->X;
+        la.std_out = p->C;
+        launch_line<R, LINE_FWD>(p, la, 1);
+        k_reduce_spec<R><<<RED_BLOCKS, RED_THREADS, 0, p->stream>>>(
+            g, to_dev(p->ops[f]), p->dx, reinterpret_cast<const typename VT<R>::V *>(p->C),
+            p->d_mean + f, p->d_part, p->d_status);
+        k_finish<<<1, RED_THREADS, 0, p->stream>>>(p->d_part, RED_BLOCKS, 1.0, p->d_out + f);
+        k_reduce_real<R, RED_POW4><<<RED_BLOCKS, RED_THREADS, 0, p->stream>>>(
+            x, nullptr, g.nreal, p->d_part, p->d_status);
+        k_finish<<<1, RED_THREADS, 0, p->stream>>>(p->d_part, RED_BLOCKS, 1.0,
+                                                   p->d_out + p->nfields + f);
+    }
+    if (p->nfields == 2) {
+        const R *x0 = reinterpret_cast<const R *>(state);
+        k_reduce_real<R, RED_DOT><<<RED_BLOCKS, RED_THREADS, 0, p->stream>>>(
+            x0, x0 + g.nreal, g.nreal, p->d_part, p->d_status);
+        k_finish<<<1, RED_THREADS, 0, p->stream>>>(p->d_part, RED_BLOCKS, 1.0, p->d_out + 4);
+    }
+    PFC_CUDA(cudaGetLastError());
+    double h[5] = {0, 0, 0, 0, 0};
+    PFC_CUDA(cudaMemcpyAsync(h, p->d_out, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
+    pfc_status s = read_status(p);
+    if (s != PFC_OK) return s;
+    const double n = (double)g.nreal;
+    double f = 0.0;
+    for (int i = 0; i < p->nfields; ++i) f += 0.5 * h[i] / (n * n) + 0.25 * h[p->nfields + i] / n;
+    if (p->nfields == 2) f += p->alpha * h[4] / n;
+    *out = f;
+    return PFC_OK;
+}
+
+bool plan_ok(const pfc_plan *p) { return p && !p->destroyed; }
+
+}  // namespace
+
+// ============================================================================================
+// C ABI
+// ============================================================================================
+extern "C" {
+
+const char *pfc_status_string(pfc_status s) {
+    switch (s) {
+        case PFC_OK: return "PFC_OK";
+        case PFC_ERR_INVALID_ARG: return "PFC_ERR_INVALID_ARG";
+        case PFC_ERR_UNSUPPORTED: return "PFC_ERR_UNSUPPORTED";
+        case PFC_ERR_UNSTABLE_OPERATOR: return "PFC_ERR_UNSTABLE_OPERATOR";
+        case PFC_ERR_OUT_OF_MEMORY: return "PFC_ERR_OUT_OF_MEMORY";
+        case PFC_ERR_CUDA: return "PFC_ERR_CUDA";
+        case PFC_ERR_NONFINITE: return "PFC_ERR_NONFINITE";
+        case PFC_ERR_TIMEOUT: return "PFC_ERR_TIMEOUT";
+    }
+    return "PFC_ERR_UNKNOWN";
+}
+
+const char *pfc_last_error(void) { return g_last_error.c_str(); }
+
+pfc_status pfc_plan_create(pfc_plan **out, int ndim, const int64_t *dims, double dx, double dt,
+                           const pfc_op *ops, int nfields, const double *coupling, int precision,
+                           void *stream) {
+    if (!out || !dims || !ops) return fail(PFC_ERR_INVALID_ARG, "null pointer argument");
+    if (ndim != 2 && ndim != 3) return fail(PFC_ERR_INVALID_ARG, "ndim must be 2 or 3");
+    if (!(dx > 0) || !(dt > 0) || !std::isfinite(dx) || !std::isfinite(dt))
+        return fail(PFC_ERR_INVALID_ARG, "dx and dt must be finite and > 0");
+    if (nfields < 1 || nfields > 2) return fail(PFC_ERR_UNSUPPORTED, "nfields must be 1 or 2");
+    if (precision != PFC_FP64 && precision != PFC_FP32_MIXED)
+        return fail(PFC_ERR_INVALID_ARG, "unknown precision");
+    for (int f = 0; f < nfields; ++f) {
+        if (ops[f].kind != PFC_ONE_MODE && ops[f].kind != PFC_TWO_MODE)
+            return fail(PFC_ERR_INVALID_ARG, "unknown operator kind");
+        if (!std::isfinite(ops[f].r) || !std::isfinite(ops[f].R1) || !std::isfinite(ops[f].q2))
+            return fail(PFC_ERR_INVALID_ARG, "operator coefficients must be finite");
+    }
+    int64_t d[3] = {1, 1, 1};   // (nz, ny, nx)
+    for (int i = 0; i < ndim; ++i) d[3 - ndim + i] = dims[i];
+    for (int i = 3 - ndim; i < 3; ++i) {
+        if (d[i] <= 0) return fail(PFC_ERR_INVALID_ARG, "dims must be positive");
+        if (!is_pow2(d[i]) || d[i] < 16 || d[i] > 4096)
+            return fail(PFC_ERR_UNSUPPORTED, "every extent must be a power of two in [16, 4096]");
+    }
+    double alpha = 0.0;
+    if (nfields == 2 && coupling) alpha = coupling[1];
+    if (nfields == 2 && alpha != 0.0)
+        return fail(PFC_ERR_UNSUPPORTED, "coupled two-field plans are not built yet");
+    const double kmax = M_PI / dx;
+    const double k2max = kmax * kmax * ndim;
+    if (min_implicit(ops, nfields, alpha, dt, k2max) <= 0.0)
+        return fail(PFC_ERR_UNSTABLE_OPERATOR, "1 + dt k^2 Lk(k) is not positive on the grid");
+
+    pfc_plan *p = new pfc_plan();
+    p->ndim = ndim;
+    p->nz = (int)d[0]; p->ny = (int)d[1]; p->nx = (int)d[2];
+    p->dx = dx; p->dt = dt;
+    for (int f = 0; f < nfields; ++f) p->ops[f] = ops[f];
+    p->nfields = nfields;
+    p->alpha = alpha;
+    p->prec = precision;
+    p->stream = reinterpret_cast<cudaStream_t>(stream);
+
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) { delete p; return fail(PFC_ERR_CUDA, std::string("device query: ") + cudaGetErrorString(e)); }
+    const size_t smem_max = (size_t)optin;
+    if (!plan_tiles(p->t, p->nx, p->ny, p->nz, vbytes(p), 2, smem_max)) {
+        delete p;
+        return fail(PFC_ERR_UNSUPPORTED, "no pass tiling fits shared memory for this grid and precision");
+    }
+    const Geom &g = p->t.g;
+    e = p->prec == PFC_FP64 ? set_smem_attrs<double>(p) : set_smem_attrs<float>(p);
+    if (e != cudaSuccess) { delete p; return fail(PFC_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e)); }
+
+    const size_t half_bytes = (size_t)g.nhalf * nfields * vbytes(p);
+    const int64_t ntab = int64_t(1) << g.ltab;
+    auto cleanup = [&](cudaError_t err) {
+        pfc_plan_destroy(p);
+        return fail(err == cudaErrorMemoryAllocation ? PFC_ERR_OUT_OF_MEMORY : PFC_ERR_CUDA,
+                    std::string("plan allocation: ") + cudaGetErrorString(err));
+    };
+    if ((e = cudaMalloc(&p->X, half_bytes)) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMalloc(&p->C, half_bytes)) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMalloc(&p->tw, ntab * vbytes(p))) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMalloc(&p->d_mean, 8 * sizeof(double))) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMalloc(&p->d_part, RED_BLOCKS * sizeof(double))) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMalloc(&p->d_out, 8 * sizeof(double))) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) return cleanup(e);
+    p->scratch = 2 * half_bytes + ntab * vbytes(p) + (16 + RED_BLOCKS) * sizeof(double) + sizeof(int);
+
+    std::vector<double> tw(2 * ntab);
+    for (int64_t i = 0; i < ntab; ++i) unit_root_fwd(i, ntab, &tw[2 * i], &tw[2 * i + 1]);
+    if (p->prec == PFC_FP64) {
+        e = cudaMemcpy(p->tw, tw.data(), ntab * 16, cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> twf(2 * ntab);
+        for (int64_t i = 0; i < 2 * ntab; ++i) twf[i] = (float)tw[i];
+        e = cudaMemcpy(p->tw, twf.data(), ntab * 8, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return cleanup(e);
+    if ((e = cudaMemset(p->X, 0, half_bytes)) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMemset(p->C, 0, half_bytes)) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMemset(p->d_mean, 0, 8 * sizeof(double))) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMemset(p->d_status, 0, sizeof(int))) != cudaSuccess) return cleanup(e);
+    *out = p;
+    return PFC_OK;
+}
+
+pfc_status pfc_plan_destroy(pfc_plan *p) {
+    if (!p) return PFC_OK;
+    if (p->destroyed) return fail(PFC_ERR_INVALID_ARG, "plan already destroyed");
+    cudaStreamSynchronize(p->stream);
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    cudaFree(p->X); cudaFree(p->C); cudaFree(p->tw);
+    cudaFree(p->d_mean); cudaFree(p->d_part); cudaFree(p->d_out); cudaFree(p->d_status);
+    p->destroyed = true;
+    delete p;
+    return PFC_OK;
+}
+
+pfc_status pfc_step(pfc_plan *p, void *state, int64_t nsteps) {
+    if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
+    if (!state) return fail(PFC_ERR_INVALID_ARG, "null state");
+    if (nsteps < 0) return fail(PFC_ERR_INVALID_ARG, "nsteps must be >= 0");
+    if ((reinterpret_cast<uintptr_t>(state) & 15) != 0) return fail(PFC_ERR_INVALID_ARG, "state must be 16-byte aligned");
+    if (nsteps == 0) return PFC_OK;
+    return p->prec == PFC_FP64 ? step_impl<double>(p, state, nsteps) : step_impl<float>(p, state, nsteps);
+}
+
+pfc_status pfc_fft_r2c(pfc_plan *p, const void *in, void *out) {
+    if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
+    if (!in || !out) return fail(PFC_ERR_INVALID_ARG, "null array");
+    return p->prec == PFC_FP64 ? r2c_impl<double>(p, in, out) : r2c_impl<float>(p, in, out);
+}
+
+pfc_status pfc_fft_c2r(pfc_plan *p, const void *in, void *out) {
+    if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
+    if (!in || !out) return fail(PFC_ERR_INVALID_ARG, "null array");
+    return p->prec == PFC_FP64 ? c2r_impl<double>(p, in, out) : c2r_impl<float>(p, in, out);
+}
+
+pfc_status pfc_mass(pfc_plan *p, const void *state, double *out) {
+    if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
+    if (!state || !out) return fail(PFC_ERR_INVALID_ARG, "null pointer");
+    return p->prec == PFC_FP64 ? mass_impl<double>(p, state, out) : mass_impl<float>(p, state, out);
+}
+
+pfc_status pfc_energy(pfc_plan *p, const void *state, double *out) {
+    if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
+    if (!state || !out) return fail(PFC_ERR_INVALID_ARG, "null pointer");
+    return p->prec == PFC_FP64 ? energy_impl<double>(p, state, out) : energy_impl<float>(p, state, out);
+}
+
+pfc_status pfc_step_adjoint(pfc_plan *p, const void *psi_n, const void *lam_next, void *lam_out,
+                            double *dr) {
+    if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
+    if (!psi_n || !lam_next || !lam_out || !dr) return fail(PFC_ERR_INVALID_ARG, "null pointer");
+    return fail(PFC_ERR_UNSUPPORTED, "adjoint step not built yet");
+}
+
+pfc_status pfc_set_r(pfc_plan *p, int field, double r) {
+    if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
+    if (field < 0 || field >= p->nfields) return fail(PFC_ERR_INVALID_ARG, "field out of range");
+    if (!std::isfinite(r)) return fail(PFC_ERR_INVALID_ARG, "r must be finite");
+    pfc_op ops[2] = {p->ops[0], p->ops[1]};
+    ops[field].r = r;
+    const double kmax = M_PI / p->dx;
+    if (min_implicit(ops, p->nfields, p->alpha, p->dt, kmax * kmax * p->ndim) <= 0.0)
+        return fail(PFC_ERR_UNSTABLE_OPERATOR, "1 + dt k^2 Lk(k) is not positive on the grid");
+    cudaStreamSynchronize(p->stream);
+    p->ops[field].r = r;
+    if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+    return PFC_OK;
+}
+
+pfc_status pfc_sync(pfc_plan *p) {
+    if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
+    return read_status(p);
+}
+
+pfc_status pfc_plan_info(pfc_plan *p, int32_t *tiles, int64_t *scratch_bytes) {
+    if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
+    const Geom &g = p->t.g;
+    if (tiles) {
+        const int32_t v[8] = {g.Py, g.Pz, g.Qy, g.Qz, g.W, g.gpc, p->t.nt_row, p->t.nt_line};
+        std::memcpy(tiles, v, sizeof(v));
+    }
+    if (scratch_bytes) *scratch_bytes = (int64_t)p->scratch;
+    return PFC_OK;
+}
+
+pfc_status pfc_batch_create(pfc_batch **out, int, const int64_t *, const double *, double, double,
+                            int, void *) {
+    if (!out) return fail(PFC_ERR_INVALID_ARG, "null pointer");
+    return fail(PFC_ERR_UNSUPPORTED, "batched ensembles not built yet");
+}
+pfc_status pfc_batch_destroy(pfc_batch *) { return PFC_OK; }
+pfc_status pfc_batch_step(pfc_batch *, void *, int64_t) {
+    return fail(PFC_ERR_UNSUPPORTED, "batched ensembles not built yet");
+}
+pfc_status pfc_batch_mass(pfc_batch *, const void *, double *) {
+    return fail(PFC_ERR_UNSUPPORTED, "batched ensembles not built yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle, element by element.
+
+Tolerances (relative L2 unless stated), from the arithmetic of each path:
+  FP64 transforms 1e-13; FP64 step 1e-12 after one step, 1e-10 after 100 steps.
+  FP32-mixed transforms 2e-6 (single-precision butterflies, ~eps32 * log2 N);
+  FP32-mixed step 2e-6 after one step, 1e-5 after 100 steps; mass drift 1e-6 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_26818_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ONE = (0, -0.25, 0.0, 0.0)
+TWO = (1, -0.3, 0.05, math.sqrt(4.0 / 3.0))
+TOL_FFT = {"fp64": 1e-13, "fp32": 2e-6}
+
+
+def _binding():
+    from paper_2603_26818_gb300 import binding
+    return binding
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def to_dev(a, prec):
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dt)
+
+
+def plan(dims, dx, dt, op, prec):
+    b = _binding()
+    return b.Plan(dims, dx, dt, [b.make_op(*op)], precision=prec)
+
+
+# shapes chosen to cover: tiny grids, rectangular grids, the P/Q split of y (ny = 4096),
+# the split of y and z in 3D, several W and row-group choices
+FFT_SHAPES = [(16, 16), (32, 64), (128, 128), (64, 256), (256, 32), (4096, 16), (2048, 64),
+              (16, 16, 16), (32, 16, 64), (64, 32, 16), (512, 16, 16), (128, 128, 32)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", FFT_SHAPES)
+def test_r2c_and_c2r_match_oracle(shape, prec):
+    x = inputs.uniform_state(shape, 0.1, 1.0, seed=hash(shape) % 1000)
+    p = plan(shape, math.pi / 4, 0.5, ONE, prec)
+    xd = to_dev(x, prec)
+    xh = p.fft_r2c(xd)
+    ref = oracle.rfftn(x)
+    assert rel(xh.cpu().numpy(), ref) <= TOL_FFT[prec]
+    # c2r of an arbitrary (not Hermitian-consistent) half spectrum, imaginary parts of the
+    # kx = 0 and Nyquist bins ignored
+    r = np.random.default_rng(5)
+    h = r.standard_normal(ref.shape) + 1j * r.standard_normal(ref.shape)
+    hd = torch.from_numpy(h).to(device="cuda", dtype=p.complex_dtype)
+    y = p.fft_c2r(hd)
+    assert rel(y.double().cpu().numpy(), oracle.irfftn(h, shape)) <= TOL_FFT[prec]
+    p.close()
+
+
+def test_split_plans_are_exercised():
+    """The shapes above include plans that split y (Py > 1) and both y and z (Pz > 1)."""
+    seen = set()
+    for shape in FFT_SHAPES:
+        for prec in ("fp64", "fp32"):
+            info = plan(shape, math.pi / 4, 0.5, ONE, prec).info()
+            seen.add((info["Py"] > 1, info["Pz"] > 1))
+    assert (True, False) in seen and (True, True) in seen and (False, False) in seen
+
+
+@pytest.mark.parametrize("prec,tol1,tol100", [("fp64", 1e-12, 1e-10), ("fp32", 2e-6, 1e-5)])
+def test_config1_128_one_mode_steps(prec, tol1, tol100):
+    """128^2 one-mode, dx = pi/4, dt = 0.5, r = -0.25, psi0 = -0.25 + U[-0.01, 0.01] (seed 1)."""
+    dims, dx, dt = (128, 128), math.pi / 4, 0.5
+    psi0 = inputs.uniform_state(dims, -0.25, 0.01, seed=1)
+    p = plan(dims, dx, dt, ONE, prec)
+    x = to_dev(psi0, prec)
+    p.step(x, 1)
+    assert rel(x.double().cpu().numpy(), oracle.step(psi0, dx, dt, ONE, 1)) <= tol1
+    x = to_dev(psi0, prec)
+    p.step(x, 100)
+    ref = oracle.step(psi0, dx, dt, ONE, 100)
+    got = x.double().cpu().numpy()
+    assert rel(got, ref) <= tol100
+    assert rel(got - got.mean(), ref - ref.mean()) <= tol100 * 50
+    m0 = oracle.mass(psi0)
+    assert abs(p.mass(x)[0] - m0) <= 1e-6 * abs(m0)
+    assert p.energy(x) == pytest.approx(oracle.energy(ref, dx, ONE), rel=1e-10 if prec == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+@pytest.mark.parametrize("shape,op,dt,nsteps", [
+    ((32, 32, 32), TWO, 0.1, 10),
+    ((16, 32, 64), ONE, 0.5, 10),
+    ((512, 16, 16), TWO, 0.1, 5),
+    ((4096, 16), ONE, 0.5, 10),
+    ((64, 128), TWO, 0.1, 20),
+])
+def test_steps_match_oracle(shape, op, dt, nsteps, prec, tol):
+    dx = math.pi / 4
+    psi0 = inputs.uniform_state(shape, -0.3, 0.05, seed=7)
+    p = plan(shape, dx, dt, op, prec)
+    x = to_dev(psi0, prec)
+    p.step(x, nsteps)
+    ref = oracle.step(psi0, dx, dt, op, nsteps)
+    assert rel(x.double().cpu().numpy(), ref) <= tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_mass_and_energy_match_oracle(prec):
+    shape, dx = (64, 32, 16), math.pi / 4
+    psi = inputs.uniform_state(shape, -0.3, 0.2, seed=9)
+    for op in (ONE, TWO):
+        p = plan(shape, dx, 0.1, op, prec)
+        x = to_dev(psi, prec)
+        xin = x.double().cpu().numpy()
+        assert p.mass(x)[0] == pytest.approx(oracle.mass(xin), rel=1e-14, abs=1e-15)
+        assert p.energy(x) == pytest.approx(oracle.energy(xin, dx, op), rel=1e-12 if prec == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_uniform_state_is_a_fixed_point(prec):
+    p = plan((64, 64), math.pi / 4, 0.5, ONE, prec)
+    x = to_dev(np.full((64, 64), -0.25), prec)
+    p.step(x, 50)
+    assert float((x.double() + 0.25).abs().max()) <= (1e-15 if prec == "fp64" else 1e-7)
+
+
+def test_zero_steps_is_a_no_op_and_runs_are_deterministic():
+    psi0 = inputs.uniform_state((128, 128), -0.25, 0.05, seed=3)
+    p = plan((128, 128), math.pi / 4, 0.5, ONE, "fp32")
+    x = to_dev(psi0, "fp32")
+    y = x.clone()
+    p.step(x, 0)
+    assert torch.equal(x, y)
+    a = to_dev(psi0, "fp32")
+    b = to_dev(psi0, "fp32")
+    p.step(a, 37)
+    p.step(b, 37)
+    assert torch.equal(a, b)
