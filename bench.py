@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Benchmark of the semi-implicit Fourier pseudo-spectral PFC step on GB300.
+
+Workload (one bench step = one pfc_step call advancing the state by INNER time steps):
+  2D one-mode PFC, 4096 x 4096 periodic grid, dx = pi/4, dt = 0.5, r = -0.25, psi0 = -0.25 plus a
+  periodic-Voronoi polycrystal of 64 triangular one-mode grains (amplitude 0.2, lattice
+  wavenumber 1, SplitMix64 seed 2) and U[-0.01, 0.01] noise; FP32-mixed path (FP32 data and
+  butterflies, FP64-generated twiddles, FP64 mean and reductions).
+Metric: grid-point-steps/s = (grid points) x (time steps) / time, whole job over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference implementation: the paper
+ships no code) on the host cores, one time step of the same workload per bench step.
+Multi-GPU runs are independent replicas (the single-domain step has no data-parallel split).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PFC grid-point-steps/s and FFT HBM GB/s (% peak) vs plain FP64 step, 1 GB300"
+UNIT = "grid-point-steps/s"
+NY = NX = 4096
+DX, DT, R_OP, MEAN = math.pi / 4, 0.5, -0.25, -0.25
+INNER = 100
+WORKLOAD = ("2D one-mode PFC 4096x4096, dx=pi/4, dt=0.5, r=-0.25, psi0=-0.25 + 64-grain "
+            "triangular polycrystal (amp 0.2, q=1, seed 2) + U[-0.01,0.01] noise; "
+            f"{INNER} semi-implicit time steps per bench step; FP32-mixed")
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / cuFFT context timings")
+    return ap.parse_args()
+
+
+def make_input():
+    from paper_2603_26818_gb300 import inputs
+    return inputs.polycrystal_2d(NY, NX, DX, MEAN, 64, 0.2, 1.0, 0.01, seed=2)
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+# ------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = [l.strip().split(",") for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------- peaks
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2603_26818_gb300", "csrc")
+    for n in sorted(os.listdir(csrc)):
+        if n.endswith((".cu", ".cuh")) and not n.startswith("cufft"):
+            h.update(open(os.path.join(csrc, n), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        t = json.load(f)
+    if t.get("source_hash") != kernel_source_hash():
+        return None
+    k = t.get("kernels", {}).get(kernel_key)
+    return None if k is None else k.get("dram_bytes_per_launch_full_size")
+
+
+# ------------------------------------------------------------------------------- oracle
+def cpu_baseline(psi0, nsteps):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.step(psi0, DX, DT, (0, R_OP, 0.0, 0.0), nsteps)
+    dt = time.perf_counter() - t0
+    return {"value": NY * NX * nsteps / dt, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{nsteps} time steps of the 4096x4096 workload, FP64 C oracle (own FFT, "
+                      f"OpenMP over lines), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, _, world = env_rank()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    psi = make_input()
+    for _ in range(args.warmup):
+        psi = oracle.step(psi, DX, DT, (0, R_OP, 0.0, 0.0), 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        psi = oracle.step(psi, DX, DT, (0, R_OP, 0.0, 0.0), 1)
+    el = time.perf_counter() - t0
+    v = NY * NX * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace(f"{INNER} semi-implicit time steps per bench step; FP32-mixed",
+                                                    "1 time step per bench step; FP64 CPU oracle"),
+                       "grid": [NY, NX], "time_steps_per_step": 1},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} timed time steps of the 4096x4096 workload"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------- ours
+def time_cufft(torch, dev, psi0, precision, nsteps):
+    """Vendor cuFFT plain step (baseline library), grid-point-steps/s."""
+    import ctypes
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2603_26818_gb300", "libpfc_cufft_baseline.so"))
+    lib.pfcb_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p]
+    lib.pfcb_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+    lib.pfcb_destroy.argtypes = [ctypes.c_void_p]
+    dt = torch.float64 if precision == 0 else torch.float32
+    x = torch.from_numpy(psi0).to(device=dev, dtype=dt)
+    h = ctypes.c_void_p()
+    dims = (ctypes.c_int64 * 2)(NY, NX)
+    st = torch.cuda.current_stream().cuda_stream
+    if lib.pfcb_create(ctypes.byref(h), 2, dims, DX, DT, 0, R_OP, 0.0, 0.0, precision, ctypes.c_void_p(st)) != 0:
+        return None, None
+    lib.pfcb_step(h, ctypes.c_void_p(x.data_ptr()), 3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    lib.pfcb_step(h, ctypes.c_void_p(x.data_ptr()), nsteps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    lib.pfcb_destroy(h)
+    return NY * NX * nsteps / (ms * 1e-3), x
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2603_26818_gb300 import binding
+
+    rank, local, world = env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+
+    psi0 = make_input()
+    op = binding.make_op(0, R_OP)
+    plan = binding.Plan((NY, NX), DX, DT, [op], precision="fp32")
+    state = torch.from_numpy(psi0).to(device=dev, dtype=torch.float32)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    npts = NY * NX
+
+    for _ in range(args.warmup):
+        plan.step(state, INNER)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs resident in HBM, L2 flushed between timed steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(1.0)
+            evs[k][0].record()
+            plan.step(state, INNER)
+            evs[k][1].record()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * npts * INNER * args.steps / (ms_max * 1e-3)
+    launches_per_call = 2 * 1 + 1 + 2 * INNER + 1
+
+    # ---- end to end through the public API with host buffers (pinned), copies timed
+    h_in = torch.from_numpy(psi0.astype(np.float32)).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d = torch.empty_like(state)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record()
+    for k in range(args.steps):
+        d.copy_(h_in, non_blocking=True)
+        plan.step(d, INNER)
+        h_out.copy_(d, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * npts * INNER * args.steps / (float(t.item()) * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": h_in.numel() * 4, "d2h_bytes_per_step": h_out.numel() * 4}
+
+    # ---- per-kernel timing with events between launches on the plan's stream
+    prof, nl = plan.profile_steps(state, INNER)
+    H = NY * (NX // 2 + 1)
+    alg = {"row": 2 * 8 * H, "line": 3 * 8 * H}          # bytes per launch: 2 and 3 sweeps
+    dom = max(("row", "line"), key=lambda k: prof[k])
+    dur = prof[dom] * 1e-3 / INNER
+    peak, peak_kind = hbm_peak()
+    achieved = alg[dom] / dur / 1e9
+    key = {"row": "k_row<float, ROW_CUBE>", "line": "k_line<float, LINE_STEP>"}[dom]
+    roof = {"bound": "hbm", "kernel": key, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": ncu_traffic(key),
+            "algorithmic_bytes_per_launch": alg[dom], "avg_launch_ms": dur * 1e3,
+            "per_kernel_ms_per_step": {k: prof[k] / INNER for k in ("row", "line")},
+            "per_kernel_gbs": {k: alg[k] / (prof[k] * 1e-3 / INNER) / 1e9 for k in ("row", "line")},
+            "step_gbs_at_20_B_per_pt": 20 * npts * INNER / (ms_max * 1e-3 / args.steps) / 1e9}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [NY, NX], "time_steps_per_step": INNER,
+                       "precision": "fp32-mixed", "parallelism": f"replicas{world}",
+                       "l2": "512 MiB buffer written between timed steps",
+                       "plan": plan.info()},
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_call * args.steps,
+            "clocks": clk.summary()}
+
+    if not args.no_extras and rank == 0:
+        extras = {}
+        # our FP64 path and the vendor plain steps, for context (same workload, fewer steps)
+        p64 = binding.Plan((NY, NX), DX, DT, [op], precision="fp64")
+        x64 = torch.from_numpy(psi0).to(device=dev)
+        p64.step(x64, 2)
+        torch.cuda.synchronize()
+        e0.record()
+        p64.step(x64, 20)
+        e1.record()
+        torch.cuda.synchronize()
+        extras["ours_fp64"] = npts * 20 / (e0.elapsed_time(e1) * 1e-3)
+        v, _ = time_cufft(torch, dev, psi0, 0, 20)
+        extras["cufft_plain_fp64"] = v
+        v, _ = time_cufft(torch, dev, psi0, 1, 100)
+        extras["cufft_plain_fp32"] = v
+        extras["speedup_vs_plain_fp64"] = value / world / extras["cufft_plain_fp64"] if extras["cufft_plain_fp64"] else None
+        # precision report: FP32-mixed vs our FP64 path after 1000 steps from psi0
+        a = torch.from_numpy(psi0).to(device=dev, dtype=torch.float32)
+        b = torch.from_numpy(psi0).to(device=dev)
+        m0 = float(psi0.mean())
+        plan.step(a, 1000)
+        p64.step(b, 1000)
+        torch.cuda.synchronize()
+        diff = (a.double() - b).norm() / b.norm()
+        fl = (b - b.mean()).norm()
+        extras["precision_1000_steps"] = {
+            "rel_l2_fp32_vs_fp64": float(diff),
+            "rel_l2_of_fluctuation": float((a.double() - b).norm() / fl),
+            "mass_drift_rel_fp32": abs(plan.mass(a)[0] - m0) / abs(m0),
+            "mass_drift_rel_fp64": abs(p64.mass(b)[0] - m0) / abs(m0)}
+        line["context"] = extras
+        p64.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(psi0, 8)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -14,8 +14,8 @@
  *
  * Conventions shared by every call:
  *   - dims are given slowest first, like a C array or a torch/numpy shape: 2D (ny, nx),
- *     3D (nz, ny, nx); x is contiguous. Every extent must be a power of two in [8, 4096]
- *     (ny, nz >= 8 also), otherwise PFC_ERR_UNSUPPORTED.
+ *     3D (nz, ny, nx); x is contiguous. Every extent must be a power of two in [16, 4096],
+ *     otherwise PFC_ERR_UNSUPPORTED.
  *   - Box length per axis is n dx; k = 2 pi m / (n dx) with m in FFT order.
  *   - Real arrays hold nfields fields back to back, each nz*ny*nx values; complex arrays
  *     are interleaved (re, im) with the half-spectrum shape (nz, ny, nx/2 + 1).
@@ -127,6 +127,14 @@ pfc_status pfc_sync(pfc_plan *plan);
  *   tiles[8] = {Py, Pz, Qy, Qz, W, row_groups_per_cta, threads_row, threads_line}
  *   scratch_bytes = device bytes the plan owns. */
 pfc_status pfc_plan_info(pfc_plan *plan, int32_t *tiles, int64_t *scratch_bytes);
+
+/* Measurement support. Runs exactly the work of pfc_step(plan, state, nsteps) but records a
+ * CUDA event on the plan's stream between consecutive kernel launches (no CUDA graph), then
+ * synchronises and returns the summed event time per kernel kind in ms_out[4] (host):
+ *   {row pass forming psi^3, line pass with the update, entry conversion, exit conversion}
+ * and the number of kernel launches in *launches (host). */
+pfc_status pfc_profile_steps(pfc_plan *plan, void *state, int64_t nsteps, double *ms_out,
+                             int64_t *launches);
 
 /* Names of a status code and of the last error on this thread. Never NULL. */
 const char *pfc_status_string(pfc_status status);

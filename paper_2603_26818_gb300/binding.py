@@ -24,6 +24,7 @@ PFC_ONE_MODE, PFC_TWO_MODE = 0, 1
 # every extern "C" symbol of include/pfc.h
 EXPORTS = ["pfc_plan_create", "pfc_plan_destroy", "pfc_step", "pfc_fft_r2c", "pfc_fft_c2r",
            "pfc_mass", "pfc_energy", "pfc_step_adjoint", "pfc_set_r", "pfc_sync", "pfc_plan_info",
+           "pfc_profile_steps",
            "pfc_status_string", "pfc_last_error", "pfc_batch_create", "pfc_batch_destroy",
            "pfc_batch_step", "pfc_batch_mass"]
 
@@ -66,6 +67,7 @@ def load_library(path: str = LIB_PATH):
         "pfc_set_r": [vp, cint, dbl],
         "pfc_sync": [vp],
         "pfc_plan_info": [vp, P(ctypes.c_int32), P(i64)],
+        "pfc_profile_steps": [vp, vp, i64, P(dbl), P(i64)],
         "pfc_batch_create": [P(vp), cint, P(i64), P(dbl), dbl, dbl, cint, vp],
         "pfc_batch_destroy": [vp],
         "pfc_batch_step": [vp, vp, i64],
@@ -201,6 +203,15 @@ class Plan:
 
     def sync(self):
         check(load_library().pfc_sync(self._h))
+
+    def profile_steps(self, state: torch.Tensor, nsteps: int):
+        """pfc_profile_steps: ms per kernel kind {row, line, entry, exit} and the launch count."""
+        p = self._check_real(state, "state")
+        ms = (ctypes.c_double * 4)()
+        nl = ctypes.c_int64()
+        check(load_library().pfc_profile_steps(self._h, ctypes.c_void_p(p), int(nsteps), ms,
+                                               ctypes.byref(nl)))
+        return dict(zip(["row", "line", "entry", "exit"], list(ms))), nl.value
 
     def info(self):
         tiles = (ctypes.c_int32 * 8)()

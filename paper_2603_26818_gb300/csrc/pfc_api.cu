@@ -264,6 +264,7 @@ template <typename R> void enqueue_one_step(pfc_plan *p) {
     RowArgs<R> ra = row_args<R>(p);
     ra.in = p->X;
     ra.out = p->C;
+    ra.proj = p->X;
     ra.mean = p->d_mean;
     launch_row<R, ROW_CUBE>(p, ra, p->nfields);
     LineArgs<R> la = line_args<R>(p);
@@ -421,6 +422,68 @@ template <typename R> pfc_status energy_impl(pfc_plan *p, const void *state, dou
 }
 
 bool plan_ok(const pfc_plan *p) { return p && !p->destroyed; }
+
+// pfc_step with an event between consecutive launches; kinds: 0 row, 1 line, 2 entry, 3 exit.
+template <typename R>
+pfc_status profile_impl(pfc_plan *p, void *state, int64_t nsteps, double *ms, int64_t *launches) {
+    const Geom &g = p->t.g;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;
+    auto mark = [&](int k) -> cudaError_t {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        ev.push_back(e);
+        kind.push_back(k);
+        return cudaEventRecord(e, p->stream);
+    };
+    int64_t nl = 0;
+    cudaError_t err = mark(2);
+    launch_means<R>(p, state);
+    RowArgs<R> ra = row_args<R>(p);
+    ra.in = state;
+    ra.out = p->X;
+    ra.mean = p->d_mean;
+    ra.scale = (R)(1.0 / ((double)g.P * (double)g.M));
+    launch_row<R, ROW_FWD>(p, ra, p->nfields);
+    nl += 2 * p->nfields + 1;
+    for (int64_t s = 0; s < nsteps && err == cudaSuccess; ++s) {
+        RowArgs<R> rc = row_args<R>(p);
+        rc.in = p->X;
+        rc.out = p->C;
+        rc.proj = p->X;
+        rc.mean = p->d_mean;
+        if ((err = mark(0)) != cudaSuccess) break;
+        launch_row<R, ROW_CUBE>(p, rc, p->nfields);
+        LineArgs<R> la = line_args<R>(p);
+        la.x = p->X;
+        la.c = p->C;
+        if ((err = mark(1)) != cudaSuccess) break;
+        launch_line<R, LINE_STEP>(p, la, p->nfields);
+        nl += 2;
+    }
+    if (err == cudaSuccess) err = mark(3);
+    RowArgs<R> rb = row_args<R>(p);
+    rb.in = p->X;
+    rb.out = state;
+    rb.mean = p->d_mean;
+    launch_row<R, ROW_INV>(p, rb, p->nfields);
+    nl += 1;
+    if (err == cudaSuccess) err = mark(-1);
+    if (err == cudaSuccess) err = cudaGetLastError();
+    if (err == cudaSuccess) err = cudaStreamSynchronize(p->stream);
+    double acc[4] = {0, 0, 0, 0};
+    for (size_t i = 0; err == cudaSuccess && i + 1 < ev.size(); ++i) {
+        float t = 0.f;
+        err = cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+        if (kind[i] >= 0) acc[kind[i]] += t;
+    }
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    if (err != cudaSuccess) return fail(PFC_ERR_CUDA, std::string("profile: ") + cudaGetErrorString(err));
+    std::memcpy(ms, acc, sizeof(acc));
+    *launches = nl;
+    return PFC_OK;
+}
 
 }  // namespace
 
@@ -584,6 +647,15 @@ pfc_status pfc_step_adjoint(pfc_plan *p, const void *psi_n, const void *lam_next
     if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
     if (!psi_n || !lam_next || !lam_out || !dr) return fail(PFC_ERR_INVALID_ARG, "null pointer");
     return fail(PFC_ERR_UNSUPPORTED, "adjoint step not built yet");
+}
+
+pfc_status pfc_profile_steps(pfc_plan *p, void *state, int64_t nsteps, double *ms_out,
+                             int64_t *launches) {
+    if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
+    if (!state || !ms_out || !launches) return fail(PFC_ERR_INVALID_ARG, "null pointer");
+    if (nsteps < 0) return fail(PFC_ERR_INVALID_ARG, "nsteps must be >= 0");
+    return p->prec == PFC_FP64 ? profile_impl<double>(p, state, nsteps, ms_out, launches)
+                               : profile_impl<float>(p, state, nsteps, ms_out, launches);
 }
 
 pfc_status pfc_set_r(pfc_plan *p, int field, double r) {

@@ -57,6 +57,7 @@ template <typename R> struct RowArgs {
     void *out;            // ROW_INV: real; else X' layout
     const void *in2;      // ROW_ADJ_MIX: second X' input (V = B lam) ; real psi_n in in3
     const void *in3;
+    void *proj;           // ROW_CUBE: X' to receive the projected kx = 0 and nx/2 columns
     const double *mean;   // per field, may be null
     R scale;
     const typename VT<R>::V *tw;
@@ -184,6 +185,48 @@ __device__ void ppart_forward_store(const Geom &g, typename VT<R>::V *sm, int gr
     }
 }
 
+// Hermitian projection of the carried state. The kx = 0 and kx = nx/2 columns of X' are
+// redundant: in row space (after the inverse P-part) they must be real, and the row inverse
+// ignores their imaginary parts. Rounding leaves a small imaginary part there which psi^3
+// never sees and which the update multiplies by 1/D(k) > 1 at the linearly unstable
+// wavenumbers, so without projection it grows until it overflows. After the inverse P-part
+// this writes the real parts of both columns back to X' through the forward P-part
+// (X' = DFT_P(row values) / P), two values per row.
+template <typename R>
+__device__ void project_edge_columns(const Geom &g, const typename VT<R>::V *sm, int grp0,
+                                     const typename VT<R>::V *__restrict__ tw,
+                                     typename VT<R>::V *__restrict__ xout) {
+    using V = typename VT<R>::V;
+    const int P = g.P;
+    const R invP = (R)1 / (R)P;
+    for (int t = threadIdx.x; t < 2 * g.gpc; t += blockDim.x) {
+        const int gi = t >> 1, k = (t & 1) ? g.M : 0, grp = grp0 + gi;
+        V vals[64];
+        for (int pr = 0; pr < P; ++pr) vals[pr] = V{sm[(gi * P + pr) * g.rs + row_pad(k)].x, (R)0};
+        V tt[8];
+        if (g.Py > 1) {
+            for (int zp = 0; zp < g.Pz; ++zp) {
+                for (int b = 0; b < g.Py; ++b) tt[b] = vals[zp * g.Py + b];
+                dft_small<-1>(tt, g.Py);
+                for (int b = 0; b < g.Py; ++b) vals[zp * g.Py + b] = tt[b];
+            }
+        }
+        if (g.Pz > 1) {
+            for (int kpy = 0; kpy < g.Py; ++kpy) {
+                for (int a = 0; a < g.Pz; ++a) tt[a] = vals[a * g.Py + kpy];
+                dft_small<-1>(tt, g.Pz);
+                for (int a = 0; a < g.Pz; ++a) vals[a * g.Py + kpy] = tt[a];
+            }
+        }
+        for (int kpz = 0; kpz < g.Pz; ++kpz)
+            for (int kpy = 0; kpy < g.Py; ++kpy) {
+                V x = vals[kpz * g.Py + kpy];
+                if (P > 1) x = cmul(x, split_twiddle(g, tw, grp, kpz, kpy));
+                xout[(size_t)((kpz * g.Py + kpy) * g.Q + grp) * g.xs + k] = cscale(x, invP);
+            }
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // Real transform along x via a half-length complex transform (M = nx/2):
 //   z[j] = x[2j] + i x[2j+1],  Z = DFT_M z,
@@ -298,6 +341,11 @@ __global__ void __launch_bounds__(512) k_row(const Geom g, const RowArgs<R> a) {
 
     if (MODE != ROW_FWD) {
         ppart_inverse<R>(g, sm, grp0, a.tw);
+        if (MODE == ROW_CUBE) {
+            V *xw = reinterpret_cast<V *>(a.proj) + (size_t)field * g.nhalf;
+            project_edge_columns<R>(g, sm, grp0, a.tw, xw);
+            __syncthreads();
+        }
         c2r_pre_rows<R>(g, sm, rows, a.tw);
         __syncthreads();
     }
