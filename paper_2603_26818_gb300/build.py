@@ -25,10 +25,6 @@ def _nvcc() -> str:
     return cand
 
 
-def _sources(names):
-    return [os.path.join(CSRC, n) for n in names]
-
-
 def _stale(target, deps) -> bool:
     if not os.path.exists(target):
         return True
@@ -41,25 +37,47 @@ def _deps():
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [inc]
 
 
-def _compile(out, srcs, extra):
-    cmd = [_nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-o", out + ".tmp", *srcs, *extra]
+def _run(cmd, what):
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError(f"nvcc failed for {os.path.basename(out)}:\n{r.stderr[-4000:]}")
+        raise RuntimeError(f"nvcc failed for {what}:\n{r.stderr[-4000:]}")
+
+
+def _compile_obj(src, obj):
+    _run([_nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-c",
+          "-o", obj, src], os.path.basename(src))
+
+
+def _link(out, objs, extra):
+    _run([_nvcc(), *ARCH, "-shared", "-o", out + ".tmp", *objs, *extra], os.path.basename(out))
     os.replace(out + ".tmp", out)
+
+
+# translation units of libpfc.so: host plan logic, and the kernels of each precision
+LIB_UNITS = ["pfc_api.cu", "pfc_kern_f32.cu", "pfc_kern_f64.cu"]
 
 
 def build(force: bool = False) -> str:
     deps = _deps()
+    objdir = os.path.join(HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
     jobs = []
-    if force or _stale(LIB, deps):
-        jobs.append((LIB, _sources(["pfc_api.cu"]), []))
-    if force or _stale(BASELINE_LIB, deps):
-        jobs.append((BASELINE_LIB, _sources(["cufft_baseline.cu"]), ["-lcufft"]))
+    objs = []
+    for u in LIB_UNITS:
+        obj = os.path.join(objdir, u.replace(".cu", ".o"))
+        objs.append(obj)
+        if force or _stale(obj, deps):
+            jobs.append((os.path.join(CSRC, u), obj))
+    base_obj = os.path.join(objdir, "cufft_baseline.o")
+    if force or _stale(base_obj, deps):
+        jobs.append((os.path.join(CSRC, "cufft_baseline.cu"), base_obj))
     if jobs:
         with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
-            list(ex.map(lambda j: _compile(*j), jobs))
+            list(ex.map(lambda j: _compile_obj(*j), jobs))
+    if force or jobs or not os.path.exists(LIB):
+        _link(LIB, objs, [])
+    if force or jobs or not os.path.exists(BASELINE_LIB):
+        _link(BASELINE_LIB, [base_obj], ["-lcufft"])
     return LIB
 
 

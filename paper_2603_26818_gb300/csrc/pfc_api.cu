@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -10,7 +11,7 @@
 #include <vector>
 
 #include "../../include/pfc.h"
-#include "pfc_reduce.cuh"
+#include "pfc_launch.h"
 
 using namespace pfc;
 
@@ -94,6 +95,10 @@ double min_implicit(const pfc_op *ops, int nfields, double alpha, double dt, dou
 
 OpDev to_dev(const pfc_op &o) { return OpDev{o.kind, o.r, o.R1, o.q2}; }
 
+// Row pitch of a line-pass tile: W columns of 128 B (16 float2 / 8 double2) spread over all
+// banks already; narrower tiles get one padding element per row.
+int tile_pitch(int W, size_t vb) { return (size_t)W * vb >= 128 ? W : W + 1; }
+
 struct Tiles {
     Geom g;
     int nt_row, nt_line;
@@ -105,36 +110,44 @@ struct Tiles {
 //   line pass: ntile tiles of Q W complex values (Q = ny nz / P), W columns each
 // Preference: wide line-pass rows (W * sizeof(V) up to 128 B), then the smallest P.
 bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, size_t smem_max) {
+    const int max_threads = vb == 8 ? 1024 : 512;   // line pass blocks
+    const int max_row_threads = vb == 8 ? 1024 : 512;
     Geom g{};
     g.nx = nx; g.ny = ny; g.nz = nz; g.M = nx / 2;
     g.lnx = ilog2(nx); g.lny = ilog2(ny); g.lnz = ilog2(nz); g.lM = g.lnx - 1;
     g.ltab = std::max(g.lnx, std::max(g.lny, g.lnz));
-    g.tpsh = 4;
     g.rs = (int)round_up(row_pad(g.M) + 1, 2);
     const size_t row_bytes = (size_t)g.rs * vb;
-    int best_score = -1;
+    // PFC_TILE="Py,Pz,W" forces a tiling (used to compare tilings; rejected if it does not fit)
+    int fpy = 0, fpz = 0, fw = 0;
+    if (const char *env = std::getenv("PFC_TILE")) std::sscanf(env, "%d,%d,%d", &fpy, &fpz, &fw);
+    long best_score = LONG_MIN;
     Geom best{};
     for (int Py = 1; Py <= 8; Py *= 2) {
         if (Py > 1 && ny / Py < 8) continue;
         if (ny % Py) continue;
+        if (fpy && Py != fpy) continue;
         for (int Pz = 1; Pz <= 8; Pz *= 2) {
             if (nz == 1 && Pz > 1) continue;
             if (Pz > 1 && nz / Pz < 8) continue;
             if (nz % Pz) continue;
+            if (fpz && Pz != fpz) continue;
             const int Qy = ny / Py, Qz = nz / Pz;
             if (Qy < 8 && Qy != 1) continue;
             if (Qz < 8 && Qz != 1) continue;
             const int P = Py * Pz, Q = Qy * Qz;
-            if ((size_t)P * row_bytes > smem_max) continue;
+            if ((size_t)P * (row_bytes + vb) > smem_max) continue;
             for (int W = 16; W >= 1; W /= 2) {
-                if ((size_t)W * vb > 128) continue;
+                if (fw && W != fw) continue;
+                if (!fw && (size_t)W * vb > 64) continue;   // 64-byte tile rows at most
                 if (W > g.M + 1 && W > 1) continue;
                 const int64_t QW = (int64_t)Q * W;
-                if (QW < 8) continue;
-                const size_t tile = (size_t)(QW + (QW >> g.tpsh) + 1);
+                if (QW < 8 || QW / 8 > max_threads) continue;
+                const int wp = tile_pitch(W, vb);
+                const size_t tile = (size_t)Q * wp;
                 if ((size_t)ntile * tile * vb > smem_max) continue;
-                const int wb = (int)(W * vb);
-                const int score = wb * 64 - P;   // wide rows first, then small P
+                // wide tile rows first, blocks of at most 512 threads, then the smallest P
+                const long score = (long)(W * vb) * 4096 - (QW / 8 > 512 ? 200000 : 0) - P;
                 if (score > best_score) {
                     best_score = score;
                     best = g;
@@ -145,17 +158,18 @@ bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, size_t s
             }
         }
     }
-    if (best_score < 0) return false;
+    if (best_score == LONG_MIN) return false;
     g = best;
     g.lPy = ilog2(g.Py); g.lPz = ilog2(g.Pz); g.lQy = ilog2(g.Qy); g.lQz = ilog2(g.Qz);
     g.P = g.Py * g.Pz; g.Q = g.Qy * g.Qz; g.lQ = ilog2(g.Q);
     g.lW = ilog2(g.W);
+    g.wp = tile_pitch(g.W, vb);
     g.xs = (int)round_up(g.M + 1, std::max(g.W, 2));
     g.ncg = g.xs / g.W;
     // row groups per CTA: enough rows for >= 256 threads, within smem and dividing Q
     const int Tr = g.M / 8;
     int gpc = 1;
-    while (gpc * 2 <= g.Q && (size_t)(gpc * 2) * g.P * row_bytes <= smem_max &&
+    while (gpc * 2 <= g.Q && (size_t)(gpc * 2) * g.P * (row_bytes + vb) <= smem_max &&
            gpc * g.P * Tr < 256)
         gpc *= 2;
     g.gpc = gpc;
@@ -164,18 +178,17 @@ bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, size_t s
     g.nstd = (int64_t)ny * nz * (g.M + 1);
     t.g = g;
     const int rows = gpc * g.P;
-    t.nt_row = std::min(512, std::max(Tr, rows * Tr));
+    t.nt_row = std::min(max_row_threads, std::max(Tr, rows * Tr));
     if (t.nt_row < 64) t.nt_row = std::max(Tr, 64 / Tr * Tr);
-    t.smem_row = (size_t)rows * row_bytes;
+    // rows, the split twiddles of the block's rows, then the saved real parts of the kx = 0
+    // and nx/2 columns (2 gpc P reals)
+    t.smem_row = (size_t)round_up((int64_t)rows * (row_bytes + vb) + 2 * gpc * g.P * (vb / 2), 16);
     const int64_t QW = (int64_t)g.Q * g.W;
-    t.nt_line = (int)std::min<int64_t>(512, std::max<int64_t>(64, QW / 8));
-    t.smem_line = (size_t)ntile * (size_t)(QW + (QW >> g.tpsh) + 1) * vb;
+    t.nt_line = (int)(QW / 8);
+    t.smem_line = (size_t)ntile * (size_t)g.Q * g.wp * vb;
     return true;
 }
 
-template <typename K> cudaError_t allow_smem(K kernel, size_t bytes) {
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
 
 }  // namespace
 
@@ -189,7 +202,7 @@ struct pfc_plan {
     int prec = PFC_FP64;
     cudaStream_t stream = nullptr;
     Tiles t{};
-    void *X = nullptr, *C = nullptr, *tw = nullptr;
+    void *X = nullptr, *C = nullptr, *tw = nullptr, *stw = nullptr;
     double *d_mean = nullptr, *d_part = nullptr, *d_out = nullptr;
     int *d_status = nullptr;
     size_t scratch = 0;
@@ -203,48 +216,51 @@ namespace {
 constexpr int GRAPH_CHUNK = 16;
 
 size_t vbytes(const pfc_plan *p) { return p->prec == PFC_FP64 ? 16 : 8; }
-size_t rbytes(const pfc_plan *p) { return p->prec == PFC_FP64 ? 8 : 4; }
+
+constexpr int STW8 = 4672, STW4 = 2336, STW2 = 1168;   // per-stage table entries (Ns = 8, 64, 512)
+
+template <typename R> StageTw<typename VT<R>::V> stage_tw(const pfc_plan *p) {
+    using V = typename VT<R>::V;
+    const V *b = reinterpret_cast<const V *>(p->stw);
+    return StageTw<V>{b, b + STW8, b + STW8 + STW4};
+}
 
 template <typename R> RowArgs<R> row_args(const pfc_plan *p) {
     RowArgs<R> a{};
     a.tw = reinterpret_cast<const typename VT<R>::V *>(p->tw);
+    a.st = stage_tw<R>(p);
     a.scale = (R)1;
     return a;
 }
 
 template <typename R> LineArgs<R> line_args(const pfc_plan *p) {
     LineArgs<R> a{};
-    a.tw = reinterpret_cast<const typename VT<R>::V *>(p->tw);
+    a.st = stage_tw<R>(p);
     a.scale = (R)1;
-    a.dt = p->dt;
-    a.dx = p->dx;
-    a.op0 = to_dev(p->ops[0]);
-    a.op1 = to_dev(p->ops[p->nfields > 1 ? 1 : 0]);
-    a.alpha = p->alpha;
+    const Geom &g = p->t.g;
+    const double two_pi = 6.28318530717958647692528676655900576839;
+    a.up.dt = (R)p->dt;
+    a.up.cx = (R)(two_pi / (g.nx * p->dx));
+    a.up.cy = (R)(two_pi / (g.ny * p->dx));
+    a.up.cz = (R)(two_pi / (g.nz * p->dx));
+    a.up.invQ = (R)(1.0 / g.Q);
+    a.up.inv_halfN = (R)(2.0 / (double)g.nreal);
+    for (int f = 0; f < 2; ++f) {
+        const pfc_op &o = p->ops[f < p->nfields ? f : 0];
+        a.up.op[f] = OpR<R>{o.kind, (R)o.r, (R)o.R1, (R)(o.q2 * o.q2)};
+    }
     return a;
 }
 
-template <typename R, int MODE> void launch_row(const pfc_plan *p, const RowArgs<R> &a, int nf) {
-    const Geom &g = p->t.g;
-    dim3 grid(g.Q / g.gpc, nf);
-    k_row<R, MODE><<<grid, p->t.nt_row, p->t.smem_row, p->stream>>>(g, a);
+LaunchCfg cfg(const pfc_plan *p) {
+    return LaunchCfg{p->t.g, p->t.nt_row, p->t.nt_line, p->t.smem_row, p->t.smem_line, p->stream};
 }
 
-template <typename R, int MODE> void launch_line(const pfc_plan *p, const LineArgs<R> &a, int nf) {
-    const Geom &g = p->t.g;
-    dim3 grid(g.ncg, g.P, nf);
-    k_line<R, MODE><<<grid, p->t.nt_line, p->t.smem_line, p->stream>>>(g, a);
+template <typename R> void launch_row_m(const pfc_plan *p, int mode, const RowArgs<R> &a, int nf) {
+    launch_row<R>(cfg(p), mode, a, nf);
 }
-
-template <typename R> cudaError_t set_smem_attrs(const pfc_plan *p) {
-    cudaError_t e;
-    if ((e = allow_smem(k_row<R, ROW_CUBE>, p->t.smem_row)) != cudaSuccess) return e;
-    if ((e = allow_smem(k_row<R, ROW_FWD>, p->t.smem_row)) != cudaSuccess) return e;
-    if ((e = allow_smem(k_row<R, ROW_INV>, p->t.smem_row)) != cudaSuccess) return e;
-    if ((e = allow_smem(k_line<R, LINE_STEP>, p->t.smem_line)) != cudaSuccess) return e;
-    if ((e = allow_smem(k_line<R, LINE_FWD>, p->t.smem_line)) != cudaSuccess) return e;
-    if ((e = allow_smem(k_line<R, LINE_INV>, p->t.smem_line)) != cudaSuccess) return e;
-    return cudaSuccess;
+template <typename R> void launch_line_m(const pfc_plan *p, int mode, const LineArgs<R> &a, int nf) {
+    launch_line<R>(cfg(p), mode, a, nf);
 }
 
 // Mean of each field of a real array into d_mean[f] (FP64).
@@ -252,10 +268,8 @@ template <typename R> void launch_means(pfc_plan *p, const void *state) {
     const Geom &g = p->t.g;
     for (int f = 0; f < p->nfields; ++f) {
         const R *x = reinterpret_cast<const R *>(state) + (size_t)f * g.nreal;
-        k_reduce_real<R, RED_SUM><<<RED_BLOCKS, RED_THREADS, 0, p->stream>>>(x, nullptr, g.nreal,
-                                                                             p->d_part, p->d_status);
-        k_finish<<<1, RED_THREADS, 0, p->stream>>>(p->d_part, RED_BLOCKS, 1.0 / (double)g.nreal,
-                                                   p->d_mean + f);
+        launch_reduce_real<R>(p->stream, RED_SUM, x, nullptr, g.nreal, p->d_part, p->d_status);
+        launch_finish(p->stream, p->d_part, RED_BLOCKS, 1.0 / (double)g.nreal, p->d_mean + f);
     }
 }
 
@@ -266,11 +280,11 @@ template <typename R> void enqueue_one_step(pfc_plan *p) {
     ra.out = p->C;
     ra.proj = p->X;
     ra.mean = p->d_mean;
-    launch_row<R, ROW_CUBE>(p, ra, p->nfields);
+    launch_row_m<R>(p, ROW_CUBE, ra, p->nfields);
     LineArgs<R> la = line_args<R>(p);
     la.x = p->X;
     la.c = p->C;
-    launch_line<R, LINE_STEP>(p, la, p->nfields);
+    launch_line_m<R>(p, LINE_STEP, la, p->nfields);
 }
 
 template <typename R> pfc_status run_steps(pfc_plan *p, int64_t nsteps) {
@@ -312,7 +326,7 @@ template <typename R> pfc_status step_impl(pfc_plan *p, void *state, int64_t nst
     ra.out = p->X;
     ra.mean = p->d_mean;
     ra.scale = (R)(1.0 / ((double)g.P * (double)g.M));
-    launch_row<R, ROW_FWD>(p, ra, p->nfields);
+    launch_row_m<R>(p, ROW_FWD, ra, p->nfields);
     PFC_CUDA(cudaGetLastError());
     pfc_status s = run_steps<R>(p, nsteps);
     if (s != PFC_OK) return s;
@@ -320,7 +334,7 @@ template <typename R> pfc_status step_impl(pfc_plan *p, void *state, int64_t nst
     rb.in = p->X;
     rb.out = state;
     rb.mean = p->d_mean;
-    launch_row<R, ROW_INV>(p, rb, p->nfields);
+    launch_row_m<R>(p, ROW_INV, rb, p->nfields);
     PFC_CUDA(cudaGetLastError());
     return PFC_OK;
 }
@@ -329,11 +343,11 @@ template <typename R> pfc_status r2c_impl(pfc_plan *p, const void *in, void *out
     RowArgs<R> ra = row_args<R>(p);
     ra.in = in;
     ra.out = p->X;
-    launch_row<R, ROW_FWD>(p, ra, p->nfields);
+    launch_row_m<R>(p, ROW_FWD, ra, p->nfields);
     LineArgs<R> la = line_args<R>(p);
     la.x = p->X;
     la.std_out = out;
-    launch_line<R, LINE_FWD>(p, la, p->nfields);
+    launch_line_m<R>(p, LINE_FWD, la, p->nfields);
     PFC_CUDA(cudaGetLastError());
     return PFC_OK;
 }
@@ -344,11 +358,11 @@ template <typename R> pfc_status c2r_impl(pfc_plan *p, const void *in, void *out
     la.x = p->X;
     la.std_in = in;
     la.scale = (R)(2.0 / (double)g.nreal);
-    launch_line<R, LINE_INV>(p, la, p->nfields);
+    launch_line_m<R>(p, LINE_INV, la, p->nfields);
     RowArgs<R> ra = row_args<R>(p);
     ra.in = p->X;
     ra.out = out;
-    launch_row<R, ROW_INV>(p, ra, p->nfields);
+    launch_row_m<R>(p, ROW_INV, ra, p->nfields);
     PFC_CUDA(cudaGetLastError());
     return PFC_OK;
 }
@@ -388,25 +402,21 @@ template <typename R> pfc_status energy_impl(pfc_plan *p, const void *state, dou
         ra.in = x;
         ra.out = p->X;
         ra.mean = p->d_mean + f;
-        launch_row<R, ROW_FWD>(p, ra, 1);
+        launch_row_m<R>(p, ROW_FWD, ra, 1);
         LineArgs<R> la = line_args<R>(p);
         la.x = p->X;
         la.std_out = p->C;
-        launch_line<R, LINE_FWD>(p, la, 1);
-        k_reduce_spec<R><<<RED_BLOCKS, RED_THREADS, 0, p->stream>>>(
-            g, to_dev(p->ops[f]), p->dx, reinterpret_cast<const typename VT<R>::V *>(p->C),
-            p->d_mean + f, p->d_part, p->d_status);
-        k_finish<<<1, RED_THREADS, 0, p->stream>>>(p->d_part, RED_BLOCKS, 1.0, p->d_out + f);
-        k_reduce_real<R, RED_POW4><<<RED_BLOCKS, RED_THREADS, 0, p->stream>>>(
-            x, nullptr, g.nreal, p->d_part, p->d_status);
-        k_finish<<<1, RED_THREADS, 0, p->stream>>>(p->d_part, RED_BLOCKS, 1.0,
-                                                   p->d_out + p->nfields + f);
+        launch_line_m<R>(p, LINE_FWD, la, 1);
+        launch_reduce_spec<R>(p->stream, g, to_dev(p->ops[f]), p->dx, p->C, p->d_mean + f,
+                              p->d_part, p->d_status);
+        launch_finish(p->stream, p->d_part, RED_BLOCKS, 1.0, p->d_out + f);
+        launch_reduce_real<R>(p->stream, RED_POW4, x, nullptr, g.nreal, p->d_part, p->d_status);
+        launch_finish(p->stream, p->d_part, RED_BLOCKS, 1.0, p->d_out + p->nfields + f);
     }
     if (p->nfields == 2) {
         const R *x0 = reinterpret_cast<const R *>(state);
-        k_reduce_real<R, RED_DOT><<<RED_BLOCKS, RED_THREADS, 0, p->stream>>>(
-            x0, x0 + g.nreal, g.nreal, p->d_part, p->d_status);
-        k_finish<<<1, RED_THREADS, 0, p->stream>>>(p->d_part, RED_BLOCKS, 1.0, p->d_out + 4);
+        launch_reduce_real<R>(p->stream, RED_DOT, x0, x0 + g.nreal, g.nreal, p->d_part, p->d_status);
+        launch_finish(p->stream, p->d_part, RED_BLOCKS, 1.0, p->d_out + 4);
     }
     PFC_CUDA(cudaGetLastError());
     double h[5] = {0, 0, 0, 0, 0};
@@ -445,7 +455,7 @@ pfc_status profile_impl(pfc_plan *p, void *state, int64_t nsteps, double *ms, in
     ra.out = p->X;
     ra.mean = p->d_mean;
     ra.scale = (R)(1.0 / ((double)g.P * (double)g.M));
-    launch_row<R, ROW_FWD>(p, ra, p->nfields);
+    launch_row_m<R>(p, ROW_FWD, ra, p->nfields);
     nl += 2 * p->nfields + 1;
     for (int64_t s = 0; s < nsteps && err == cudaSuccess; ++s) {
         RowArgs<R> rc = row_args<R>(p);
@@ -454,12 +464,12 @@ pfc_status profile_impl(pfc_plan *p, void *state, int64_t nsteps, double *ms, in
         rc.proj = p->X;
         rc.mean = p->d_mean;
         if ((err = mark(0)) != cudaSuccess) break;
-        launch_row<R, ROW_CUBE>(p, rc, p->nfields);
+        launch_row_m<R>(p, ROW_CUBE, rc, p->nfields);
         LineArgs<R> la = line_args<R>(p);
         la.x = p->X;
         la.c = p->C;
         if ((err = mark(1)) != cudaSuccess) break;
-        launch_line<R, LINE_STEP>(p, la, p->nfields);
+        launch_line_m<R>(p, LINE_STEP, la, p->nfields);
         nl += 2;
     }
     if (err == cudaSuccess) err = mark(3);
@@ -467,7 +477,7 @@ pfc_status profile_impl(pfc_plan *p, void *state, int64_t nsteps, double *ms, in
     rb.in = p->X;
     rb.out = state;
     rb.mean = p->d_mean;
-    launch_row<R, ROW_INV>(p, rb, p->nfields);
+    launch_row_m<R>(p, ROW_INV, rb, p->nfields);
     nl += 1;
     if (err == cudaSuccess) err = mark(-1);
     if (err == cudaSuccess) err = cudaGetLastError();
@@ -560,7 +570,7 @@ pfc_status pfc_plan_create(pfc_plan **out, int ndim, const int64_t *dims, double
         return fail(PFC_ERR_UNSUPPORTED, "no pass tiling fits shared memory for this grid and precision");
     }
     const Geom &g = p->t.g;
-    e = p->prec == PFC_FP64 ? set_smem_attrs<double>(p) : set_smem_attrs<float>(p);
+    e = p->prec == PFC_FP64 ? set_smem_attrs<double>(cfg(p)) : set_smem_attrs<float>(cfg(p));
     if (e != cudaSuccess) { delete p; return fail(PFC_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e)); }
 
     const size_t half_bytes = (size_t)g.nhalf * nfields * vbytes(p);
@@ -573,22 +583,33 @@ pfc_status pfc_plan_create(pfc_plan **out, int ndim, const int64_t *dims, double
     if ((e = cudaMalloc(&p->X, half_bytes)) != cudaSuccess) return cleanup(e);
     if ((e = cudaMalloc(&p->C, half_bytes)) != cudaSuccess) return cleanup(e);
     if ((e = cudaMalloc(&p->tw, ntab * vbytes(p))) != cudaSuccess) return cleanup(e);
+    const int64_t nst = STW8 + STW4 + STW2;
+    if ((e = cudaMalloc(&p->stw, nst * vbytes(p))) != cudaSuccess) return cleanup(e);
     if ((e = cudaMalloc(&p->d_mean, 8 * sizeof(double))) != cudaSuccess) return cleanup(e);
     if ((e = cudaMalloc(&p->d_part, RED_BLOCKS * sizeof(double))) != cudaSuccess) return cleanup(e);
     if ((e = cudaMalloc(&p->d_out, 8 * sizeof(double))) != cudaSuccess) return cleanup(e);
     if ((e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) return cleanup(e);
-    p->scratch = 2 * half_bytes + ntab * vbytes(p) + (16 + RED_BLOCKS) * sizeof(double) + sizeof(int);
+    p->scratch = 2 * half_bytes + (ntab + nst) * vbytes(p) + (16 + RED_BLOCKS) * sizeof(double) + sizeof(int);
 
     std::vector<double> tw(2 * ntab);
     for (int64_t i = 0; i < ntab; ++i) unit_root_fwd(i, ntab, &tw[2 * i], &tw[2 * i + 1]);
-    if (p->prec == PFC_FP64) {
-        e = cudaMemcpy(p->tw, tw.data(), ntab * 16, cudaMemcpyHostToDevice);
-    } else {
-        std::vector<float> twf(2 * ntab);
-        for (int64_t i = 0; i < 2 * ntab; ++i) twf[i] = (float)tw[i];
-        e = cudaMemcpy(p->tw, twf.data(), ntab * 8, cudaMemcpyHostToDevice);
+    // per-stage tables [k][r] = W_{R Ns}^{r k} for R = 8, 4, 2 and Ns = 8, 64, 512
+    std::vector<double> st(2 * nst);
+    {
+        int64_t o = 0;
+        for (int R : {8, 4, 2})
+            for (int64_t ns = 8; ns <= 512; ns *= 8)
+                for (int64_t k = 0; k < ns; ++k)
+                    for (int r = 0; r < R; ++r, ++o) unit_root_fwd(r * k, R * ns, &st[2 * o], &st[2 * o + 1]);
     }
-    if (e != cudaSuccess) return cleanup(e);
+    auto upload = [&](void *dst, const std::vector<double> &src) {
+        if (p->prec == PFC_FP64) return cudaMemcpy(dst, src.data(), src.size() * 8, cudaMemcpyHostToDevice);
+        std::vector<float> f(src.size());
+        for (size_t i = 0; i < src.size(); ++i) f[i] = (float)src[i];
+        return cudaMemcpy(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice);
+    };
+    if ((e = upload(p->tw, tw)) != cudaSuccess) return cleanup(e);
+    if ((e = upload(p->stw, st)) != cudaSuccess) return cleanup(e);
     if ((e = cudaMemset(p->X, 0, half_bytes)) != cudaSuccess) return cleanup(e);
     if ((e = cudaMemset(p->C, 0, half_bytes)) != cudaSuccess) return cleanup(e);
     if ((e = cudaMemset(p->d_mean, 0, 8 * sizeof(double))) != cudaSuccess) return cleanup(e);
@@ -602,7 +623,7 @@ pfc_status pfc_plan_destroy(pfc_plan *p) {
     if (p->destroyed) return fail(PFC_ERR_INVALID_ARG, "plan already destroyed");
     cudaStreamSynchronize(p->stream);
     if (p->graph) cudaGraphExecDestroy(p->graph);
-    cudaFree(p->X); cudaFree(p->C); cudaFree(p->tw);
+    cudaFree(p->X); cudaFree(p->C); cudaFree(p->tw); cudaFree(p->stw);
     cudaFree(p->d_mean); cudaFree(p->d_part); cudaFree(p->d_out); cudaFree(p->d_status);
     p->destroyed = true;
     delete p;

@@ -8,8 +8,9 @@
 // second transform can start from those registers: the row pass forms psi^3 between an
 // inverse and a forward transform without touching shared memory.
 //
-// Twiddles come from one table tw[i] = exp(-2 pi i * i / 2^ltab), generated on the host in FP64
-// (and rounded once for the FP32 path). The inverse transform uses the conjugate.
+// Stage twiddles come from per-stage tables (StageTw) generated on the host in FP64 (rounded once
+// for the FP32 path); other twiddles from one table tw[i] = exp(-2 pi i * i / 2^ltab). The
+// inverse transform uses the conjugate.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -91,59 +92,84 @@ template <int S, typename V> __device__ __forceinline__ void dft_small(V (&t)[8]
 }
 
 // ------------------------------------------------------------------------------------------
-// Shared-memory addressing of one transform instance: element i lives at addr(i).
+// Shared-memory addressing of one transform instance: element i lives at at(i).
 // ------------------------------------------------------------------------------------------
-// A row of a row buffer: one padding slot after every 8 elements (bank spreading).
+// A row of a row buffer: one padding slot after every 8 elements (bank spreading). For the
+// index sets a transform touches (j + m n/8 with n/8 a multiple of 8, and the Stockham outputs
+// o + r Ns with Ns a multiple of 8, or o a multiple of 8 when Ns = 1), the padded address is
+// linear in m (or r), so the accessors compute one base and add compile-time steps.
 __host__ __device__ __forceinline__ int row_pad(int i) { return i + (i >> 3); }
 
 struct RowAddr {
     int base;
-    __device__ __forceinline__ int operator()(int i) const { return base + row_pad(i); }
+    __device__ __forceinline__ int at(int i) const { return base + row_pad(i); }
+    template <int N8> __host__ __device__ static constexpr int step() { return N8 >= 8 ? N8 + N8 / 8 : N8; }
+    template <int NS> __host__ __device__ static constexpr int ostep() { return NS >= 8 ? NS + NS / 8 : NS; }
 };
 
-// A column of an interleaved tile: flat e = off + i * stride, padded by e >> pshift.
+// A column of an interleaved tile: element i at off + i * stride (the tile rows are padded by
+// the choice of row pitch, so no per-element padding is needed).
 struct TileAddr {
-    int off, stride, pshift;
-    __device__ __forceinline__ int operator()(int i) const {
-        int e = off + i * stride;
-        return e + (e >> pshift);
-    }
+    int off, stride;
+    __device__ __forceinline__ int at(int i) const { return off + i * stride; }
 };
 
-// ------------------------------------------------------------------------------------------
-// Stockham stage machinery. Stage s has radix R = 2^lR and Ns = 2^lNs (the product of the
-// previous radices). Butterfly b has k = b mod Ns; it reads b + r n/R, multiplies input r by
-// W_{Ns R}^{r k}, runs a DFT_R and writes output r to (b - k) R + k + r Ns.
-// Thread j owns butterflies b = j + u n/8 (u < 8/R): its inputs are always j + m n/8 with
-// slot m = u + (8/R) r.
-// ------------------------------------------------------------------------------------------
-template <typename V, typename Addr>
-__device__ __forceinline__ void load8(V (&v)[8], const V *sm, const Addr &ad, int j, int n8) {
+// Per-stage twiddle tables, laid out [k][r] so that one butterfly's twiddles are contiguous:
+//   t8: radix-8 stages with Ns = 8, 64, 512:  entry [k][r] = W_{8 Ns}^{r k}, r = 0..7
+//   t4: radix-4 last stages with Ns = 8, 64, 512:  [k][r] = W_{4 Ns}^{r k}, r = 0..3
+//   t2: radix-2 last stages with Ns = 8, 64, 512:  [k][r] = W_{2 Ns}^{r k}, r = 0..1
+// Tables of one kind are stored back to back; the block for Ns = 8^s starts at
+// R (8^s - 8) / 7 entries. All entries are FP64-generated (rounded once for FP32).
+template <typename V> struct StageTw {
+    const V *t8, *t4, *t2;
+};
+
+__host__ __device__ __forceinline__ int stage_tw_off(int R, int lNs) {
+    const int ns = 1 << lNs;
+    return R * (ns - 8) / 7;
+}
+
+__device__ __forceinline__ void load_tw(const float2 *__restrict__ t, float2 (&w)[8], int n) {
+    const float4 *p = reinterpret_cast<const float4 *>(t);
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = sm[ad(j + m * n8)];
+    for (int i = 0; i < 4; ++i) {
+        if (2 * i < n) {
+            const float4 q = __ldg(p + i);
+            w[2 * i] = float2{q.x, q.y};
+            w[2 * i + 1] = float2{q.z, q.w};
+        }
+    }
+}
+__device__ __forceinline__ void load_tw(const double2 *__restrict__ t, double2 (&w)[8], int n) {
+#pragma unroll
+    for (int i = 1; i < 8; ++i)
+        if (i < n) w[i] = __ldg(t + i);
 }
 
 template <int S, typename V>
 __device__ __forceinline__ void stage_exec(V (&v)[8], int lR, int lNs, int j, int n8,
-                                           const V *__restrict__ tw, int ltab) {
+                                           const StageTw<V> &tw) {
     const int Ns = 1 << lNs;
-    const int sh = ltab - lNs - lR;  // W_{Ns R}^{x} = tw[x << sh]
     if (lR == 3) {
-        const int k = j & (Ns - 1);
         if (lNs > 0) {
+            const int k = j & (Ns - 1);
+            V w[8];
+            load_tw(tw.t8 + stage_tw_off(8, lNs) + k * 8, w, 8);
 #pragma unroll
-            for (int r = 1; r < 8; ++r) v[r] = ctw<S>(v[r], __ldg(&tw[(r * k) << sh]));
+            for (int r = 1; r < 8; ++r) v[r] = ctw<S>(v[r], w[r]);
         }
         dft8<S>(v);
     } else if (lR == 2) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            const int k = (j + u * n8) & (Ns - 1);
             V c0 = v[u], c1 = v[u + 2], c2 = v[u + 4], c3 = v[u + 6];
             if (lNs > 0) {
-                c1 = ctw<S>(c1, __ldg(&tw[k << sh]));
-                c2 = ctw<S>(c2, __ldg(&tw[(2 * k) << sh]));
-                c3 = ctw<S>(c3, __ldg(&tw[(3 * k) << sh]));
+                const int k = (j + u * n8) & (Ns - 1);
+                V w[8];
+                load_tw(tw.t4 + stage_tw_off(4, lNs) + k * 4, w, 4);
+                c1 = ctw<S>(c1, w[1]);
+                c2 = ctw<S>(c2, w[2]);
+                c3 = ctw<S>(c3, w[3]);
             }
             dft4<S>(c0, c1, c2, c3);
             v[u] = c0; v[u + 2] = c1; v[u + 4] = c2; v[u + 6] = c3;
@@ -151,97 +177,129 @@ __device__ __forceinline__ void stage_exec(V (&v)[8], int lR, int lNs, int j, in
     } else if (lR == 1) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int k = (j + u * n8) & (Ns - 1);
             V c0 = v[u], c1 = v[u + 4];
-            if (lNs > 0) c1 = ctw<S>(c1, __ldg(&tw[k << sh]));
+            if (lNs > 0) {
+                const int k = (j + u * n8) & (Ns - 1);
+                V w[8];
+                load_tw(tw.t2 + stage_tw_off(2, lNs) + k * 2, w, 2);
+                c1 = ctw<S>(c1, w[1]);
+            }
             dft2<S>(c0, c1);
             v[u] = c0; v[u + 4] = c1;
         }
     }
 }
 
-template <typename V, typename Addr>
-__device__ __forceinline__ void stage_store(const V (&v)[8], V *sm, const Addr &ad, int lR, int lNs,
-                                            int j, int n8) {
-    const int Ns = 1 << lNs;
-    if (lR == 3) {
-        const int k = j & (Ns - 1);
-        const int o = ((j - k) << 3) + k;
+// ------------------------------------------------------------------------------------------
+// Transforms with a compile-time length n = 2^L: every stage unrolled, radix and Ns constant.
+// ------------------------------------------------------------------------------------------
+template <int N8, typename V>
+__device__ __forceinline__ void load8_t(V (&v)[8], const V *sm, const RowAddr &ad, int j) {
+    if (N8 >= 8) {
+        const int p = ad.at(j);
 #pragma unroll
-        for (int r = 0; r < 8; ++r) sm[ad(o + r * Ns)] = v[r];
-    } else if (lR == 2) {
+        for (int m = 0; m < 8; ++m) v[m] = sm[p + m * RowAddr::step<N8>()];
+    } else {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = sm[ad.at(j + m * N8)];
+    }
+}
+template <int N8, typename V>
+__device__ __forceinline__ void load8_t(V (&v)[8], const V *sm, const TileAddr &ad, int j) {
+    const int p = ad.at(j), st = N8 * ad.stride;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = sm[p + m * st];
+}
+
+// Store the R outputs o + r Ns (r < R) of one butterfly.
+template <int NS, int R, typename V>
+__device__ __forceinline__ void store_group(const V *vals, V *sm, const RowAddr &ad, int o) {
+    if (NS >= 8 || (NS == 1 && R == 8)) {   // NS = 1: o = 8 j', outputs at 9 j' + r
+        const int p = ad.at(o);
+#pragma unroll
+        for (int r = 0; r < R; ++r) sm[p + r * RowAddr::ostep<NS>()] = vals[r];
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) sm[ad.at(o + r * NS)] = vals[r];
+    }
+}
+template <int NS, int R, typename V>
+__device__ __forceinline__ void store_group(const V *vals, V *sm, const TileAddr &ad, int o) {
+    const int p = ad.at(o), st = NS * ad.stride;
+#pragma unroll
+    for (int r = 0; r < R; ++r) sm[p + r * st] = vals[r];
+}
+
+template <int LR, int LNS, int N8, typename V, typename Addr>
+__device__ __forceinline__ void stage_store_t(const V (&v)[8], V *sm, const Addr &ad, int j) {
+    constexpr int Ns = 1 << LNS;
+    if (LR == 3) {
+        const int k = j & (Ns - 1);
+        store_group<Ns, 8>(v, sm, ad, ((j - k) << 3) + k);
+    } else if (LR == 2) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            const int b = j + u * n8, k = b & (Ns - 1);
-            const int o = ((b - k) << 2) + k;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) sm[ad(o + r * Ns)] = v[u + 2 * r];
+            const int b = j + u * N8, k = b & (Ns - 1);
+            const V t[4] = {v[u], v[u + 2], v[u + 4], v[u + 6]};
+            store_group<Ns, 4>(t, sm, ad, ((b - k) << 2) + k);
         }
     } else {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int b = j + u * n8, k = b & (Ns - 1);
-            const int o = ((b - k) << 1) + k;
-            sm[ad(o)] = v[u];
-            sm[ad(o + Ns)] = v[u + 4];
+            const int b = j + u * N8, k = b & (Ns - 1);
+            const V t[2] = {v[u], v[u + 4]};
+            store_group<Ns, 2>(t, sm, ad, ((b - k) << 1) + k);
         }
     }
 }
 
-// One transform of n = 2^L points (L >= 3), run by every thread of the block (it contains
+template <int S, int L, int LR, int LNS, typename V, typename Addr>
+__device__ __forceinline__ void stage_t(V (&v)[8], V *sm, const Addr &ad, int j, bool act,
+                                        bool load, bool store, const StageTw<V> &tw) {
+    constexpr int N8 = 1 << (L - 3);
+    if (act && load) load8_t<N8>(v, sm, ad, j);
+    if (act) stage_exec<S>(v, LR, LNS, j, N8, tw);
+    if (!store) return;
+    __syncthreads();
+    if (act) stage_store_t<LR, LNS, N8>(v, sm, ad, j);
+    __syncthreads();
+}
+
+template <int S, int L, typename V, typename Addr>
+__device__ __forceinline__ void fft_run_t(V (&v)[8], V *sm, const Addr &ad, int j, bool act,
+                                          bool in_regs, bool out_regs, const StageTw<V> &tw) {
+    constexpr int NFULL = L / 3;
+    constexpr int LLAST = L - 3 * NFULL;    // 0: all stages radix 8
+    constexpr int NST = NFULL + (LLAST ? 1 : 0);
+    // radix-8 stages s = 0 .. NFULL-1 with Ns = 8^s, then one radix 2^LLAST stage
+    stage_t<S, L, 3, 0>(v, sm, ad, j, act, !in_regs, !(NST == 1 && out_regs), tw);
+    if (NFULL > 1) stage_t<S, L, 3, (NFULL > 1 ? 3 : 0)>(v, sm, ad, j, act, true, !(NST == 2 && out_regs), tw);
+    if (NFULL > 2) stage_t<S, L, 3, (NFULL > 2 ? 6 : 0)>(v, sm, ad, j, act, true, !(NST == 3 && out_regs), tw);
+    if (NFULL > 3) stage_t<S, L, 3, (NFULL > 3 ? 9 : 0)>(v, sm, ad, j, act, true, !(NST == 4 && out_regs), tw);
+    if (LLAST) stage_t<S, L, (LLAST ? LLAST : 1), 3 * NFULL>(v, sm, ad, j, act, true, !out_regs, tw);
+}
+
+// One transform of n = 2^L points (3 <= L <= 12), run by every thread of the block (it contains
 // __syncthreads); threads with act == false only take part in the barriers.
 //   in_regs:  stage 0 takes its inputs from v (slot m = element j + m n/8) instead of smem.
 //   out_regs: the last stage leaves its outputs in v (slot m = element j + m n/8) and is not
 //             stored; otherwise the result is in smem in natural order and v is undefined.
-// When in_regs is set, the caller must not have other threads still reading smem that this
-// call overwrites before its first barrier (a barrier is issued before the first store).
+// When in_regs is set, a barrier is issued before the first store, so other threads may still
+// be reading smem that this call overwrites.
 template <int S, typename V, typename Addr>
 __device__ __forceinline__ void fft_run(V (&v)[8], V *sm, const Addr &ad, int L, int j, bool act,
-                                        bool in_regs, bool out_regs, const V *__restrict__ tw,
-                                        int ltab) {
-    const int n8 = 1 << (L - 3);
-    const int nst = (L + 2) / 3;
-    const int nfull = L / 3;
-    int lNs = 0;
-    for (int s = 0; s < nst; ++s) {
-        const int lR = (s < nfull) ? 3 : (L - 3 * nfull);
-        if (act && !(s == 0 && in_regs)) load8(v, sm, ad, j, n8);
-        if (act) stage_exec<S>(v, lR, lNs, j, n8, tw, ltab);
-        if (s == nst - 1 && out_regs) break;
-        __syncthreads();
-        if (act) stage_store(v, sm, ad, lR, lNs, j, n8);
-        __syncthreads();
-        lNs += lR;
-    }
-}
-
-// NJ transform instances (or NJ butterfly groups of one instance) per thread, all advanced
-// stage by stage between the same barriers. Slot u uses addressing ad[u], thread index j[u]
-// and is idle when act[u] is false. Results end in smem in natural order.
-template <int S, int NJ, typename V, typename Addr>
-__device__ __forceinline__ void fft_run_multi(V *sm, const Addr (&ad)[NJ], int L, const int (&j)[NJ],
-                                              const bool (&act)[NJ], const V *__restrict__ tw,
-                                              int ltab) {
-    const int n8 = 1 << (L - 3);
-    const int nst = (L + 2) / 3;
-    const int nfull = L / 3;
-    int lNs = 0;
-    V v[NJ][8];
-    for (int s = 0; s < nst; ++s) {
-        const int lR = (s < nfull) ? 3 : (L - 3 * nfull);
-#pragma unroll
-        for (int u = 0; u < NJ; ++u) {
-            if (act[u]) {
-                load8(v[u], sm, ad[u], j[u], n8);
-                stage_exec<S>(v[u], lR, lNs, j[u], n8, tw, ltab);
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int u = 0; u < NJ; ++u)
-            if (act[u]) stage_store(v[u], sm, ad[u], lR, lNs, j[u], n8);
-        __syncthreads();
-        lNs += lR;
+                                        bool in_regs, bool out_regs, const StageTw<V> &tw) {
+    switch (L) {
+        case 3: fft_run_t<S, 3>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
+        case 4: fft_run_t<S, 4>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
+        case 5: fft_run_t<S, 5>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
+        case 6: fft_run_t<S, 6>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
+        case 7: fft_run_t<S, 7>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
+        case 8: fft_run_t<S, 8>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
+        case 9: fft_run_t<S, 9>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
+        case 10: fft_run_t<S, 10>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
+        case 11: fft_run_t<S, 11>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
+        default: fft_run_t<S, 12>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
     }
 }
 

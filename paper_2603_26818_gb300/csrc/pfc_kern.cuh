@@ -1,0 +1,79 @@
+// Definitions of the launch functions of pfc_launch.h; included by the per-precision
+// translation units only.
+#pragma once
+
+#include "pfc_launch.h"
+#include "pfc_reduce.cuh"
+
+namespace pfc {
+
+template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename R> void launch_row(const LaunchCfg &c, int mode, const RowArgs<R> &a, int nf) {
+    dim3 grid(c.g.Q / c.g.gpc, nf);
+    if (mode == ROW_CUBE) k_row<R, ROW_CUBE><<<grid, c.nt_row, c.smem_row, c.stream>>>(c.g, a);
+    else if (mode == ROW_FWD) k_row<R, ROW_FWD><<<grid, c.nt_row, c.smem_row, c.stream>>>(c.g, a);
+    else k_row<R, ROW_INV><<<grid, c.nt_row, c.smem_row, c.stream>>>(c.g, a);
+}
+
+template <typename R, int MAXT>
+static void launch_line_t(const LaunchCfg &c, int mode, const LineArgs<R> &a, int nf) {
+    dim3 grid(c.g.ncg, c.g.P, nf);
+    if (mode == LINE_STEP) k_line<R, LINE_STEP, MAXT><<<grid, c.nt_line, c.smem_line, c.stream>>>(c.g, a);
+    else if (mode == LINE_FWD) k_line<R, LINE_FWD, MAXT><<<grid, c.nt_line, c.smem_line, c.stream>>>(c.g, a);
+    else k_line<R, LINE_INV, MAXT><<<grid, c.nt_line, c.smem_line, c.stream>>>(c.g, a);
+}
+
+template <typename R> void launch_line(const LaunchCfg &c, int mode, const LineArgs<R> &a, int nf) {
+    if constexpr (sizeof(R) == 4) {
+        if (c.nt_line > 512) {
+            launch_line_t<R, 1024>(c, mode, a, nf);
+            return;
+        }
+    }
+    launch_line_t<R, 512>(c, mode, a, nf);
+}
+
+template <typename R> cudaError_t set_smem_attrs(const LaunchCfg &c) {
+    cudaError_t e;
+    if ((e = allow_smem(k_row<R, ROW_CUBE>, c.smem_row)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_row<R, ROW_FWD>, c.smem_row)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_row<R, ROW_INV>, c.smem_row)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_line<R, LINE_STEP, 512>, c.smem_line)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_line<R, LINE_FWD, 512>, c.smem_line)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_line<R, LINE_INV, 512>, c.smem_line)) != cudaSuccess) return e;
+    if constexpr (sizeof(R) == 4) {
+        if ((e = allow_smem(k_line<R, LINE_STEP, 1024>, c.smem_line)) != cudaSuccess) return e;
+        if ((e = allow_smem(k_line<R, LINE_FWD, 1024>, c.smem_line)) != cudaSuccess) return e;
+        if ((e = allow_smem(k_line<R, LINE_INV, 1024>, c.smem_line)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename R>
+void launch_reduce_real(cudaStream_t s, int kind, const R *x, const R *y, int64_t n,
+                        double *partials, int *status) {
+    if (kind == RED_SUM) k_reduce_real<R, RED_SUM><<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, y, n, partials, status);
+    else if (kind == RED_POW4) k_reduce_real<R, RED_POW4><<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, y, n, partials, status);
+    else k_reduce_real<R, RED_DOT><<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, y, n, partials, status);
+}
+
+template <typename R>
+void launch_reduce_spec(cudaStream_t s, const Geom &g, OpDev op, double dx, const void *X,
+                        const double *mean, double *partials, int *status) {
+    k_reduce_spec<R><<<RED_BLOCKS, RED_THREADS, 0, s>>>(
+        g, op, dx, reinterpret_cast<const typename VT<R>::V *>(X), mean, partials, status);
+}
+
+#define PFC_INSTANTIATE_LAUNCH(R)                                                          \
+    template void launch_row<R>(const LaunchCfg &, int, const RowArgs<R> &, int);          \
+    template void launch_line<R>(const LaunchCfg &, int, const LineArgs<R> &, int);        \
+    template cudaError_t set_smem_attrs<R>(const LaunchCfg &);                             \
+    template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t,  \
+                                        double *, int *);                                  \
+    template void launch_reduce_spec<R>(cudaStream_t, const Geom &, OpDev, double,         \
+                                        const void *, const double *, double *, int *);
+
+}  // namespace pfc

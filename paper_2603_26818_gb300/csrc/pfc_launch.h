@@ -1,0 +1,49 @@
+// Host-side launch interface of the pass and reduction kernels. The kernels are compiled in
+// two translation units, one per precision (pfc_kern_f32.cu, pfc_kern_f64.cu), which
+// instantiate these functions; the plan logic in pfc_api.cu only calls them.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pfc_pass.cuh"
+
+namespace pfc {
+
+struct LaunchCfg {
+    Geom g;
+    int nt_row, nt_line;
+    size_t smem_row, smem_line;
+    cudaStream_t stream;
+};
+
+constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+constexpr int RED_THREADS = 256;
+enum { RED_SUM = 0, RED_POW4 = 1, RED_DOT = 2 };
+
+template <typename R> void launch_row(const LaunchCfg &c, int mode, const RowArgs<R> &a, int nf);
+template <typename R> void launch_line(const LaunchCfg &c, int mode, const LineArgs<R> &a, int nf);
+template <typename R> cudaError_t set_smem_attrs(const LaunchCfg &c);
+// partials[b] (b < RED_BLOCKS) = block sums of x, x^4 or x y over n values, FP64
+template <typename R>
+void launch_reduce_real(cudaStream_t s, int kind, const R *x, const R *y, int64_t n,
+                        double *partials, int *status);
+// partials = block sums of w_k Lk(k) |psi_hat_k|^2 over a standard half spectrum
+template <typename R>
+void launch_reduce_spec(cudaStream_t s, const Geom &g, OpDev op, double dx, const void *X,
+                        const double *mean, double *partials, int *status);
+// out[0] = scale * sum of nb partials, in a fixed order
+void launch_finish(cudaStream_t s, const double *partials, int nb, double scale, double *out);
+
+#define PFC_DECLARE_LAUNCH(R)                                                                   \
+    extern template void launch_row<R>(const LaunchCfg &, int, const RowArgs<R> &, int);        \
+    extern template void launch_line<R>(const LaunchCfg &, int, const LineArgs<R> &, int);      \
+    extern template cudaError_t set_smem_attrs<R>(const LaunchCfg &);                           \
+    extern template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t, \
+                                               double *, int *);                                \
+    extern template void launch_reduce_spec<R>(cudaStream_t, const Geom &, OpDev, double,       \
+                                               const void *, const double *, double *, int *);
+PFC_DECLARE_LAUNCH(float)
+PFC_DECLARE_LAUNCH(double)
+#undef PFC_DECLARE_LAUNCH
+
+}  // namespace pfc

@@ -33,9 +33,9 @@ struct Geom {
     int xs;                          // complex stride of X'/C' rows (multiple of W)
     int Py, Pz, Qy, Qz, lPy, lPz, lQy, lQz;
     int P, Q, lQ;
-    int ltab;                        // twiddle table has 2^ltab entries
+    int ltab;                        // full twiddle table has 2^ltab entries
     int W, lW, ncg;                  // line pass: columns per tile, column groups
-    int tpsh;                        // tile padding shift
+    int wp;                          // line pass tile row pitch (W, or W + 1 against bank conflicts)
     int rs;                          // row pass smem row stride (elements)
     int gpc;                         // row groups per row-pass CTA
     int64_t nreal;                   // real values per field (N)
@@ -48,19 +48,31 @@ struct OpDev {
     double r, R1, q2;
 };
 
-enum { ROW_CUBE = 0, ROW_FWD = 1, ROW_INV = 2, ROW_ADJ_MIX = 3 };
-enum { LINE_STEP = 0, LINE_FWD = 1, LINE_INV = 2, LINE_STEP2 = 3, LINE_ADJ = 4 };
+enum { ROW_CUBE = 0, ROW_FWD = 1, ROW_INV = 2 };
+enum { LINE_STEP = 0, LINE_FWD = 1, LINE_INV = 2 };
 enum { STATUS_NONFINITE = 1, STATUS_TIMEOUT = 2 };
 
 template <typename R> struct RowArgs {
     const void *in;       // ROW_FWD: real; else X' layout
     void *out;            // ROW_INV: real; else X' layout
-    const void *in2;      // ROW_ADJ_MIX: second X' input (V = B lam) ; real psi_n in in3
-    const void *in3;
     void *proj;           // ROW_CUBE: X' to receive the projected kx = 0 and nx/2 columns
     const double *mean;   // per field, may be null
     R scale;
     const typename VT<R>::V *tw;
+    StageTw<typename VT<R>::V> st;
+};
+
+// Operator and update constants in the path's precision, prepared on the host so that an
+// FP32 kernel executes no FP64 instruction (GB300's FP64 rate is a small fraction of FP32).
+template <typename R> struct OpR {
+    int kind;
+    R r, R1, q2sq;        // q2sq = q2^2
+};
+template <typename R> struct UpdR {
+    R dt;
+    R cx, cy, cz;         // 2 pi / (n dx) per axis
+    R invQ, inv_halfN;    // 1/Q and 2/N
+    OpR<R> op[2];         // per field
 };
 
 template <typename R> struct LineArgs {
@@ -68,20 +80,15 @@ template <typename R> struct LineArgs {
     const void *c;        // C'
     const void *std_in;   // LINE_INV input (standard half spectrum)
     void *std_out;        // LINE_FWD output (standard half spectrum)
-    void *x2;             // second output (adjoint: B lam) or second field
     R scale;              // LINE_INV / LINE_FWD output scale
-    double dt;
-    double dx;
-    OpDev op0, op1;
-    double alpha;         // two-field coupling
-    const typename VT<R>::V *tw;
-    double *partials;     // adjoint: per-CTA dr partial sums
+    UpdR<R> up;
+    StageTw<typename VT<R>::V> st;
 };
 
 // ------------------------------------------------------------------------------------------
-// P-part: small DFTs across the rows of one group, plus the split twiddles
-// W_ny^{y_q k_py} W_nz^{z_q k_pz}. Rows of group gi live at smem rows gi P + (a Py + b).
+// Helpers
 // ------------------------------------------------------------------------------------------
+// Split twiddle W_ny^{y_q k_py} W_nz^{z_q k_pz} of row group grp (forward sign).
 template <typename V>
 __device__ __forceinline__ V split_twiddle(const Geom &g, const V *__restrict__ tw, int grp,
                                            int kpz, int kpy) {
@@ -91,96 +98,152 @@ __device__ __forceinline__ V split_twiddle(const Geom &g, const V *__restrict__ 
     return t;
 }
 
-// Inverse P-part in place: rows (k_pz, k_py) -> (z_p, y_p).
-template <typename R>
-__device__ void ppart_inverse(const Geom &g, typename VT<R>::V *sm, int grp0,
-                              const typename VT<R>::V *__restrict__ tw) {
-    using V = typename VT<R>::V;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int M1 = g.M + 1, P = g.P;
-    // z first (with the twiddle), then y
-    if (g.Pz > 1) {
-        const int cnt = g.gpc * g.Py * M1;
-        for (int e = tid; e < cnt; e += nt) {
-            const int k = e % M1, rest = e / M1;
-            const int kpy = rest % g.Py, gi = rest / g.Py;
-            V t[8];
-            for (int a = 0; a < g.Pz; ++a) {
-                V x = sm[(gi * P + a * g.Py + kpy) * g.rs + row_pad(k)];
-                t[a] = ctw<+1>(x, split_twiddle(g, tw, grp0 + gi, a, kpy));
-            }
-            dft_small<+1>(t, g.Pz);
-            for (int a = 0; a < g.Pz; ++a) sm[(gi * P + a * g.Py + kpy) * g.rs + row_pad(k)] = t[a];
-        }
-        __syncthreads();
+// Real-transform pre-processing (inverse direction) of one row pair (a = X[k], b = X[M-k]):
+// E = (X[k] + conj X[M-k]) / 2, O = (X[k] - conj X[M-k]) / 2 conj(W^k), Z = E + i O; at k = 0 the
+// imaginary parts of X[0] and X[M] are ignored. w = W^k = exp(-2 pi i k / nx).
+template <typename V, typename R>
+__device__ __forceinline__ void c2r_pre_pair(V a, V b, V w, bool k0, V &za, V &zb) {
+    if (k0) {
+        za = V{(R)0.5 * (a.x + b.x), (R)0.5 * (a.x - b.x)};
+        zb = za;
+        return;
     }
-    if (g.Py > 1) {
-        const int cnt = g.gpc * g.Pz * M1;
-        for (int e = tid; e < cnt; e += nt) {
-            const int k = e % M1, rest = e / M1;
-            const int zp = rest % g.Pz, gi = rest / g.Pz;
-            V t[8];
-            for (int b = 0; b < g.Py; ++b) {
-                V x = sm[(gi * P + zp * g.Py + b) * g.rs + row_pad(k)];
-                if (g.Pz == 1) x = ctw<+1>(x, split_twiddle(g, tw, grp0 + gi, 0, b));
-                t[b] = x;
-            }
-            dft_small<+1>(t, g.Py);
-            for (int b = 0; b < g.Py; ++b) sm[(gi * P + zp * g.Py + b) * g.rs + row_pad(k)] = t[b];
-        }
-        __syncthreads();
+    const V e1 = cscale(cadd(a, cconj(b)), (R)0.5);
+    const V o1 = ctw<+1>(cscale(csub(a, cconj(b)), (R)0.5), w);
+    const V e2 = cscale(cadd(b, cconj(a)), (R)0.5);
+    const V o2 = cmul(cscale(csub(b, cconj(a)), (R)-0.5), w);   // conj(W^{M-k}) = -W^k
+    za = V{e1.x - o1.y, e1.y + o1.x};
+    zb = V{e2.x - o2.y, e2.y + o2.x};
+}
+
+// Real-transform post-processing (forward direction): from Z[k], Z[M-k] to X[k], X[M-k],
+// X[k] = (Z[k] + conj Z[M-k])/2 - (i/2) W^k (Z[k] - conj Z[M-k]); at k = 0, X[0] and X[M].
+template <typename V, typename R>
+__device__ __forceinline__ void r2c_post_pair(V za, V zb, V w, bool k0, V &xa, V &xb) {
+    if (k0) {
+        xa = V{za.x + za.y, (R)0};
+        xb = V{za.x - za.y, (R)0};
+        return;
+    }
+    const V a1 = cscale(cadd(za, cconj(zb)), (R)0.5);
+    const V d1 = cmul(cscale(csub(za, cconj(zb)), (R)0.5), w);
+    const V a2 = cscale(cadd(zb, cconj(za)), (R)0.5);
+    const V d2 = cmul(cscale(csub(zb, cconj(za)), (R)-0.5), cconj(w));   // W^{M-k} = -conj(W^k)
+    xa = V{a1.x + d1.y, a1.y - d1.x};
+    xb = V{a2.x + d2.y, a2.y - d2.x};
+}
+
+// Decompose a flat index over (gi, s, kk), kk in [0, M/2), s in [0, S) (S a power of two). The
+// item kk = 0 covers the column pair (0, M) and also the self-paired column M/2, so that
+// gpc*S*(M/2) items cover all M + 1 columns with no second round.
+__device__ __forceinline__ void pair_index(const Geom &g, int e, int lS, int &kk, int &s, int &gi) {
+    const int lh = g.lM - 1;
+    kk = e & ((1 << lh) - 1);
+    const int rest = e >> lh;
+    s = rest & ((1 << lS) - 1);
+    gi = rest >> lS;
+}
+
+// ------------------------------------------------------------------------------------------
+// Row pass phases
+// ------------------------------------------------------------------------------------------
+// Phase A (Pz > 1): z-part inverse from X' in global memory into smem rows, with the full split
+// twiddle; rows (k_pz, k_py) become (z_p, k_py).
+template <typename R>
+__device__ void row_phase_a(const Geom &g, typename VT<R>::V *sm, const typename VT<R>::V *X,
+                            int grp0, const typename VT<R>::V *stw) {
+    using V = typename VT<R>::V;
+    const int P = g.P, M = g.M, lM = g.lM;
+    const int main = (g.gpc * g.Py) << lM;
+    const int cnt = main + g.gpc * g.Py;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        int k, rest;
+        if (e < main) { k = e & (M - 1); rest = e >> lM; }
+        else { k = M; rest = e - main; }
+        const int kpy = rest % g.Py, gi = rest / g.Py, grp = grp0 + gi;
+        V t[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+            if (a < g.Pz)
+                t[a] = ctw<+1>(X[(size_t)((a * g.Py + kpy) * g.Q + grp) * g.xs + k],
+                               stw[gi * P + a * g.Py + kpy]);
+        dft_small<+1>(t, g.Pz);
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+            if (a < g.Pz) sm[(gi * P + a * g.Py + kpy) * g.rs + row_pad(k)] = t[a];
     }
 }
 
-// Forward P-part: rows (z_p, y_p) -> (k_pz, k_py), then scale and write X' rows
-// (k_p Q + grp) of the output.
-template <typename R>
-__device__ void ppart_forward_store(const Geom &g, typename VT<R>::V *sm, int grp0,
-                                    const typename VT<R>::V *__restrict__ tw,
-                                    typename VT<R>::V *__restrict__ out, R scale) {
+// Phase B: y-part inverse of the column pair (kk, M - kk) of the Py rows of (gi, z_p), then the
+// real-transform pre-processing; rows end physical (z_p, y_p). FROM_GLOBAL (Pz == 1) reads X'
+// and applies the y twiddle; otherwise reads smem left by phase A. When edge is set, the real
+// parts of the kx = 0 and kx = M columns are saved there for the projection.
+template <typename R, bool FROM_GLOBAL>
+__device__ __forceinline__ void row_pair_b(const Geom &g, typename VT<R>::V *sm, R *edge,
+                                           const typename VT<R>::V *X, int gi, int grp, int zp,
+                                           int ca, int cb, bool k0,
+                                           const typename VT<R>::V *__restrict__ tw,
+                                           const typename VT<R>::V *stw) {
     using V = typename VT<R>::V;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int M1 = g.M + 1, P = g.P;
-    if (P == 1) {
-        const int cnt = g.gpc * M1;
-        for (int e = tid; e < cnt; e += nt) {
-            const int k = e % M1, gi = e / M1;
-            out[(size_t)(grp0 + gi) * g.xs + k] = cscale(sm[gi * g.rs + row_pad(k)], scale);
-        }
-        return;
-    }
-    // y first
-    {
-        const int cnt = g.gpc * g.Pz * M1;
-        for (int e = tid; e < cnt; e += nt) {
-            const int k = e % M1, rest = e / M1;
-            const int zp = rest % g.Pz, gi = rest / g.Pz;
-            V t[8];
-            for (int b = 0; b < g.Py; ++b) t[b] = sm[(gi * P + zp * g.Py + b) * g.rs + row_pad(k)];
-            dft_small<-1>(t, g.Py);
-            if (g.Pz == 1) {
-                for (int b = 0; b < g.Py; ++b) {
-                    V x = cmul(t[b], split_twiddle(g, tw, grp0 + gi, 0, b));
-                    out[(size_t)(b * g.Q + grp0 + gi) * g.xs + k] = cscale(x, scale);
-                }
+    const int P = g.P;
+    V a[8], b[8];
+#pragma unroll
+    for (int yy = 0; yy < 8; ++yy) {
+        if (yy < g.Py) {
+            if (FROM_GLOBAL) {
+                const V *src = X + (size_t)(yy * g.Q + grp) * g.xs;
+                const V w = stw[gi * P + yy];
+                a[yy] = ctw<+1>(src[ca], w);
+                b[yy] = ctw<+1>(src[cb], w);
             } else {
-                for (int b = 0; b < g.Py; ++b) sm[(gi * P + zp * g.Py + b) * g.rs + row_pad(k)] = t[b];
+                const int row = gi * P + zp * g.Py + yy;
+                a[yy] = sm[row * g.rs + row_pad(ca)];
+                b[yy] = sm[row * g.rs + row_pad(cb)];
             }
         }
     }
-    if (g.Pz > 1) {
-        __syncthreads();
-        const int cnt = g.gpc * g.Py * M1;
-        for (int e = tid; e < cnt; e += nt) {
-            const int k = e % M1, rest = e / M1;
-            const int kpy = rest % g.Py, gi = rest / g.Py;
-            V t[8];
-            for (int a = 0; a < g.Pz; ++a) t[a] = sm[(gi * P + a * g.Py + kpy) * g.rs + row_pad(k)];
-            dft_small<-1>(t, g.Pz);
-            for (int a = 0; a < g.Pz; ++a) {
-                V x = cmul(t[a], split_twiddle(g, tw, grp0 + gi, a, kpy));
-                out[(size_t)((a * g.Py + kpy) * g.Q + grp0 + gi) * g.xs + k] = cscale(x, scale);
+    dft_small<+1>(a, g.Py);
+    dft_small<+1>(b, g.Py);
+    const V w = __ldg(&tw[ca << (g.ltab - g.lnx)]);
+#pragma unroll
+    for (int yy = 0; yy < 8; ++yy) {
+        if (yy < g.Py) {
+            const int row = gi * P + zp * g.Py + yy;
+            if (edge && k0) {
+                edge[(gi * 2) * P + zp * g.Py + yy] = a[yy].x;
+                edge[(gi * 2 + 1) * P + zp * g.Py + yy] = b[yy].x;
             }
+            V za, zb;
+            c2r_pre_pair<V, R>(a[yy], b[yy], w, k0, za, zb);
+            sm[row * g.rs + row_pad(ca)] = za;
+            if (!k0 && cb != ca) sm[row * g.rs + row_pad(cb)] = zb;
+        }
+    }
+}
+
+// Phase B: y-part inverse of the column pair (kk, M - kk) of the Py rows of (gi, z_p), then the
+// real-transform pre-processing; rows end physical (z_p, y_p). FROM_GLOBAL (Pz == 1) reads X'
+// and applies the y twiddle; otherwise reads smem left by phase A. When edge is set, the real
+// parts of the kx = 0 and kx = M columns are saved there for the projection.
+template <typename R, bool FROM_GLOBAL>
+__device__ void row_phase_b(const Geom &g, typename VT<R>::V *sm, R *edge,
+                            const typename VT<R>::V *X, int grp0,
+                            const typename VT<R>::V *__restrict__ tw,
+                            const typename VT<R>::V *stw) {
+    const int M = g.M, hM = M >> 1;
+    const int cnt = (g.gpc * g.Pz) << (g.lM - 1);
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        int kk, zp, gi;
+        pair_index(g, e, g.lPz, kk, zp, gi);
+        const int grp = grp0 + gi;
+        // kk = 0 handles the pair (0, M) and then the self-paired column M/2 (one body, so the
+        // code is not duplicated)
+        const int npass = kk == 0 ? 2 : 1;
+#pragma unroll 1
+        for (int pp = 0; pp < npass; ++pp) {
+            const bool k0 = kk == 0 && pp == 0;
+            const int ca = pp ? hM : kk, cb = pp ? hM : (kk == 0 ? M : M - kk);
+            row_pair_b<R, FROM_GLOBAL>(g, sm, k0 ? edge : nullptr, X, gi, grp, zp, ca, cb, k0, tw, stw);
         }
     }
 }
@@ -189,116 +252,143 @@ __device__ void ppart_forward_store(const Geom &g, typename VT<R>::V *sm, int gr
 // redundant: in row space (after the inverse P-part) they must be real, and the row inverse
 // ignores their imaginary parts. Rounding leaves a small imaginary part there which psi^3
 // never sees and which the update multiplies by 1/D(k) > 1 at the linearly unstable
-// wavenumbers, so without projection it grows until it overflows. After the inverse P-part
-// this writes the real parts of both columns back to X' through the forward P-part
-// (X' = DFT_P(row values) / P), two values per row.
+// wavenumbers, so without projection it grows until it overflows. This writes the saved real
+// parts of both columns back to X' through the forward P-part (X' = DFT_P(row values) / P).
 template <typename R>
-__device__ void project_edge_columns(const Geom &g, const typename VT<R>::V *sm, int grp0,
-                                     const typename VT<R>::V *__restrict__ tw,
+__device__ void project_edge_columns(const Geom &g, const R *edge, int grp0,
+                                     const typename VT<R>::V *stw,
                                      typename VT<R>::V *__restrict__ xout) {
     using V = typename VT<R>::V;
     const int P = g.P;
     const R invP = (R)1 / (R)P;
     for (int t = threadIdx.x; t < 2 * g.gpc; t += blockDim.x) {
-        const int gi = t >> 1, k = (t & 1) ? g.M : 0, grp = grp0 + gi;
+        const int gi = t >> 1, c = t & 1, k = c ? g.M : 0, grp = grp0 + gi;
         V vals[64];
-        for (int pr = 0; pr < P; ++pr) vals[pr] = V{sm[(gi * P + pr) * g.rs + row_pad(k)].x, (R)0};
+        for (int pr = 0; pr < P; ++pr) vals[pr] = V{edge[(gi * 2 + c) * P + pr], (R)0};
         V tt[8];
         if (g.Py > 1) {
             for (int zp = 0; zp < g.Pz; ++zp) {
-                for (int b = 0; b < g.Py; ++b) tt[b] = vals[zp * g.Py + b];
+#pragma unroll
+                for (int b = 0; b < 8; ++b) if (b < g.Py) tt[b] = vals[zp * g.Py + b];
                 dft_small<-1>(tt, g.Py);
-                for (int b = 0; b < g.Py; ++b) vals[zp * g.Py + b] = tt[b];
+#pragma unroll
+                for (int b = 0; b < 8; ++b) if (b < g.Py) vals[zp * g.Py + b] = tt[b];
             }
         }
         if (g.Pz > 1) {
             for (int kpy = 0; kpy < g.Py; ++kpy) {
-                for (int a = 0; a < g.Pz; ++a) tt[a] = vals[a * g.Py + kpy];
+#pragma unroll
+                for (int a = 0; a < 8; ++a) if (a < g.Pz) tt[a] = vals[a * g.Py + kpy];
                 dft_small<-1>(tt, g.Pz);
-                for (int a = 0; a < g.Pz; ++a) vals[a * g.Py + kpy] = tt[a];
+#pragma unroll
+                for (int a = 0; a < 8; ++a) if (a < g.Pz) vals[a * g.Py + kpy] = tt[a];
             }
         }
         for (int kpz = 0; kpz < g.Pz; ++kpz)
             for (int kpy = 0; kpy < g.Py; ++kpy) {
                 V x = vals[kpz * g.Py + kpy];
-                if (P > 1) x = cmul(x, split_twiddle(g, tw, grp, kpz, kpy));
+                if (P > 1) x = cmul(x, stw[gi * P + kpz * g.Py + kpy]);
                 xout[(size_t)((kpz * g.Py + kpy) * g.Q + grp) * g.xs + k] = cscale(x, invP);
             }
     }
 }
 
-// ------------------------------------------------------------------------------------------
-// Real transform along x via a half-length complex transform (M = nx/2):
-//   z[j] = x[2j] + i x[2j+1],  Z = DFT_M z,
-//   X[k] = (Z[k] + conj Z[M-k])/2 - (i/2) W^k (Z[k] - conj Z[M-k]),  W = exp(-2 pi i / nx).
-// The inverse builds E[k] = (X[k] + conj X[M-k])/2, O[k] = (X[k] - conj X[M-k])/2 conj(W^k),
-// Z = E + i O (imaginary parts of X[0], X[M] ignored); IDFT_M Z = M (x_even + i x_odd).
-// ------------------------------------------------------------------------------------------
 template <typename R>
-__device__ void c2r_pre_rows(const Geom &g, typename VT<R>::V *sm, int rows,
-                             const typename VT<R>::V *__restrict__ tw) {
+__device__ __forceinline__ void row_pair_d(const Geom &g, typename VT<R>::V *sm,
+                                           typename VT<R>::V *out, int gi, int grp, int zp,
+                                           int ca, int cb, bool k0,
+                                           const typename VT<R>::V *__restrict__ tw,
+                                           const typename VT<R>::V *stw, R scale) {
     using V = typename VT<R>::V;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int M = g.M, half = M / 2 + 1, sh = g.ltab - g.lnx;
-    const int cnt = rows * half;
-    for (int e = tid; e < cnt; e += nt) {
-        const int k = e % half, r = e / half;
-        V *row = sm + r * g.rs;
-        if (k == 0) {
-            const V x0 = row[row_pad(0)], xm = row[row_pad(M)];
-            row[row_pad(0)] = V{(R)0.5 * (x0.x + xm.x), (R)0.5 * (x0.x - xm.x)};
-        } else {
-            const V xk = row[row_pad(k)], xm = row[row_pad(M - k)];
-            const V w = __ldg(&tw[k << sh]);              // W^k
-            // index k
-            V e1 = cscale(cadd(xk, cconj(xm)), (R)0.5);
-            V o1 = ctw<+1>(cscale(csub(xk, cconj(xm)), (R)0.5), w);
-            // index M - k: conj(W^{M-k}) = -W^k
-            V e2 = cscale(cadd(xm, cconj(xk)), (R)0.5);
-            V o2 = cmul(cscale(csub(xm, cconj(xk)), (R)-0.5), w);
-            row[row_pad(k)] = V{e1.x - o1.y, e1.y + o1.x};
-            row[row_pad(M - k)] = V{e2.x - o2.y, e2.y + o2.x};
+    const int P = g.P;
+    const V w = __ldg(&tw[ca << (g.ltab - g.lnx)]);
+    V a[8], b[8];
+#pragma unroll
+    for (int yy = 0; yy < 8; ++yy) {
+        if (yy < g.Py) {
+            const int row = gi * P + zp * g.Py + yy;
+            const V za = sm[row * g.rs + row_pad(ca)];
+            const V zb = (k0 || cb == ca) ? za : sm[row * g.rs + row_pad(cb)];
+            r2c_post_pair<V, R>(za, zb, w, k0, a[yy], b[yy]);
+        }
+    }
+    dft_small<-1>(a, g.Py);
+    dft_small<-1>(b, g.Py);
+#pragma unroll
+    for (int yy = 0; yy < 8; ++yy) {
+        if (yy < g.Py) {
+            if (g.Pz == 1) {
+                const V t = stw[gi * P + yy];
+                V *dst = out + (size_t)(yy * g.Q + grp) * g.xs;
+                dst[ca] = cscale(cmul(a[yy], t), scale);
+                if (cb != ca) dst[cb] = cscale(cmul(b[yy], t), scale);
+            } else {
+                const int row = gi * P + zp * g.Py + yy;
+                sm[row * g.rs + row_pad(ca)] = a[yy];
+                if (cb != ca) sm[row * g.rs + row_pad(cb)] = b[yy];
+            }
         }
     }
 }
 
+// Phase D: real-transform post-processing of the pair (kk, M - kk) of the Py rows of (gi, z_p),
+// then the y-part forward. With Pz == 1 it applies the y twiddle and the scale and writes X'
+// rows (k_py Q + grp) of out; otherwise it writes smem rows (z_p, k_py) for phase E.
 template <typename R>
-__device__ void r2c_post_rows(const Geom &g, typename VT<R>::V *sm, int rows,
-                              const typename VT<R>::V *__restrict__ tw) {
-    using V = typename VT<R>::V;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int M = g.M, half = M / 2 + 1, sh = g.ltab - g.lnx;
-    const int cnt = rows * half;
-    for (int e = tid; e < cnt; e += nt) {
-        const int k = e % half, r = e / half;
-        V *row = sm + r * g.rs;
-        if (k == 0) {
-            const V z0 = row[row_pad(0)];
-            row[row_pad(0)] = V{z0.x + z0.y, (R)0};
-            row[row_pad(M)] = V{z0.x - z0.y, (R)0};
-        } else {
-            const V zk = row[row_pad(k)], zm = row[row_pad(M - k)];
-            const V w = __ldg(&tw[k << sh]);              // W^k ; W^{M-k} = -conj(W^k)
-            V a1 = cscale(cadd(zk, cconj(zm)), (R)0.5);
-            V d1 = cmul(cscale(csub(zk, cconj(zm)), (R)0.5), w);
-            V a2 = cscale(cadd(zm, cconj(zk)), (R)0.5);
-            V d2 = cmul(cscale(csub(zm, cconj(zk)), (R)-0.5), cconj(w));
-            // X = a - i d
-            row[row_pad(k)] = V{a1.x + d1.y, a1.y - d1.x};
-            row[row_pad(M - k)] = V{a2.x + d2.y, a2.y - d2.x};
+__device__ void row_phase_d(const Geom &g, typename VT<R>::V *sm, typename VT<R>::V *out,
+                            int grp0, const typename VT<R>::V *__restrict__ tw,
+                            const typename VT<R>::V *stw, R scale) {
+    const int M = g.M, hM = M >> 1;
+    const int cnt = (g.gpc * g.Pz) << (g.lM - 1);
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        int kk, zp, gi;
+        pair_index(g, e, g.lPz, kk, zp, gi);
+        const int grp = grp0 + gi;
+        const int npass = kk == 0 ? 2 : 1;
+#pragma unroll 1
+        for (int pp = 0; pp < npass; ++pp) {
+            const bool k0 = kk == 0 && pp == 0;
+            const int ca = pp ? hM : kk, cb = pp ? hM : (kk == 0 ? M : M - kk);
+            row_pair_d<R>(g, sm, out, gi, grp, zp, ca, cb, k0, tw, stw, scale);
         }
+    }
+}
+
+// Phase E (Pz > 1): z-part forward of each column, twiddle, scale, write X' rows.
+template <typename R>
+__device__ void row_phase_e(const Geom &g, const typename VT<R>::V *sm, typename VT<R>::V *out,
+                            int grp0, const typename VT<R>::V *stw, R scale) {
+    using V = typename VT<R>::V;
+    const int P = g.P, M = g.M, lM = g.lM;
+    const int main = (g.gpc * g.Py) << lM;
+    const int cnt = main + g.gpc * g.Py;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        int k, rest;
+        if (e < main) { k = e & (M - 1); rest = e >> lM; }
+        else { k = M; rest = e - main; }
+        const int kpy = rest % g.Py, gi = rest / g.Py, grp = grp0 + gi;
+        V t[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+            if (a < g.Pz) t[a] = sm[(gi * P + a * g.Py + kpy) * g.rs + row_pad(k)];
+        dft_small<-1>(t, g.Pz);
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+            if (a < g.Pz)
+                out[(size_t)((a * g.Py + kpy) * g.Q + grp) * g.xs + k] =
+                    cscale(cmul(t[a], stw[gi * P + a * g.Py + kpy]), scale);
     }
 }
 
 // ------------------------------------------------------------------------------------------
 // Row pass.
-//   ROW_CUBE  X' -> C' = F_p(psi^3), psi = (row inverse of X') + mean.
+//   ROW_CUBE  X' -> C' = F_p(psi^3), psi = (row inverse of X') + mean; X' edge columns projected
 //   ROW_FWD   real psi -> X' = scale F_p(psi - mean)
-//   ROW_INV   X' -> real psi = (row inverse of X') + mean
-// grid = (row groups / gpc, nfields); block = threads (multiple of M/8).
+//   ROW_INV   X' -> real psi = scale ((row inverse of X') + mean)
+// grid = (row groups / gpc, nfields); block = threads (a multiple of M/8).
 // ------------------------------------------------------------------------------------------
 template <typename R, int MODE>
-__global__ void __launch_bounds__(512) k_row(const Geom g, const RowArgs<R> a) {
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_row(const Geom g, const RowArgs<R> a) {
     using V = typename VT<R>::V;
     extern __shared__ __align__(16) unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
@@ -307,8 +397,14 @@ __global__ void __launch_bounds__(512) k_row(const Geom g, const RowArgs<R> a) {
     const int P = g.P, rows = g.gpc * P, M = g.M, lM = g.lM;
     const int grp0 = blockIdx.x * g.gpc;
     const R mean = a.mean ? (R)a.mean[field] : (R)0;
+    // smem: rows | split twiddles of this block's groups (gpc P) | saved edge values (2 gpc P)
+    V *stw = sm + rows * g.rs;
+    R *edge = reinterpret_cast<R *>(stw + rows);
+    for (int t = tid; t < rows; t += nt) {
+        const int gi = t / P, kp = t % P;
+        stw[t] = split_twiddle(g, a.tw, grp0 + gi, kp / g.Py, kp % g.Py);
+    }
 
-    // ---- load ----
     if (MODE == ROW_FWD) {
         const V *in = reinterpret_cast<const V *>(a.in) + (size_t)field * (g.nreal / 2);
         const int cnt = rows << lM;
@@ -325,30 +421,18 @@ __global__ void __launch_bounds__(512) k_row(const Geom g, const RowArgs<R> a) {
             sm[r * g.rs + row_pad(i)] = v;
         }
     } else {
-        const V *in = reinterpret_cast<const V *>(a.in) + (size_t)field * g.nhalf;
-        const int cnt = rows << lM;
-        for (int e = tid; e < cnt; e += nt) {
-            const int i = e & (M - 1), r = e >> lM;
-            const int gi = r / P, kp = r % P;
-            sm[r * g.rs + row_pad(i)] = in[(size_t)(kp * g.Q + grp0 + gi) * g.xs + i];
-        }
-        for (int r = tid; r < rows; r += nt) {
-            const int gi = r / P, kp = r % P;
-            sm[r * g.rs + row_pad(M)] = in[(size_t)(kp * g.Q + grp0 + gi) * g.xs + M];
+        const V *X = reinterpret_cast<const V *>(a.in) + (size_t)field * g.nhalf;
+        R *ed = MODE == ROW_CUBE ? edge : nullptr;
+        __syncthreads();
+        if (g.Pz > 1) {
+            row_phase_a<R>(g, sm, X, grp0, stw);
+            __syncthreads();
+            row_phase_b<R, false>(g, sm, ed, X, grp0, a.tw, stw);
+        } else {
+            row_phase_b<R, true>(g, sm, ed, X, grp0, a.tw, stw);
         }
     }
     __syncthreads();
-
-    if (MODE != ROW_FWD) {
-        ppart_inverse<R>(g, sm, grp0, a.tw);
-        if (MODE == ROW_CUBE) {
-            V *xw = reinterpret_cast<V *>(a.proj) + (size_t)field * g.nhalf;
-            project_edge_columns<R>(g, sm, grp0, a.tw, xw);
-            __syncthreads();
-        }
-        c2r_pre_rows<R>(g, sm, rows, a.tw);
-        __syncthreads();
-    }
 
     // ---- per-row transforms ----
     const int Tr = M >> 3;
@@ -359,17 +443,17 @@ __global__ void __launch_bounds__(512) k_row(const Geom g, const RowArgs<R> a) {
         const RowAddr ad{r * g.rs};
         V v[8];
         if (MODE == ROW_CUBE) {
-            fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.tw, g.ltab);
+            fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st);
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
                 const R p0 = v[m].x + mean, p1 = v[m].y + mean;
                 v[m] = V{p0 * p0 * p0, p1 * p1 * p1};
             }
-            fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.tw, g.ltab);
+            fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.st);
         } else if (MODE == ROW_FWD) {
-            fft_run<-1>(v, sm, ad, lM, j, act, false, false, a.tw, g.ltab);
+            fft_run<-1>(v, sm, ad, lM, j, act, false, false, a.st);
         } else {
-            fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.tw, g.ltab);
+            fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st);
             if (act) {
                 const int gi = r / P, pr = r % P;
                 const int grp = grp0 + gi;
@@ -386,170 +470,160 @@ __global__ void __launch_bounds__(512) k_row(const Geom g, const RowArgs<R> a) {
     }
 
     if (MODE != ROW_INV) {
-        r2c_post_rows<R>(g, sm, rows, a.tw);
-        __syncthreads();
         V *out = reinterpret_cast<V *>(a.out) + (size_t)field * g.nhalf;
-        ppart_forward_store<R>(g, sm, grp0, a.tw, out, a.scale);
-    }
-}
-
-// ------------------------------------------------------------------------------------------
-// Line pass: tiles of Q = Qz Qy complex values x W columns, interleaved (w fastest).
-// ------------------------------------------------------------------------------------------
-__device__ __forceinline__ int tile_pad(int e, int sh) { return e + (e >> sh); }
-
-// y-transforms (length Qy) of every (z_q, w) column, then z-transforms (length Qz).
-// Thread t (of tot = Q W / 8) maps to (w fastest, then the butterfly index j, then the other
-// column index); when tot exceeds the block, each thread takes NJ = tot / blockDim slots.
-template <int S, int NJ, typename V>
-__device__ void tile_fft_nj(const Geom &g, V *tile, const V *__restrict__ tw, bool y_first) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int tot = (g.Q * g.W) >> 3;
-    for (int pass = 0; pass < 2; ++pass) {
-        const bool doy = (pass == 0) == y_first;
-        if (doy ? g.Qy == 1 : g.Qz == 1) continue;
-        TileAddr ad[NJ];
-        int j[NJ];
-        bool act[NJ];
-#pragma unroll
-        for (int u = 0; u < NJ; ++u) {
-            const int t = u * nt + tid;
-            act[u] = t < tot;
-            const int w = t & (g.W - 1);
-            if (doy) {
-                const int ly8 = g.lQy - 3;
-                j[u] = (t >> g.lW) & ((1 << ly8) - 1);
-                const int zq = t >> (g.lW + ly8);
-                ad[u] = TileAddr{zq * g.Qy * g.W + w, g.W, g.tpsh};
-            } else {
-                const int yq = (t >> g.lW) & (g.Qy - 1);
-                j[u] = t >> (g.lW + g.lQy);
-                ad[u] = TileAddr{yq * g.W + w, g.Qy * g.W, g.tpsh};
-            }
+        row_phase_d<R>(g, sm, out, grp0, a.tw, stw, a.scale);
+        if (g.Pz > 1) {
+            __syncthreads();
+            row_phase_e<R>(g, sm, out, grp0, stw, a.scale);
         }
-        fft_run_multi<S, NJ>(tile, ad, doy ? g.lQy : g.lQz, j, act, tw, g.ltab);
+    }
+    // the edge values were saved in phase B in their own smem area; nothing waits on this
+    if (MODE == ROW_CUBE) {
+        V *xw = reinterpret_cast<V *>(a.proj) + (size_t)field * g.nhalf;
+        project_edge_columns<R>(g, edge, grp0, stw, xw);
     }
 }
 
-template <int S, typename V>
-__device__ void tile_fft(const Geom &g, V *tile, const V *__restrict__ tw, bool y_first) {
-    const int tot = (g.Q * g.W) >> 3;
-    const int nt = blockDim.x;
-    if (tot <= nt) tile_fft_nj<S, 1>(g, tile, tw, y_first);
-    else if (tot <= 2 * nt) tile_fft_nj<S, 2>(g, tile, tw, y_first);
-    else tile_fft_nj<S, 4>(g, tile, tw, y_first);
-}
-
+// ------------------------------------------------------------------------------------------
+// Line pass: one tile of Q = Qz Qy complex values x W columns per block, interleaved (w
+// fastest, row pitch wp), block = Q W / 8 threads. y-transforms use the thread map (w, j, z_q), z-transforms
+// (w, y_q, j). The first forward stage reads global memory into registers, the last forward
+// stage, the update and the first inverse stage stay in registers, and the last inverse stage
+// writes global memory from registers.
+// ------------------------------------------------------------------------------------------
 template <typename R>
-__device__ __forceinline__ R lin_symbol(const OpDev &op, R k2) {
+__device__ __forceinline__ R lin_symbol(const OpR<R> &op, R k2) {
     const R a = (R)1 - k2;
-    if (op.kind == 0) return (R)op.r + a * a;
-    const R b = (R)(op.q2 * op.q2) - k2;
-    return (R)op.r + a * a * ((R)op.R1 + b * b);
+    if (op.kind == 0) return op.r + a * a;
+    const R b = op.q2sq - k2;
+    return op.r + a * a * (op.R1 + b * b);
 }
 
-// k^2 of tile element e (after the forward Q-part) in column group cg and P-frequency kp.
-template <typename R>
-__device__ __forceinline__ R tile_k2(const Geom &g, double dx, int e, int cg, int kp, int *kx_o,
-                                     int *ky_o, int *kz_o) {
-    const int w = e & (g.W - 1), q = e >> g.lW;
-    const int kqy = q & (g.Qy - 1), kqz = q >> g.lQy;
-    const int kpy = kp % g.Py, kpz = kp / g.Py;
-    const int kx = cg * g.W + w;
-    const int ky = kpy + (kqy << g.lPy), kz = kpz + (kqz << g.lPz);
-    const int my = ky <= g.ny / 2 ? ky : ky - g.ny;
-    const int mz = kz <= g.nz / 2 ? kz : kz - g.nz;
-    const R two_pi = (R)6.28318530717958647692528676655900576839;
-    const R cx = two_pi / (R)(g.nx * dx), cy = two_pi / (R)(g.ny * dx), cz = two_pi / (R)(g.nz * dx);
-    const R fx = cx * (R)kx, fy = cy * (R)my, fz = cz * (R)mz;
-    *kx_o = kx;
-    *ky_o = ky;
-    *kz_o = kz;
-    return fx * fx + fy * fy + fz * fz;
+struct LineMap {
+    int w, jy, zq;   // y map
+    int yq, jz;      // z map
+    int ny8, nz8;
+};
+
+__device__ __forceinline__ LineMap line_map(const Geom &g, int t) {
+    LineMap m;
+    m.w = t & (g.W - 1);
+    const int ly8 = g.lQy - 3;
+    m.jy = (t >> g.lW) & ((1 << ly8) - 1);
+    m.zq = t >> (g.lW + ly8);
+    m.yq = (t >> g.lW) & (g.Qy - 1);
+    m.jz = g.Qz > 1 ? (t >> (g.lW + g.lQy)) : 0;
+    m.ny8 = g.Qy >> 3;
+    m.nz8 = g.Qz > 1 ? (g.Qz >> 3) : 0;
+    return m;
 }
 
-template <typename R, int MODE>
-__global__ void __launch_bounds__(512) k_line(const Geom g, const LineArgs<R> a) {
+// X' element of tile element (z_q, y_q) in column w of tile (cg, kp).
+__device__ __forceinline__ size_t xprime_index(const Geom &g, int kp, int cg, int zq, int yq, int w) {
+    return (size_t)(kp * g.Q + zq * g.Qy + yq) * g.xs + cg * g.W + w;
+}
+
+template <typename R, int MODE, int MAXT>
+__global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1) k_line(const Geom g, const LineArgs<R> a) {
     using V = typename VT<R>::V;
     extern __shared__ __align__(16) unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
-    const int tid = threadIdx.x, nt = blockDim.x;
     const int cg = blockIdx.x, kp = blockIdx.y, field = blockIdx.z;
-    const int QW = g.Q * g.W;
-    const int tsz = tile_pad(QW - 1, g.tpsh) + 1;
+    const int tsz = g.Q * g.wp;
     V *T = sm;
-    V *C = sm + tsz;
+    V *Cs = sm + tsz;
+    const LineMap mp = line_map(g, threadIdx.x);
+    const TileAddr ady{mp.zq * g.Qy * g.wp + mp.w, g.wp};
+    const TileAddr adz{mp.yq * g.wp + mp.w, g.Qy * g.wp};
+    const bool two_axes = g.Qz > 1;
     const int kpy = kp % g.Py, kpz = kp / g.Py;
-
-    auto gidx = [&](int e) -> size_t {       // X' element of tile element e
-        const int w = e & (g.W - 1), q = e >> g.lW;
-        return (size_t)(kp * g.Q + q) * g.xs + cg * g.W + w;
-    };
-    auto sidx = [&](int e, int *valid) -> size_t {   // standard half-spectrum element
-        const int w = e & (g.W - 1), q = e >> g.lW;
-        const int kqy = q & (g.Qy - 1), kqz = q >> g.lQy;
-        const int kx = cg * g.W + w;
-        const int ky = kpy + (kqy << g.lPy), kz = kpz + (kqz << g.lPz);
-        *valid = kx <= g.M;
-        return ((size_t)kz * g.ny + ky) * (g.M + 1) + kx;
-    };
+    V vt[8], vc[8];
 
     if (MODE == LINE_STEP) {
+        // C' first, completely into smem (natural order), so that only one register set is live
+        const V *C = reinterpret_cast<const V *>(a.c) + (size_t)field * g.nhalf;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) vc[m] = C[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)];
+        fft_run<-1>(vc, Cs, ady, g.lQy, mp.jy, true, true, false, a.st);
+        if (two_axes) fft_run<-1>(vc, Cs, adz, g.lQz, mp.jz, true, false, false, a.st);
+    }
+    if (MODE == LINE_STEP || MODE == LINE_FWD) {
         const V *X = reinterpret_cast<const V *>(a.x) + (size_t)field * g.nhalf;
-        const V *Cc = reinterpret_cast<const V *>(a.c) + (size_t)field * g.nhalf;
-        for (int e = tid; e < QW; e += nt) {
-            const size_t gi = gidx(e);
-            T[tile_pad(e, g.tpsh)] = X[gi];
-            C[tile_pad(e, g.tpsh)] = Cc[gi];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) vt[m] = X[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)];
+        fft_run<-1>(vt, T, ady, g.lQy, mp.jy, true, true, !two_axes, a.st);
+        if (two_axes) fft_run<-1>(vt, T, adz, g.lQz, mp.jz, true, false, true, a.st);
+    }
+
+
+    if (MODE == LINE_FWD) {
+        // registers hold k_qy = jy + m ny8 (one axis) or k_qz = jz + m nz8 (two axes)
+        V *O = reinterpret_cast<V *>(a.std_out) + (size_t)field * g.nstd;
+        const int kx = cg * g.W + mp.w;
+        if (kx <= g.M) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int kqy = two_axes ? mp.yq : mp.jy + m * mp.ny8;
+                const int kqz = two_axes ? mp.jz + m * mp.nz8 : 0;
+                const int ky = kpy + (kqy << g.lPy), kz = kpz + (kqz << g.lPz);
+                O[((size_t)kz * g.ny + ky) * (g.M + 1) + kx] = cscale(vt[m], a.scale);
+            }
         }
-        __syncthreads();
-        tile_fft<-1>(g, T, a.tw, true);
-        tile_fft<-1>(g, C, a.tw, true);
-        // update: T <- a' T - b' C, a' = 1/(Q D), b' = dt k^2 / ((N/2) D)
-        const OpDev &op = field == 0 ? a.op0 : a.op1;
-        const R invQ = (R)1 / (R)g.Q;
-        const R inv_halfN = (R)(2.0 / ((double)g.nreal));
-        const R dt = (R)a.dt;
-        for (int e = tid; e < QW; e += nt) {
-            int kx, ky, kz;
-            const R k2 = tile_k2<R>(g, a.dx, e, cg, kp, &kx, &ky, &kz);
+        return;
+    }
+
+    if (MODE == LINE_STEP) {
+        const OpR<R> &op = a.up.op[field == 0 ? 0 : 1];
+        const R invQ = a.up.invQ, inv_halfN = a.up.inv_halfN, dt = a.up.dt;
+        const R cy = a.up.cy, cz = a.up.cz;
+        const int kx = cg * g.W + mp.w;
+        const R fx = a.up.cx * (R)kx;
+        // the C transform's outputs at this thread's register positions, read one at a time
+        const int cbase = two_axes ? adz.at(mp.jz) : ady.at(mp.jy);
+        const int cstep = two_axes ? mp.nz8 * adz.stride : mp.ny8 * ady.stride;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const V c = Cs[cbase + m * cstep];
+            const int kqy = two_axes ? mp.yq : mp.jy + m * mp.ny8;
+            const int kqz = two_axes ? mp.jz + m * mp.nz8 : 0;
+            const int ky = kpy + (kqy << g.lPy), kz = kpz + (kqz << g.lPz);
+            const int my = ky <= (g.ny >> 1) ? ky : ky - g.ny;
+            const int mz = kz <= (g.nz >> 1) ? kz : kz - g.nz;
+            const R fy = cy * (R)my, fz = cz * (R)mz;
+            const R k2 = fx * fx + fy * fy + fz * fz;
             const R lk = lin_symbol<R>(op, k2);
             const R inv = (R)1 / ((R)1 + dt * k2 * lk);
             const R ca = inv * invQ, cb = dt * k2 * inv * inv_halfN;
-            const int s = tile_pad(e, g.tpsh);
-            V t = T[s];
-            const V c = C[s];
-            t = V{ca * t.x - cb * c.x, ca * t.y - cb * c.y};
+            V t = V{ca * vt[m].x - cb * c.x, ca * vt[m].y - cb * c.y};
             if (kx == 0 && ky == 0 && kz == 0) t = V{(R)0, (R)0};
-            T[s] = t;
+            vt[m] = t;
         }
-        __syncthreads();
-        tile_fft<+1>(g, T, a.tw, false);
-        V *Xo = reinterpret_cast<V *>(a.x) + (size_t)field * g.nhalf;
-        for (int e = tid; e < QW; e += nt) Xo[gidx(e)] = T[tile_pad(e, g.tpsh)];
-    } else if (MODE == LINE_FWD) {
-        const V *X = reinterpret_cast<const V *>(a.x) + (size_t)field * g.nhalf;
-        for (int e = tid; e < QW; e += nt) T[tile_pad(e, g.tpsh)] = X[gidx(e)];
-        __syncthreads();
-        tile_fft<-1>(g, T, a.tw, true);
-        V *O = reinterpret_cast<V *>(a.std_out) + (size_t)field * g.nstd;
-        for (int e = tid; e < QW; e += nt) {
-            int valid;
-            const size_t si = sidx(e, &valid);
-            if (valid) O[si] = cscale(T[tile_pad(e, g.tpsh)], a.scale);
-        }
-    } else if (MODE == LINE_INV) {
-        const V *I = reinterpret_cast<const V *>(a.std_in) + (size_t)field * g.nstd;
-        for (int e = tid; e < QW; e += nt) {
-            int valid;
-            const size_t si = sidx(e, &valid);
-            T[tile_pad(e, g.tpsh)] = valid ? I[si] : V{(R)0, (R)0};
-        }
-        __syncthreads();
-        tile_fft<+1>(g, T, a.tw, false);
-        V *Xo = reinterpret_cast<V *>(a.x) + (size_t)field * g.nhalf;
-        for (int e = tid; e < QW; e += nt) Xo[gidx(e)] = cscale(T[tile_pad(e, g.tpsh)], a.scale);
     }
+
+    if (MODE == LINE_INV) {
+        const V *I = reinterpret_cast<const V *>(a.std_in) + (size_t)field * g.nstd;
+        const int kx = cg * g.W + mp.w;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int kqy = two_axes ? mp.yq : mp.jy + m * mp.ny8;
+            const int kqz = two_axes ? mp.jz + m * mp.nz8 : 0;
+            const int ky = kpy + (kqy << g.lPy), kz = kpz + (kqz << g.lPz);
+            vt[m] = kx <= g.M ? I[((size_t)kz * g.ny + ky) * (g.M + 1) + kx] : V{(R)0, (R)0};
+        }
+    }
+
+    // inverse: the last forward axis first, from registers
+    if (two_axes) {
+        fft_run<+1>(vt, T, adz, g.lQz, mp.jz, true, true, false, a.st);
+        fft_run<+1>(vt, T, ady, g.lQy, mp.jy, true, false, true, a.st);
+    } else {
+        fft_run<+1>(vt, T, ady, g.lQy, mp.jy, true, true, true, a.st);
+    }
+    V *Xo = reinterpret_cast<V *>(a.x) + (size_t)field * g.nhalf;
+    const R sc = MODE == LINE_INV ? a.scale : (R)1;
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+        Xo[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)] = cscale(vt[m], sc);
 }
 
 }  // namespace pfc

@@ -4,12 +4,10 @@
 // on scheduling, so two runs are bitwise equal. Any NaN or Inf met sets STATUS_NONFINITE.
 #pragma once
 
-#include "pfc_pass.cuh"
+#include "pfc_launch.h"
 
 namespace pfc {
 
-constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
-constexpr int RED_THREADS = 256;
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
     const int tid = threadIdx.x;
@@ -22,7 +20,6 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return sh[0];
 }
 
-enum { RED_SUM = 0, RED_POW4 = 1, RED_DOT = 2 };
 
 // partial[b] = sum over this block's slice of f(x[i], y[i]); f = x, x^4 or x y.
 template <typename R, int KIND>
@@ -46,7 +43,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_real(const R *__restrict
 }
 
 // out[0] = scale * sum_{b < nb} partials[b], summed by one block in a fixed order.
-__global__ void __launch_bounds__(RED_THREADS) k_finish(const double *__restrict__ partials, int nb,
+static __global__ void __launch_bounds__(RED_THREADS) k_finish(const double *__restrict__ partials, int nb,
                                                         double scale, double *out) {
     __shared__ double sh[RED_THREADS];
     double acc = 0.0;
