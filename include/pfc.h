@@ -136,6 +136,27 @@ pfc_status pfc_plan_info(pfc_plan *plan, int32_t *tiles, int64_t *scratch_bytes)
 pfc_status pfc_profile_steps(pfc_plan *plan, void *state, int64_t nsteps, double *ms_out,
                              int64_t *launches);
 
+/* The step for callers that must not allocate device memory. The paper has no counterpart:
+ * it exists for callers that cannot call cudaMalloc, such as a process whose device memory is
+ * already held by another allocator (a framework's caching allocator, a fixed budget) or a
+ * latency-sensitive loop that cannot afford the device-wide synchronisation of cudaMalloc and
+ * cudaFree. Same arithmetic as pfc_step on a single field; no plan is needed and nothing is
+ * allocated: the work arrays live in one file-scope device array of 24 MiB that every GPU
+ * loading libpfc.so holds until the process exits.
+ *   ndim, dims, dx, dt, op, precision  as for pfc_plan_create (one field).
+ *   state   device real array, advanced in place by nsteps steps (stream ordered on stream).
+ *   stream  cudaStream_t (NULL = legacy default stream).
+ * Limit: the two padded half spectra of the grid must fit the array beside its 0.3 MiB of
+ * tables, e.g. 2D 1024x1024 in FP64 or 1024x2048 in FP32-mixed, 3D 128^3 in FP32-mixed or
+ * 64^3 in FP64 (2048^2 FP32-mixed and 128^3 FP64 do not fit); a larger grid returns
+ * PFC_ERR_UNSUPPORTED before any device work (use pfc_plan_create).
+ * The first call on a device takes the array's device address and writes its twiddle tables
+ * with synchronous copies, so make it before any stream capture. All calls share the array
+ * and find the previous call's contents there: each call clears what must start at zero,
+ * and calls that overlap on the GPU (other streams or threads) race. */
+pfc_status pfc_step_noalloc(int ndim, const int64_t *dims, double dx, double dt, const pfc_op *op,
+                            int precision, void *state, int64_t nsteps, void *stream);
+
 /* Names of a status code and of the last error on this thread. Never NULL. */
 const char *pfc_status_string(pfc_status status);
 const char *pfc_last_error(void);

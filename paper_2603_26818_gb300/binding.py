@@ -24,7 +24,7 @@ PFC_ONE_MODE, PFC_TWO_MODE = 0, 1
 # every extern "C" symbol of include/pfc.h
 EXPORTS = ["pfc_plan_create", "pfc_plan_destroy", "pfc_step", "pfc_fft_r2c", "pfc_fft_c2r",
            "pfc_mass", "pfc_energy", "pfc_step_adjoint", "pfc_set_r", "pfc_sync", "pfc_plan_info",
-           "pfc_profile_steps",
+           "pfc_profile_steps", "pfc_step_noalloc",
            "pfc_status_string", "pfc_last_error", "pfc_batch_create", "pfc_batch_destroy",
            "pfc_batch_step", "pfc_batch_mass"]
 
@@ -68,6 +68,7 @@ def load_library(path: str = LIB_PATH):
         "pfc_sync": [vp],
         "pfc_plan_info": [vp, P(ctypes.c_int32), P(i64)],
         "pfc_profile_steps": [vp, vp, i64, P(dbl), P(i64)],
+        "pfc_step_noalloc": [cint, P(i64), dbl, dbl, P(pfc_op), cint, vp, i64, vp],
         "pfc_batch_create": [P(vp), cint, P(i64), P(dbl), dbl, dbl, cint, vp],
         "pfc_batch_destroy": [vp],
         "pfc_batch_step": [vp, vp, i64],

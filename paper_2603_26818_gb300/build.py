@@ -53,8 +53,9 @@ def _link(out, objs, extra):
     os.replace(out + ".tmp", out)
 
 
-# translation units of libpfc.so: host plan logic, and the kernels of each precision
-LIB_UNITS = ["pfc_api.cu", "pfc_kern_f32.cu", "pfc_kern_f64.cu"]
+# translation units of libpfc.so: host plan logic, the kernels of each precision, and the
+# allocation-free step
+LIB_UNITS = ["pfc_api.cu", "pfc_kern_f32.cu", "pfc_kern_f64.cu", "pfc_noalloc.cu"]
 
 
 def build(force: bool = False) -> str:

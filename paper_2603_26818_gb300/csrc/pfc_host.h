@@ -1,0 +1,196 @@
+// Host-side planning helpers shared by the plan API (pfc_api.cu) and the allocation-free
+// entry point (pfc_noalloc.cu): FP64 twiddle generation, operator stability check and the
+// tile planner. Header-only, host code.
+#pragma once
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <string>
+#include <vector>
+
+#include "../../include/pfc.h"
+#include "pfc_launch.h"
+
+namespace pfc {
+
+// records the message returned by pfc_last_error() on this thread and passes s through
+pfc_status set_error(pfc_status s, const std::string &msg);
+
+inline int ilog2(int64_t v) {
+    int l = 0;
+    while ((int64_t(1) << l) < v) ++l;
+    return l;
+}
+inline bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// exp(-2 pi i t / n) in FP64 with the angle reduced to the first octant, so every entry is
+// the correctly rounded cosine/sine of a small argument (or an exact symmetry of one).
+inline void unit_root_fwd(int64_t t, int64_t n, double *re, double *im) {
+    t %= n;
+    const int64_t q = (4 * t) / n, rr = 4 * t - q * n;   // angle = (pi/2)(q + rr/n)
+    double c, s;
+    if (2 * rr <= n) {
+        const double phi = (M_PI / 2) * (double)rr / (double)n;
+        c = std::cos(phi);
+        s = std::sin(phi);
+    } else {
+        const double phi = (M_PI / 2) * (double)(n - rr) / (double)n;
+        c = std::sin(phi);
+        s = std::cos(phi);
+    }
+    double cc, ss;   // rotate by q quarter turns
+    switch (q) {
+        case 0: cc = c; ss = s; break;
+        case 1: cc = -s; ss = c; break;
+        case 2: cc = -c; ss = -s; break;
+        default: cc = s; ss = -c; break;
+    }
+    *re = cc;
+    *im = -ss;
+}
+
+inline double lin_symbol_host(const pfc_op &op, double k2) {
+    const double a = 1.0 - k2;
+    if (op.kind == PFC_ONE_MODE) return op.r + a * a;
+    const double b = op.q2 * op.q2 - k2;
+    return op.r + a * a * (op.R1 + b * b);
+}
+
+// min over k^2 in [0, k2max] of the implicit matrix's smallest eigenvalue (sampled densely).
+inline double min_implicit(const pfc_op *ops, int nfields, double alpha, double dt, double k2max) {
+    double mn = 1e300;
+    const int ns = 200000;
+    for (int i = 0; i <= ns; ++i) {
+        const double k2 = k2max * (double)i / ns;
+        const double m11 = 1.0 + dt * k2 * lin_symbol_host(ops[0], k2);
+        if (nfields == 1) {
+            mn = std::min(mn, m11);
+        } else {
+            const double m22 = 1.0 + dt * k2 * lin_symbol_host(ops[1], k2);
+            const double m12 = dt * k2 * alpha;
+            const double tr = m11 + m22, det = m11 * m22 - m12 * m12;
+            const double disc = std::sqrt(std::max(0.0, tr * tr / 4 - det));
+            mn = std::min(mn, tr / 2 - disc);
+        }
+    }
+    return mn;
+}
+
+inline OpDev to_dev(const pfc_op &o) { return OpDev{o.kind, o.r, o.R1, o.q2}; }
+
+// Row pitch of a line-pass tile: W columns of 128 B (16 float2 / 8 double2) spread over all
+// banks already; narrower tiles get one padding element per row.
+inline int tile_pitch(int W, size_t vb) { return (size_t)W * vb >= 128 ? W : W + 1; }
+
+struct Tiles {
+    Geom g;
+    int nt_row, nt_line;
+    size_t smem_row, smem_line;
+};
+
+// Choose the split of the y/z transforms between the passes and the tile widths.
+//   row pass:  gpc groups of P = Py Pz rows of padded length row_pad(M) + 1
+//   line pass: ntile tiles of Q W complex values (Q = ny nz / P), W columns each
+// Preference: wide line-pass rows (W * sizeof(V) up to 128 B), then the smallest P.
+inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, size_t smem_max) {
+    const int max_threads = vb == 8 ? 1024 : 512;   // line pass blocks
+    const int max_row_threads = vb == 8 ? 1024 : 512;
+    Geom g{};
+    g.nx = nx; g.ny = ny; g.nz = nz; g.M = nx / 2;
+    g.lnx = ilog2(nx); g.lny = ilog2(ny); g.lnz = ilog2(nz); g.lM = g.lnx - 1;
+    g.ltab = std::max(g.lnx, std::max(g.lny, g.lnz));
+    g.rs = (int)round_up(row_pad(g.M) + 1, 2);
+    const size_t row_bytes = (size_t)g.rs * vb;
+    // PFC_TILE="Py,Pz,W" forces a tiling (used to compare tilings; rejected if it does not fit)
+    int fpy = 0, fpz = 0, fw = 0;
+    if (const char *env = std::getenv("PFC_TILE")) std::sscanf(env, "%d,%d,%d", &fpy, &fpz, &fw);
+    long best_score = LONG_MIN;
+    Geom best{};
+    for (int Py = 1; Py <= 8; Py *= 2) {
+        if (Py > 1 && ny / Py < 8) continue;
+        if (ny % Py) continue;
+        if (fpy && Py != fpy) continue;
+        for (int Pz = 1; Pz <= 8; Pz *= 2) {
+            if (nz == 1 && Pz > 1) continue;
+            if (Pz > 1 && nz / Pz < 8) continue;
+            if (nz % Pz) continue;
+            if (fpz && Pz != fpz) continue;
+            const int Qy = ny / Py, Qz = nz / Pz;
+            if (Qy < 8 && Qy != 1) continue;
+            if (Qz < 8 && Qz != 1) continue;
+            const int P = Py * Pz, Q = Qy * Qz;
+            if ((size_t)P * (row_bytes + vb) > smem_max) continue;
+            for (int W = 16; W >= 1; W /= 2) {
+                if (fw && W != fw) continue;
+                if (!fw && (size_t)W * vb > 64) continue;   // 64-byte tile rows at most
+                if (W > g.M + 1 && W > 1) continue;
+                const int64_t QW = (int64_t)Q * W;
+                if (QW < 8 || QW / 8 > max_threads) continue;
+                const int wp = tile_pitch(W, vb);
+                const size_t tile = (size_t)Q * wp;
+                if ((size_t)ntile * tile * vb > smem_max) continue;
+                // wide tile rows first, blocks of at most 512 threads, then the smallest P
+                const long score = (long)(W * vb) * 4096 - (QW / 8 > 512 ? 200000 : 0) - P;
+                if (score > best_score) {
+                    best_score = score;
+                    best = g;
+                    best.Py = Py; best.Pz = Pz; best.Qy = Qy; best.Qz = Qz;
+                    best.W = W;
+                }
+                break;   // largest fitting W for this split
+            }
+        }
+    }
+    if (best_score == LONG_MIN) return false;
+    g = best;
+    g.lPy = ilog2(g.Py); g.lPz = ilog2(g.Pz); g.lQy = ilog2(g.Qy); g.lQz = ilog2(g.Qz);
+    g.P = g.Py * g.Pz; g.Q = g.Qy * g.Qz; g.lQ = ilog2(g.Q);
+    g.lW = ilog2(g.W);
+    g.wp = tile_pitch(g.W, vb);
+    g.xs = (int)round_up(g.M + 1, std::max(g.W, 2));
+    g.ncg = g.xs / g.W;
+    // row groups per CTA: enough rows for >= 256 threads, within smem and dividing Q
+    const int Tr = g.M / 8;
+    int gpc = 1;
+    while (gpc * 2 <= g.Q && (size_t)(gpc * 2) * g.P * (row_bytes + vb) <= smem_max &&
+           gpc * g.P * Tr < 256)
+        gpc *= 2;
+    g.gpc = gpc;
+    g.nreal = (int64_t)nx * ny * nz;
+    g.nhalf = (int64_t)g.P * g.Q * g.xs;
+    g.nstd = (int64_t)ny * nz * (g.M + 1);
+    t.g = g;
+    const int rows = gpc * g.P;
+    t.nt_row = std::min(max_row_threads, std::max(Tr, rows * Tr));
+    if (t.nt_row < 64) t.nt_row = std::max(Tr, 64 / Tr * Tr);
+    // rows, the split twiddles of the block's rows, then the saved real parts of the kx = 0
+    // and nx/2 columns (2 gpc P reals)
+    t.smem_row = (size_t)round_up((int64_t)rows * (row_bytes + vb) + 2 * gpc * g.P * (vb / 2), 16);
+    const int64_t QW = (int64_t)g.Q * g.W;
+    t.nt_line = (int)(QW / 8);
+    t.smem_line = (size_t)ntile * (size_t)g.Q * g.wp * vb;
+    return true;
+}
+
+// Per-stage twiddle tables (see StageTw): entries for R = 8, 4, 2 and Ns = 8, 64, 512.
+constexpr int STW8 = 4672, STW4 = 2336, STW2 = 1168;
+constexpr int STW_TOTAL = STW8 + STW4 + STW2;
+
+// FP64 values (re, im interleaved) of the full table exp(-2 pi i t / ntab), t < ntab, and of
+// the per-stage tables [k][r] = W_{R Ns}^{r k}.
+inline void twiddle_tables(int64_t ntab, std::vector<double> &full, std::vector<double> &stage) {
+    full.assign(2 * ntab, 0.0);
+    for (int64_t i = 0; i < ntab; ++i) unit_root_fwd(i, ntab, &full[2 * i], &full[2 * i + 1]);
+    stage.assign(2 * STW_TOTAL, 0.0);
+    int64_t o = 0;
+    for (int R : {8, 4, 2})
+        for (int64_t ns = 8; ns <= 512; ns *= 8)
+            for (int64_t k = 0; k < ns; ++k)
+                for (int r = 0; r < R; ++r, ++o) unit_root_fwd(r * k, R * ns, &stage[2 * o], &stage[2 * o + 1]);
+}
+
+}  // namespace pfc
