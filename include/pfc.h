@@ -111,8 +111,9 @@ pfc_status pfc_energy(pfc_plan *plan, const void *state, double *out_host);
  * A = IFFT (1/D) FFT, B = IFFT (dt k^2/D) FFT, D = 1 + dt k^2 Lk:
  *     lam_out = A lam_next - 3 psi_n^2 (B lam_next)
  *     *dr_accum_dev += < lam_next, d psi_{n+1} / d r >,  d psi_{n+1}/dr = IFFT(-(dt k^2/D) psi_hat_{n+1})
- * psi_n, lam_next, lam_out: device real arrays (lam_out may alias lam_next).
- * dr_accum_dev: one device double, accumulated in FP64 (stream ordered, not synchronised). */
+ * psi_n, lam_next, lam_out: device real arrays (lam_out may alias lam_next, not psi_n).
+ * dr_accum_dev: one device double, accumulated in FP64 (stream ordered, not synchronised).
+ * The first call allocates a third half spectrum in the plan. Single-field plans only. */
 pfc_status pfc_step_adjoint(pfc_plan *plan, const void *psi_n, const void *lam_next,
                             void *lam_out, double *dr_accum_dev);
 

@@ -42,6 +42,8 @@ struct pfc_plan {
     cudaStream_t stream = nullptr;
     Tiles t{};
     void *X = nullptr, *C = nullptr, *tw = nullptr, *stw = nullptr;
+    void *A = nullptr;            // third half spectrum, allocated by the first adjoint call
+    double *d_adjpart = nullptr;  // adjoint line-pass partial sums (one per block)
     double *d_mean = nullptr, *d_part = nullptr, *d_out = nullptr;
     int *d_status = nullptr;
     size_t scratch = 0;
@@ -271,6 +273,60 @@ template <typename R> pfc_status energy_impl(pfc_plan *p, const void *state, dou
 
 bool plan_ok(const pfc_plan *p) { return p && !p->destroyed; }
 
+// Adjoint of one step: lam_out = A lam_next - 3 psi_n^2 B lam_next, *dr += <lam_next, d psi'/dr>.
+template <typename R>
+pfc_status adjoint_impl(pfc_plan *p, const void *psi_n, const void *lam_next, void *lam_out, double *dr) {
+    const Geom &g = p->t.g;
+    if (p->nfields != 1) return fail(PFC_ERR_UNSUPPORTED, "the adjoint step is built for single-field plans");
+    if (p->t.nt_line > 512) return fail(PFC_ERR_UNSUPPORTED, "the adjoint line pass needs tiles of at most 512 threads");
+    if (psi_n == lam_out) return fail(PFC_ERR_INVALID_ARG, "lam_out must not alias psi_n");
+    const size_t half_bytes = (size_t)g.nhalf * vbytes(p);
+    const int nblk = g.ncg * g.P;
+    if (!p->A) {
+        PFC_CUDA(cudaMalloc(&p->A, half_bytes));
+        PFC_CUDA(cudaMemset(p->A, 0, half_bytes));
+        PFC_CUDA(cudaMalloc(&p->d_adjpart, (size_t)nblk * sizeof(double)));
+        p->scratch += half_bytes + (size_t)nblk * sizeof(double);
+    }
+    const R scale_x = (R)(1.0 / ((double)g.P * (double)g.M));
+    RowArgs<R> f1 = row_args<R>(p);          // Psi' = X' form of psi_n
+    f1.in = psi_n;
+    f1.out = p->A;
+    f1.scale = scale_x;
+    launch_row_m<R>(p, ROW_FWD, f1, 1);
+    RowArgs<R> f2 = row_args<R>(p);          // C' = F_p(psi_n^3)
+    f2.in = p->A;
+    f2.out = p->C;
+    f2.proj = p->A;
+    launch_row_m<R>(p, ROW_CUBE, f2, 1);
+    RowArgs<R> f3 = row_args<R>(p);          // Lam' = X' form of lam_next
+    f3.in = lam_next;
+    f3.out = p->X;
+    f3.scale = scale_x;
+    launch_row_m<R>(p, ROW_FWD, f3, 1);
+    AdjArgs<R> aa{};
+    aa.lam = p->X;
+    aa.psi = p->A;
+    aa.c = p->C;
+    aa.partials = p->d_adjpart;
+    aa.up = line_args<R>(p).up;
+    aa.PM = (R)((double)g.P * (double)g.M);
+    aa.st = stage_tw<R>(p);
+    launch_line_adj<R>(cfg(p), aa);
+    launch_finish(p->stream, p->d_adjpart, nblk, 1.0 / (2.0 * g.Q), dr, true);
+    RowArgs<R> i1 = row_args<R>(p);          // lam_out = U
+    i1.in = p->X;
+    i1.out = lam_out;
+    launch_row_m<R>(p, ROW_INV, i1, 1);
+    RowArgs<R> i2 = row_args<R>(p);          // lam_out -= 3 psi_n^2 V
+    i2.in = p->A;
+    i2.out = lam_out;
+    i2.aux = psi_n;
+    launch_row_m<R>(p, ROW_ADJ_MIX, i2, 1);
+    PFC_CUDA(cudaGetLastError());
+    return PFC_OK;
+}
+
 // pfc_step with an event between consecutive launches; kinds: 0 row, 1 line, 2 entry, 3 exit.
 template <typename R>
 pfc_status profile_impl(pfc_plan *p, void *state, int64_t nsteps, double *ms, int64_t *launches) {
@@ -458,6 +514,7 @@ pfc_status pfc_plan_destroy(pfc_plan *p) {
     cudaStreamSynchronize(p->stream);
     if (p->graph) cudaGraphExecDestroy(p->graph);
     cudaFree(p->X); cudaFree(p->C); cudaFree(p->tw); cudaFree(p->stw);
+    cudaFree(p->A); cudaFree(p->d_adjpart);
     cudaFree(p->d_mean); cudaFree(p->d_part); cudaFree(p->d_out); cudaFree(p->d_status);
     p->destroyed = true;
     delete p;
@@ -501,7 +558,8 @@ pfc_status pfc_step_adjoint(pfc_plan *p, const void *psi_n, const void *lam_next
                             double *dr) {
     if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
     if (!psi_n || !lam_next || !lam_out || !dr) return fail(PFC_ERR_INVALID_ARG, "null pointer");
-    return fail(PFC_ERR_UNSUPPORTED, "adjoint step not built yet");
+    return p->prec == PFC_FP64 ? adjoint_impl<double>(p, psi_n, lam_next, lam_out, dr)
+                               : adjoint_impl<float>(p, psi_n, lam_next, lam_out, dr);
 }
 
 pfc_status pfc_profile_steps(pfc_plan *p, void *state, int64_t nsteps, double *ms_out,

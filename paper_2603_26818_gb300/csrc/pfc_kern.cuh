@@ -15,7 +15,8 @@ template <typename R> void launch_row(const LaunchCfg &c, int mode, const RowArg
     dim3 grid(c.g.Q / c.g.gpc, nf);
     if (mode == ROW_CUBE) k_row<R, ROW_CUBE><<<grid, c.nt_row, c.smem_row, c.stream>>>(c.g, a);
     else if (mode == ROW_FWD) k_row<R, ROW_FWD><<<grid, c.nt_row, c.smem_row, c.stream>>>(c.g, a);
-    else k_row<R, ROW_INV><<<grid, c.nt_row, c.smem_row, c.stream>>>(c.g, a);
+    else if (mode == ROW_INV) k_row<R, ROW_INV><<<grid, c.nt_row, c.smem_row, c.stream>>>(c.g, a);
+    else k_row<R, ROW_ADJ_MIX><<<grid, c.nt_row, c.smem_row, c.stream>>>(c.g, a);
 }
 
 template <typename R, int MAXT>
@@ -41,6 +42,8 @@ template <typename R> cudaError_t set_smem_attrs(const LaunchCfg &c) {
     if ((e = allow_smem(k_row<R, ROW_CUBE>, c.smem_row)) != cudaSuccess) return e;
     if ((e = allow_smem(k_row<R, ROW_FWD>, c.smem_row)) != cudaSuccess) return e;
     if ((e = allow_smem(k_row<R, ROW_INV>, c.smem_row)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_row<R, ROW_ADJ_MIX>, c.smem_row)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_line_adj<R>, c.smem_line)) != cudaSuccess) return e;
     if ((e = allow_smem(k_line<R, LINE_STEP, 512>, c.smem_line)) != cudaSuccess) return e;
     if ((e = allow_smem(k_line<R, LINE_FWD, 512>, c.smem_line)) != cudaSuccess) return e;
     if ((e = allow_smem(k_line<R, LINE_INV, 512>, c.smem_line)) != cudaSuccess) return e;
@@ -50,6 +53,11 @@ template <typename R> cudaError_t set_smem_attrs(const LaunchCfg &c) {
         if ((e = allow_smem(k_line<R, LINE_INV, 1024>, c.smem_line)) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+template <typename R> void launch_line_adj(const LaunchCfg &c, const AdjArgs<R> &a) {
+    dim3 grid(c.g.ncg, c.g.P);
+    k_line_adj<R><<<grid, c.nt_line, c.smem_line, c.stream>>>(c.g, a);
 }
 
 template <typename R>
@@ -71,6 +79,7 @@ void launch_reduce_spec(cudaStream_t s, const Geom &g, OpDev op, double dx, cons
     template void launch_row<R>(const LaunchCfg &, int, const RowArgs<R> &, int);          \
     template void launch_line<R>(const LaunchCfg &, int, const LineArgs<R> &, int);        \
     template cudaError_t set_smem_attrs<R>(const LaunchCfg &);                             \
+    template void launch_line_adj<R>(const LaunchCfg &, const AdjArgs<R> &);               \
     template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t,  \
                                         double *, int *);                                  \
     template void launch_reduce_spec<R>(cudaStream_t, const Geom &, OpDev, double,         \

@@ -4,7 +4,8 @@
 namespace pfc {
 PFC_INSTANTIATE_LAUNCH(double)
 
-void launch_finish(cudaStream_t s, const double *partials, int nb, double scale, double *out) {
-    k_finish<<<1, RED_THREADS, 0, s>>>(partials, nb, scale, out);
+void launch_finish(cudaStream_t s, const double *partials, int nb, double scale, double *out,
+                   bool accumulate) {
+    k_finish<<<1, RED_THREADS, 0, s>>>(partials, nb, scale, out, accumulate ? 1 : 0);
 }
 }  // namespace pfc

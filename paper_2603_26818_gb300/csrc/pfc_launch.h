@@ -5,7 +5,7 @@
 
 #include <cuda_runtime.h>
 
-#include "pfc_pass.cuh"
+#include "pfc_adjoint.cuh"
 
 namespace pfc {
 
@@ -31,13 +31,17 @@ void launch_reduce_real(cudaStream_t s, int kind, const R *x, const R *y, int64_
 template <typename R>
 void launch_reduce_spec(cudaStream_t s, const Geom &g, OpDev op, double dx, const void *X,
                         const double *mean, double *partials, int *status);
-// out[0] = scale * sum of nb partials, in a fixed order
-void launch_finish(cudaStream_t s, const double *partials, int nb, double scale, double *out);
+// out[0] = scale * sum of nb partials, in a fixed order (added to out[0] if accumulate)
+void launch_finish(cudaStream_t s, const double *partials, int nb, double scale, double *out,
+                   bool accumulate = false);
+// adjoint line pass (blocks of nt_line <= 512 threads), one partial per block
+template <typename R> void launch_line_adj(const LaunchCfg &c, const AdjArgs<R> &a);
 
 #define PFC_DECLARE_LAUNCH(R)                                                                   \
     extern template void launch_row<R>(const LaunchCfg &, int, const RowArgs<R> &, int);        \
     extern template void launch_line<R>(const LaunchCfg &, int, const LineArgs<R> &, int);      \
     extern template cudaError_t set_smem_attrs<R>(const LaunchCfg &);                           \
+    extern template void launch_line_adj<R>(const LaunchCfg &, const AdjArgs<R> &);             \
     extern template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t, \
                                                double *, int *);                                \
     extern template void launch_reduce_spec<R>(cudaStream_t, const Geom &, OpDev, double,       \

@@ -48,7 +48,7 @@ struct OpDev {
     double r, R1, q2;
 };
 
-enum { ROW_CUBE = 0, ROW_FWD = 1, ROW_INV = 2 };
+enum { ROW_CUBE = 0, ROW_FWD = 1, ROW_INV = 2, ROW_ADJ_MIX = 3 };
 enum { LINE_STEP = 0, LINE_FWD = 1, LINE_INV = 2 };
 enum { STATUS_NONFINITE = 1, STATUS_TIMEOUT = 2 };
 
@@ -56,6 +56,7 @@ template <typename R> struct RowArgs {
     const void *in;       // ROW_FWD: real; else X' layout
     void *out;            // ROW_INV: real; else X' layout
     void *proj;           // ROW_CUBE: X' to receive the projected kx = 0 and nx/2 columns
+    const void *aux;      // ROW_ADJ_MIX: real psi_n
     const double *mean;   // per field, may be null
     R scale;
     const typename VT<R>::V *tw;
@@ -452,7 +453,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_row(const Geom 
             fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.st);
         } else if (MODE == ROW_FWD) {
             fft_run<-1>(v, sm, ad, lM, j, act, false, false, a.st);
-        } else {
+        } else {   // ROW_INV, ROW_ADJ_MIX
             fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st);
             if (act) {
                 const int gi = r / P, pr = r % P;
@@ -462,14 +463,26 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_row(const Geom 
                 const int z = zq + g.Qz * zp, y = yq + g.Qy * yp;
                 V *out = reinterpret_cast<V *>(a.out) + (size_t)field * (g.nreal / 2) +
                          ((size_t)z * g.ny + y) * M;
+                if (MODE == ROW_INV) {
 #pragma unroll
-                for (int m = 0; m < 8; ++m)
-                    out[j + m * Tr] = V{(v[m].x + mean) * a.scale, (v[m].y + mean) * a.scale};
+                    for (int m = 0; m < 8; ++m)
+                        out[j + m * Tr] = V{(v[m].x + mean) * a.scale, (v[m].y + mean) * a.scale};
+                } else {
+                    // adjoint: out <- out - 3 psi_n^2 (this row inverse)
+                    const V *ps = reinterpret_cast<const V *>(a.aux) + (size_t)field * (g.nreal / 2) +
+                                  ((size_t)z * g.ny + y) * M;
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        const V u = out[j + m * Tr], p = ps[j + m * Tr];
+                        out[j + m * Tr] = V{u.x - (R)3 * p.x * p.x * (v[m].x * a.scale),
+                                            u.y - (R)3 * p.y * p.y * (v[m].y * a.scale)};
+                    }
+                }
             }
         }
     }
 
-    if (MODE != ROW_INV) {
+    if (MODE == ROW_CUBE || MODE == ROW_FWD) {
         V *out = reinterpret_cast<V *>(a.out) + (size_t)field * g.nhalf;
         row_phase_d<R>(g, sm, out, grp0, a.tw, stw, a.scale);
         if (g.Pz > 1) {

@@ -42,14 +42,15 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_real(const R *__restrict
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-// out[0] = scale * sum_{b < nb} partials[b], summed by one block in a fixed order.
+// out[0] = scale * sum_{b < nb} partials[b] (+ out[0] when accumulate), summed by one block in
+// a fixed order.
 static __global__ void __launch_bounds__(RED_THREADS) k_finish(const double *__restrict__ partials, int nb,
-                                                        double scale, double *out) {
+                                                               double scale, double *out, int accumulate) {
     __shared__ double sh[RED_THREADS];
     double acc = 0.0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partials[i];
     const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) out[0] = s * scale;
+    if (threadIdx.x == 0) out[0] = (accumulate ? out[0] : 0.0) + s * scale;
 }
 
 // Spectral part of the energy for one field from its standard half spectrum X of psi - m,

@@ -1,0 +1,117 @@
+"""GPU adjoint: pfc_step_adjoint and the checkpointed autograd rollout against the FP64 oracle's
+adjoint and against central finite differences.
+
+Tolerances: FP64 adjoint step 1e-12 (relative L2 of lam, relative dr); rollout gradients vs the
+oracle 1e-10; finite differences 1e-6 relative (FP64, the bar set for the adjoint). FP32-mixed
+adjoint step 2e-5 (single-precision transforms around an O(1) multiplier range).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_26818_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ONE = (0, -0.25, 0.0, 0.0)
+TWO = (1, -0.3, 0.05, math.sqrt(4.0 / 3.0))
+
+
+def _plan(shape, dt, op, prec):
+    from paper_2603_26818_gb300 import binding
+    return binding.Plan(shape, math.pi / 4, dt, [binding.make_op(*op)], precision=prec)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("shape,op,dt", [((64, 64), ONE, 0.5), ((16, 32, 32), TWO, 0.1),
+                                         ((4096, 16), ONE, 0.5), ((512, 16, 16), TWO, 0.1)])
+def test_adjoint_step_matches_oracle(shape, op, dt, prec, tol):
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    psi = inputs.uniform_state(shape, -0.25, 0.2, seed=51)
+    lam = inputs.uniform_state(shape, 0.0, 1.0, seed=52)
+    ref_lam, ref_dr = oracle.step_adjoint(psi, lam, math.pi / 4, dt, op)
+    p = _plan(shape, dt, op, prec)
+    pd = torch.from_numpy(psi).to(device="cuda", dtype=dtype)
+    ld = torch.from_numpy(lam).to(device="cuda", dtype=dtype)
+    out = torch.empty_like(ld)
+    dr = torch.full((1,), 0.5, dtype=torch.float64, device="cuda")   # accumulates onto 0.5
+    p.step_adjoint(pd, ld, out, dr)
+    torch.cuda.synchronize()
+    assert rel(out.double().cpu().numpy(), ref_lam) <= tol
+    assert abs(float(dr) - 0.5 - ref_dr) <= tol * max(1.0, abs(ref_dr)) * 10
+    # lam_out may alias lam_next
+    p.step_adjoint(pd, ld, ld, dr)
+    torch.cuda.synchronize()
+    assert rel(ld.double().cpu().numpy(), ref_lam) <= tol
+
+
+def _loss_and_grads(shape, dt, op, prec, nsteps, every, psi0, target, r):
+    from paper_2603_26818_gb300.autograd import rollout
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    p = _plan(shape, dt, op, prec)
+    x0 = torch.from_numpy(psi0).to(device="cuda", dtype=dtype).requires_grad_(True)
+    rt = torch.tensor(r, dtype=torch.float64, requires_grad=True)
+    tg = torch.from_numpy(target).to(device="cuda", dtype=dtype)
+    out = rollout(x0, rt, p, nsteps, every)
+    loss = 0.5 * ((out - tg) ** 2).sum()
+    loss.backward()
+    return float(loss.detach()), x0.grad.double().cpu().numpy(), float(rt.grad)
+
+
+@pytest.mark.parametrize("shape,op,dt", [((32, 32), ONE, 0.5), ((16, 16, 32), TWO, 0.1)])
+def test_rollout_gradients_match_oracle_adjoint(shape, op, dt):
+    nsteps = 9
+    psi0 = inputs.uniform_state(shape, -0.25, 0.1, seed=53)
+    target = oracle.step(psi0, math.pi / 4, dt, (op[0], op[1] + 0.05, op[2], op[3]), nsteps)
+    ref_loss, ref_g, ref_gr = oracle.adjoint_run(psi0, target, math.pi / 4, dt, op, nsteps)
+    loss, g, gr = _loss_and_grads(shape, dt, op, "fp64", nsteps, 4, psi0, target, op[1])
+    assert loss == pytest.approx(ref_loss, rel=1e-10)
+    assert rel(g, ref_g) <= 1e-10
+    assert gr == pytest.approx(ref_gr, rel=1e-10)
+
+
+def test_checkpoint_interval_does_not_change_gradients():
+    shape, dt, nsteps = (32, 32), 0.5, 12
+    psi0 = inputs.uniform_state(shape, -0.25, 0.1, seed=54)
+    target = inputs.uniform_state(shape, -0.25, 0.1, seed=55)
+    a = _loss_and_grads(shape, dt, ONE, "fp64", nsteps, 1, psi0, target, -0.25)
+    b = _loss_and_grads(shape, dt, ONE, "fp64", nsteps, 5, psi0, target, -0.25)
+    c = _loss_and_grads(shape, dt, ONE, "fp64", nsteps, 12, psi0, target, -0.25)
+    for x in (b, c):
+        assert rel(x[1], a[1]) <= 1e-12
+        assert x[2] == pytest.approx(a[2], rel=1e-12)
+
+
+def test_adjoint_config_256_cubed_r_gradient_matches_finite_differences():
+    """3D one-mode 256^3 FP64, dx = pi/4, dt = 0.5, r = -0.25, psi0 = -0.25 + U[-0.01, 0.01]
+    (seed 6), 200 steps with checkpoints every 20; target = the same run at r = -0.2;
+    loss = 0.5 ||psi_T - target||^2. dL/dr from the adjoint vs central differences in r."""
+    from paper_2603_26818_gb300 import binding
+    shape, dt, nsteps, every = (256, 256, 256), 0.5, 200, 20
+    psi0 = inputs.uniform_state(shape, -0.25, 0.01, seed=6)
+    p = _plan(shape, dt, ONE, "fp64")
+    x0 = torch.from_numpy(psi0).cuda()
+
+    def run(r):
+        p.set_r(r)
+        x = x0.clone()
+        p.step(x, nsteps)
+        return x
+
+    tg = run(-0.2)
+    loss, g, gr = _loss_and_grads(shape, dt, ONE, "fp64", nsteps, every, psi0, tg.cpu().numpy(), -0.25)
+    # the loss varies like exp(-2 k^2 t r) over t = 100, so a second-order difference would carry
+    # a truncation error of ~3e-6 at h = 2e-5: use the fourth-order central difference
+    h = 2e-5
+    L = lambda r: 0.5 * float(((run(r) - tg) ** 2).sum())
+    fd = (8 * (L(-0.25 + h) - L(-0.25 - h)) - (L(-0.25 + 2 * h) - L(-0.25 - 2 * h))) / (12 * h)
+    assert gr == pytest.approx(fd, rel=1e-6)
+    assert np.isfinite(g).all()
+    p.close()
