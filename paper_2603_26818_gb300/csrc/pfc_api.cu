@@ -113,6 +113,28 @@ template <typename R> void launch_means(pfc_plan *p, const void *state) {
     }
 }
 
+// The line pass of one step: per field, or the coupled 2x2 solve for a two-field plan.
+template <typename R> void launch_update(pfc_plan *p) {
+    LineArgs<R> la = line_args<R>(p);
+    if (p->nfields == 2) {
+        using V = typename VT<R>::V;
+        const Geom &g = p->t.g;
+        Step2Args<R> a2{};
+        a2.x0 = p->X;
+        a2.x1 = reinterpret_cast<V *>(p->X) + g.nhalf;
+        a2.c0 = p->C;
+        a2.c1 = reinterpret_cast<const V *>(p->C) + g.nhalf;
+        a2.alpha = (R)p->alpha;
+        a2.up = la.up;
+        a2.st = la.st;
+        launch_line_step2<R>(cfg(p), a2);
+        return;
+    }
+    la.x = p->X;
+    la.c = p->C;
+    launch_line_m<R>(p, LINE_STEP, la, 1);
+}
+
 // One step on the carried state X' (row pass + line pass).
 template <typename R> void enqueue_one_step(pfc_plan *p) {
     RowArgs<R> ra = row_args<R>(p);
@@ -121,10 +143,7 @@ template <typename R> void enqueue_one_step(pfc_plan *p) {
     ra.proj = p->X;
     ra.mean = p->d_mean;
     launch_row_m<R>(p, ROW_CUBE, ra, p->nfields);
-    LineArgs<R> la = line_args<R>(p);
-    la.x = p->X;
-    la.c = p->C;
-    launch_line_m<R>(p, LINE_STEP, la, p->nfields);
+    launch_update<R>(p);
 }
 
 template <typename R> pfc_status run_steps(pfc_plan *p, int64_t nsteps) {
@@ -359,11 +378,8 @@ pfc_status profile_impl(pfc_plan *p, void *state, int64_t nsteps, double *ms, in
         rc.mean = p->d_mean;
         if ((err = mark(0)) != cudaSuccess) break;
         launch_row_m<R>(p, ROW_CUBE, rc, p->nfields);
-        LineArgs<R> la = line_args<R>(p);
-        la.x = p->X;
-        la.c = p->C;
         if ((err = mark(1)) != cudaSuccess) break;
-        launch_line_m<R>(p, LINE_STEP, la, p->nfields);
+        launch_update<R>(p);
         nl += 2;
     }
     if (err == cudaSuccess) err = mark(3);
@@ -442,8 +458,6 @@ pfc_status pfc_plan_create(pfc_plan **out, int ndim, const int64_t *dims, double
     }
     double alpha = 0.0;
     if (nfields == 2 && coupling) alpha = coupling[1];
-    if (nfields == 2 && alpha != 0.0)
-        return fail(PFC_ERR_UNSUPPORTED, "coupled two-field plans are not built yet");
     const double kmax = M_PI / dx;
     const double k2max = kmax * kmax * ndim;
     if (min_implicit(ops, nfields, alpha, dt, k2max) <= 0.0)
@@ -464,7 +478,9 @@ pfc_status pfc_plan_create(pfc_plan **out, int ndim, const int64_t *dims, double
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) { delete p; return fail(PFC_ERR_CUDA, std::string("device query: ") + cudaGetErrorString(e)); }
     const size_t smem_max = (size_t)optin;
-    if (!plan_tiles(p->t, p->nx, p->ny, p->nz, vbytes(p), 2, smem_max)) {
+    // a two-field plan's line pass holds four tiles (both fields' state and cube)
+    if (!plan_tiles(p->t, p->nx, p->ny, p->nz, vbytes(p), nfields == 2 ? 4 : 2, smem_max) ||
+        (nfields == 2 && p->t.nt_line > 512)) {
         delete p;
         return fail(PFC_ERR_UNSUPPORTED, "no pass tiling fits shared memory for this grid and precision");
     }

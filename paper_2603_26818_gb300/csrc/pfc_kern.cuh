@@ -44,6 +44,7 @@ template <typename R> cudaError_t set_smem_attrs(const LaunchCfg &c) {
     if ((e = allow_smem(k_row<R, ROW_INV>, c.smem_row)) != cudaSuccess) return e;
     if ((e = allow_smem(k_row<R, ROW_ADJ_MIX>, c.smem_row)) != cudaSuccess) return e;
     if ((e = allow_smem(k_line_adj<R>, c.smem_line)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_line_step2<R>, c.smem_line)) != cudaSuccess) return e;
     if ((e = allow_smem(k_line<R, LINE_STEP, 512>, c.smem_line)) != cudaSuccess) return e;
     if ((e = allow_smem(k_line<R, LINE_FWD, 512>, c.smem_line)) != cudaSuccess) return e;
     if ((e = allow_smem(k_line<R, LINE_INV, 512>, c.smem_line)) != cudaSuccess) return e;
@@ -58,6 +59,11 @@ template <typename R> cudaError_t set_smem_attrs(const LaunchCfg &c) {
 template <typename R> void launch_line_adj(const LaunchCfg &c, const AdjArgs<R> &a) {
     dim3 grid(c.g.ncg, c.g.P);
     k_line_adj<R><<<grid, c.nt_line, c.smem_line, c.stream>>>(c.g, a);
+}
+
+template <typename R> void launch_line_step2(const LaunchCfg &c, const Step2Args<R> &a) {
+    dim3 grid(c.g.ncg, c.g.P);
+    k_line_step2<R><<<grid, c.nt_line, c.smem_line, c.stream>>>(c.g, a);
 }
 
 template <typename R>
@@ -80,6 +86,7 @@ void launch_reduce_spec(cudaStream_t s, const Geom &g, OpDev op, double dx, cons
     template void launch_line<R>(const LaunchCfg &, int, const LineArgs<R> &, int);        \
     template cudaError_t set_smem_attrs<R>(const LaunchCfg &);                             \
     template void launch_line_adj<R>(const LaunchCfg &, const AdjArgs<R> &);               \
+    template void launch_line_step2<R>(const LaunchCfg &, const Step2Args<R> &);           \
     template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t,  \
                                         double *, int *);                                  \
     template void launch_reduce_spec<R>(cudaStream_t, const Geom &, OpDev, double,         \

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "pfc_adjoint.cuh"
+#include "pfc_coupled.cuh"
 
 namespace pfc {
 
@@ -36,12 +37,15 @@ void launch_finish(cudaStream_t s, const double *partials, int nb, double scale,
                    bool accumulate = false);
 // adjoint line pass (blocks of nt_line <= 512 threads), one partial per block
 template <typename R> void launch_line_adj(const LaunchCfg &c, const AdjArgs<R> &a);
+// coupled two-field line pass (blocks of nt_line <= 512 threads, smem_line for four tiles)
+template <typename R> void launch_line_step2(const LaunchCfg &c, const Step2Args<R> &a);
 
 #define PFC_DECLARE_LAUNCH(R)                                                                   \
     extern template void launch_row<R>(const LaunchCfg &, int, const RowArgs<R> &, int);        \
     extern template void launch_line<R>(const LaunchCfg &, int, const LineArgs<R> &, int);      \
     extern template cudaError_t set_smem_attrs<R>(const LaunchCfg &);                           \
     extern template void launch_line_adj<R>(const LaunchCfg &, const AdjArgs<R> &);             \
+    extern template void launch_line_step2<R>(const LaunchCfg &, const Step2Args<R> &);         \
     extern template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t, \
                                                double *, int *);                                \
     extern template void launch_reduce_spec<R>(cudaStream_t, const Geom &, OpDev, double,       \

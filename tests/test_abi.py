@@ -50,13 +50,14 @@ def test_status_strings(lib):
         assert lib.pfc_status_string(code) == name
 
 
-def _create(lib, dims, dx=0.785, dt=0.5, ops=None, nfields=1, prec=0):
+def _create(lib, dims, dx=0.785, dt=0.5, ops=None, nfields=1, prec=0, coupling=None):
     from paper_2603_26818_gb300 import binding
     ops = ops or [binding.make_op(0, -0.25)]
     h = ctypes.c_void_p()
     d = (ctypes.c_int64 * len(dims))(*dims)
     o = (binding.pfc_op * len(ops))(*ops)
-    return lib.pfc_plan_create(ctypes.byref(h), len(dims), d, dx, dt, o, nfields, None, prec, None)
+    cp = None if coupling is None else (ctypes.c_double * 4)(0.0, coupling, coupling, 0.0)
+    return lib.pfc_plan_create(ctypes.byref(h), len(dims), d, dx, dt, o, nfields, cp, prec, None)
 
 
 def test_host_side_validation(lib):
@@ -72,6 +73,9 @@ def test_host_side_validation(lib):
     # an operator whose implicit factor 1 + dt k^2 Lk(k) crosses zero
     assert _create(lib, (128, 128), ops=[binding.make_op(0, -20.0)]) == 3
     assert b"positive" in lib.pfc_last_error()
+    # a coupling strong enough to make the implicit 2x2 matrix indefinite at some k
+    assert _create(lib, (128, 128), ops=[binding.make_op(0, -0.25), binding.make_op(0, -0.2)],
+                   nfields=2, coupling=5.0) == 3
     assert lib.pfc_step(None, None, 1) == 1
     assert lib.pfc_plan_destroy(None) == 0
 
