@@ -170,9 +170,11 @@ const char *pfc_last_error(void);
 typedef struct pfc_batch pfc_batch;
 
 /* ndomains >= 1 domains; dims_host[2*d] = ny, dims_host[2*d+1] = nx of domain d (powers of two
- * in [8, 512]); r_host[d] its one-mode r. All share dx, dt and the precision. The packed state
+ * in [16, 512]); r_host[d] its one-mode r. All share dx, dt and the precision. The packed state
  * holds the domains back to back in index order, domain d at element offset
- * sum_{e<d} ny_e nx_e. */
+ * sum_{e<d} ny_e nx_e. Domains are grouped by size; each size class runs as one branch of a
+ * CUDA graph captured at the first pfc_batch_step with nsteps >= 16 (replayed afterwards), so
+ * classes run concurrently. Allocates two half spectra per domain. */
 pfc_status pfc_batch_create(pfc_batch **out, int ndomains, const int64_t *dims_host,
                             const double *r_host, double dx, double dt, int precision,
                             void *stream);

@@ -239,3 +239,60 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """A pfc_batch: many independent 2D one-mode domains of uneven sizes, one packed state.
+
+    dims: list of (ny, nx); r: list of per-domain r. The packed state is a 1D CUDA tensor holding
+    the domains back to back in list order (domain d at offsets[d], ny_d nx_d values)."""
+
+    def __init__(self, dims, r, dx, dt, precision="fp32", stream=None):
+        lib = load_library()
+        self.dims = [(int(a), int(b)) for a, b in dims]
+        self.nd = len(self.dims)
+        self.real_dtype = torch.float64 if precision == "fp64" else torch.float32
+        flat = (ctypes.c_int64 * (2 * self.nd))(*[v for d in self.dims for v in d])
+        rr = (ctypes.c_double * self.nd)(*[float(x) for x in r])
+        self.offsets = []
+        off = 0
+        for ny, nx in self.dims:
+            self.offsets.append(off)
+            off += ny * nx
+        self.total = off
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        check(lib.pfc_batch_create(ctypes.byref(h), self.nd, flat, rr, float(dx), float(dt),
+                                   PFC_FP64 if precision == "fp64" else PFC_FP32_MIXED,
+                                   ctypes.c_void_p(_stream_handle(self._stream))))
+        self._h = h
+
+    def _ptr(self, state):
+        if tuple(state.shape) != (self.total,):
+            raise PfcError(1, f"state has shape {tuple(state.shape)}, expected ({self.total},)")
+        return _dev_ptr(state, self.real_dtype, "state")
+
+    def step(self, state: torch.Tensor, nsteps: int = 1) -> torch.Tensor:
+        check(load_library().pfc_batch_step(self._h, ctypes.c_void_p(self._ptr(state)), int(nsteps)))
+        return state
+
+    def mass(self, state: torch.Tensor):
+        out = (ctypes.c_double * self.nd)()
+        check(load_library().pfc_batch_mass(self._h, ctypes.c_void_p(self._ptr(state)), out))
+        return list(out)
+
+    def view(self, state: torch.Tensor, d: int) -> torch.Tensor:
+        """Domain d of a packed state as a (ny, nx) view."""
+        ny, nx = self.dims[d]
+        return state[self.offsets[d]:self.offsets[d] + ny * nx].view(ny, nx)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            check(load_library().pfc_batch_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -618,17 +618,4 @@ pfc_status pfc_plan_info(pfc_plan *p, int32_t *tiles, int64_t *scratch_bytes) {
     return PFC_OK;
 }
 
-pfc_status pfc_batch_create(pfc_batch **out, int, const int64_t *, const double *, double, double,
-                            int, void *) {
-    if (!out) return fail(PFC_ERR_INVALID_ARG, "null pointer");
-    return fail(PFC_ERR_UNSUPPORTED, "batched ensembles not built yet");
-}
-pfc_status pfc_batch_destroy(pfc_batch *) { return PFC_OK; }
-pfc_status pfc_batch_step(pfc_batch *, void *, int64_t) {
-    return fail(PFC_ERR_UNSUPPORTED, "batched ensembles not built yet");
-}
-pfc_status pfc_batch_mass(pfc_batch *, const void *, double *) {
-    return fail(PFC_ERR_UNSUPPORTED, "batched ensembles not built yet");
-}
-
 }  // extern "C"

@@ -1,0 +1,341 @@
+// Batched ensemble of independent 2D one-mode domains of uneven sizes (pfc_batch_* of pfc.h).
+//
+// Domains are grouped by size class (ny, nx). Within a class a domain is one member of each
+// launch (the member index is blockIdx.y of the row pass and blockIdx.z of the line pass), with
+// its r and its FP64 mean read from device arrays and its place in the caller's packed state
+// from an offset table. The nsteps loop runs as a CUDA graph captured once per batch: every
+// size class gets its own branch (a forked stream), so classes proceed concurrently and each
+// class carries its own chain of row and line passes.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <map>
+
+#include "pfc_host.h"
+
+using namespace pfc;
+
+namespace {
+
+constexpr int BATCH_GRAPH_CHUNK = 16;
+constexpr int BATCH_LTAB = 9;   // tables for 512 points serve every class
+
+struct BatchClass {
+    int ny = 0, nx = 0;
+    Tiles t{};
+    std::vector<int> members;   // domain indices, in class order
+    int cbase = 0;              // first class-major slot of this class
+    void *X = nullptr, *C = nullptr, *r = nullptr;
+    int64_t *moff = nullptr;    // device: member offsets into the packed state
+    cudaStream_t s = nullptr;
+};
+
+}  // namespace
+
+struct pfc_batch {
+    int nd = 0, prec = PFC_FP32_MIXED;
+    double dx = 0, dt = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<BatchClass> cls;
+    std::vector<int> slot_of;       // domain -> class-major slot
+    int64_t *d_off = nullptr, *d_n = nullptr;   // class-major offsets and sizes
+    double *d_mean = nullptr;       // class-major means
+    int *d_status = nullptr;
+    void *tw = nullptr, *stw = nullptr;
+    size_t smem_row = 0, smem_line = 0;
+    cudaGraphExec_t graph = nullptr;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
+    bool destroyed = false;
+};
+
+namespace {
+
+#define PFC_BCUDA(call)                                                                          \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return set_error(e_ == cudaErrorMemoryAllocation ? PFC_ERR_OUT_OF_MEMORY : PFC_ERR_CUDA, \
+                             std::string(#call) + ": " + cudaGetErrorString(e_));                \
+    } while (0)
+
+// each class launches with its own shared-memory size (the kernels' attribute is the maximum)
+LaunchCfg bcfg(const pfc_batch *, const BatchClass &c, cudaStream_t s) {
+    return LaunchCfg{c.t.g, c.t.nt_row, c.t.nt_line, c.t.smem_row, c.t.smem_line, s};
+}
+
+template <typename R> StageTw<typename VT<R>::V> bstage(const pfc_batch *b) {
+    using V = typename VT<R>::V;
+    const V *p = reinterpret_cast<const V *>(b->stw);
+    return StageTw<V>{p, p + STW8, p + STW8 + STW4};
+}
+
+template <typename R> RowArgs<R> brow(const pfc_batch *b, const BatchClass &c) {
+    RowArgs<R> a{};
+    a.tw = reinterpret_cast<const typename VT<R>::V *>(b->tw);
+    a.st = bstage<R>(b);
+    a.scale = (R)1;
+    a.mean = b->d_mean + c.cbase;
+    a.moff = c.moff;
+    return a;
+}
+
+template <typename R> void enqueue_class_step(const pfc_batch *b, const BatchClass &c, cudaStream_t s) {
+    const Geom &g = c.t.g;
+    const int nm = (int)c.members.size();
+    RowArgs<R> ra = brow<R>(b, c);
+    ra.in = c.X;
+    ra.out = c.C;
+    ra.proj = c.X;
+    launch_row<R>(bcfg(b, c, s), ROW_CUBE, ra, nm);
+    LineArgs<R> la{};
+    la.x = c.X;
+    la.c = c.C;
+    la.scale = (R)1;
+    la.st = bstage<R>(b);
+    const double two_pi = 6.28318530717958647692528676655900576839;
+    la.up.dt = (R)b->dt;
+    la.up.cx = (R)(two_pi / (g.nx * b->dx));
+    la.up.cy = (R)(two_pi / (g.ny * b->dx));
+    la.up.cz = (R)(two_pi / (g.nz * b->dx));
+    la.up.invQ = (R)(1.0 / g.Q);
+    la.up.inv_halfN = (R)(2.0 / (double)g.nreal);
+    la.up.op[0] = la.up.op[1] = OpR<R>{PFC_ONE_MODE, (R)0, (R)0, (R)0};
+    la.rmem = reinterpret_cast<const R *>(c.r);
+    launch_line<R>(bcfg(b, c, s), LINE_STEP, la, nm);
+}
+
+// nsteps steps of every class, each class on its own stream forked from `origin` and joined
+// back into it (used both while capturing the graph and for the remainder steps).
+template <typename R> pfc_status enqueue_steps(pfc_batch *b, cudaStream_t origin, int64_t nsteps) {
+    PFC_BCUDA(cudaEventRecord(b->ev_fork, origin));
+    for (size_t i = 0; i < b->cls.size(); ++i) {
+        BatchClass &c = b->cls[i];
+        PFC_BCUDA(cudaStreamWaitEvent(c.s, b->ev_fork, 0));
+        for (int64_t k = 0; k < nsteps; ++k) enqueue_class_step<R>(b, c, c.s);
+        PFC_BCUDA(cudaEventRecord(b->ev_join[i], c.s));
+        PFC_BCUDA(cudaStreamWaitEvent(origin, b->ev_join[i], 0));
+    }
+    PFC_BCUDA(cudaGetLastError());
+    return PFC_OK;
+}
+
+template <typename R> pfc_status batch_step_impl(pfc_batch *b, void *state, int64_t nsteps) {
+    launch_batch_mean<R>(b->stream, reinterpret_cast<const R *>(state), b->d_off, b->d_n, b->nd,
+                         b->d_mean, b->d_status);
+    for (BatchClass &c : b->cls) {
+        RowArgs<R> ra = brow<R>(b, c);
+        ra.in = state;
+        ra.out = c.X;
+        ra.scale = (R)(1.0 / ((double)c.t.g.P * (double)c.t.g.M));
+        launch_row<R>(bcfg(b, c, b->stream), ROW_FWD, ra, (int)c.members.size());
+    }
+    PFC_BCUDA(cudaGetLastError());
+    if (nsteps >= BATCH_GRAPH_CHUNK && !b->graph) {
+        cudaStream_t cap;
+        PFC_BCUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t graph;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        pfc_status st = PFC_OK;
+        if (e == cudaSuccess) {
+            st = enqueue_steps<R>(b, cap, BATCH_GRAPH_CHUNK);
+            e = cudaStreamEndCapture(cap, &graph);
+        }
+        if (e == cudaSuccess && st == PFC_OK) {
+            e = cudaGraphInstantiate(&b->graph, graph, 0);
+            cudaGraphDestroy(graph);
+        }
+        cudaStreamDestroy(cap);
+        if (st != PFC_OK) return st;
+        if (e != cudaSuccess) return set_error(PFC_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    }
+    int64_t done = 0;
+    if (b->graph)
+        for (; done + BATCH_GRAPH_CHUNK <= nsteps; done += BATCH_GRAPH_CHUNK)
+            PFC_BCUDA(cudaGraphLaunch(b->graph, b->stream));
+    if (done < nsteps) {
+        pfc_status st = enqueue_steps<R>(b, b->stream, nsteps - done);
+        if (st != PFC_OK) return st;
+    }
+    for (BatchClass &c : b->cls) {
+        RowArgs<R> ra = brow<R>(b, c);
+        ra.in = c.X;
+        ra.out = state;
+        launch_row<R>(bcfg(b, c, b->stream), ROW_INV, ra, (int)c.members.size());
+    }
+    PFC_BCUDA(cudaGetLastError());
+    return PFC_OK;
+}
+
+void free_batch(pfc_batch *b) {
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (BatchClass &c : b->cls) {
+        cudaFree(c.X); cudaFree(c.C); cudaFree(c.r); cudaFree(c.moff);
+        if (c.s) cudaStreamDestroy(c.s);
+    }
+    for (cudaEvent_t e : b->ev_join) cudaEventDestroy(e);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    cudaFree(b->d_off); cudaFree(b->d_n); cudaFree(b->d_mean); cudaFree(b->d_status);
+    cudaFree(b->tw); cudaFree(b->stw);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+pfc_status pfc_batch_create(pfc_batch **out, int nd, const int64_t *dims_host, const double *r_host,
+                            double dx, double dt, int precision, void *stream) {
+    if (!out || !dims_host || !r_host) return set_error(PFC_ERR_INVALID_ARG, "null pointer argument");
+    if (nd < 1) return set_error(PFC_ERR_INVALID_ARG, "ndomains must be >= 1");
+    if (!(dx > 0) || !(dt > 0) || !std::isfinite(dx) || !std::isfinite(dt))
+        return set_error(PFC_ERR_INVALID_ARG, "dx and dt must be finite and > 0");
+    if (precision != PFC_FP64 && precision != PFC_FP32_MIXED)
+        return set_error(PFC_ERR_INVALID_ARG, "unknown precision");
+    const double kmax = M_PI / dx;
+    std::map<std::pair<int, int>, std::vector<int>> groups;
+    for (int d = 0; d < nd; ++d) {
+        const int64_t ny = dims_host[2 * d], nx = dims_host[2 * d + 1];
+        if (!is_pow2(ny) || !is_pow2(nx) || ny < 16 || nx < 16 || ny > 512 || nx > 512)
+            return set_error(PFC_ERR_UNSUPPORTED, "domain extents must be powers of two in [16, 512]");
+        if (!std::isfinite(r_host[d])) return set_error(PFC_ERR_INVALID_ARG, "r must be finite");
+        const pfc_op op{PFC_ONE_MODE, r_host[d], 0.0, 0.0};
+        if (min_implicit(&op, 1, 0.0, dt, 2 * kmax * kmax) <= 0.0)
+            return set_error(PFC_ERR_UNSTABLE_OPERATOR, "1 + dt k^2 Lk(k) is not positive for domain " + std::to_string(d));
+        groups[{(int)ny, (int)nx}].push_back(d);
+    }
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return set_error(PFC_ERR_CUDA, std::string("device query: ") + cudaGetErrorString(e));
+
+    pfc_batch *b = new pfc_batch();
+    b->nd = nd;
+    b->prec = precision;
+    b->dx = dx;
+    b->dt = dt;
+    b->stream = reinterpret_cast<cudaStream_t>(stream);
+    b->slot_of.assign(nd, 0);
+    const size_t vb = precision == PFC_FP64 ? 16 : 8;
+    std::vector<int64_t> off_idx(nd + 1, 0);
+    for (int d = 0; d < nd; ++d) off_idx[d + 1] = off_idx[d] + dims_host[2 * d] * dims_host[2 * d + 1];
+    std::vector<int64_t> off_cm, n_cm;
+    auto bail = [&](pfc_status s, const std::string &msg) {
+        free_batch(b);
+        return set_error(s, msg);
+    };
+    int slot = 0;
+    for (auto &kv : groups) {
+        BatchClass c;
+        c.ny = kv.first.first;
+        c.nx = kv.first.second;
+        c.members = kv.second;
+        c.cbase = slot;
+        if (!plan_tiles(c.t, c.nx, c.ny, 1, vb, 2, (size_t)optin))
+            return bail(PFC_ERR_UNSUPPORTED, "no pass tiling fits shared memory for a domain size");
+        c.t.g.ltab = BATCH_LTAB;
+        std::vector<int64_t> moff;
+        std::vector<double> rr;
+        for (int d : c.members) {
+            b->slot_of[d] = slot++;
+            off_cm.push_back(off_idx[d]);
+            n_cm.push_back(off_idx[d + 1] - off_idx[d]);
+            moff.push_back(off_idx[d]);
+            rr.push_back(r_host[d]);
+        }
+        const size_t nm = c.members.size();
+        const size_t half = (size_t)c.t.g.nhalf * vb * nm;
+        b->cls.push_back(c);
+        BatchClass &cc = b->cls.back();
+        if ((e = cudaMalloc(&cc.X, half)) != cudaSuccess || (e = cudaMalloc(&cc.C, half)) != cudaSuccess ||
+            (e = cudaMemset(cc.X, 0, half)) != cudaSuccess || (e = cudaMemset(cc.C, 0, half)) != cudaSuccess ||
+            (e = cudaMalloc(&cc.moff, nm * sizeof(int64_t))) != cudaSuccess ||
+            (e = cudaMemcpy(cc.moff, moff.data(), nm * sizeof(int64_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMalloc(&cc.r, nm * (vb / 2))) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&cc.s, cudaStreamNonBlocking)) != cudaSuccess)
+            return bail(e == cudaErrorMemoryAllocation ? PFC_ERR_OUT_OF_MEMORY : PFC_ERR_CUDA,
+                        std::string("batch allocation: ") + cudaGetErrorString(e));
+        if (precision == PFC_FP64) {
+            e = cudaMemcpy(cc.r, rr.data(), nm * 8, cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float> rf(rr.begin(), rr.end());
+            e = cudaMemcpy(cc.r, rf.data(), nm * 4, cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) return bail(PFC_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e));
+        b->smem_row = std::max(b->smem_row, cc.t.smem_row);
+        b->smem_line = std::max(b->smem_line, cc.t.smem_line);
+    }
+    if ((e = cudaMalloc(&b->d_off, nd * sizeof(int64_t))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_n, nd * sizeof(int64_t))) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_off, off_cm.data(), nd * sizeof(int64_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_n, n_cm.data(), nd * sizeof(int64_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_mean, nd * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_status, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(b->d_status, 0, sizeof(int))) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming)) != cudaSuccess)
+        return bail(PFC_ERR_CUDA, std::string("batch allocation: ") + cudaGetErrorString(e));
+    b->ev_join.assign(b->cls.size(), nullptr);
+    for (auto &ev : b->ev_join)
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return bail(PFC_ERR_CUDA, std::string("batch events: ") + cudaGetErrorString(e));
+    std::vector<double> full, stage;
+    twiddle_tables(int64_t(1) << BATCH_LTAB, full, stage);
+    if ((e = cudaMalloc(&b->tw, full.size() / 2 * vb)) != cudaSuccess ||
+        (e = cudaMalloc(&b->stw, stage.size() / 2 * vb)) != cudaSuccess)
+        return bail(PFC_ERR_OUT_OF_MEMORY, std::string("batch tables: ") + cudaGetErrorString(e));
+    if (precision == PFC_FP64) {
+        if ((e = cudaMemcpy(b->tw, full.data(), full.size() * 8, cudaMemcpyHostToDevice)) == cudaSuccess)
+            e = cudaMemcpy(b->stw, stage.data(), stage.size() * 8, cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> f(full.begin(), full.end()), s2(stage.begin(), stage.end());
+        if ((e = cudaMemcpy(b->tw, f.data(), f.size() * 4, cudaMemcpyHostToDevice)) == cudaSuccess)
+            e = cudaMemcpy(b->stw, s2.data(), s2.size() * 4, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return bail(PFC_ERR_CUDA, std::string("batch tables: ") + cudaGetErrorString(e));
+    const LaunchCfg mx{b->cls[0].t.g, 0, 0, b->smem_row, b->smem_line, b->stream};
+    e = precision == PFC_FP64 ? set_smem_attrs<double>(mx) : set_smem_attrs<float>(mx);
+    if (e != cudaSuccess) return bail(PFC_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
+    *out = b;
+    return PFC_OK;
+}
+
+pfc_status pfc_batch_destroy(pfc_batch *b) {
+    if (!b) return PFC_OK;
+    free_batch(b);
+    return PFC_OK;
+}
+
+pfc_status pfc_batch_step(pfc_batch *b, void *packed_state, int64_t nsteps) {
+    if (!b) return set_error(PFC_ERR_INVALID_ARG, "invalid batch");
+    if (!packed_state) return set_error(PFC_ERR_INVALID_ARG, "null state");
+    if (nsteps < 0) return set_error(PFC_ERR_INVALID_ARG, "nsteps must be >= 0");
+    if ((reinterpret_cast<uintptr_t>(packed_state) & 15) != 0)
+        return set_error(PFC_ERR_INVALID_ARG, "state must be 16-byte aligned");
+    if (nsteps == 0) return PFC_OK;
+    return b->prec == PFC_FP64 ? batch_step_impl<double>(b, packed_state, nsteps)
+                               : batch_step_impl<float>(b, packed_state, nsteps);
+}
+
+pfc_status pfc_batch_mass(pfc_batch *b, const void *packed_state, double *out_host) {
+    if (!b || !packed_state || !out_host) return set_error(PFC_ERR_INVALID_ARG, "null pointer argument");
+    if (b->prec == PFC_FP64)
+        launch_batch_mean<double>(b->stream, reinterpret_cast<const double *>(packed_state), b->d_off,
+                                  b->d_n, b->nd, b->d_mean, b->d_status);
+    else
+        launch_batch_mean<float>(b->stream, reinterpret_cast<const float *>(packed_state), b->d_off,
+                                 b->d_n, b->nd, b->d_mean, b->d_status);
+    std::vector<double> cm(b->nd);
+    int st = 0;
+    PFC_BCUDA(cudaMemcpyAsync(cm.data(), b->d_mean, b->nd * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    PFC_BCUDA(cudaMemcpyAsync(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    PFC_BCUDA(cudaStreamSynchronize(b->stream));
+    if (st) {
+        PFC_BCUDA(cudaMemset(b->d_status, 0, sizeof(int)));
+        return set_error(PFC_ERR_NONFINITE, "the state holds NaN or Inf");
+    }
+    for (int d = 0; d < b->nd; ++d) out_host[d] = cm[b->slot_of[d]];
+    return PFC_OK;
+}
+
+}  // extern "C"

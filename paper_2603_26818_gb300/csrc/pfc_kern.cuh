@@ -67,6 +67,12 @@ template <typename R> void launch_line_step2(const LaunchCfg &c, const Step2Args
 }
 
 template <typename R>
+void launch_batch_mean(cudaStream_t s, const R *base, const int64_t *off, const int64_t *n,
+                       int members, double *mean, int *status) {
+    k_batch_mean<R><<<members, RED_THREADS, 0, s>>>(base, off, n, mean, status);
+}
+
+template <typename R>
 void launch_reduce_real(cudaStream_t s, int kind, const R *x, const R *y, int64_t n,
                         double *partials, int *status) {
     if (kind == RED_SUM) k_reduce_real<R, RED_SUM><<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, y, n, partials, status);
@@ -87,6 +93,8 @@ void launch_reduce_spec(cudaStream_t s, const Geom &g, OpDev op, double dx, cons
     template cudaError_t set_smem_attrs<R>(const LaunchCfg &);                             \
     template void launch_line_adj<R>(const LaunchCfg &, const AdjArgs<R> &);               \
     template void launch_line_step2<R>(const LaunchCfg &, const Step2Args<R> &);           \
+    template void launch_batch_mean<R>(cudaStream_t, const R *, const int64_t *,           \
+                                       const int64_t *, int, double *, int *);             \
     template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t,  \
                                         double *, int *);                                  \
     template void launch_reduce_spec<R>(cudaStream_t, const Geom &, OpDev, double,         \

@@ -35,6 +35,10 @@ void launch_reduce_spec(cudaStream_t s, const Geom &g, OpDev op, double dx, cons
 // out[0] = scale * sum of nb partials, in a fixed order (added to out[0] if accumulate)
 void launch_finish(cudaStream_t s, const double *partials, int nb, double scale, double *out,
                    bool accumulate = false);
+// per-member means of a packed batch (one block per member)
+template <typename R>
+void launch_batch_mean(cudaStream_t s, const R *base, const int64_t *off, const int64_t *n,
+                       int members, double *mean, int *status);
 // adjoint line pass (blocks of nt_line <= 512 threads), one partial per block
 template <typename R> void launch_line_adj(const LaunchCfg &c, const AdjArgs<R> &a);
 // coupled two-field line pass (blocks of nt_line <= 512 threads, smem_line for four tiles)
@@ -46,6 +50,8 @@ template <typename R> void launch_line_step2(const LaunchCfg &c, const Step2Args
     extern template cudaError_t set_smem_attrs<R>(const LaunchCfg &);                           \
     extern template void launch_line_adj<R>(const LaunchCfg &, const AdjArgs<R> &);             \
     extern template void launch_line_step2<R>(const LaunchCfg &, const Step2Args<R> &);         \
+    extern template void launch_batch_mean<R>(cudaStream_t, const R *, const int64_t *,         \
+                                              const int64_t *, int, double *, int *);           \
     extern template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t, \
                                                double *, int *);                                \
     extern template void launch_reduce_spec<R>(cudaStream_t, const Geom &, OpDev, double,       \

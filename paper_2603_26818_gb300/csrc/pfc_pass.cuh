@@ -57,6 +57,7 @@ template <typename R> struct RowArgs {
     void *out;            // ROW_INV: real; else X' layout
     void *proj;           // ROW_CUBE: X' to receive the projected kx = 0 and nx/2 columns
     const void *aux;      // ROW_ADJ_MIX: real psi_n
+    const int64_t *moff;  // batched members: element offset of member m in the real arrays
     const double *mean;   // per field, may be null
     R scale;
     const typename VT<R>::V *tw;
@@ -83,6 +84,7 @@ template <typename R> struct LineArgs {
     void *std_out;        // LINE_FWD output (standard half spectrum)
     R scale;              // LINE_INV / LINE_FWD output scale
     UpdR<R> up;
+    const R *rmem;        // batched members: r of member m (overrides up.op[0].r), may be null
     StageTw<typename VT<R>::V> st;
 };
 
@@ -407,7 +409,8 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_row(const Geom 
     }
 
     if (MODE == ROW_FWD) {
-        const V *in = reinterpret_cast<const V *>(a.in) + (size_t)field * (g.nreal / 2);
+        const V *in = reinterpret_cast<const V *>(a.in) +
+                      (a.moff ? (size_t)(a.moff[field] / 2) : (size_t)field * (g.nreal / 2));
         const int cnt = rows << lM;
         for (int e = tid; e < cnt; e += nt) {
             const int i = e & (M - 1), r = e >> lM;
@@ -461,7 +464,8 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_row(const Geom 
                 const int zq = grp >> g.lQy, yq = grp & (g.Qy - 1);
                 const int zp = pr >> g.lPy, yp = pr & (g.Py - 1);
                 const int z = zq + g.Qz * zp, y = yq + g.Qy * yp;
-                V *out = reinterpret_cast<V *>(a.out) + (size_t)field * (g.nreal / 2) +
+                V *out = reinterpret_cast<V *>(a.out) +
+                         (a.moff ? (size_t)(a.moff[field] / 2) : (size_t)field * (g.nreal / 2)) +
                          ((size_t)z * g.ny + y) * M;
                 if (MODE == ROW_INV) {
 #pragma unroll
@@ -586,7 +590,8 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
     }
 
     if (MODE == LINE_STEP) {
-        const OpR<R> &op = a.up.op[field == 0 ? 0 : 1];
+        OpR<R> op = a.up.op[field == 0 ? 0 : 1];
+        if (a.rmem) op.r = a.rmem[field];
         const R invQ = a.up.invQ, inv_halfN = a.up.inv_halfN, dt = a.up.dt;
         const R cy = a.up.cy, cz = a.up.cz;
         const int kx = cg * g.W + mp.w;

@@ -92,4 +92,27 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_spec(const Geom g, OpDev
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// Mean of every member of a packed batch: block m sums member m (n_m values at offset off[m])
+// in FP64 in a fixed order and writes mean[m].
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) k_batch_mean(const R *__restrict__ base,
+                                                            const int64_t *__restrict__ off,
+                                                            const int64_t *__restrict__ n,
+                                                            double *mean, int *status) {
+    __shared__ double sh[RED_THREADS];
+    const int m = blockIdx.x;
+    const R *x = base + off[m];
+    const int64_t nm = n[m];
+    double acc = 0.0;
+    bool bad = false;
+    for (int64_t i = threadIdx.x; i < nm; i += blockDim.x) {
+        const double v = (double)x[i];
+        if (!isfinite(v)) bad = true;
+        acc += v;
+    }
+    if (bad) atomicOr(status, STATUS_NONFINITE);
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) mean[m] = s / (double)nm;
+}
+
 }  // namespace pfc
