@@ -343,7 +343,7 @@ def run_ours(args):
         p64.close()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(psi0, 8)
+        line["cpu_baseline"] = cpu_baseline(psi0, 32)
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
