@@ -114,12 +114,21 @@ struct TileAddr {
     __device__ __forceinline__ int at(int i) const { return off + i * stride; }
 };
 
-// Per-stage twiddle tables, laid out [k][r] so that one butterfly's twiddles are contiguous:
-//   t8: radix-8 stages with Ns = 8, 64, 512:  entry [k][r] = W_{8 Ns}^{r k}, r = 0..7
-//   t4: radix-4 last stages with Ns = 8, 64, 512:  [k][r] = W_{4 Ns}^{r k}, r = 0..3
-//   t2: radix-2 last stages with Ns = 8, 64, 512:  [k][r] = W_{2 Ns}^{r k}, r = 0..1
+// Per-stage twiddle tables, laid out [r][k] so that the threads of a warp (consecutive k) read
+// consecutive addresses for every r:
+//   t8: radix-8 stages with Ns = 8, 64, 512:  entry r Ns + k = W_{8 Ns}^{r k}, r = 0..7
+//   t4: radix-4 last stages with Ns = 8, 64, 512:  r Ns + k = W_{4 Ns}^{r k}, r = 0..3
+//   t2: radix-2 last stages with Ns = 8, 64, 512:  r Ns + k = W_{2 Ns}^{r k}, r = 0..1
 // Tables of one kind are stored back to back; the block for Ns = 8^s starts at
 // R (8^s - 8) / 7 entries. All entries are FP64-generated (rounded once for FP32).
+struct BlockBarrier {
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+struct NamedBarrier {
+    int id, n;
+    __device__ __forceinline__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+};
+
 template <typename V> struct StageTw {
     const V *t8, *t4, *t2;
 };
@@ -129,23 +138,6 @@ __host__ __device__ __forceinline__ int stage_tw_off(int R, int lNs) {
     return R * (ns - 8) / 7;
 }
 
-__device__ __forceinline__ void load_tw(const float2 *__restrict__ t, float2 (&w)[8], int n) {
-    const float4 *p = reinterpret_cast<const float4 *>(t);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        if (2 * i < n) {
-            const float4 q = __ldg(p + i);
-            w[2 * i] = float2{q.x, q.y};
-            w[2 * i + 1] = float2{q.z, q.w};
-        }
-    }
-}
-__device__ __forceinline__ void load_tw(const double2 *__restrict__ t, double2 (&w)[8], int n) {
-#pragma unroll
-    for (int i = 1; i < 8; ++i)
-        if (i < n) w[i] = __ldg(t + i);
-}
-
 template <int S, typename V>
 __device__ __forceinline__ void stage_exec(V (&v)[8], int lR, int lNs, int j, int n8,
                                            const StageTw<V> &tw) {
@@ -153,10 +145,9 @@ __device__ __forceinline__ void stage_exec(V (&v)[8], int lR, int lNs, int j, in
     if (lR == 3) {
         if (lNs > 0) {
             const int k = j & (Ns - 1);
-            V w[8];
-            load_tw(tw.t8 + stage_tw_off(8, lNs) + k * 8, w, 8);
+            const V *t = tw.t8 + stage_tw_off(8, lNs) + k;
 #pragma unroll
-            for (int r = 1; r < 8; ++r) v[r] = ctw<S>(v[r], w[r]);
+            for (int r = 1; r < 8; ++r) v[r] = ctw<S>(v[r], __ldg(t + r * Ns));
         }
         dft8<S>(v);
     } else if (lR == 2) {
@@ -165,11 +156,10 @@ __device__ __forceinline__ void stage_exec(V (&v)[8], int lR, int lNs, int j, in
             V c0 = v[u], c1 = v[u + 2], c2 = v[u + 4], c3 = v[u + 6];
             if (lNs > 0) {
                 const int k = (j + u * n8) & (Ns - 1);
-                V w[8];
-                load_tw(tw.t4 + stage_tw_off(4, lNs) + k * 4, w, 4);
-                c1 = ctw<S>(c1, w[1]);
-                c2 = ctw<S>(c2, w[2]);
-                c3 = ctw<S>(c3, w[3]);
+                const V *t = tw.t4 + stage_tw_off(4, lNs) + k;
+                c1 = ctw<S>(c1, __ldg(t + Ns));
+                c2 = ctw<S>(c2, __ldg(t + 2 * Ns));
+                c3 = ctw<S>(c3, __ldg(t + 3 * Ns));
             }
             dft4<S>(c0, c1, c2, c3);
             v[u] = c0; v[u + 2] = c1; v[u + 4] = c2; v[u + 6] = c3;
@@ -180,9 +170,7 @@ __device__ __forceinline__ void stage_exec(V (&v)[8], int lR, int lNs, int j, in
             V c0 = v[u], c1 = v[u + 4];
             if (lNs > 0) {
                 const int k = (j + u * n8) & (Ns - 1);
-                V w[8];
-                load_tw(tw.t2 + stage_tw_off(2, lNs) + k * 2, w, 2);
-                c1 = ctw<S>(c1, w[1]);
+                c1 = ctw<S>(c1, __ldg(tw.t2 + stage_tw_off(2, lNs) + Ns + k));
             }
             dft2<S>(c0, c1);
             v[u] = c0; v[u + 4] = c1;
@@ -253,30 +241,30 @@ __device__ __forceinline__ void stage_store_t(const V (&v)[8], V *sm, const Addr
     }
 }
 
-template <int S, int L, int LR, int LNS, typename V, typename Addr>
+template <int S, int L, int LR, int LNS, typename V, typename Addr, typename Bar>
 __device__ __forceinline__ void stage_t(V (&v)[8], V *sm, const Addr &ad, int j, bool act,
-                                        bool load, bool store, const StageTw<V> &tw) {
+                                        bool load, bool store, const StageTw<V> &tw, const Bar &bar) {
     constexpr int N8 = 1 << (L - 3);
     if (act && load) load8_t<N8>(v, sm, ad, j);
     if (act) stage_exec<S>(v, LR, LNS, j, N8, tw);
     if (!store) return;
-    __syncthreads();
+    bar.sync();
     if (act) stage_store_t<LR, LNS, N8>(v, sm, ad, j);
-    __syncthreads();
+    bar.sync();
 }
 
-template <int S, int L, typename V, typename Addr>
+template <int S, int L, typename V, typename Addr, typename Bar>
 __device__ __forceinline__ void fft_run_t(V (&v)[8], V *sm, const Addr &ad, int j, bool act,
-                                          bool in_regs, bool out_regs, const StageTw<V> &tw) {
+                                          bool in_regs, bool out_regs, const StageTw<V> &tw, const Bar &bar) {
     constexpr int NFULL = L / 3;
     constexpr int LLAST = L - 3 * NFULL;    // 0: all stages radix 8
     constexpr int NST = NFULL + (LLAST ? 1 : 0);
     // radix-8 stages s = 0 .. NFULL-1 with Ns = 8^s, then one radix 2^LLAST stage
-    stage_t<S, L, 3, 0>(v, sm, ad, j, act, !in_regs, !(NST == 1 && out_regs), tw);
-    if (NFULL > 1) stage_t<S, L, 3, (NFULL > 1 ? 3 : 0)>(v, sm, ad, j, act, true, !(NST == 2 && out_regs), tw);
-    if (NFULL > 2) stage_t<S, L, 3, (NFULL > 2 ? 6 : 0)>(v, sm, ad, j, act, true, !(NST == 3 && out_regs), tw);
-    if (NFULL > 3) stage_t<S, L, 3, (NFULL > 3 ? 9 : 0)>(v, sm, ad, j, act, true, !(NST == 4 && out_regs), tw);
-    if (LLAST) stage_t<S, L, (LLAST ? LLAST : 1), 3 * NFULL>(v, sm, ad, j, act, true, !out_regs, tw);
+    stage_t<S, L, 3, 0>(v, sm, ad, j, act, !in_regs, !(NST == 1 && out_regs), tw, bar);
+    if (NFULL > 1) stage_t<S, L, 3, (NFULL > 1 ? 3 : 0)>(v, sm, ad, j, act, true, !(NST == 2 && out_regs), tw, bar);
+    if (NFULL > 2) stage_t<S, L, 3, (NFULL > 2 ? 6 : 0)>(v, sm, ad, j, act, true, !(NST == 3 && out_regs), tw, bar);
+    if (NFULL > 3) stage_t<S, L, 3, (NFULL > 3 ? 9 : 0)>(v, sm, ad, j, act, true, !(NST == 4 && out_regs), tw, bar);
+    if (LLAST) stage_t<S, L, (LLAST ? LLAST : 1), 3 * NFULL>(v, sm, ad, j, act, true, !out_regs, tw, bar);
 }
 
 // One transform of n = 2^L points (3 <= L <= 12), run by every thread of the block (it contains
@@ -286,20 +274,21 @@ __device__ __forceinline__ void fft_run_t(V (&v)[8], V *sm, const Addr &ad, int 
 //             stored; otherwise the result is in smem in natural order and v is undefined.
 // When in_regs is set, a barrier is issued before the first store, so other threads may still
 // be reading smem that this call overwrites.
-template <int S, typename V, typename Addr>
+template <int S, typename V, typename Addr, typename Bar = BlockBarrier>
 __device__ __forceinline__ void fft_run(V (&v)[8], V *sm, const Addr &ad, int L, int j, bool act,
-                                        bool in_regs, bool out_regs, const StageTw<V> &tw) {
+                                        bool in_regs, bool out_regs, const StageTw<V> &tw,
+                                        const Bar &bar = Bar()) {
     switch (L) {
-        case 3: fft_run_t<S, 3>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
-        case 4: fft_run_t<S, 4>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
-        case 5: fft_run_t<S, 5>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
-        case 6: fft_run_t<S, 6>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
-        case 7: fft_run_t<S, 7>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
-        case 8: fft_run_t<S, 8>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
-        case 9: fft_run_t<S, 9>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
-        case 10: fft_run_t<S, 10>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
-        case 11: fft_run_t<S, 11>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
-        default: fft_run_t<S, 12>(v, sm, ad, j, act, in_regs, out_regs, tw); break;
+        case 3: fft_run_t<S, 3>(v, sm, ad, j, act, in_regs, out_regs, tw, bar); break;
+        case 4: fft_run_t<S, 4>(v, sm, ad, j, act, in_regs, out_regs, tw, bar); break;
+        case 5: fft_run_t<S, 5>(v, sm, ad, j, act, in_regs, out_regs, tw, bar); break;
+        case 6: fft_run_t<S, 6>(v, sm, ad, j, act, in_regs, out_regs, tw, bar); break;
+        case 7: fft_run_t<S, 7>(v, sm, ad, j, act, in_regs, out_regs, tw, bar); break;
+        case 8: fft_run_t<S, 8>(v, sm, ad, j, act, in_regs, out_regs, tw, bar); break;
+        case 9: fft_run_t<S, 9>(v, sm, ad, j, act, in_regs, out_regs, tw, bar); break;
+        case 10: fft_run_t<S, 10>(v, sm, ad, j, act, in_regs, out_regs, tw, bar); break;
+        case 11: fft_run_t<S, 11>(v, sm, ad, j, act, in_regs, out_regs, tw, bar); break;
+        default: fft_run_t<S, 12>(v, sm, ad, j, act, in_regs, out_regs, tw, bar); break;
     }
 }
 

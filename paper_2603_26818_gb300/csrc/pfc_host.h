@@ -181,7 +181,7 @@ constexpr int STW8 = 4672, STW4 = 2336, STW2 = 1168;
 constexpr int STW_TOTAL = STW8 + STW4 + STW2;
 
 // FP64 values (re, im interleaved) of the full table exp(-2 pi i t / ntab), t < ntab, and of
-// the per-stage tables [k][r] = W_{R Ns}^{r k}.
+// the per-stage tables [r][k] = W_{R Ns}^{r k}.
 inline void twiddle_tables(int64_t ntab, std::vector<double> &full, std::vector<double> &stage) {
     full.assign(2 * ntab, 0.0);
     for (int64_t i = 0; i < ntab; ++i) unit_root_fwd(i, ntab, &full[2 * i], &full[2 * i + 1]);
@@ -189,8 +189,8 @@ inline void twiddle_tables(int64_t ntab, std::vector<double> &full, std::vector<
     int64_t o = 0;
     for (int R : {8, 4, 2})
         for (int64_t ns = 8; ns <= 512; ns *= 8)
-            for (int64_t k = 0; k < ns; ++k)
-                for (int r = 0; r < R; ++r, ++o) unit_root_fwd(r * k, R * ns, &stage[2 * o], &stage[2 * o + 1]);
+            for (int r = 0; r < R; ++r)
+                for (int64_t k = 0; k < ns; ++k, ++o) unit_root_fwd(r * k, R * ns, &stage[2 * o], &stage[2 * o + 1]);
 }
 
 }  // namespace pfc

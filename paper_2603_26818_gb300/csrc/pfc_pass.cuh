@@ -186,7 +186,7 @@ __device__ __forceinline__ void row_pair_b(const Geom &g, typename VT<R>::V *sm,
                                            const typename VT<R>::V *X, int gi, int grp, int zp,
                                            int ca, int cb, bool k0,
                                            const typename VT<R>::V *__restrict__ tw,
-                                           const typename VT<R>::V *stw) {
+                                           const typename VT<R>::V *stw, typename VT<R>::V *proj) {
     using V = typename VT<R>::V;
     const int P = g.P;
     V a[8], b[8];
@@ -222,6 +222,27 @@ __device__ __forceinline__ void row_pair_b(const Geom &g, typename VT<R>::V *sm,
             if (!k0 && cb != ca) sm[row * g.rs + row_pad(cb)] = zb;
         }
     }
+    if (FROM_GLOBAL && proj && k0) {
+        // Hermitian projection (see project_edge_columns) done here when the thread holds every
+        // row of the kx = 0 and kx = M columns (Pz == 1): X' = DFT_P(real parts) / P. a and b are
+        // reused: the pre-processing above no longer needs them.
+#pragma unroll
+        for (int yy = 0; yy < 8; ++yy) {
+            a[yy].y = (R)0;
+            b[yy].y = (R)0;
+        }
+        dft_small<-1>(a, g.Py);
+        dft_small<-1>(b, g.Py);
+        const R invP = (R)1 / (R)P;
+#pragma unroll
+        for (int yy = 0; yy < 8; ++yy) {
+            if (yy < g.Py) {
+                V *dst = proj + (size_t)(yy * g.Q + grp) * g.xs;
+                dst[0] = cscale(cmul(a[yy], stw[gi * P + yy]), invP);
+                dst[g.M] = cscale(cmul(b[yy], stw[gi * P + yy]), invP);
+            }
+        }
+    }
 }
 
 // Phase B: y-part inverse of the column pair (kk, M - kk) of the Py rows of (gi, z_p), then the
@@ -232,7 +253,7 @@ template <typename R, bool FROM_GLOBAL>
 __device__ void row_phase_b(const Geom &g, typename VT<R>::V *sm, R *edge,
                             const typename VT<R>::V *X, int grp0,
                             const typename VT<R>::V *__restrict__ tw,
-                            const typename VT<R>::V *stw) {
+                            const typename VT<R>::V *stw, typename VT<R>::V *proj) {
     const int M = g.M, hM = M >> 1;
     const int cnt = (g.gpc * g.Pz) << (g.lM - 1);
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
@@ -246,7 +267,7 @@ __device__ void row_phase_b(const Geom &g, typename VT<R>::V *sm, R *edge,
         for (int pp = 0; pp < npass; ++pp) {
             const bool k0 = kk == 0 && pp == 0;
             const int ca = pp ? hM : kk, cb = pp ? hM : (kk == 0 ? M : M - kk);
-            row_pair_b<R, FROM_GLOBAL>(g, sm, k0 ? edge : nullptr, X, gi, grp, zp, ca, cb, k0, tw, stw);
+            row_pair_b<R, FROM_GLOBAL>(g, sm, k0 ? edge : nullptr, X, gi, grp, zp, ca, cb, k0, tw, stw, proj);
         }
     }
 }
@@ -428,12 +449,13 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_row(const Geom 
         const V *X = reinterpret_cast<const V *>(a.in) + (size_t)field * g.nhalf;
         R *ed = MODE == ROW_CUBE ? edge : nullptr;
         __syncthreads();
+        V *pw = MODE == ROW_CUBE ? reinterpret_cast<V *>(a.proj) + (size_t)field * g.nhalf : nullptr;
         if (g.Pz > 1) {
             row_phase_a<R>(g, sm, X, grp0, stw);
             __syncthreads();
-            row_phase_b<R, false>(g, sm, ed, X, grp0, a.tw, stw);
+            row_phase_b<R, false>(g, sm, ed, X, grp0, a.tw, stw, nullptr);
         } else {
-            row_phase_b<R, true>(g, sm, ed, X, grp0, a.tw, stw);
+            row_phase_b<R, true>(g, sm, nullptr, X, grp0, a.tw, stw, pw);
         }
     }
     __syncthreads();
@@ -441,19 +463,25 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_row(const Geom 
     // ---- per-row transforms ----
     const int Tr = M >> 3;
     const int RB = nt / Tr;
+    // groups of Tr threads, each with its own barrier, take rows gidx, gidx + RB, ...
+    const bool grouped = Tr >= 32 && RB <= 15 && rows % RB == 0;
+    const int gidx = tid / Tr;
+    const NamedBarrier nbar{1 + gidx, Tr};
     for (int rb = 0; rb < rows; rb += RB) {
-        const int r = rb + tid / Tr, j = tid % Tr;
+        const int r = rb + gidx, j = tid % Tr;
         const bool act = r < rows;
         const RowAddr ad{r * g.rs};
         V v[8];
         if (MODE == ROW_CUBE) {
-            fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st);
+            if (grouped) fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st, nbar);
+            else fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st);
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
                 const R p0 = v[m].x + mean, p1 = v[m].y + mean;
                 v[m] = V{p0 * p0 * p0, p1 * p1 * p1};
             }
-            fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.st);
+            if (grouped) fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.st, nbar);
+            else fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.st);
         } else if (MODE == ROW_FWD) {
             fft_run<-1>(v, sm, ad, lM, j, act, false, false, a.st);
         } else {   // ROW_INV, ROW_ADJ_MIX
@@ -486,6 +514,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_row(const Geom 
         }
     }
 
+    __syncthreads();
     if (MODE == ROW_CUBE || MODE == ROW_FWD) {
         V *out = reinterpret_cast<V *>(a.out) + (size_t)field * g.nhalf;
         row_phase_d<R>(g, sm, out, grp0, a.tw, stw, a.scale);
@@ -495,7 +524,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_row(const Geom 
         }
     }
     // the edge values were saved in phase B in their own smem area; nothing waits on this
-    if (MODE == ROW_CUBE) {
+    if (MODE == ROW_CUBE && g.Pz > 1) {   // (Pz == 1 projects in phase B)
         V *xw = reinterpret_cast<V *>(a.proj) + (size_t)field * g.nhalf;
         project_edge_columns<R>(g, edge, grp0, stw, xw);
     }
