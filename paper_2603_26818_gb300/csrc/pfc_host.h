@@ -133,15 +133,21 @@ inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, s
                 const int wp = tile_pitch(W, vb);
                 const size_t tile = (size_t)Q * wp;
                 if ((size_t)ntile * tile * vb > smem_max) continue;
-                // wide tile rows first, blocks of at most 512 threads, then the smallest P
-                const long score = (long)(W * vb) * 4096 - (QW / 8 > 512 ? 200000 : 0) - P;
+                // 32-byte tile rows first (one DRAM sector per tile row), then blocks of at most
+                // 512 threads, nearest to 256 (several small blocks per SM interleave their load,
+                // transform and store phases), then the smallest P. At 4096^2 FP32, 32-byte rows
+                // in 256-thread blocks measured fastest, ahead of 64-byte rows or 512 threads.
+                const size_t wb = (size_t)W * vb;
+                const long pref = wb == 32 ? 5 : wb == 64 ? 4 : wb == 16 ? 3 : wb == 128 ? 2 : 1;
+                const int lnt = ilog2((int)(QW / 8));
+                const long score = pref * 1000000 - (QW / 8 > 512 ? 200000 : 0) -
+                                   (long)std::abs(lnt - 8) * 1000 - P;
                 if (score > best_score) {
                     best_score = score;
                     best = g;
                     best.Py = Py; best.Pz = Pz; best.Qy = Qy; best.Qz = Qz;
                     best.W = W;
                 }
-                break;   // largest fitting W for this split
             }
         }
     }

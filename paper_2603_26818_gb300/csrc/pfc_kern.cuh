@@ -28,6 +28,10 @@ static void launch_line_t(const LaunchCfg &c, int mode, const LineArgs<R> &a, in
 }
 
 template <typename R> void launch_line(const LaunchCfg &c, int mode, const LineArgs<R> &a, int nf) {
+    if (mode == LINE_STEP && line_fixed_fits(c)) {
+        launch_line_step_fixed<R>(c, a, nf);
+        return;
+    }
     if constexpr (sizeof(R) == 4) {
         if (c.nt_line > 512) {
             launch_line_t<R, 1024>(c, mode, a, nf);
@@ -53,7 +57,7 @@ template <typename R> cudaError_t set_smem_attrs(const LaunchCfg &c) {
         if ((e = allow_smem(k_line<R, LINE_FWD, 1024>, c.smem_line)) != cudaSuccess) return e;
         if ((e = allow_smem(k_line<R, LINE_INV, 1024>, c.smem_line)) != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return set_smem_attrs_fixed<R>(c);
 }
 
 template <typename R> void launch_line_adj(const LaunchCfg &c, const AdjArgs<R> &a) {

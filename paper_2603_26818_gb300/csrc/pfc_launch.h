@@ -1,6 +1,7 @@
 // Host-side launch interface of the pass and reduction kernels. The kernels are compiled in
-// two translation units, one per precision (pfc_kern_f32.cu, pfc_kern_f64.cu), which
-// instantiate these functions; the plan logic in pfc_api.cu only calls them.
+// translation units per precision (pfc_kern_f32.cu, pfc_kern_f64.cu, pfc_line_fixed_f32.cu,
+// pfc_line_fixed_f64.cu), which instantiate these functions; the plan logic in pfc_api.cu only
+// calls them.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -44,9 +45,21 @@ template <typename R> void launch_line_adj(const LaunchCfg &c, const AdjArgs<R> 
 // coupled two-field line pass (blocks of nt_line <= 512 threads, smem_line for four tiles)
 template <typename R> void launch_line_step2(const LaunchCfg &c, const Step2Args<R> &a);
 
+// The update pass (LINE_STEP) with its y transform length fixed at compile time, compiled in
+// pfc_line_fixed_f32.cu / pfc_line_fixed_f64.cu: one-axis tiles (Qz = 1) with Qy = 2^6 .. 2^10
+// in blocks of at most 512 threads. launch_line takes it whenever line_fixed_fits.
+constexpr int LINE_FIXED_MIN = 6, LINE_FIXED_MAX = 10;
+inline bool line_fixed_fits(const LaunchCfg &c) {
+    return c.g.Qz == 1 && c.nt_line <= 512 && c.g.lQy >= LINE_FIXED_MIN && c.g.lQy <= LINE_FIXED_MAX;
+}
+template <typename R> void launch_line_step_fixed(const LaunchCfg &c, const LineArgs<R> &a, int nf);
+template <typename R> cudaError_t set_smem_attrs_fixed(const LaunchCfg &c);
+
 #define PFC_DECLARE_LAUNCH(R)                                                                   \
     extern template void launch_row<R>(const LaunchCfg &, int, const RowArgs<R> &, int);        \
     extern template void launch_line<R>(const LaunchCfg &, int, const LineArgs<R> &, int);      \
+    extern template void launch_line_step_fixed<R>(const LaunchCfg &, const LineArgs<R> &, int); \
+    extern template cudaError_t set_smem_attrs_fixed<R>(const LaunchCfg &);                     \
     extern template cudaError_t set_smem_attrs<R>(const LaunchCfg &);                           \
     extern template void launch_line_adj<R>(const LaunchCfg &, const AdjArgs<R> &);             \
     extern template void launch_line_step2<R>(const LaunchCfg &, const Step2Args<R> &);         \

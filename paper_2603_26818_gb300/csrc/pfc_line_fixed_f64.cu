@@ -1,0 +1,6 @@
+// FP64 update-pass kernels with compile-time y transform lengths.
+#include "pfc_line_fixed.cuh"
+
+namespace pfc {
+PFC_INSTANTIATE_LINE_FIXED(double)
+}  // namespace pfc

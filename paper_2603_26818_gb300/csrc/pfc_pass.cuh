@@ -569,7 +569,17 @@ __device__ __forceinline__ size_t xprime_index(const Geom &g, int kp, int cg, in
     return (size_t)(kp * g.Q + zq * g.Qy + yq) * g.xs + cg * g.W + w;
 }
 
-template <typename R, int MODE, int MAXT>
+// y transform of a line tile: length 2^LY fixed at compile time when LY > 0 (one-axis tiles;
+// straight-line code with no switch over lengths, fewer live registers), else the plan's length
+template <int S, int LY, typename V>
+__device__ __forceinline__ void line_yfft(V (&v)[8], V *sm, const TileAddr &ad, const Geom &g, int j,
+                                          bool in_regs, bool out_regs, const StageTw<V> &tw) {
+    if constexpr (LY > 0) fft_run_t<S, LY>(v, sm, ad, j, true, in_regs, out_regs, tw, BlockBarrier());
+    else fft_run<S>(v, sm, ad, g.lQy, j, true, in_regs, out_regs, tw);
+}
+
+// LY > 0: the kernel only serves plans with Qz = 1 and Qy = 2^LY.
+template <typename R, int MODE, int MAXT, int LY = 0>
 __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1) k_line(const Geom g, const LineArgs<R> a) {
     using V = typename VT<R>::V;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -581,7 +591,7 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
     const LineMap mp = line_map(g, threadIdx.x);
     const TileAddr ady{mp.zq * g.Qy * g.wp + mp.w, g.wp};
     const TileAddr adz{mp.yq * g.wp + mp.w, g.Qy * g.wp};
-    const bool two_axes = g.Qz > 1;
+    const bool two_axes = LY == 0 && g.Qz > 1;
     const int kpy = kp % g.Py, kpz = kp / g.Py;
     V vt[8], vc[8];
 
@@ -590,14 +600,14 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
         const V *C = reinterpret_cast<const V *>(a.c) + (size_t)field * g.nhalf;
 #pragma unroll
         for (int m = 0; m < 8; ++m) vc[m] = C[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)];
-        fft_run<-1>(vc, Cs, ady, g.lQy, mp.jy, true, true, false, a.st);
+        line_yfft<-1, LY>(vc, Cs, ady, g, mp.jy, true, false, a.st);
         if (two_axes) fft_run<-1>(vc, Cs, adz, g.lQz, mp.jz, true, false, false, a.st);
     }
     if (MODE == LINE_STEP || MODE == LINE_FWD) {
         const V *X = reinterpret_cast<const V *>(a.x) + (size_t)field * g.nhalf;
 #pragma unroll
         for (int m = 0; m < 8; ++m) vt[m] = X[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)];
-        fft_run<-1>(vt, T, ady, g.lQy, mp.jy, true, true, !two_axes, a.st);
+        line_yfft<-1, LY>(vt, T, ady, g, mp.jy, true, !two_axes, a.st);
         if (two_axes) fft_run<-1>(vt, T, adz, g.lQz, mp.jz, true, false, true, a.st);
     }
 
@@ -619,7 +629,7 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
     }
 
     if (MODE == LINE_STEP) {
-        OpR<R> op = a.up.op[field == 0 ? 0 : 1];
+        OpR<R> op = field == 0 ? a.up.op[0] : a.up.op[1];
         if (a.rmem) op.r = a.rmem[field];
         const R invQ = a.up.invQ, inv_halfN = a.up.inv_halfN, dt = a.up.dt;
         const R cy = a.up.cy, cz = a.up.cz;
@@ -662,9 +672,9 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
     // inverse: the last forward axis first, from registers
     if (two_axes) {
         fft_run<+1>(vt, T, adz, g.lQz, mp.jz, true, true, false, a.st);
-        fft_run<+1>(vt, T, ady, g.lQy, mp.jy, true, false, true, a.st);
+        line_yfft<+1, LY>(vt, T, ady, g, mp.jy, false, true, a.st);
     } else {
-        fft_run<+1>(vt, T, ady, g.lQy, mp.jy, true, true, true, a.st);
+        line_yfft<+1, LY>(vt, T, ady, g, mp.jy, true, true, a.st);
     }
     V *Xo = reinterpret_cast<V *>(a.x) + (size_t)field * g.nhalf;
     const R sc = MODE == LINE_INV ? a.scale : (R)1;
