@@ -125,7 +125,8 @@ pfc_status pfc_set_r(pfc_plan *plan, int field, double r);
 pfc_status pfc_sync(pfc_plan *plan);
 
 /* Tile choice and memory of a plan (host out-params).
- *   tiles[8] = {Py, Pz, Qy, Qz, W, row_groups_per_cta, threads_row, threads_line}
+ *   tiles[9] = {Py, Pz, Qy, Qz, W, row_groups_per_cta, threads_row, threads_line,
+ *               row_cluster}   (row_cluster: blocks per cluster of the psi^3 row pass, 0 = none)
  *   scratch_bytes = device bytes the plan owns. */
 pfc_status pfc_plan_info(pfc_plan *plan, int32_t *tiles, int64_t *scratch_bytes);
 

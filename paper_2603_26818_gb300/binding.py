@@ -215,10 +215,10 @@ class Plan:
         return dict(zip(["row", "line", "entry", "exit"], list(ms))), nl.value
 
     def info(self):
-        tiles = (ctypes.c_int32 * 8)()
+        tiles = (ctypes.c_int32 * 9)()
         sb = ctypes.c_int64()
         check(load_library().pfc_plan_info(self._h, tiles, ctypes.byref(sb)))
-        keys = ["Py", "Pz", "Qy", "Qz", "W", "gpc", "threads_row", "threads_line"]
+        keys = ["Py", "Pz", "Qy", "Qz", "W", "gpc", "threads_row", "threads_line", "row_cluster"]
         d = dict(zip(keys, list(tiles)))
         d["scratch_bytes"] = sb.value
         return d

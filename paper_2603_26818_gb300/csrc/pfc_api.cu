@@ -93,7 +93,11 @@ template <typename R> LineArgs<R> line_args(const pfc_plan *p) {
 }
 
 LaunchCfg cfg(const pfc_plan *p) {
-    return LaunchCfg{p->t.g, p->t.nt_row, p->t.nt_line, p->t.smem_row, p->t.smem_line, p->stream};
+    LaunchCfg c{p->t.g, p->t.nt_row, p->t.nt_line, p->t.smem_row, p->t.smem_line, p->stream};
+    c.row_cs = p->t.row_cs;
+    c.nt_row_cs = p->t.nt_row_cs;
+    c.smem_row_cs = p->t.smem_row_cs;
+    return c;
 }
 
 template <typename R> void launch_row_m(const pfc_plan *p, int mode, const RowArgs<R> &a, int nf) {
@@ -611,7 +615,7 @@ pfc_status pfc_plan_info(pfc_plan *p, int32_t *tiles, int64_t *scratch_bytes) {
     if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
     const Geom &g = p->t.g;
     if (tiles) {
-        const int32_t v[8] = {g.Py, g.Pz, g.Qy, g.Qz, g.W, g.gpc, p->t.nt_row, p->t.nt_line};
+        const int32_t v[9] = {g.Py, g.Pz, g.Qy, g.Qz, g.W, g.gpc, p->t.nt_row, p->t.nt_line, p->t.row_cs};
         std::memcpy(tiles, v, sizeof(v));
     }
     if (scratch_bytes) *scratch_bytes = (int64_t)p->scratch;

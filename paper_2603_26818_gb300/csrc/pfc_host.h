@@ -90,6 +90,8 @@ struct Tiles {
     Geom g;
     int nt_row, nt_line;
     size_t smem_row, smem_line;
+    int row_cs = 0, nt_row_cs = 0;   // ROW_CUBE split over clusters of row_cs blocks (0: off)
+    size_t smem_row_cs = 0;
 };
 
 // Choose the split of the y/z transforms between the passes and the tile widths.
@@ -179,6 +181,17 @@ inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, s
     const int64_t QW = (int64_t)g.Q * g.W;
     t.nt_line = (int)(QW / 8);
     t.smem_line = (size_t)ntile * (size_t)g.Q * g.wp * vb;
+    // A group of eight FP32 rows too large for two blocks per SM is split over a cluster of two
+    // blocks of four rows each, 2 M/8 threads per block (PFC_ROW_CLUSTER=0 turns this off).
+    t.row_cs = 0;
+    const char *rc = std::getenv("PFC_ROW_CLUSTER");
+    const bool rc_on = !(rc && rc[0] == '0');
+    if (rc_on && vb == 8 && g.Pz == 1 && g.Py == 8 && gpc == 1 && 2 * t.smem_row > smem_max &&
+        Tr >= 32 && 2 * Tr <= 512) {
+        t.row_cs = 2;
+        t.nt_row_cs = 2 * Tr;
+        t.smem_row_cs = (size_t)round_up((int64_t)4 * row_bytes + 8 * vb, 16);
+    }
     return true;
 }
 

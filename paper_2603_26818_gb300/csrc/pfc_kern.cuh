@@ -4,6 +4,7 @@
 
 #include "pfc_launch.h"
 #include "pfc_reduce.cuh"
+#include "pfc_row_cluster.cuh"
 
 namespace pfc {
 
@@ -12,6 +13,12 @@ template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
 }
 
 template <typename R> void launch_row(const LaunchCfg &c, int mode, const RowArgs<R> &a, int nf) {
+    if constexpr (sizeof(R) == 4) {
+        if (mode == ROW_CUBE && c.row_cs == 2) {
+            k_row_cube_cl<R, 2><<<dim3(2 * c.g.Q, nf), c.nt_row_cs, c.smem_row_cs, c.stream>>>(c.g, a);
+            return;
+        }
+    }
     dim3 grid(c.g.Q / c.g.gpc, nf);
     if (mode == ROW_CUBE) k_row<R, ROW_CUBE><<<grid, c.nt_row, c.smem_row, c.stream>>>(c.g, a);
     else if (mode == ROW_FWD) k_row<R, ROW_FWD><<<grid, c.nt_row, c.smem_row, c.stream>>>(c.g, a);
@@ -56,6 +63,10 @@ template <typename R> cudaError_t set_smem_attrs(const LaunchCfg &c) {
         if ((e = allow_smem(k_line<R, LINE_STEP, 1024>, c.smem_line)) != cudaSuccess) return e;
         if ((e = allow_smem(k_line<R, LINE_FWD, 1024>, c.smem_line)) != cudaSuccess) return e;
         if ((e = allow_smem(k_line<R, LINE_INV, 1024>, c.smem_line)) != cudaSuccess) return e;
+    }
+    if constexpr (sizeof(R) == 4) {
+        if (c.row_cs == 2 &&
+            (e = allow_smem(k_row_cube_cl<R, 2>, c.smem_row_cs)) != cudaSuccess) return e;
     }
     return set_smem_attrs_fixed<R>(c);
 }

@@ -16,6 +16,9 @@ struct LaunchCfg {
     int nt_row, nt_line;
     size_t smem_row, smem_line;
     cudaStream_t stream;
+    // ROW_CUBE over clusters of row_cs blocks (k_row_cube_cl, FP32 only); 0: single blocks
+    int row_cs = 0, nt_row_cs = 0;
+    size_t smem_row_cs = 0;
 };
 
 constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs

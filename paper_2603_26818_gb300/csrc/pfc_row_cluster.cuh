@@ -1,0 +1,161 @@
+// Row pass psi^3 (ROW_CUBE) with one row group split over a cluster of CS thread blocks.
+//
+// The single-block row kernel keeps all P rows of its group in shared memory. With Py = 8 rows of
+// nx = 4096 (18 KB each in FP32) that is 147 KB, so only one block fits an SM and its load,
+// transform and store phases cannot overlap with another block's. Here the CS blocks of a cluster
+// share the group: block h keeps rows y_p in [h Py/CS, (h+1) Py/CS) in its own shared memory, so
+// two blocks (of two different groups) fit an SM. Phase B (load of X', y twiddle, inverse P-part
+// across the Py rows, real-transform pre-processing) and phase D (post-processing, forward
+// P-part, twiddle, store of C') give each thread all Py rows of one column pair; the rows held by
+// the other blocks of the cluster are written and read through distributed shared memory. The
+// blocks split the column pairs between them. The per-row transforms and psi^3 are the single-
+// block kernel's, on the block's own rows. Used for Pz = 1, Py = 8, one group per cluster.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "pfc_pass.cuh"
+
+namespace pfc {
+
+constexpr int ROWCL_PY = 8;
+
+template <typename R, int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
+    k_row_cube_cl(const Geom g, const RowArgs<R> a) {
+    using V = typename VT<R>::V;
+    namespace cg = cooperative_groups;
+    constexpr int RPC = ROWCL_PY / CS;   // rows per block
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V *sm = reinterpret_cast<V *>(smraw);
+    const cg::cluster_group cl = cg::this_cluster();
+    const int h = (int)cl.block_rank();
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int field = blockIdx.y;
+    const int M = g.M, lM = g.lM, hM = M >> 1;
+    const int grp = blockIdx.x / CS;
+    const R mean = a.mean ? (R)a.mean[field] : (R)0;
+    V *stw = sm + RPC * g.rs;   // split twiddles of the group's Py rows
+    for (int t = tid; t < ROWCL_PY; t += nt) stw[t] = split_twiddle(g, a.tw, grp, 0, t);
+    V *rows[CS];                // row 0 of each block of the cluster (generic addresses)
+#pragma unroll
+    for (int c = 0; c < CS; ++c) rows[c] = cl.map_shared_rank(sm, c);
+    // every block has started (its shared memory exists) and stw is visible
+    cl.sync();
+
+    // ---- phase B: this block's share of the column pairs (kk, M - kk), kk in [0, M/2) ----
+    {
+        const V *X = reinterpret_cast<const V *>(a.in) + (size_t)field * g.nhalf;
+        V *pw = reinterpret_cast<V *>(a.proj) + (size_t)field * g.nhalf;
+        const int per = hM / CS;
+        for (int e = tid; e < per; e += nt) {
+            const int kk = h * per + e;
+            const int npass = kk == 0 ? 2 : 1;   // kk = 0: the pair (0, M), then the column M/2
+#pragma unroll 1
+            for (int pp = 0; pp < npass; ++pp) {
+                const bool k0 = kk == 0 && pp == 0;
+                const int ca = pp ? hM : kk, cb = pp ? hM : (kk == 0 ? M : M - kk);
+                V va[ROWCL_PY], vb[ROWCL_PY];
+#pragma unroll
+                for (int yy = 0; yy < ROWCL_PY; ++yy) {
+                    const V *src = X + (size_t)(yy * g.Q + grp) * g.xs;
+                    const V w = stw[yy];
+                    va[yy] = ctw<+1>(src[ca], w);
+                    vb[yy] = ctw<+1>(src[cb], w);
+                }
+                dft8<+1>(va);
+                dft8<+1>(vb);
+                const V w = __ldg(&a.tw[ca << (g.ltab - g.lnx)]);
+#pragma unroll
+                for (int yy = 0; yy < ROWCL_PY; ++yy) {
+                    V za, zb;
+                    c2r_pre_pair<V, R>(va[yy], vb[yy], w, k0, za, zb);
+                    V *dst = rows[yy / RPC] + (yy % RPC) * g.rs;
+                    dst[row_pad(ca)] = za;
+                    if (!k0 && cb != ca) dst[row_pad(cb)] = zb;
+                }
+                if (k0 && a.proj) {
+                    // Hermitian projection of the kx = 0 and nx/2 columns (see
+                    // project_edge_columns): X' = DFT_P(real parts of the row values) / P
+#pragma unroll
+                    for (int yy = 0; yy < ROWCL_PY; ++yy) {
+                        va[yy].y = (R)0;
+                        vb[yy].y = (R)0;
+                    }
+                    dft8<-1>(va);
+                    dft8<-1>(vb);
+                    const R invP = (R)1 / (R)ROWCL_PY;
+#pragma unroll
+                    for (int yy = 0; yy < ROWCL_PY; ++yy) {
+                        V *dst = pw + (size_t)(yy * g.Q + grp) * g.xs;
+                        dst[0] = cscale(cmul(va[yy], stw[yy]), invP);
+                        dst[M] = cscale(cmul(vb[yy], stw[yy]), invP);
+                    }
+                }
+            }
+        }
+    }
+    cl.sync();
+
+    // ---- per-row transforms and psi^3 on this block's rows ----
+    {
+        const int Tr = M >> 3;
+        const int RB = nt / Tr;
+        const bool grouped = Tr >= 32 && RB <= 15 && RPC % RB == 0;
+        const int gidx = tid / Tr;
+        const NamedBarrier nbar{1 + gidx, Tr};
+        for (int rb = 0; rb < RPC; rb += RB) {
+            const int r = rb + gidx, j = tid % Tr;
+            const bool act = r < RPC;
+            const RowAddr ad{r * g.rs};
+            V v[8];
+            if (grouped) fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st, nbar);
+            else fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const R p0 = v[m].x + mean, p1 = v[m].y + mean;
+                v[m] = V{p0 * p0 * p0, p1 * p1 * p1};
+            }
+            if (grouped) fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.st, nbar);
+            else fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.st);
+        }
+    }
+    cl.sync();
+
+    // ---- phase D: this block's share of the column pairs ----
+    {
+        V *out = reinterpret_cast<V *>(a.out) + (size_t)field * g.nhalf;
+        const int per = hM / CS;
+        for (int e = tid; e < per; e += nt) {
+            const int kk = h * per + e;
+            const int npass = kk == 0 ? 2 : 1;
+#pragma unroll 1
+            for (int pp = 0; pp < npass; ++pp) {
+                const bool k0 = kk == 0 && pp == 0;
+                const int ca = pp ? hM : kk, cb = pp ? hM : (kk == 0 ? M : M - kk);
+                const V w = __ldg(&a.tw[ca << (g.ltab - g.lnx)]);
+                V va[ROWCL_PY], vb[ROWCL_PY];
+#pragma unroll
+                for (int yy = 0; yy < ROWCL_PY; ++yy) {
+                    const V *src = rows[yy / RPC] + (yy % RPC) * g.rs;
+                    const V za = src[row_pad(ca)];
+                    const V zb = (k0 || cb == ca) ? za : src[row_pad(cb)];
+                    r2c_post_pair<V, R>(za, zb, w, k0, va[yy], vb[yy]);
+                }
+                dft8<-1>(va);
+                dft8<-1>(vb);
+#pragma unroll
+                for (int yy = 0; yy < ROWCL_PY; ++yy) {
+                    const V t = stw[yy];
+                    V *dst = out + (size_t)(yy * g.Q + grp) * g.xs;
+                    dst[ca] = cscale(cmul(va[yy], t), a.scale);
+                    if (cb != ca) dst[cb] = cscale(cmul(vb[yy], t), a.scale);
+                }
+            }
+        }
+    }
+    // no block leaves while another may still read its rows
+    cl.sync();
+}
+
+}  // namespace pfc

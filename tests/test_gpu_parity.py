@@ -175,3 +175,30 @@ def test_long_single_call_3d_split_plan_stays_finite():
         p.step(y, 100)
     a, b = x.double().cpu().numpy(), y.double().cpu().numpy()
     assert np.isfinite(a).all() and rel(a, b) <= 1e-3
+
+
+def test_row_cluster_path_at_4096sq_matches_single_blocks_and_oracle(monkeypatch):
+    """4096^2 FP32 (Py = 8): the psi^3 row pass runs on clusters of two blocks, each holding four
+    of the group's eight rows and reaching the others through distributed shared memory. The same
+    operations as the single-block row pass (the compiler may contract them into FMAs
+    differently, so agreement is to rounding, not bitwise); and both match the oracle after 3
+    steps (polycrystal input of the bench workload)."""
+    shape, dx, dt, nsteps = (4096, 4096), math.pi / 4, 0.5, 3
+    psi0 = inputs.polycrystal_2d(4096, 4096, dx, -0.25, 64, 0.2, 1.0, 0.01, seed=11)
+    monkeypatch.delenv("PFC_ROW_CLUSTER", raising=False)
+    p = plan(shape, dx, dt, ONE, "fp32")
+    assert p.info()["row_cluster"] == 2
+    x = to_dev(psi0, "fp32")
+    p.step(x, nsteps)
+    p.close()
+    monkeypatch.setenv("PFC_ROW_CLUSTER", "0")
+    q = plan(shape, dx, dt, ONE, "fp32")
+    assert q.info()["row_cluster"] == 0
+    y = to_dev(psi0, "fp32")
+    q.step(y, nsteps)
+    q.close()
+    a, b = x.double().cpu().numpy(), y.double().cpu().numpy()
+    ref = oracle.step(psi0, dx, dt, ONE, nsteps)
+    print("cluster vs single", rel(a, b), "cluster vs oracle", rel(a, ref), "single vs oracle", rel(b, ref))
+    assert rel(a, b) <= 1e-6
+    assert rel(a, ref) <= 1e-5 and rel(b, ref) <= 1e-5
