@@ -38,10 +38,10 @@ __global__ void __launch_bounds__(512) k_line_adj(const Geom g, const AdjArgs<R>
     V *sm = reinterpret_cast<V *>(smraw);
     const int cg = blockIdx.x, kp = blockIdx.y;
     V *T = sm;
-    V *Cs = sm + g.Q * g.wp;
+    V *Cs = sm + g.tsz;
     const LineMap mp = line_map(g, threadIdx.x);
-    const TileAddr ady{mp.zq * g.Qy * g.wp + mp.w, g.wp};
-    const TileAddr adz{mp.yq * g.wp + mp.w, g.Qy * g.wp};
+    const PadTileAddr ady = tile_y(g, mp);
+    const TileAddr adz = tile_z(g, mp);
     const bool two_axes = g.Qz > 1;
     const int kpy = kp % g.Py, kpz = kp / g.Py;
     V v[8];
@@ -54,9 +54,6 @@ __global__ void __launch_bounds__(512) k_line_adj(const Geom g, const AdjArgs<R>
         fft_run<-1>(v, tile, ady, g.lQy, mp.jy, true, true, to_regs && !two_axes, a.st);
         if (two_axes) fft_run<-1>(v, tile, adz, g.lQz, mp.jz, true, false, to_regs, a.st);
     };
-    // smem position of register slot m after a forward transform into registers
-    const int pbase = two_axes ? adz.at(mp.jz) : ady.at(mp.jy);
-    const int pstep = two_axes ? mp.nz8 * adz.stride : mp.ny8 * ady.stride;
 
     // multipliers a, b of register slot m
     const int kx = cg * g.W + mp.w;
@@ -81,10 +78,11 @@ __global__ void __launch_bounds__(512) k_line_adj(const Geom g, const AdjArgs<R>
     for (int m = 0; m < 8; ++m) {
         R ca, cb;
         mult(m, ca, cb);
-        const V n = Cs[pbase + m * pstep];
+        const int pos = tile_slot(mp, two_axes, ady, adz, m);
+        const V n = Cs[pos];
         const R s = ca * a.PM;
         const V p1 = V{s * v[m].x - cb * n.x, s * v[m].y - cb * n.y};
-        Cs[pbase + m * pstep] = V{-cb * p1.x, -cb * p1.y};
+        Cs[pos] = V{-cb * p1.x, -cb * p1.y};
     }
     // 2. Lam_hat into registers; partial sum; B-input into Cs, A-input stays in registers
     forward(reinterpret_cast<const V *>(a.lam), T, true);
@@ -95,9 +93,10 @@ __global__ void __launch_bounds__(512) k_line_adj(const Geom g, const AdjArgs<R>
     for (int m = 0; m < 8; ++m) {
         R ca, cb;
         mult(m, ca, cb);
-        const V gv = Cs[pbase + m * pstep];
+        const int pos = tile_slot(mp, two_axes, ady, adz, m);
+        const V gv = Cs[pos];
         acc += (double)(wk * (v[m].x * gv.x + v[m].y * gv.y));
-        Cs[pbase + m * pstep] = V{cb * invQ * v[m].x, cb * invQ * v[m].y};
+        Cs[pos] = V{cb * invQ * v[m].x, cb * invQ * v[m].y};
         v[m] = V{ca * invQ * v[m].x, ca * invQ * v[m].y};
     }
     // 3. U' = inverse of the registers -> lam; V' = inverse of Cs -> psi

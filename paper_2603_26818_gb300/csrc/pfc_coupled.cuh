@@ -29,14 +29,14 @@ __global__ void __launch_bounds__(512) k_line_step2(const Geom g, const Step2Arg
     extern __shared__ __align__(16) unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
     const int cg = blockIdx.x, kp = blockIdx.y;
-    const int tsz = g.Q * g.wp;
+    const int tsz = g.tsz;
     V *T0 = sm;                 // psi transform
     V *T1 = sm + tsz;           // c transform (natural order)
     V *N0 = sm + 2 * tsz;       // psi^3 transform (natural order)
     V *N1 = sm + 3 * tsz;       // c^3 transform (natural order)
     const LineMap mp = line_map(g, threadIdx.x);
-    const TileAddr ady{mp.zq * g.Qy * g.wp + mp.w, g.wp};
-    const TileAddr adz{mp.yq * g.wp + mp.w, g.Qy * g.wp};
+    const PadTileAddr ady = tile_y(g, mp);
+    const TileAddr adz = tile_z(g, mp);
     const bool two_axes = g.Qz > 1;
     const int kpy = kp % g.Py, kpz = kp / g.Py;
     V v[8];
@@ -52,8 +52,6 @@ __global__ void __launch_bounds__(512) k_line_step2(const Geom g, const Step2Arg
     forward(reinterpret_cast<const V *>(a.x1), T1, false);
     forward(reinterpret_cast<const V *>(a.x0), T0, true);
 
-    const int pbase = two_axes ? adz.at(mp.jz) : ady.at(mp.jy);
-    const int pstep = two_axes ? mp.nz8 * adz.stride : mp.ny8 * ady.stride;
     const int kx = cg * g.W + mp.w;
     const R fx = a.up.cx * (R)kx;
     const R dt = a.up.dt, invQ = a.up.invQ, ihn = a.up.inv_halfN;
@@ -71,7 +69,7 @@ __global__ void __launch_bounds__(512) k_line_step2(const Geom g, const Step2Arg
         const R m22 = (R)1 + dk * lin_symbol<R>(a.up.op[1], k2);
         const R m12 = dk * a.alpha;
         const R idet = (R)1 / (m11 * m22 - m12 * m12);
-        const int pos = pbase + m * pstep;
+        const int pos = tile_slot(mp, two_axes, ady, adz, m);
         const V n0 = N0[pos], n1 = N1[pos], t1 = T1[pos];
         const V e1 = V{v[m].x * invQ - dk * ihn * n0.x, v[m].y * invQ - dk * ihn * n0.y};
         const V e2 = V{t1.x * invQ - dk * ihn * n1.x, t1.y * invQ - dk * ihn * n1.y};

@@ -107,11 +107,19 @@ struct RowAddr {
     template <int NS> __host__ __device__ static constexpr int ostep() { return NS >= 8 ? NS + NS / 8 : NS; }
 };
 
-// A column of an interleaved tile: element i at off + i * stride (the tile rows are padded by
-// the choice of row pitch, so no per-element padding is needed).
+// A column of an interleaved tile with a uniform stride: element i at off + i * stride.
 struct TileAddr {
     int off, stride;
     __device__ __forceinline__ int at(int i) const { return off + i * stride; }
+};
+
+// A column of an interleaved tile whose rows of w elements get one padding row after every 8
+// rows: element i at off + row_pad(i) w. For the transform index sets (see RowAddr) the address
+// is linear in m (or r) with steps RowAddr::step * w, and with tile rows of at least 16 bytes
+// every half-warp access of the transforms touches 16 distinct banks.
+struct PadTileAddr {
+    int off, w;
+    __device__ __forceinline__ int at(int i) const { return off + row_pad(i) * w; }
 };
 
 // Per-stage twiddle tables, laid out [r][k] so that the threads of a warp (consecutive k) read
@@ -193,6 +201,17 @@ __device__ __forceinline__ void load8_t(V (&v)[8], const V *sm, const RowAddr &a
     }
 }
 template <int N8, typename V>
+__device__ __forceinline__ void load8_t(V (&v)[8], const V *sm, const PadTileAddr &ad, int j) {
+    if (N8 >= 8) {
+        const int p = ad.at(j), st = RowAddr::step<N8>() * ad.w;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = sm[p + m * st];
+    } else {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = sm[ad.at(j + m * N8)];
+    }
+}
+template <int N8, typename V>
 __device__ __forceinline__ void load8_t(V (&v)[8], const V *sm, const TileAddr &ad, int j) {
     const int p = ad.at(j), st = N8 * ad.stride;
 #pragma unroll
@@ -206,6 +225,17 @@ __device__ __forceinline__ void store_group(const V *vals, V *sm, const RowAddr 
         const int p = ad.at(o);
 #pragma unroll
         for (int r = 0; r < R; ++r) sm[p + r * RowAddr::ostep<NS>()] = vals[r];
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) sm[ad.at(o + r * NS)] = vals[r];
+    }
+}
+template <int NS, int R, typename V>
+__device__ __forceinline__ void store_group(const V *vals, V *sm, const PadTileAddr &ad, int o) {
+    if (NS >= 8 || (NS == 1 && R == 8)) {
+        const int p = ad.at(o), st = RowAddr::ostep<NS>() * ad.w;
+#pragma unroll
+        for (int r = 0; r < R; ++r) sm[p + r * st] = vals[r];
     } else {
 #pragma unroll
         for (int r = 0; r < R; ++r) sm[ad.at(o + r * NS)] = vals[r];

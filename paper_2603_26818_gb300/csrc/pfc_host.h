@@ -84,7 +84,6 @@ inline OpDev to_dev(const pfc_op &o) { return OpDev{o.kind, o.r, o.R1, o.q2}; }
 
 // Row pitch of a line-pass tile: W columns of 128 B (16 float2 / 8 double2) spread over all
 // banks already; narrower tiles get one padding element per row.
-inline int tile_pitch(int W, size_t vb) { return (size_t)W * vb >= 128 ? W : W + 1; }
 
 struct Tiles {
     Geom g;
@@ -132,8 +131,7 @@ inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, s
                 if (W > g.M + 1 && W > 1) continue;
                 const int64_t QW = (int64_t)Q * W;
                 if (QW < 8 || QW / 8 > max_threads) continue;
-                const int wp = tile_pitch(W, vb);
-                const size_t tile = (size_t)Q * wp;
+                const size_t tile = (size_t)(Q + Q / 8) * W;   // one padding row per 8 rows
                 if ((size_t)ntile * tile * vb > smem_max) continue;
                 // 32-byte tile rows first (one DRAM sector per tile row), then blocks of at most
                 // 512 threads, nearest to 256 (several small blocks per SM interleave their load,
@@ -158,7 +156,7 @@ inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, s
     g.lPy = ilog2(g.Py); g.lPz = ilog2(g.Pz); g.lQy = ilog2(g.Qy); g.lQz = ilog2(g.Qz);
     g.P = g.Py * g.Pz; g.Q = g.Qy * g.Qz; g.lQ = ilog2(g.Q);
     g.lW = ilog2(g.W);
-    g.wp = tile_pitch(g.W, vb);
+    g.tsz = (g.Q + g.Q / 8) * g.W;
     g.xs = (int)round_up(g.M + 1, std::max(g.W, 2));
     g.ncg = g.xs / g.W;
     // row groups per CTA: enough rows for >= 256 threads, within smem and dividing Q
@@ -180,7 +178,7 @@ inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, s
     t.smem_row = (size_t)round_up((int64_t)rows * (row_bytes + vb) + 2 * gpc * g.P * (vb / 2), 16);
     const int64_t QW = (int64_t)g.Q * g.W;
     t.nt_line = (int)(QW / 8);
-    t.smem_line = (size_t)ntile * (size_t)g.Q * g.wp * vb;
+    t.smem_line = (size_t)ntile * (size_t)g.tsz * vb;
     // A group of eight FP32 rows too large for two blocks per SM is split over a cluster of two
     // blocks of four rows each, 2 M/8 threads per block (PFC_ROW_CLUSTER=0 turns this off).
     t.row_cs = 0;

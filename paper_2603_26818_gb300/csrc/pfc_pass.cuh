@@ -35,7 +35,7 @@ struct Geom {
     int P, Q, lQ;
     int ltab;                        // full twiddle table has 2^ltab entries
     int W, lW, ncg;                  // line pass: columns per tile, column groups
-    int wp;                          // line pass tile row pitch (W, or W + 1 against bank conflicts)
+    int tsz;                         // line pass tile size in elements, (Q + Q/8) W (see tile_y)
     int rs;                          // row pass smem row stride (elements)
     int gpc;                         // row groups per row-pass CTA
     int64_t nreal;                   // real values per field (N)
@@ -532,8 +532,8 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_row(const Geom 
 
 // ------------------------------------------------------------------------------------------
 // Line pass: one tile of Q = Qz Qy complex values x W columns per block, interleaved (w
-// fastest, row pitch wp), block = Q W / 8 threads. y-transforms use the thread map (w, j, z_q), z-transforms
-// (w, y_q, j). The first forward stage reads global memory into registers, the last forward
+// fastest, one padding row after every 8 tile rows), block = Q W / 8 threads. y-transforms use
+// the thread map (w, j, z_q), z-transforms (w, y_q, j). The first forward stage reads global memory into registers, the last forward
 // stage, the update and the first inverse stage stay in registers, and the last inverse stage
 // writes global memory from registers.
 // ------------------------------------------------------------------------------------------
@@ -565,6 +565,21 @@ __device__ __forceinline__ LineMap line_map(const Geom &g, int t) {
 }
 
 // X' element of tile element (z_q, y_q) in column w of tile (cg, kp).
+// Line tile layout: tile row q (W elements) at row_pad(q) W, one padding row after every 8 rows
+// (bank spreading, see PadTileAddr). Qy is a multiple of 8, so a y column (fixed z_q) and a z
+// column (fixed y_q) are:
+__device__ __forceinline__ PadTileAddr tile_y(const Geom &g, const LineMap &mp) {
+    return PadTileAddr{row_pad(mp.zq * g.Qy) * g.W + mp.w, g.W};
+}
+__device__ __forceinline__ TileAddr tile_z(const Geom &g, const LineMap &mp) {
+    return TileAddr{row_pad(mp.yq) * g.W + mp.w, row_pad(g.Qy) * g.W};
+}
+// smem position of register slot m after a forward transform that ends in registers
+__device__ __forceinline__ int tile_slot(const LineMap &mp, bool two_axes, const PadTileAddr &ady,
+                                         const TileAddr &adz, int m) {
+    return two_axes ? adz.at(mp.jz + m * mp.nz8) : ady.at(mp.jy + m * mp.ny8);
+}
+
 __device__ __forceinline__ size_t xprime_index(const Geom &g, int kp, int cg, int zq, int yq, int w) {
     return (size_t)(kp * g.Q + zq * g.Qy + yq) * g.xs + cg * g.W + w;
 }
@@ -572,7 +587,7 @@ __device__ __forceinline__ size_t xprime_index(const Geom &g, int kp, int cg, in
 // y transform of a line tile: length 2^LY fixed at compile time when LY > 0 (one-axis tiles;
 // straight-line code with no switch over lengths, fewer live registers), else the plan's length
 template <int S, int LY, typename V>
-__device__ __forceinline__ void line_yfft(V (&v)[8], V *sm, const TileAddr &ad, const Geom &g, int j,
+__device__ __forceinline__ void line_yfft(V (&v)[8], V *sm, const PadTileAddr &ad, const Geom &g, int j,
                                           bool in_regs, bool out_regs, const StageTw<V> &tw) {
     if constexpr (LY > 0) fft_run_t<S, LY>(v, sm, ad, j, true, in_regs, out_regs, tw, BlockBarrier());
     else fft_run<S>(v, sm, ad, g.lQy, j, true, in_regs, out_regs, tw);
@@ -585,12 +600,11 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
     extern __shared__ __align__(16) unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
     const int cg = blockIdx.x, kp = blockIdx.y, field = blockIdx.z;
-    const int tsz = g.Q * g.wp;
     V *T = sm;
-    V *Cs = sm + tsz;
+    V *Cs = sm + g.tsz;
     const LineMap mp = line_map(g, threadIdx.x);
-    const TileAddr ady{mp.zq * g.Qy * g.wp + mp.w, g.wp};
-    const TileAddr adz{mp.yq * g.wp + mp.w, g.Qy * g.wp};
+    const PadTileAddr ady = tile_y(g, mp);
+    const TileAddr adz = tile_z(g, mp);
     const bool two_axes = LY == 0 && g.Qz > 1;
     const int kpy = kp % g.Py, kpz = kp / g.Py;
     V vt[8], vc[8];
@@ -636,11 +650,9 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
         const int kx = cg * g.W + mp.w;
         const R fx = a.up.cx * (R)kx;
         // the C transform's outputs at this thread's register positions, read one at a time
-        const int cbase = two_axes ? adz.at(mp.jz) : ady.at(mp.jy);
-        const int cstep = two_axes ? mp.nz8 * adz.stride : mp.ny8 * ady.stride;
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
-            const V c = Cs[cbase + m * cstep];
+            const V c = Cs[tile_slot(mp, two_axes, ady, adz, m)];
             const int kqy = two_axes ? mp.yq : mp.jy + m * mp.ny8;
             const int kqz = two_axes ? mp.jz + m * mp.nz8 : 0;
             const int ky = kpy + (kqy << g.lPy), kz = kpz + (kqz << g.lPz);
