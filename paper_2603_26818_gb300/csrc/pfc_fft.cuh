@@ -94,17 +94,27 @@ template <int S, typename V> __device__ __forceinline__ void dft_small(V (&t)[8]
 // ------------------------------------------------------------------------------------------
 // Shared-memory addressing of one transform instance: element i lives at at(i).
 // ------------------------------------------------------------------------------------------
-// A row of a row buffer: one padding slot after every 8 elements (bank spreading). For the
-// index sets a transform touches (j + m n/8 with n/8 a multiple of 8, and the Stockham outputs
-// o + r Ns with Ns a multiple of 8, or o a multiple of 8 when Ns = 1), the padded address is
-// linear in m (or r), so the accessors compute one base and add compile-time steps.
+// One padding slot after every 8 elements (bank spreading of line tile rows, see PadTileAddr).
+// For the index sets a transform touches (j + m n/8 with n/8 a multiple of 8, and the Stockham
+// outputs o + r Ns with Ns a multiple of 8, or o a multiple of 8 when Ns = 1), the padded index
+// is linear in m (or r) with the steps below.
 __host__ __device__ __forceinline__ int row_pad(int i) { return i + (i >> 3); }
+template <int N8> __host__ __device__ constexpr int pad_step() { return N8 >= 8 ? N8 + N8 / 8 : N8; }
+template <int NS> __host__ __device__ constexpr int pad_ostep() { return NS >= 8 ? NS + NS / 8 : NS; }
+
+// A row of a row buffer, starting at element base (a multiple of 16). Element i lives at
+// base + row_swz(i), row_swz(i) = i ^ ((i >> 3) & 15): the XOR permutes each aligned block of 16
+// elements, so rows need no padding, and each index set the transforms and the pair phases
+// touch in one half-warp (16 consecutive elements, the stride-8 outputs of a first stage, the
+// 8-element runs of a second stage) lands on 16 distinct bank groups. (A padding slot per 8
+// elements leaves two-way conflicts on the consecutive sets.) When an index set has a stride
+// that is a multiple of 128, the XOR term is the same for all of its members and the accessors
+// add compile-time steps to one computed address.
+__host__ __device__ __forceinline__ int row_swz(int i) { return i ^ ((i >> 3) & 15); }
 
 struct RowAddr {
     int base;
-    __device__ __forceinline__ int at(int i) const { return base + row_pad(i); }
-    template <int N8> __host__ __device__ static constexpr int step() { return N8 >= 8 ? N8 + N8 / 8 : N8; }
-    template <int NS> __host__ __device__ static constexpr int ostep() { return NS >= 8 ? NS + NS / 8 : NS; }
+    __device__ __forceinline__ int at(int i) const { return base + row_swz(i); }
 };
 
 // A column of an interleaved tile with a uniform stride: element i at off + i * stride.
@@ -191,10 +201,10 @@ __device__ __forceinline__ void stage_exec(V (&v)[8], int lR, int lNs, int j, in
 // ------------------------------------------------------------------------------------------
 template <int N8, typename V>
 __device__ __forceinline__ void load8_t(V (&v)[8], const V *sm, const RowAddr &ad, int j) {
-    if (N8 >= 8) {
+    if (N8 % 128 == 0) {
         const int p = ad.at(j);
 #pragma unroll
-        for (int m = 0; m < 8; ++m) v[m] = sm[p + m * RowAddr::step<N8>()];
+        for (int m = 0; m < 8; ++m) v[m] = sm[p + m * N8];
     } else {
 #pragma unroll
         for (int m = 0; m < 8; ++m) v[m] = sm[ad.at(j + m * N8)];
@@ -203,7 +213,7 @@ __device__ __forceinline__ void load8_t(V (&v)[8], const V *sm, const RowAddr &a
 template <int N8, typename V>
 __device__ __forceinline__ void load8_t(V (&v)[8], const V *sm, const PadTileAddr &ad, int j) {
     if (N8 >= 8) {
-        const int p = ad.at(j), st = RowAddr::step<N8>() * ad.w;
+        const int p = ad.at(j), st = pad_step<N8>() * ad.w;
 #pragma unroll
         for (int m = 0; m < 8; ++m) v[m] = sm[p + m * st];
     } else {
@@ -221,10 +231,15 @@ __device__ __forceinline__ void load8_t(V (&v)[8], const V *sm, const TileAddr &
 // Store the R outputs o + r Ns (r < R) of one butterfly.
 template <int NS, int R, typename V>
 __device__ __forceinline__ void store_group(const V *vals, V *sm, const RowAddr &ad, int o) {
-    if (NS >= 8 || (NS == 1 && R == 8)) {   // NS = 1: o = 8 j', outputs at 9 j' + r
+    if (NS % 128 == 0) {
         const int p = ad.at(o);
 #pragma unroll
-        for (int r = 0; r < R; ++r) sm[p + r * RowAddr::ostep<NS>()] = vals[r];
+        for (int r = 0; r < R; ++r) sm[p + r * NS] = vals[r];
+    } else if (NS == 1 && R == 8) {
+        // o = 8 j': row_swz(o + r) = row_swz(o) ^ r, and base is a multiple of 16
+        const int p = ad.at(o);
+#pragma unroll
+        for (int r = 0; r < R; ++r) sm[p ^ r] = vals[r];
     } else {
 #pragma unroll
         for (int r = 0; r < R; ++r) sm[ad.at(o + r * NS)] = vals[r];
@@ -233,7 +248,7 @@ __device__ __forceinline__ void store_group(const V *vals, V *sm, const RowAddr 
 template <int NS, int R, typename V>
 __device__ __forceinline__ void store_group(const V *vals, V *sm, const PadTileAddr &ad, int o) {
     if (NS >= 8 || (NS == 1 && R == 8)) {
-        const int p = ad.at(o), st = RowAddr::ostep<NS>() * ad.w;
+        const int p = ad.at(o), st = pad_ostep<NS>() * ad.w;
 #pragma unroll
         for (int r = 0; r < R; ++r) sm[p + r * st] = vals[r];
     } else {

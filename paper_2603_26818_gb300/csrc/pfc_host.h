@@ -94,7 +94,7 @@ struct Tiles {
 };
 
 // Choose the split of the y/z transforms between the passes and the tile widths.
-//   row pass:  gpc groups of P = Py Pz rows of padded length row_pad(M) + 1
+//   row pass:  gpc groups of P = Py Pz rows of M + 1 elements (stride rounded up to 16)
 //   line pass: ntile tiles of Q W complex values (Q = ny nz / P), W columns each
 // Preference: wide line-pass rows (W * sizeof(V) up to 128 B), then the smallest P.
 inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, size_t smem_max) {
@@ -104,7 +104,7 @@ inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, s
     g.nx = nx; g.ny = ny; g.nz = nz; g.M = nx / 2;
     g.lnx = ilog2(nx); g.lny = ilog2(ny); g.lnz = ilog2(nz); g.lM = g.lnx - 1;
     g.ltab = std::max(g.lnx, std::max(g.lny, g.lnz));
-    g.rs = (int)round_up(row_pad(g.M) + 1, 2);
+    g.rs = (int)round_up(g.M + 1, 16);   // row_swz keeps each aligned block of 16
     const size_t row_bytes = (size_t)g.rs * vb;
     // PFC_TILE="Py,Pz,W" forces a tiling (used to compare tilings; rejected if it does not fit)
     int fpy = 0, fpz = 0, fw = 0;

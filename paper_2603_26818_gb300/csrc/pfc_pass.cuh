@@ -173,7 +173,7 @@ __device__ void row_phase_a(const Geom &g, typename VT<R>::V *sm, const typename
         dft_small<+1>(t, g.Pz);
 #pragma unroll
         for (int a = 0; a < 8; ++a)
-            if (a < g.Pz) sm[(gi * P + a * g.Py + kpy) * g.rs + row_pad(k)] = t[a];
+            if (a < g.Pz) sm[(gi * P + a * g.Py + kpy) * g.rs + row_swz(k)] = t[a];
     }
 }
 
@@ -200,8 +200,8 @@ __device__ __forceinline__ void row_pair_b(const Geom &g, typename VT<R>::V *sm,
                 b[yy] = ctw<+1>(src[cb], w);
             } else {
                 const int row = gi * P + zp * g.Py + yy;
-                a[yy] = sm[row * g.rs + row_pad(ca)];
-                b[yy] = sm[row * g.rs + row_pad(cb)];
+                a[yy] = sm[row * g.rs + row_swz(ca)];
+                b[yy] = sm[row * g.rs + row_swz(cb)];
             }
         }
     }
@@ -218,8 +218,8 @@ __device__ __forceinline__ void row_pair_b(const Geom &g, typename VT<R>::V *sm,
             }
             V za, zb;
             c2r_pre_pair<V, R>(a[yy], b[yy], w, k0, za, zb);
-            sm[row * g.rs + row_pad(ca)] = za;
-            if (!k0 && cb != ca) sm[row * g.rs + row_pad(cb)] = zb;
+            sm[row * g.rs + row_swz(ca)] = za;
+            if (!k0 && cb != ca) sm[row * g.rs + row_swz(cb)] = zb;
         }
     }
     if (FROM_GLOBAL && proj && k0) {
@@ -331,8 +331,8 @@ __device__ __forceinline__ void row_pair_d(const Geom &g, typename VT<R>::V *sm,
     for (int yy = 0; yy < 8; ++yy) {
         if (yy < g.Py) {
             const int row = gi * P + zp * g.Py + yy;
-            const V za = sm[row * g.rs + row_pad(ca)];
-            const V zb = (k0 || cb == ca) ? za : sm[row * g.rs + row_pad(cb)];
+            const V za = sm[row * g.rs + row_swz(ca)];
+            const V zb = (k0 || cb == ca) ? za : sm[row * g.rs + row_swz(cb)];
             r2c_post_pair<V, R>(za, zb, w, k0, a[yy], b[yy]);
         }
     }
@@ -348,8 +348,8 @@ __device__ __forceinline__ void row_pair_d(const Geom &g, typename VT<R>::V *sm,
                 if (cb != ca) dst[cb] = cscale(cmul(b[yy], t), scale);
             } else {
                 const int row = gi * P + zp * g.Py + yy;
-                sm[row * g.rs + row_pad(ca)] = a[yy];
-                if (cb != ca) sm[row * g.rs + row_pad(cb)] = b[yy];
+                sm[row * g.rs + row_swz(ca)] = a[yy];
+                if (cb != ca) sm[row * g.rs + row_swz(cb)] = b[yy];
             }
         }
     }
@@ -394,7 +394,7 @@ __device__ void row_phase_e(const Geom &g, const typename VT<R>::V *sm, typename
         V t[8];
 #pragma unroll
         for (int a = 0; a < 8; ++a)
-            if (a < g.Pz) t[a] = sm[(gi * P + a * g.Py + kpy) * g.rs + row_pad(k)];
+            if (a < g.Pz) t[a] = sm[(gi * P + a * g.Py + kpy) * g.rs + row_swz(k)];
         dft_small<-1>(t, g.Pz);
 #pragma unroll
         for (int a = 0; a < 8; ++a)
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_row(const Geom 
             V v = in[((size_t)z * g.ny + y) * M + i];
             v.x -= mean;
             v.y -= mean;
-            sm[r * g.rs + row_pad(i)] = v;
+            sm[r * g.rs + row_swz(i)] = v;
         }
     } else {
         const V *X = reinterpret_cast<const V *>(a.in) + (size_t)field * g.nhalf;

@@ -71,8 +71,8 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
                     V za, zb;
                     c2r_pre_pair<V, R>(va[yy], vb[yy], w, k0, za, zb);
                     V *dst = rows[yy / RPC] + (yy % RPC) * g.rs;
-                    dst[row_pad(ca)] = za;
-                    if (!k0 && cb != ca) dst[row_pad(cb)] = zb;
+                    dst[row_swz(ca)] = za;
+                    if (!k0 && cb != ca) dst[row_swz(cb)] = zb;
                 }
                 if (k0 && a.proj) {
                     // Hermitian projection of the kx = 0 and nx/2 columns (see
@@ -138,8 +138,8 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
 #pragma unroll
                 for (int yy = 0; yy < ROWCL_PY; ++yy) {
                     const V *src = rows[yy / RPC] + (yy % RPC) * g.rs;
-                    const V za = src[row_pad(ca)];
-                    const V zb = (k0 || cb == ca) ? za : src[row_pad(cb)];
+                    const V za = src[row_swz(ca)];
+                    const V zb = (k0 || cb == ca) ? za : src[row_swz(cb)];
                     r2c_post_pair<V, R>(za, zb, w, k0, va[yy], vb[yy]);
                 }
                 dft8<-1>(va);
