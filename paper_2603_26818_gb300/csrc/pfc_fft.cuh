@@ -124,8 +124,8 @@ struct TileAddr {
 };
 
 // A column of an interleaved tile whose rows of w elements get one padding row after every 8
-// rows: element i at off + row_pad(i) w. For the transform index sets (see RowAddr) the address
-// is linear in m (or r) with steps RowAddr::step * w, and with tile rows of at least 16 bytes
+// rows: element i at off + row_pad(i) w. For the transform index sets (see row_pad) the address
+// is linear in m (or r) with steps pad_step * w, and with tile rows of at least 16 bytes
 // every half-warp access of the transforms touches 16 distinct banks.
 struct PadTileAddr {
     int off, w;
@@ -310,6 +310,68 @@ __device__ __forceinline__ void fft_run_t(V (&v)[8], V *sm, const Addr &ad, int 
     if (NFULL > 2) stage_t<S, L, 3, (NFULL > 2 ? 6 : 0)>(v, sm, ad, j, act, true, !(NST == 3 && out_regs), tw, bar);
     if (NFULL > 3) stage_t<S, L, 3, (NFULL > 3 ? 9 : 0)>(v, sm, ad, j, act, true, !(NST == 4 && out_regs), tw, bar);
     if (LLAST) stage_t<S, L, (LLAST ? LLAST : 1), 3 * NFULL>(v, sm, ad, j, act, true, !out_regs, tw, bar);
+}
+
+// Ping-pong stage: the inputs come from src, the outputs go to a different buffer dst, so one
+// barrier (after the store) separates this stage's reads from the next stage's writes.
+template <int S, int L, int LR, int LNS, typename V, typename Addr, typename Bar>
+__device__ __forceinline__ void stage_pp_t(V (&v)[8], V *sm, const Addr &src, const Addr &dst, int j,
+                                           bool act, bool load, bool store, const StageTw<V> &tw,
+                                           const Bar &bar) {
+    constexpr int N8 = 1 << (L - 3);
+    if (act && load) load8_t<N8>(v, sm, src, j);
+    if (act) stage_exec<S>(v, LR, LNS, j, N8, tw);
+    if (!store) return;
+    if (act) stage_store_t<LR, LNS, N8>(v, sm, dst, j);
+    bar.sync();
+}
+
+// The transform of fft_run_t with its stages alternating between buffer A and a scratch buffer B
+// of the same shape: half the barriers of the in-place form. Exactly one of in_regs / out_regs:
+//   out_regs: the input is in A; the stores alternate B, A, B, ...; the result is left in v.
+//   in_regs:  the input is in v; the stores alternate so that the last one lands in A. A barrier
+//             is issued first, so other threads may still be reading A or B.
+template <int S, int L, typename V, typename Addr, typename Bar>
+__device__ __forceinline__ void fft_run_pp_t(V (&v)[8], V *sm, const Addr &A, const Addr &B, int j,
+                                             bool act, bool in_regs, bool out_regs,
+                                             const StageTw<V> &tw, const Bar &bar) {
+    constexpr int NFULL = L / 3;
+    constexpr int LLAST = L - 3 * NFULL;
+    constexpr int NST = NFULL + (LLAST ? 1 : 0);
+    const int nstore = NST - (out_regs ? 1 : 0);
+    auto dst = [&](int k) -> Addr {
+        const bool to_a = in_regs ? ((nstore - 1 - k) & 1) == 0 : (k & 1) != 0;
+        return to_a ? A : B;
+    };
+    auto src = [&](int k) -> Addr { return k == 0 ? A : dst(k - 1); };
+    if (in_regs) bar.sync();
+    stage_pp_t<S, L, 3, 0>(v, sm, src(0), dst(0), j, act, !in_regs, !(NST == 1 && out_regs), tw, bar);
+    if (NFULL > 1)
+        stage_pp_t<S, L, 3, (NFULL > 1 ? 3 : 0)>(v, sm, src(1), dst(1), j, act, true, !(NST == 2 && out_regs), tw, bar);
+    if (NFULL > 2)
+        stage_pp_t<S, L, 3, (NFULL > 2 ? 6 : 0)>(v, sm, src(2), dst(2), j, act, true, !(NST == 3 && out_regs), tw, bar);
+    if (NFULL > 3)
+        stage_pp_t<S, L, 3, (NFULL > 3 ? 9 : 0)>(v, sm, src(3), dst(3), j, act, true, !(NST == 4 && out_regs), tw, bar);
+    if (LLAST)
+        stage_pp_t<S, L, (LLAST ? LLAST : 1), 3 * NFULL>(v, sm, src(NFULL), dst(NFULL), j, act, true, !out_regs, tw, bar);
+}
+
+template <int S, typename V, typename Addr, typename Bar = BlockBarrier>
+__device__ __forceinline__ void fft_run_pp(V (&v)[8], V *sm, const Addr &A, const Addr &B, int L, int j,
+                                           bool act, bool in_regs, bool out_regs,
+                                           const StageTw<V> &tw, const Bar &bar = Bar()) {
+    switch (L) {
+        case 3: fft_run_pp_t<S, 3>(v, sm, A, B, j, act, in_regs, out_regs, tw, bar); break;
+        case 4: fft_run_pp_t<S, 4>(v, sm, A, B, j, act, in_regs, out_regs, tw, bar); break;
+        case 5: fft_run_pp_t<S, 5>(v, sm, A, B, j, act, in_regs, out_regs, tw, bar); break;
+        case 6: fft_run_pp_t<S, 6>(v, sm, A, B, j, act, in_regs, out_regs, tw, bar); break;
+        case 7: fft_run_pp_t<S, 7>(v, sm, A, B, j, act, in_regs, out_regs, tw, bar); break;
+        case 8: fft_run_pp_t<S, 8>(v, sm, A, B, j, act, in_regs, out_regs, tw, bar); break;
+        case 9: fft_run_pp_t<S, 9>(v, sm, A, B, j, act, in_regs, out_regs, tw, bar); break;
+        case 10: fft_run_pp_t<S, 10>(v, sm, A, B, j, act, in_regs, out_regs, tw, bar); break;
+        case 11: fft_run_pp_t<S, 11>(v, sm, A, B, j, act, in_regs, out_regs, tw, bar); break;
+        default: fft_run_pp_t<S, 12>(v, sm, A, B, j, act, in_regs, out_regs, tw, bar); break;
+    }
 }
 
 // One transform of n = 2^L points (3 <= L <= 12), run by every thread of the block (it contains

@@ -169,13 +169,13 @@ inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, s
     g.nreal = (int64_t)nx * ny * nz;
     g.nhalf = (int64_t)g.P * g.Q * g.xs;
     g.nstd = (int64_t)ny * nz * (g.M + 1);
-    t.g = g;
     const int rows = gpc * g.P;
     t.nt_row = std::min(max_row_threads, std::max(Tr, rows * Tr));
     if (t.nt_row < 64) t.nt_row = std::max(Tr, 64 / Tr * Tr);
     // rows, the split twiddles of the block's rows, then the saved real parts of the kx = 0
     // and nx/2 columns (2 gpc P reals)
     t.smem_row = (size_t)round_up((int64_t)rows * (row_bytes + vb) + 2 * gpc * g.P * (vb / 2), 16);
+    t.g = g;
     const int64_t QW = (int64_t)g.Q * g.W;
     t.nt_line = (int)(QW / 8);
     t.smem_line = (size_t)ntile * (size_t)g.tsz * vb;
@@ -184,11 +184,12 @@ inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, s
     t.row_cs = 0;
     const char *rc = std::getenv("PFC_ROW_CLUSTER");
     const bool rc_on = !(rc && rc[0] == '0');
-    if (rc_on && vb == 8 && g.Pz == 1 && g.Py == 8 && gpc == 1 && 2 * t.smem_row > smem_max &&
+    if (rc_on && vb == 8 && g.Pz == 1 && g.Py == 8 && gpc == 1 && 2 * (size_t)rows * row_bytes > smem_max &&
         Tr >= 32 && 2 * Tr <= 512) {
+        // four rows and one scratch row per row in flight (two) for ping-pong transforms
         t.row_cs = 2;
         t.nt_row_cs = 2 * Tr;
-        t.smem_row_cs = (size_t)round_up((int64_t)4 * row_bytes + 8 * vb, 16);
+        t.smem_row_cs = (size_t)round_up((int64_t)(4 + 2) * row_bytes + 8 * vb, 16);
     }
     return true;
 }

@@ -404,6 +404,16 @@ __device__ void row_phase_e(const Geom &g, const typename VT<R>::V *sm, typename
     }
 }
 
+// psi^3 of the 16 real values held in v (both halves of each complex slot), psi = v + mean
+template <typename V, typename R>
+__device__ __forceinline__ void cube_shifted(V (&v)[8], R mean) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const R p0 = v[m].x + mean, p1 = v[m].y + mean;
+        v[m] = V{p0 * p0 * p0, p1 * p1 * p1};
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // Row pass.
 //   ROW_CUBE  X' -> C' = F_p(psi^3), psi = (row inverse of X') + mean; X' edge columns projected
@@ -475,11 +485,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_row(const Geom 
         if (MODE == ROW_CUBE) {
             if (grouped) fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st, nbar);
             else fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st);
-#pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const R p0 = v[m].x + mean, p1 = v[m].y + mean;
-                v[m] = V{p0 * p0 * p0, p1 * p1 * p1};
-            }
+            cube_shifted(v, mean);
             if (grouped) fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.st, nbar);
             else fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.st);
         } else if (MODE == ROW_FWD) {

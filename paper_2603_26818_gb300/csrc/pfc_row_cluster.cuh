@@ -35,7 +35,11 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
     const int M = g.M, lM = g.lM, hM = M >> 1;
     const int grp = blockIdx.x / CS;
     const R mean = a.mean ? (R)a.mean[field] : (R)0;
-    V *stw = sm + RPC * g.rs;   // split twiddles of the group's Py rows
+    // smem: RPC rows | one scratch row per row in flight (ping-pong transforms) | split
+    // twiddles of the group's Py rows
+    const int Tr = M >> 3;
+    const int RB = nt / Tr;
+    V *stw = sm + (RPC + RB) * g.rs;
     for (int t = tid; t < ROWCL_PY; t += nt) stw[t] = split_twiddle(g, a.tw, grp, 0, t);
     V *rows[CS];                // row 0 of each block of the cluster (generic addresses)
 #pragma unroll
@@ -99,8 +103,6 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
 
     // ---- per-row transforms and psi^3 on this block's rows ----
     {
-        const int Tr = M >> 3;
-        const int RB = nt / Tr;
         const bool grouped = Tr >= 32 && RB <= 15 && RPC % RB == 0;
         const int gidx = tid / Tr;
         const NamedBarrier nbar{1 + gidx, Tr};
@@ -109,15 +111,13 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
             const bool act = r < RPC;
             const RowAddr ad{r * g.rs};
             V v[8];
-            if (grouped) fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st, nbar);
-            else fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st);
-#pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const R p0 = v[m].x + mean, p1 = v[m].y + mean;
-                v[m] = V{p0 * p0 * p0, p1 * p1 * p1};
-            }
-            if (grouped) fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.st, nbar);
-            else fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.st);
+            // ping-pong through this row group's scratch row
+            const RowAddr sc{(RPC + gidx) * g.rs};
+            if (grouped) fft_run_pp<+1>(v, sm, ad, sc, lM, j, act, false, true, a.st, nbar);
+            else fft_run_pp<+1>(v, sm, ad, sc, lM, j, act, false, true, a.st);
+            cube_shifted(v, mean);
+            if (grouped) fft_run_pp<-1>(v, sm, ad, sc, lM, j, act, true, false, a.st, nbar);
+            else fft_run_pp<-1>(v, sm, ad, sc, lM, j, act, true, false, a.st);
         }
     }
     cl.sync();
