@@ -133,6 +133,15 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def kernel_names(info):
+    """Names (as ncu prints them, without arguments) of the row and line kernels a plan runs."""
+    row = "k_row_cube_cl<float, 2>" if info.get("row_cluster") == 2 else "k_row<float, ROW_CUBE>"
+    ly = info["Qy"].bit_length() - 1
+    fixed = info["Qz"] == 1 and info["threads_line"] <= 512 and 6 <= ly <= 10
+    line = f"k_line<float, LINE_STEP, 512, {ly}>" if fixed else "k_line<float, LINE_STEP>"
+    return {"row": row, "line": line}
+
+
 def ncu_traffic(kernel_key):
     """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
@@ -290,7 +299,7 @@ def run_ours(args):
     dur = prof[dom] * 1e-3 / INNER
     peak, peak_kind = hbm_peak()
     achieved = alg[dom] / dur / 1e9
-    key = {"row": "k_row<float, ROW_CUBE>", "line": "k_line<float, LINE_STEP>"}[dom]
+    key = kernel_names(plan.info())[dom]
     roof = {"bound": "hbm", "kernel": key, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind, "traffic": ncu_traffic(key),
             "algorithmic_bytes_per_launch": alg[dom], "avg_launch_ms": dur * 1e3,
