@@ -20,6 +20,11 @@ namespace pfc {
 
 constexpr int ROWCL_PY = 8;
 
+// Cluster barrier without memory ordering (barrier.cluster.arrive.relaxed, then wait).
+__device__ __forceinline__ void cluster_sync_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+}
+
 template <typename R, int CS>
 __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
     k_row_cube_cl(const Geom g, const RowArgs<R> a) {
@@ -44,8 +49,11 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
     V *rows[CS];                // row 0 of each block of the cluster (generic addresses)
 #pragma unroll
     for (int c = 0; c < CS; ++c) rows[c] = cl.map_shared_rank(sm, c);
-    // every block has started (its shared memory exists) and stw is visible
-    cl.sync();
+    // stw visible in the block; every block of the cluster has started (its shared memory
+    // exists) before any block writes into it. Nothing is published across blocks yet, so the
+    // cluster barrier needs no release ordering.
+    __syncthreads();
+    cluster_sync_relaxed();
 
     // ---- phase B: this block's share of the column pairs (kk, M - kk), kk in [0, M/2) ----
     {
@@ -154,8 +162,10 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
             }
         }
     }
-    // no block leaves while another may still read its rows
-    cl.sync();
+    // no block leaves while another may still read its rows. Every read of phase D fed a store
+    // issued before this point, so a barrier without release ordering suffices (it does not wait
+    // for this block's global stores to complete).
+    cluster_sync_relaxed();
 }
 
 }  // namespace pfc
