@@ -196,8 +196,8 @@ __device__ __forceinline__ void row_pair_b(const Geom &g, typename VT<R>::V *sm,
             if (FROM_GLOBAL) {
                 const V *src = X + (size_t)(yy * g.Q + grp) * g.xs;
                 const V w = stw[gi * P + yy];
-                a[yy] = ctw<+1>(src[ca], w);
-                b[yy] = ctw<+1>(src[cb], w);
+                a[yy] = ctw<+1>(__ldcg(&src[ca]), w);
+                b[yy] = ctw<+1>(__ldcg(&src[cb]), w);
             } else {
                 const int row = gi * P + zp * g.Py + yy;
                 a[yy] = sm[row * g.rs + row_swz(ca)];
@@ -344,8 +344,8 @@ __device__ __forceinline__ void row_pair_d(const Geom &g, typename VT<R>::V *sm,
             if (g.Pz == 1) {
                 const V t = stw[gi * P + yy];
                 V *dst = out + (size_t)(yy * g.Q + grp) * g.xs;
-                dst[ca] = cscale(cmul(a[yy], t), scale);
-                if (cb != ca) dst[cb] = cscale(cmul(b[yy], t), scale);
+                __stcg(&dst[ca], cscale(cmul(a[yy], t), scale));
+                if (cb != ca) __stcg(&dst[cb], cscale(cmul(b[yy], t), scale));
             } else {
                 const int row = gi * P + zp * g.Py + yy;
                 sm[row * g.rs + row_swz(ca)] = a[yy];
@@ -586,6 +586,9 @@ __device__ __forceinline__ int tile_slot(const LineMap &mp, bool two_axes, const
     return two_axes ? adz.at(mp.jz + m * mp.nz8) : ady.at(mp.jy + m * mp.ny8);
 }
 
+// X' and C' are streamed once per pass: the passes read them with __ldcg and write them with
+// __stcg (cached in L2 only), so they do not evict the twiddle tables and register spills that
+// the transforms keep in L1.
 __device__ __forceinline__ size_t xprime_index(const Geom &g, int kp, int cg, int zq, int yq, int w) {
     return (size_t)(kp * g.Q + zq * g.Qy + yq) * g.xs + cg * g.W + w;
 }
@@ -619,14 +622,14 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
         // C' first, completely into smem (natural order), so that only one register set is live
         const V *C = reinterpret_cast<const V *>(a.c) + (size_t)field * g.nhalf;
 #pragma unroll
-        for (int m = 0; m < 8; ++m) vc[m] = C[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)];
+        for (int m = 0; m < 8; ++m) vc[m] = __ldcg(&C[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)]);
         line_yfft<-1, LY>(vc, Cs, ady, g, mp.jy, true, false, a.st);
         if (two_axes) fft_run<-1>(vc, Cs, adz, g.lQz, mp.jz, true, false, false, a.st);
     }
     if (MODE == LINE_STEP || MODE == LINE_FWD) {
         const V *X = reinterpret_cast<const V *>(a.x) + (size_t)field * g.nhalf;
 #pragma unroll
-        for (int m = 0; m < 8; ++m) vt[m] = X[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)];
+        for (int m = 0; m < 8; ++m) vt[m] = __ldcg(&X[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)]);
         line_yfft<-1, LY>(vt, T, ady, g, mp.jy, true, !two_axes, a.st);
         if (two_axes) fft_run<-1>(vt, T, adz, g.lQz, mp.jz, true, false, true, a.st);
     }
@@ -698,7 +701,7 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
     const R sc = MODE == LINE_INV ? a.scale : (R)1;
 #pragma unroll
     for (int m = 0; m < 8; ++m)
-        Xo[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)] = cscale(vt[m], sc);
+        __stcg(&Xo[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)], cscale(vt[m], sc));
 }
 
 }  // namespace pfc

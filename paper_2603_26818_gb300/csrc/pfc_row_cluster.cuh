@@ -72,8 +72,8 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
                 for (int yy = 0; yy < ROWCL_PY; ++yy) {
                     const V *src = X + (size_t)(yy * g.Q + grp) * g.xs;
                     const V w = stw[yy];
-                    va[yy] = ctw<+1>(src[ca], w);
-                    vb[yy] = ctw<+1>(src[cb], w);
+                    va[yy] = ctw<+1>(__ldcg(&src[ca]), w);
+                    vb[yy] = ctw<+1>(__ldcg(&src[cb]), w);
                 }
                 dft8<+1>(va);
                 dft8<+1>(vb);
@@ -156,8 +156,8 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
                 for (int yy = 0; yy < ROWCL_PY; ++yy) {
                     const V t = stw[yy];
                     V *dst = out + (size_t)(yy * g.Q + grp) * g.xs;
-                    dst[ca] = cscale(cmul(va[yy], t), a.scale);
-                    if (cb != ca) dst[cb] = cscale(cmul(vb[yy], t), a.scale);
+                    __stcg(&dst[ca], cscale(cmul(va[yy], t), a.scale));
+                    if (cb != ca) __stcg(&dst[cb], cscale(cmul(vb[yy], t), a.scale));
                 }
             }
         }
