@@ -17,6 +17,7 @@ Multi-GPU runs are independent replicas (the single-domain step has no data-para
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -128,7 +129,7 @@ def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2603_26818_gb300", "csrc")
     for n in sorted(os.listdir(csrc)):
-        if n.endswith((".cu", ".cuh")) and not n.startswith("cufft"):
+        if n.endswith((".cu", ".cuh")) and not n.startswith(("cufft", "peak_probe")):
             h.update(open(os.path.join(csrc, n), "rb").read())
     return h.hexdigest()[:16]
 
@@ -195,6 +196,21 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------- ours
+def fma_peaks():
+    """Measured plain-FMA rates of this GPU (libpfc_probe.so), TFLOP/s, or None."""
+    try:
+        lib = ctypes.CDLL(os.path.join(ROOT, "paper_2603_26818_gb300", "libpfc_probe.so"))
+    except OSError:
+        return None
+    out = {}
+    for name, fp64 in (("fp32_tflops", 0), ("fp64_tflops", 1)):
+        v = ctypes.c_double()
+        if lib.pfcp_fma_peak(fp64, ctypes.byref(v)) != 0:
+            return None
+        out[name] = v.value / 1e12
+    return out
+
+
 def time_cufft(torch, dev, psi0, precision, nsteps):
     """Vendor cuFFT plain step (baseline library), grid-point-steps/s."""
     import ctypes
@@ -348,6 +364,18 @@ def run_ours(args):
             "rel_l2_of_fluctuation": float((a.double() - b).norm() / fl),
             "mass_drift_rel_fp32": abs(plan.mass(a)[0] - m0) / abs(m0),
             "mass_drift_rel_fp64": abs(p64.mass(b)[0] - m0) / abs(m0)}
+        # ALU view: the transform flops of a step (5 log2 N per point for one r2c and one c2r,
+        # plus ~20 pointwise) against the measured plain-FMA rates; the FP64 path is bound there
+        peaks = fma_peaks()
+        if peaks:
+            fpp = 5 * math.log2(npts) + 20
+            extras["alu"] = {
+                "flops_per_point_step": fpp,
+                "fp32_path_tflops": value / world * fpp / 1e12, "fp32_fma_peak_tflops": peaks["fp32_tflops"],
+                "fp32_frac": value / world * fpp / 1e12 / peaks["fp32_tflops"],
+                "fp64_path_tflops": extras["ours_fp64"] * fpp / 1e12, "fp64_fma_peak_tflops": peaks["fp64_tflops"],
+                "fp64_frac": extras["ours_fp64"] * fpp / 1e12 / peaks["fp64_tflops"],
+                "peak_kind": "measured (libpfc_probe.so: 8 independent FMA chains per thread)"}
         line["context"] = extras
         p64.close()
 

@@ -1,8 +1,9 @@
 """Compile the CUDA library libpfc.so (sm_103a) in-tree with nvcc.
 
-One translation unit holds the pass kernels and the C ABI of include/pfc.h; the vendor cuFFT
+Several translation units hold the pass kernels and the C ABI of include/pfc.h; the vendor cuFFT
 plain-step baseline is a separate library, libpfc_cufft_baseline.so, so the product library
-does not link cuFFT. Both are built in parallel.
+does not link cuFFT, and the FMA-rate probe used by the bench is a third, libpfc_probe.so. All
+are built in parallel.
 """
 from __future__ import annotations
 
@@ -15,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpfc.so")
 BASELINE_LIB = os.path.join(HERE, "libpfc_cufft_baseline.so")
+PROBE_LIB = os.path.join(HERE, "libpfc_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -73,6 +75,9 @@ def build(force: bool = False) -> str:
     base_obj = os.path.join(objdir, "cufft_baseline.o")
     if force or _stale(base_obj, deps):
         jobs.append((os.path.join(CSRC, "cufft_baseline.cu"), base_obj))
+    probe_obj = os.path.join(objdir, "peak_probe.o")
+    if force or _stale(probe_obj, deps):
+        jobs.append((os.path.join(CSRC, "peak_probe.cu"), probe_obj))
     if jobs:
         with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
             list(ex.map(lambda j: _compile_obj(*j), jobs))
@@ -80,6 +85,8 @@ def build(force: bool = False) -> str:
         _link(LIB, objs, [])
     if force or jobs or not os.path.exists(BASELINE_LIB):
         _link(BASELINE_LIB, [base_obj], ["-lcufft"])
+    if force or jobs or not os.path.exists(PROBE_LIB):
+        _link(PROBE_LIB, [probe_obj], [])
     return LIB
 
 
