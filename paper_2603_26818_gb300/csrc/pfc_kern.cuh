@@ -15,7 +15,10 @@ template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
 template <typename R> void launch_row(const LaunchCfg &c, int mode, const RowArgs<R> &a, int nf) {
     if constexpr (sizeof(R) == 4) {
         if (mode == ROW_CUBE && c.row_cs == 2) {
-            k_row_cube_cl<R, 2><<<dim3(2 * c.g.Q, nf), c.nt_row_cs, c.smem_row_cs, c.stream>>>(c.g, a);
+            if (c.g.Pz == 1)
+                k_row_cube_cl<R, 2><<<dim3(2 * c.g.Q, nf), c.nt_row_cs, c.smem_row_cs, c.stream>>>(c.g, a);
+            else
+                k_row_cube_cl3<R><<<dim3(2 * c.g.Q, nf), c.nt_row_cs, c.smem_row_cs, c.stream>>>(c.g, a);
             return;
         }
     }
@@ -65,8 +68,10 @@ template <typename R> cudaError_t set_smem_attrs(const LaunchCfg &c) {
         if ((e = allow_smem(k_line<R, LINE_INV, 1024>, c.smem_line)) != cudaSuccess) return e;
     }
     if constexpr (sizeof(R) == 4) {
-        if (c.row_cs == 2 &&
+        if (c.row_cs == 2 && c.g.Pz == 1 &&
             (e = allow_smem(k_row_cube_cl<R, 2>, c.smem_row_cs)) != cudaSuccess) return e;
+        if (c.row_cs == 2 && c.g.Pz > 1 &&
+            (e = allow_smem(k_row_cube_cl3<R>, c.smem_row_cs)) != cudaSuccess) return e;
     }
     return set_smem_attrs_fixed<R>(c);
 }

@@ -169,3 +169,157 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
 }
 
 }  // namespace pfc
+
+namespace pfc {
+
+// The psi^3 row pass of a 3D plan with Pz = 8 on clusters of two blocks: block h keeps the rows
+// of z_p in [4h, 4h + 4) (4 Py rows), so that a group of 8 Py rows too large for two blocks per
+// SM is split in two. Phase A (z-part inverse from X') and phase E (z-part forward to C') give
+// each thread all eight z_p rows of one (k_py, column) item, the block's own and, through
+// distributed shared memory, the partner's; the items are split between the blocks. Phases B
+// and D (y-part and real-transform processing) and the row transforms touch only the block's
+// own rows. The real parts of the kx = 0 and nx/2 columns are gathered in block 0, which does
+// the Hermitian projection (project_edge_columns) for the group.
+template <typename R>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 2)
+    k_row_cube_cl3(const Geom g, const RowArgs<R> a) {
+    using V = typename VT<R>::V;
+    namespace cg = cooperative_groups;
+    constexpr int PZ = 8, ZPB = 4;   // z_p rows per block
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V *sm = reinterpret_cast<V *>(smraw);
+    const cg::cluster_group cl = cg::this_cluster();
+    const int h = (int)cl.block_rank();
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int field = blockIdx.y;
+    const int M = g.M, lM = g.lM, hM = M >> 1, Py = g.Py, P = g.P;
+    const int grp = blockIdx.x >> 1;
+    const int rows = ZPB * Py;
+    const R mean = a.mean ? (R)a.mean[field] : (R)0;
+    // smem: rows (z_p local, k_py or y_p) | split twiddles of the group (P) | edge values (2 P,
+    // used in block 0)
+    V *stw = sm + rows * g.rs;
+    R *edge = reinterpret_cast<R *>(stw + P);
+    for (int t = tid; t < P; t += nt) stw[t] = split_twiddle(g, a.tw, grp, t / Py, t % Py);
+    V *rowp[2];
+    rowp[0] = cl.map_shared_rank(sm, 0);
+    rowp[1] = cl.map_shared_rank(sm, 1);
+    R *edge0 = cl.map_shared_rank(edge, 0);
+    __syncthreads();
+    cluster_sync_relaxed();
+
+    const int main = Py << lM, cnt = main + Py, hc = (cnt + 1) >> 1;
+    const int e_end = (h + 1) * hc < cnt ? (h + 1) * hc : cnt;
+    // ---- phase A: z-part inverse of this block's share of the (k_py, column) items ----
+    {
+        const V *X = reinterpret_cast<const V *>(a.in) + (size_t)field * g.nhalf;
+        for (int e = h * hc + tid; e < e_end; e += nt) {
+            int k, kpy;
+            if (e < main) { k = e & (M - 1); kpy = e >> lM; }
+            else { k = M; kpy = e - main; }
+            V t[PZ];
+#pragma unroll
+            for (int zz = 0; zz < PZ; ++zz)
+                t[zz] = ctw<+1>(__ldcg(&X[(size_t)((zz * Py + kpy) * g.Q + grp) * g.xs + k]), stw[zz * Py + kpy]);
+            dft8<+1>(t);
+#pragma unroll
+            for (int zz = 0; zz < PZ; ++zz)
+                rowp[zz / ZPB][((zz % ZPB) * Py + kpy) * g.rs + row_swz(k)] = t[zz];
+        }
+    }
+    cl.sync();
+
+    // ---- phase B: y-part inverse and c2r pre-processing of the block's own rows ----
+    for (int e = tid; e < ZPB * hM; e += nt) {
+        const int kk = e % hM, zl = e / hM, zg = h * ZPB + zl;
+        const int npass = kk == 0 ? 2 : 1;
+#pragma unroll 1
+        for (int pp = 0; pp < npass; ++pp) {
+            const bool k0 = kk == 0 && pp == 0;
+            const int ca = pp ? hM : kk, cb = pp ? hM : (kk == 0 ? M : M - kk);
+            V va[8], vb[8];
+#pragma unroll
+            for (int yy = 0; yy < 8; ++yy) {
+                if (yy < Py) {
+                    const int row = zl * Py + yy;
+                    va[yy] = sm[row * g.rs + row_swz(ca)];
+                    vb[yy] = sm[row * g.rs + row_swz(cb)];
+                }
+            }
+            dft_small<+1>(va, Py);
+            dft_small<+1>(vb, Py);
+            const V w = __ldg(&a.tw[ca << (g.ltab - g.lnx)]);
+#pragma unroll
+            for (int yy = 0; yy < 8; ++yy) {
+                if (yy < Py) {
+                    const int row = zl * Py + yy;
+                    if (k0) {
+                        edge0[zg * Py + yy] = va[yy].x;
+                        edge0[P + zg * Py + yy] = vb[yy].x;
+                    }
+                    V za, zb;
+                    c2r_pre_pair<V, R>(va[yy], vb[yy], w, k0, za, zb);
+                    sm[row * g.rs + row_swz(ca)] = za;
+                    if (!k0 && cb != ca) sm[row * g.rs + row_swz(cb)] = zb;
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- row transforms and psi^3 on the block's rows ----
+    {
+        const int Tr = M >> 3;
+        const int RB = nt / Tr;
+        for (int rb = 0; rb < rows; rb += RB) {
+            const int r = rb + tid / Tr, j = tid % Tr;
+            const bool act = r < rows;
+            const RowAddr ad{r * g.rs};
+            V v[8];
+            fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st);
+            cube_shifted(v, mean);
+            fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.st);
+        }
+    }
+    __syncthreads();
+
+    // ---- phase D: c2r post-processing and y-part forward, rows (z_p, k_py) of the block ----
+    for (int e = tid; e < ZPB * hM; e += nt) {
+        const int kk = e % hM, zl = e / hM;
+        const int npass = kk == 0 ? 2 : 1;
+#pragma unroll 1
+        for (int pp = 0; pp < npass; ++pp) {
+            const bool k0 = kk == 0 && pp == 0;
+            const int ca = pp ? hM : kk, cb = pp ? hM : (kk == 0 ? M : M - kk);
+            row_pair_d<R>(g, sm, nullptr, 0, grp, zl, ca, cb, k0, a.tw, stw, a.scale);
+        }
+    }
+    cl.sync();
+
+    // ---- phase E: z-part forward of this block's share of the items, twiddle, store C' ----
+    {
+        V *out = reinterpret_cast<V *>(a.out) + (size_t)field * g.nhalf;
+        for (int e = h * hc + tid; e < e_end; e += nt) {
+            int k, kpy;
+            if (e < main) { k = e & (M - 1); kpy = e >> lM; }
+            else { k = M; kpy = e - main; }
+            V t[PZ];
+#pragma unroll
+            for (int zz = 0; zz < PZ; ++zz) t[zz] = rowp[zz / ZPB][((zz % ZPB) * Py + kpy) * g.rs + row_swz(k)];
+            dft8<-1>(t);
+#pragma unroll
+            for (int zz = 0; zz < PZ; ++zz)
+                __stcg(&out[(size_t)((zz * Py + kpy) * g.Q + grp) * g.xs + k],
+                       cscale(cmul(t[zz], stw[zz * Py + kpy]), a.scale));
+        }
+    }
+    // block 0 projects the edge columns (all 2 P edge values arrived before the cluster barrier
+    // that follows phase D)
+    if (h == 0 && a.proj) {
+        V *xw = reinterpret_cast<V *>(a.proj) + (size_t)field * g.nhalf;
+        project_edge_columns<R>(g, edge, grp, stw, xw);
+    }
+    cluster_sync_relaxed();
+}
+
+}  // namespace pfc

@@ -202,3 +202,28 @@ def test_row_cluster_path_at_4096sq_matches_single_blocks_and_oracle(monkeypatch
     print("cluster vs single", rel(a, b), "cluster vs oracle", rel(a, ref), "single vs oracle", rel(b, ref))
     assert rel(a, b) <= 1e-6
     assert rel(a, ref) <= 1e-5 and rel(b, ref) <= 1e-5
+
+
+def test_row_cluster_3d_path_matches_single_blocks_and_oracle(monkeypatch):
+    """A 3D plan with Py = Pz = 8 and rows of nx = 512 (nz = ny = 256): the psi^3 row pass runs
+    on two-block clusters split by z_p halves (z-parts through distributed shared memory, edge
+    values gathered in block 0 for the projection). Compared with the single-block row pass and
+    with the oracle after 2 two-mode steps."""
+    shape, dx, dt, nsteps = (256, 256, 512), math.pi / 4, 0.1, 2
+    psi0 = inputs.uniform_state(shape, -0.35, 0.02, seed=12)
+    monkeypatch.delenv("PFC_ROW_CLUSTER", raising=False)
+    p = plan(shape, dx, dt, TWO, "fp32")
+    assert p.info()["row_cluster"] == 2 and p.info()["Pz"] == 8
+    x = to_dev(psi0, "fp32")
+    p.step(x, nsteps)
+    p.close()
+    monkeypatch.setenv("PFC_ROW_CLUSTER", "0")
+    q = plan(shape, dx, dt, TWO, "fp32")
+    assert q.info()["row_cluster"] == 0
+    y = to_dev(psi0, "fp32")
+    q.step(y, nsteps)
+    q.close()
+    a, b = x.double().cpu().numpy(), y.double().cpu().numpy()
+    ref = oracle.step(psi0, dx, dt, TWO, nsteps)
+    assert rel(a, b) <= 1e-6
+    assert rel(a, ref) <= 1e-5 and rel(a - a.mean(), ref - ref.mean()) <= 1e-4
