@@ -50,7 +50,125 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / cuFFT context timings")
+    ap.add_argument("--config", choices=sorted(CONFIGS), default=None,
+                    help="time one of the other workloads instead of the 4096^2 headline (1 GPU)")
     return ap.parse_args()
+
+
+# The other workloads of the method, each timed with the same discipline (warm-up, CUDA events,
+# a 512 MiB L2 flush between timed steps) and reported against the HBM roofline at its modelled
+# bytes per grid point per step. Sweeps count full reads or writes of a half spectrum (or of the
+# real field): single-field step 5 (row 2, line 3); coupled pair 10 (row 2 x 2 fields, line
+# reads X0, X1, C0, C1 and writes X0, X1); adjoint step 17 (entry of psi_n 2, psi^3 row pass 2,
+# entry of lambda 2, adjoint line pass 3 reads + 2 writes, exit 2, 3 psi_n^2 mix 4).
+CONFIGS = {
+    "1": dict(desc="2D one-mode 128x128 FP64, dx=pi/4, dt=0.5, r=-0.25, psi0=-0.25+U[-0.01,0.01] "
+                   "(seed 1); 100 time steps per bench step (launch-bound, L2-resident)",
+              kind="plan", dims=(128, 128), prec="fp64", op=(0, -0.25, 0.0, 0.0), dt=0.5, inner=100,
+              sweeps=5),
+    "3": dict(desc="3D two-mode 512^3 FP32-mixed, dx=pi/4, dt=0.1, r=-0.3, R1=0.05, q2=sqrt(4/3), "
+                   "psi0=-0.35+U[-0.02,0.02] (seed 3); 10 time steps per bench step",
+              kind="plan", dims=(512, 512, 512), prec="fp32", op=(1, -0.3, 0.05, math.sqrt(4.0 / 3.0)),
+              dt=0.1, inner=10, sweeps=5),
+    "4a": dict(desc="1024 batched 2D one-mode domains, nx, ny from {64,128,256,512}, r~U[-0.4,-0.1], "
+                    "mean~U[-0.4,-0.2] (seed 4), noise 0.01, dt=0.5, FP32-mixed; 20 time steps per bench "
+                    "step (graph of per-size-class branches)",
+               kind="batch", prec="fp32", dt=0.5, inner=20, sweeps=5),
+    "4b": dict(desc="coupled density/composition pair 256^3 FP32-mixed, alpha=0.1, one-mode r=-0.25 "
+                    "for both, means -0.25/-0.2, noise 0.01 (seeds 5, 6), dt=0.5; 10 time steps per "
+                    "bench step", kind="pair", dims=(256, 256, 256), prec="fp32", dt=0.5, inner=10,
+               sweeps=10),
+    "5": dict(desc="adjoint step, 3D one-mode 256^3 FP32-mixed, dx=pi/4, dt=0.5, r=-0.25, "
+                   "psi0=-0.25+U[-0.01,0.01] (seed 6); 10 adjoint steps per bench step",
+              kind="adjoint", dims=(256, 256, 256), prec="fp32", op=(0, -0.25, 0.0, 0.0), dt=0.5,
+              inner=10, sweeps=17),
+    "5d": dict(desc="adjoint step, 3D one-mode 256^3 FP64, as config 5; 5 adjoint steps per bench step",
+               kind="adjoint", dims=(256, 256, 256), prec="fp64", op=(0, -0.25, 0.0, 0.0), dt=0.5,
+               inner=5, sweeps=17),
+}
+
+
+def run_config(args):
+    """Time one of CONFIGS on GPU 0 and print one JSON line."""
+    import numpy as np
+    import torch
+    from paper_2603_26818_gb300 import binding, inputs
+
+    c = CONFIGS[args.config]
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(0)
+    prec = c["prec"]
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    vb = 8 if prec == "fp64" else 4
+    extra = {}
+    if c["kind"] == "batch":
+        draws = inputs.batch_draws(1024, seed=4)
+        obj = binding.Batch([(d[0], d[1]) for d in draws], [d[2] for d in draws], DX, c["dt"], precision=prec)
+        parts = [inputs.uniform_state((ny, nx), m, 0.01, seed=1000 + i).ravel() for i, (ny, nx, r, m) in enumerate(draws)]
+        state = torch.from_numpy(np.concatenate(parts)).to(device=dev, dtype=dtype)
+        npts = state.numel()
+        run = lambda: obj.step(state, c["inner"])
+    elif c["kind"] == "pair":
+        shape = c["dims"]
+        p0 = inputs.uniform_state(shape, -0.25, 0.01, seed=5)
+        c0 = inputs.uniform_state(shape, -0.2, 0.01, seed=6)
+        ops = [binding.make_op(0, -0.25), binding.make_op(0, -0.25)]
+        obj = binding.Plan(shape, DX, c["dt"], ops, precision=prec, coupling=0.1)
+        state = torch.from_numpy(np.stack([p0, c0])).to(device=dev, dtype=dtype)
+        npts = p0.size
+        run = lambda: obj.step(state, c["inner"])
+    else:
+        shape = c["dims"]
+        seed = {"1": 1, "3": 3}.get(args.config, 6)
+        mean, amp = {"1": (-0.25, 0.01), "3": (-0.35, 0.02)}.get(args.config, (-0.25, 0.01))
+        psi0 = inputs.uniform_state(shape, mean, amp, seed=seed)
+        obj = binding.Plan(shape, DX, c["dt"], [binding.make_op(*c["op"])], precision=prec)
+        state = torch.from_numpy(psi0).to(device=dev, dtype=dtype)
+        npts = psi0.size
+        extra["plan"] = obj.info()
+        if c["kind"] == "plan":
+            run = lambda: obj.step(state, c["inner"])
+        else:
+            lam = state.clone()
+            lam_out = torch.empty_like(state)
+            dr = torch.zeros(1, dtype=torch.float64, device=dev)
+
+            def run():
+                for _ in range(c["inner"]):
+                    obj.step_adjoint(state, lam, lam_out, dr)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total = 0.0
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0.record()
+            run()
+            e1.record()
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+    steps = args.steps * c["inner"]
+    value = npts * steps / (total * 1e-3)
+    bpp = c["sweeps"] * vb       # bytes per grid point per step (a half spectrum ~ N/2 complex)
+    peak, peak_kind = hbm_peak()
+    gbs = bpp * npts * steps / (total * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
+            "data": "synthetic", "config": {"workload": c["desc"], "id": args.config, "points": npts,
+                                            "time_steps_per_step": c["inner"],
+                                            "l2": "512 MiB buffer written between timed steps", **extra},
+            "roofline": {"bound": "hbm", "model_bytes_per_point_step": bpp, "achieved": gbs, "peak": peak,
+                         "unit": "GB/s", "frac": gbs / peak, "peak_kind": peak_kind, "traffic": None},
+            "clocks": clk.summary()}
+    if c["kind"] == "plan":
+        prof, _ = obj.profile_steps(state, c["inner"])
+        line["roofline"]["per_kernel_ms_per_step"] = {k: prof[k] / c["inner"] for k in ("row", "line")}
+    print(json.dumps(line), flush=True)
 
 
 def make_input():
@@ -390,6 +508,8 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.config is not None:
+        return run_config(args)
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -232,7 +232,7 @@ pfc_status pfc_batch_create(pfc_batch **out, int nd, const int64_t *dims_host, c
         c.nx = kv.first.second;
         c.members = kv.second;
         c.cbase = slot;
-        if (!plan_tiles(c.t, c.nx, c.ny, 1, vb, 2, (size_t)optin))
+        if (!plan_tiles(c.t, c.nx, c.ny, 1, vb, 2, (size_t)optin, (int)c.members.size()))
             return bail(PFC_ERR_UNSUPPORTED, "no pass tiling fits shared memory for a domain size");
         c.t.g.ltab = BATCH_LTAB;
         std::vector<int64_t> moff;

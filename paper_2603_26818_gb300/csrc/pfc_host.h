@@ -97,7 +97,9 @@ struct Tiles {
 //   row pass:  gpc groups of P = Py Pz rows of M + 1 elements (stride rounded up to 16)
 //   line pass: ntile tiles of Q W complex values (Q = ny nz / P), W columns each
 // Preference: wide line-pass rows (W * sizeof(V) up to 128 B), then the smallest P.
-inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, size_t smem_max) {
+// instances: grids of this shape stepped by the same launches (the members of a batch class)
+inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, size_t smem_max,
+                       int instances = 1) {
     const int max_threads = vb == 8 ? 1024 : 512;   // line pass blocks
     const int max_row_threads = vb == 8 ? 1024 : 512;
     Geom g{};
@@ -159,11 +161,12 @@ inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, s
     g.tsz = (g.Q + g.Q / 8) * g.W;
     g.xs = (int)round_up(g.M + 1, std::max(g.W, 2));
     g.ncg = g.xs / g.W;
-    // row groups per CTA: enough rows for >= 256 threads, within smem and dividing Q
+    // row groups per CTA: enough rows for >= 256 threads, within smem and dividing Q, while the
+    // row pass keeps at least one block per SM (a small grid alone has few groups)
     const int Tr = g.M / 8;
     int gpc = 1;
     while (gpc * 2 <= g.Q && (size_t)(gpc * 2) * g.P * (row_bytes + vb) <= smem_max &&
-           gpc * g.P * Tr < 256)
+           gpc * g.P * Tr < 256 && (int64_t)g.Q * instances / (gpc * 2) >= 152)
         gpc *= 2;
     g.gpc = gpc;
     g.nreal = (int64_t)nx * ny * nz;
@@ -171,7 +174,7 @@ inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, s
     g.nstd = (int64_t)ny * nz * (g.M + 1);
     const int rows = gpc * g.P;
     t.nt_row = std::min(max_row_threads, std::max(Tr, rows * Tr));
-    if (t.nt_row < 64) t.nt_row = std::max(Tr, 64 / Tr * Tr);
+    if (t.nt_row < 32) t.nt_row = std::max(Tr, 32 / Tr * Tr);
     // rows, the split twiddles of the block's rows, then the saved real parts of the kx = 0
     // and nx/2 columns (2 gpc P reals)
     t.smem_row = (size_t)round_up((int64_t)rows * (row_bytes + vb) + 2 * gpc * g.P * (vb / 2), 16);
