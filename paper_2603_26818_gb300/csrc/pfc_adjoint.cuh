@@ -46,14 +46,6 @@ __global__ void __launch_bounds__(512) k_line_adj(const Geom g, const AdjArgs<R>
     const int kpy = kp % g.Py, kpz = kp / g.Py;
     V v[8];
 
-    // forward transform of one X' array: the first stage from global memory, the last stage
-    // either into smem (natural order) or into registers
-    auto forward = [&](const V *src, V *tile, bool to_regs) {
-#pragma unroll
-        for (int m = 0; m < 8; ++m) v[m] = src[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)];
-        fft_run<-1>(v, tile, ady, g.lQy, mp.jy, true, true, to_regs && !two_axes, a.st);
-        if (two_axes) fft_run<-1>(v, tile, adz, g.lQz, mp.jz, true, false, to_regs, a.st);
-    };
 
     // multipliers a, b of register slot m
     const int kx = cg * g.W + mp.w;
@@ -72,8 +64,8 @@ __global__ void __launch_bounds__(512) k_line_adj(const Geom g, const AdjArgs<R>
     };
 
     // 1. N_hat into Cs, psi_hat into registers; g = -b (a P M psi_hat - b N_hat) into Cs
-    forward(reinterpret_cast<const V *>(a.c), Cs, false);
-    forward(reinterpret_cast<const V *>(a.psi), T, true);
+    line_forward(v, g, mp, kp, cg, reinterpret_cast<const V *>(a.c), Cs, ady, adz, false, a.st);
+    line_forward(v, g, mp, kp, cg, reinterpret_cast<const V *>(a.psi), T, ady, adz, true, a.st);
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
         R ca, cb;
@@ -85,7 +77,7 @@ __global__ void __launch_bounds__(512) k_line_adj(const Geom g, const AdjArgs<R>
         Cs[pos] = V{-cb * p1.x, -cb * p1.y};
     }
     // 2. Lam_hat into registers; partial sum; B-input into Cs, A-input stays in registers
-    forward(reinterpret_cast<const V *>(a.lam), T, true);
+    line_forward(v, g, mp, kp, cg, reinterpret_cast<const V *>(a.lam), T, ady, adz, true, a.st);
     const R wk = kx == 0 || kx == g.M ? (R)1 : (kx < g.M ? (R)2 : (R)0);
     const R invQ = a.up.invQ;
     double acc = 0.0;

@@ -482,8 +482,8 @@ pfc_status pfc_plan_create(pfc_plan **out, int ndim, const int64_t *dims, double
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) { delete p; return fail(PFC_ERR_CUDA, std::string("device query: ") + cudaGetErrorString(e)); }
     const size_t smem_max = (size_t)optin;
-    // a two-field plan's line pass holds four tiles (both fields' state and cube)
-    if (!plan_tiles(p->t, p->nx, p->ny, p->nz, vbytes(p), nfields == 2 ? 4 : 2, smem_max) ||
+    // the line pass holds two tiles, a two-field plan's three (see k_line_step2)
+    if (!plan_tiles(p->t, p->nx, p->ny, p->nz, vbytes(p), nfields == 2 ? 3 : 2, smem_max) ||
         (nfields == 2 && p->t.nt_line > 512)) {
         delete p;
         return fail(PFC_ERR_UNSUPPORTED, "no pass tiling fits shared memory for this grid and precision");

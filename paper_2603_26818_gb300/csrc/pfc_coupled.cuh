@@ -23,17 +23,18 @@ template <typename R> struct Step2Args {
     StageTw<typename VT<R>::V> st;
 };
 
+// Three tiles of shared memory: A keeps, per register slot of its owner thread, first N0 then
+// e1 and finally the solved c field; N holds N1; B is the transforms' workspace. Only one
+// register set is live at a time.
 template <typename R>
-__global__ void __launch_bounds__(512) k_line_step2(const Geom g, const Step2Args<R> a) {
+__global__ void __launch_bounds__(512, 1) k_line_step2(const Geom g, const Step2Args<R> a) {
     using V = typename VT<R>::V;
     extern __shared__ __align__(16) unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
     const int cg = blockIdx.x, kp = blockIdx.y;
-    const int tsz = g.tsz;
-    V *T0 = sm;                 // psi transform
-    V *T1 = sm + tsz;           // c transform (natural order)
-    V *N0 = sm + 2 * tsz;       // psi^3 transform (natural order)
-    V *N1 = sm + 3 * tsz;       // c^3 transform (natural order)
+    V *A = sm;
+    V *B = sm + g.tsz;
+    V *N = sm + 2 * g.tsz;
     const LineMap mp = line_map(g, threadIdx.x);
     const PadTileAddr ady = tile_y(g, mp);
     const TileAddr adz = tile_z(g, mp);
@@ -41,37 +42,54 @@ __global__ void __launch_bounds__(512) k_line_step2(const Geom g, const Step2Arg
     const int kpy = kp % g.Py, kpz = kp / g.Py;
     V v[8];
 
-    auto forward = [&](const V *src, V *tile, bool to_regs) {
-#pragma unroll
-        for (int m = 0; m < 8; ++m) v[m] = src[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)];
-        fft_run<-1>(v, tile, ady, g.lQy, mp.jy, true, true, to_regs && !two_axes, a.st);
-        if (two_axes) fft_run<-1>(v, tile, adz, g.lQz, mp.jz, true, false, to_regs, a.st);
-    };
-    forward(reinterpret_cast<const V *>(a.c0), N0, false);
-    forward(reinterpret_cast<const V *>(a.c1), N1, false);
-    forward(reinterpret_cast<const V *>(a.x1), T1, false);
-    forward(reinterpret_cast<const V *>(a.x0), T0, true);
-
     const int kx = cg * g.W + mp.w;
     const R fx = a.up.cx * (R)kx;
     const R dt = a.up.dt, invQ = a.up.invQ, ihn = a.up.inv_halfN;
+    // k^2 of register slot m (and its ky, kz)
+#define PFC_KSQ(m, ky, kz, k2)                                                                \
+    do {                                                                                      \
+        const int kqy_ = two_axes ? mp.yq : mp.jy + (m) * mp.ny8;                             \
+        const int kqz_ = two_axes ? mp.jz + (m) * mp.nz8 : 0;                                 \
+        ky = kpy + (kqy_ << g.lPy);                                                           \
+        kz = kpz + (kqz_ << g.lPz);                                                           \
+        const int my_ = ky <= (g.ny >> 1) ? ky : ky - g.ny;                                   \
+        const int mz_ = kz <= (g.nz >> 1) ? kz : kz - g.nz;                                   \
+        const R fy_ = a.up.cy * (R)my_, fz_ = a.up.cz * (R)mz_;                               \
+        k2 = fx * fx + fy_ * fy_ + fz_ * fz_;                                                 \
+    } while (0)
+    // 1. N0 into A (natural order)
+    line_forward(v, g, mp, kp, cg, reinterpret_cast<const V *>(a.c0), A, ady, adz, false, a.st);
+    // 2. T0 into registers; e1 = T0/Q - dt k^2 (2/N) N0 replaces N0 at the thread's own slots
+    line_forward(v, g, mp, kp, cg, reinterpret_cast<const V *>(a.x0), B, ady, adz, true, a.st);
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
-        const int kqy = two_axes ? mp.yq : mp.jy + m * mp.ny8;
-        const int kqz = two_axes ? mp.jz + m * mp.nz8 : 0;
-        const int ky = kpy + (kqy << g.lPy), kz = kpz + (kqz << g.lPz);
-        const int my = ky <= (g.ny >> 1) ? ky : ky - g.ny;
-        const int mz = kz <= (g.nz >> 1) ? kz : kz - g.nz;
-        const R fy = a.up.cy * (R)my, fz = a.up.cz * (R)mz;
-        const R k2 = fx * fx + fy * fy + fz * fz;
+        int ky, kz;
+        R k2;
+        PFC_KSQ(m, ky, kz, k2);
+        const R dk = dt * k2;
+        const int pos = tile_slot(mp, two_axes, ady, adz, m);
+        const V n0 = A[pos];
+        A[pos] = V{v[m].x * invQ - dk * ihn * n0.x, v[m].y * invQ - dk * ihn * n0.y};
+    }
+    // 3. N1 into N (natural order); 4. T1 into registers
+    line_forward(v, g, mp, kp, cg, reinterpret_cast<const V *>(a.c1), N, ady, adz, false, a.st);
+    line_forward(v, g, mp, kp, cg, reinterpret_cast<const V *>(a.x1), B, ady, adz, true, a.st);
+    // 5. per-mode 2x2 solve (Cramer), one slot at a time from shared memory: T1 goes to B at the
+    // own slots, psi replaces it there and c replaces e1 in A
+#pragma unroll
+    for (int m = 0; m < 8; ++m) B[tile_slot(mp, two_axes, ady, adz, m)] = v[m];
+#pragma unroll 1
+    for (int m = 0; m < 8; ++m) {
+        int ky, kz;
+        R k2;
+        PFC_KSQ(m, ky, kz, k2);
         const R dk = dt * k2;
         const R m11 = (R)1 + dk * lin_symbol<R>(a.up.op[0], k2);
         const R m22 = (R)1 + dk * lin_symbol<R>(a.up.op[1], k2);
         const R m12 = dk * a.alpha;
         const R idet = (R)1 / (m11 * m22 - m12 * m12);
         const int pos = tile_slot(mp, two_axes, ady, adz, m);
-        const V n0 = N0[pos], n1 = N1[pos], t1 = T1[pos];
-        const V e1 = V{v[m].x * invQ - dk * ihn * n0.x, v[m].y * invQ - dk * ihn * n0.y};
+        const V e1 = A[pos], n1 = N[pos], t1 = B[pos];
         const V e2 = V{t1.x * invQ - dk * ihn * n1.x, t1.y * invQ - dk * ihn * n1.y};
         V s0 = V{(m22 * e1.x - m12 * e2.x) * idet, (m22 * e1.y - m12 * e2.y) * idet};
         V s1 = V{(m11 * e2.x - m12 * e1.x) * idet, (m11 * e2.y - m12 * e1.y) * idet};
@@ -79,28 +97,31 @@ __global__ void __launch_bounds__(512) k_line_step2(const Geom g, const Step2Arg
             s0 = V{(R)0, (R)0};
             s1 = V{(R)0, (R)0};
         }
-        v[m] = s0;
-        T1[pos] = s1;   // own position: no other thread reads it before the barrier below
+        B[pos] = s0;
+        A[pos] = s1;
     }
+    __syncthreads();   // every thread's slots of A and B written
+    // 6. inverse of psi from B
     V *X0 = reinterpret_cast<V *>(a.x0);
     V *X1 = reinterpret_cast<V *>(a.x1);
     if (two_axes) {
-        fft_run<+1>(v, T0, adz, g.lQz, mp.jz, true, true, false, a.st);
-        fft_run<+1>(v, T0, ady, g.lQy, mp.jy, true, false, true, a.st);
+        fft_run<+1>(v, B, adz, g.lQz, mp.jz, true, false, false, a.st);
+        fft_run<+1>(v, B, ady, g.lQy, mp.jy, true, false, true, a.st);
     } else {
-        fft_run<+1>(v, T0, ady, g.lQy, mp.jy, true, true, true, a.st);
+        fft_run<+1>(v, B, ady, g.lQy, mp.jy, true, false, true, a.st);
     }
 #pragma unroll
-    for (int m = 0; m < 8; ++m) X0[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)] = v[m];
-    __syncthreads();
+    for (int m = 0; m < 8; ++m) __stcg(&X0[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)], v[m]);
+    // 7. inverse of c from A
     if (two_axes) {
-        fft_run<+1>(v, T1, adz, g.lQz, mp.jz, true, false, false, a.st);
-        fft_run<+1>(v, T1, ady, g.lQy, mp.jy, true, false, true, a.st);
+        fft_run<+1>(v, A, adz, g.lQz, mp.jz, true, false, false, a.st);
+        fft_run<+1>(v, A, ady, g.lQy, mp.jy, true, false, true, a.st);
     } else {
-        fft_run<+1>(v, T1, ady, g.lQy, mp.jy, true, false, true, a.st);
+        fft_run<+1>(v, A, ady, g.lQy, mp.jy, true, false, true, a.st);
     }
 #pragma unroll
-    for (int m = 0; m < 8; ++m) X1[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)] = v[m];
+    for (int m = 0; m < 8; ++m) __stcg(&X1[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)], v[m]);
 }
+#undef PFC_KSQ
 
 }  // namespace pfc

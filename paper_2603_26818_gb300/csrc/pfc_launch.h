@@ -45,7 +45,7 @@ void launch_batch_mean(cudaStream_t s, const R *base, const int64_t *off, const 
                        int members, double *mean, int *status);
 // adjoint line pass (blocks of nt_line <= 512 threads), one partial per block
 template <typename R> void launch_line_adj(const LaunchCfg &c, const AdjArgs<R> &a);
-// coupled two-field line pass (blocks of nt_line <= 512 threads, smem_line for four tiles)
+// coupled two-field line pass (blocks of nt_line <= 512 threads, smem_line for three tiles)
 template <typename R> void launch_line_step2(const LaunchCfg &c, const Step2Args<R> &a);
 
 // The update pass (LINE_STEP) with its y transform length fixed at compile time, compiled in

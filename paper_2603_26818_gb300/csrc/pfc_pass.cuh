@@ -586,11 +586,30 @@ __device__ __forceinline__ int tile_slot(const LineMap &mp, bool two_axes, const
     return two_axes ? adz.at(mp.jz + m * mp.nz8) : ady.at(mp.jy + m * mp.ny8);
 }
 
+// Forward y (and z) transform of one X'-layout array for a line tile: the first stage reads
+// global memory into v; the last stage leaves the result in v (to_regs) or in the tile in
+// natural order.
+template <typename V>
+__device__ __forceinline__ void line_forward(V (&v)[8], const Geom &g, const LineMap &mp, int kp, int cg,
+                                             const V *src, V *tile, const PadTileAddr &ady,
+                                             const TileAddr &adz, bool to_regs, const StageTw<V> &st);
+
 // X' and C' are streamed once per pass: the passes read them with __ldcg and write them with
 // __stcg (cached in L2 only), so they do not evict the twiddle tables and register spills that
 // the transforms keep in L1.
 __device__ __forceinline__ size_t xprime_index(const Geom &g, int kp, int cg, int zq, int yq, int w) {
     return (size_t)(kp * g.Q + zq * g.Qy + yq) * g.xs + cg * g.W + w;
+}
+
+template <typename V>
+__device__ __forceinline__ void line_forward(V (&v)[8], const Geom &g, const LineMap &mp, int kp, int cg,
+                                             const V *src, V *tile, const PadTileAddr &ady,
+                                             const TileAddr &adz, bool to_regs, const StageTw<V> &st) {
+    const bool two_axes = g.Qz > 1;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = __ldcg(&src[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)]);
+    fft_run<-1>(v, tile, ady, g.lQy, mp.jy, true, true, to_regs && !two_axes, st);
+    if (two_axes) fft_run<-1>(v, tile, adz, g.lQz, mp.jz, true, false, to_regs, st);
 }
 
 // y transform of a line tile: length 2^LY fixed at compile time when LY > 0 (one-axis tiles;
