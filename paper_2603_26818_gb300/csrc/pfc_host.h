@@ -82,9 +82,6 @@ inline double min_implicit(const pfc_op *ops, int nfields, double alpha, double 
 
 inline OpDev to_dev(const pfc_op &o) { return OpDev{o.kind, o.r, o.R1, o.q2}; }
 
-// Row pitch of a line-pass tile: W columns of 128 B (16 float2 / 8 double2) spread over all
-// banks already; narrower tiles get one padding element per row.
-
 struct Tiles {
     Geom g;
     int nt_row, nt_line;
@@ -95,8 +92,10 @@ struct Tiles {
 
 // Choose the split of the y/z transforms between the passes and the tile widths.
 //   row pass:  gpc groups of P = Py Pz rows of M + 1 elements (stride rounded up to 16)
-//   line pass: ntile tiles of Q W complex values (Q = ny nz / P), W columns each
-// Preference: wide line-pass rows (W * sizeof(V) up to 128 B), then the smallest P.
+//   line pass: ntile tiles of Q W complex values (Q = ny nz / P), W columns each, one padding
+//              row after every 8 tile rows
+// Preference: 32-byte tile rows, line blocks of at most 512 threads nearest to 256, then the
+// smallest P (see the score below).
 // instances: grids of this shape stepped by the same launches (the members of a batch class)
 inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, size_t smem_max,
                        int instances = 1) {
@@ -182,8 +181,9 @@ inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, s
     const int64_t QW = (int64_t)g.Q * g.W;
     t.nt_line = (int)(QW / 8);
     t.smem_line = (size_t)ntile * (size_t)g.tsz * vb;
-    // A group of eight FP32 rows too large for two blocks per SM is split over a cluster of two
-    // blocks of four rows each, 2 M/8 threads per block (PFC_ROW_CLUSTER=0 turns this off).
+    // A group of FP32 rows too large for two blocks per SM is split over a cluster of two blocks:
+    // 2D (Pz = 1, Py = 8) four rows per block, 3D (Pz = 8) four z_p rows of Py each
+    // (PFC_ROW_CLUSTER=0 turns this off).
     t.row_cs = 0;
     const char *rc = std::getenv("PFC_ROW_CLUSTER");
     const bool rc_on = !(rc && rc[0] == '0');
