@@ -422,7 +422,7 @@ __device__ __forceinline__ void cube_shifted(V (&v)[8], R mean) {
 // grid = (row groups / gpc, nfields); block = threads (a multiple of M/8).
 // ------------------------------------------------------------------------------------------
 template <typename R, int MODE>
-__global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_row(const Geom g, const RowArgs<R> a) {
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_row(const Geom g, const RowArgs<R> a) {
     using V = typename VT<R>::V;
     extern __shared__ __align__(16) unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
