@@ -314,6 +314,17 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------- ours
+def replica_throughput(dist, local_ms, world, work_per_rank, device):
+    """Max over ranks of the timed milliseconds, and the whole-job rate: the work of all ranks
+    (independent replicas) divided by that slowest time. dist is torch.distributed or None."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * work_per_rank / (ms_max * 1e-3)
+
+
 def fma_peaks():
     """Measured plain-FMA rates of this GPU (libpfc_probe.so), TFLOP/s, or None."""
     try:
@@ -397,11 +408,7 @@ def run_ours(args):
         if dist:
             dist.barrier()
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * npts * INNER * args.steps / (ms_max * 1e-3)
+    ms_max, value = replica_throughput(dist, ms, world, npts * INNER * args.steps, dev)
     launches_per_call = 2 * 1 + 1 + 2 * INNER + 1
 
     # ---- end to end through the public API with host buffers (pinned), copies timed
@@ -419,10 +426,8 @@ def run_ours(args):
         h_out.copy_(d, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
-    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * npts * INNER * args.steps / (float(t.item()) * 1e-3), "unit": UNIT,
+    _, e2e_value = replica_throughput(dist, e0.elapsed_time(e1), world, npts * INNER * args.steps, dev)
+    e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": h_in.numel() * 4, "d2h_bytes_per_step": h_out.numel() * 4}
 
     # ---- per-kernel timing with events between launches on the plan's stream
