@@ -38,7 +38,7 @@ static void launch_line_t(const LaunchCfg &c, int mode, const LineArgs<R> &a, in
 }
 
 template <typename R> void launch_line(const LaunchCfg &c, int mode, const LineArgs<R> &a, int nf) {
-    if (mode == LINE_STEP && line_fixed_fits(c)) {
+    if (mode == LINE_STEP && line_fixed_fits<R>(c)) {
         launch_line_step_fixed<R>(c, a, nf);
         return;
     }

@@ -48,12 +48,18 @@ template <typename R> void launch_line_adj(const LaunchCfg &c, const AdjArgs<R> 
 // coupled two-field line pass (blocks of nt_line <= 512 threads, smem_line for three tiles)
 template <typename R> void launch_line_step2(const LaunchCfg &c, const Step2Args<R> &a);
 
-// The update pass (LINE_STEP) with its y transform length fixed at compile time, compiled in
+// The update pass (LINE_STEP) with its transform lengths fixed at compile time, compiled in
 // pfc_line_fixed_f32.cu / pfc_line_fixed_f64.cu: one-axis tiles (Qz = 1) with Qy = 2^6 .. 2^10
-// in blocks of at most 512 threads. launch_line takes it whenever line_fixed_fits.
+// in blocks of at most 512 threads, and the two-axis tiles of the common 3D plans (log2 Qy,
+// log2 Qz) = (5, 5), (5, 4), (6, 4) in blocks of at most 512 threads and (6, 6) in blocks of up
+// to 1024. launch_line takes it whenever line_fixed_fits.
 constexpr int LINE_FIXED_MIN = 6, LINE_FIXED_MAX = 10;
-inline bool line_fixed_fits(const LaunchCfg &c) {
-    return c.g.Qz == 1 && c.nt_line <= 512 && c.g.lQy >= LINE_FIXED_MIN && c.g.lQy <= LINE_FIXED_MAX;
+// (6, 6) is built for FP32 only (FP64 line blocks have at most 512 threads and no such plan)
+template <typename R> inline bool line_fixed_fits(const LaunchCfg &c) {
+    const int ly = c.g.lQy, lz = c.g.lQz, nt = c.nt_line;
+    if (c.g.Qz == 1) return nt <= 512 && ly >= LINE_FIXED_MIN && ly <= LINE_FIXED_MAX;
+    if (nt <= 512 && ((ly == 5 && lz == 5) || (ly == 5 && lz == 4) || (ly == 6 && lz == 4))) return true;
+    return sizeof(R) == 4 && nt <= 1024 && ly == 6 && lz == 6;
 }
 template <typename R> void launch_line_step_fixed(const LaunchCfg &c, const LineArgs<R> &a, int nf);
 template <typename R> cudaError_t set_smem_attrs_fixed(const LaunchCfg &c);

@@ -621,8 +621,17 @@ __device__ __forceinline__ void line_yfft(V (&v)[8], V *sm, const PadTileAddr &a
     else fft_run<S>(v, sm, ad, g.lQy, j, true, in_regs, out_regs, tw);
 }
 
-// LY > 0: the kernel only serves plans with Qz = 1 and Qy = 2^LY.
-template <typename R, int MODE, int MAXT, int LY = 0>
+// z transform of a two-axis line tile: length 2^LZ fixed at compile time when LZ > 0
+template <int S, int LZ, typename V>
+__device__ __forceinline__ void line_zfft(V (&v)[8], V *sm, const TileAddr &ad, const Geom &g, int j,
+                                          bool in_regs, bool out_regs, const StageTw<V> &tw) {
+    if constexpr (LZ > 0) fft_run_t<S, LZ>(v, sm, ad, j, true, in_regs, out_regs, tw, BlockBarrier());
+    else fft_run<S>(v, sm, ad, g.lQz, j, true, in_regs, out_regs, tw);
+}
+
+// LY > 0, LZ = 0: the kernel only serves plans with Qz = 1 and Qy = 2^LY; LY, LZ > 0: plans with
+// Qy = 2^LY and Qz = 2^LZ; LY = LZ = 0: any plan (lengths at run time).
+template <typename R, int MODE, int MAXT, int LY = 0, int LZ = 0>
 __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1) k_line(const Geom g, const LineArgs<R> a) {
     using V = typename VT<R>::V;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -633,7 +642,7 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
     const LineMap mp = line_map(g, threadIdx.x);
     const PadTileAddr ady = tile_y(g, mp);
     const TileAddr adz = tile_z(g, mp);
-    const bool two_axes = LY == 0 && g.Qz > 1;
+    const bool two_axes = LZ > 0 || (LY == 0 && g.Qz > 1);
     const int kpy = kp % g.Py, kpz = kp / g.Py;
     V vt[8], vc[8];
 
@@ -643,14 +652,14 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
 #pragma unroll
         for (int m = 0; m < 8; ++m) vc[m] = __ldcg(&C[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)]);
         line_yfft<-1, LY>(vc, Cs, ady, g, mp.jy, true, false, a.st);
-        if (two_axes) fft_run<-1>(vc, Cs, adz, g.lQz, mp.jz, true, false, false, a.st);
+        if (two_axes) line_zfft<-1, LZ>(vc, Cs, adz, g, mp.jz, false, false, a.st);
     }
     if (MODE == LINE_STEP || MODE == LINE_FWD) {
         const V *X = reinterpret_cast<const V *>(a.x) + (size_t)field * g.nhalf;
 #pragma unroll
         for (int m = 0; m < 8; ++m) vt[m] = __ldcg(&X[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)]);
         line_yfft<-1, LY>(vt, T, ady, g, mp.jy, true, !two_axes, a.st);
-        if (two_axes) fft_run<-1>(vt, T, adz, g.lQz, mp.jz, true, false, true, a.st);
+        if (two_axes) line_zfft<-1, LZ>(vt, T, adz, g, mp.jz, false, true, a.st);
     }
 
 
@@ -711,7 +720,7 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
 
     // inverse: the last forward axis first, from registers
     if (two_axes) {
-        fft_run<+1>(vt, T, adz, g.lQz, mp.jz, true, true, false, a.st);
+        line_zfft<+1, LZ>(vt, T, adz, g, mp.jz, true, false, a.st);
         line_yfft<+1, LY>(vt, T, ady, g, mp.jy, false, true, a.st);
     } else {
         line_yfft<+1, LY>(vt, T, ady, g, mp.jy, true, true, a.st);

@@ -227,3 +227,27 @@ def test_row_cluster_3d_path_matches_single_blocks_and_oracle(monkeypatch):
     ref = oracle.step(psi0, dx, dt, TWO, nsteps)
     assert rel(a, b) <= 1e-6
     assert rel(a, ref) <= 1e-5 and rel(a - a.mean(), ref - ref.mean()) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_nonfinite_state_is_reported_and_the_plan_stays_usable(prec):
+    """A NaN or Inf in the state is caught by the FP64 reductions (the mean taken at the start
+    of every pfc_step call, mass, energy) and reported as PFC_ERR_NONFINITE; the status is
+    cleared once reported and the plan keeps working."""
+    b = _binding()
+    p = plan((64, 64), math.pi / 4, 0.5, ONE, prec)
+    psi0 = inputs.uniform_state((64, 64), -0.25, 0.05, seed=21)
+    x = to_dev(psi0, prec)
+    x[3, 5] = float("nan")
+    with pytest.raises(b.PfcError, match="NONFINITE"):
+        p.mass(x)
+    y = to_dev(psi0, prec)
+    y[0, 0] = float("inf")
+    p.step(y, 3)
+    with pytest.raises(b.PfcError, match="NONFINITE"):
+        p.sync()
+    z = to_dev(psi0, prec)
+    p.step(z, 3)
+    p.sync()
+    assert rel(z.double().cpu().numpy(), oracle.step(psi0, math.pi / 4, 0.5, ONE, 3)) <= (1e-12 if prec == "fp64" else 2e-6)
+    p.close()
