@@ -16,9 +16,9 @@ template <typename R> void launch_row(const LaunchCfg &c, int mode, const RowArg
     if constexpr (sizeof(R) == 4) {
         if (mode == ROW_CUBE && c.row_cs == 2) {
             if (c.g.Pz == 1)
-                k_row_cube_cl<R, 2><<<dim3(2 * c.g.Q, nf), c.nt_row_cs, c.smem_row_cs, c.stream>>>(c.g, a);
+                k_row_cube_cl<R, 2, 11><<<dim3(2 * c.g.Q, nf), c.nt_row_cs, c.smem_row_cs, c.stream>>>(c.g, a);
             else
-                k_row_cube_cl3<R><<<dim3(2 * c.g.Q, nf), c.nt_row_cs, c.smem_row_cs, c.stream>>>(c.g, a);
+                k_row_cube_cl3<R, 8><<<dim3(2 * c.g.Q, nf), c.nt_row_cs, c.smem_row_cs, c.stream>>>(c.g, a);
             return;
         }
     }
@@ -69,9 +69,9 @@ template <typename R> cudaError_t set_smem_attrs(const LaunchCfg &c) {
     }
     if constexpr (sizeof(R) == 4) {
         if (c.row_cs == 2 && c.g.Pz == 1 &&
-            (e = allow_smem(k_row_cube_cl<R, 2>, c.smem_row_cs)) != cudaSuccess) return e;
+            (e = allow_smem(k_row_cube_cl<R, 2, 11>, c.smem_row_cs)) != cudaSuccess) return e;
         if (c.row_cs == 2 && c.g.Pz > 1 &&
-            (e = allow_smem(k_row_cube_cl3<R>, c.smem_row_cs)) != cudaSuccess) return e;
+            (e = allow_smem(k_row_cube_cl3<R, 8>, c.smem_row_cs)) != cudaSuccess) return e;
     }
     return set_smem_attrs_fixed<R>(c);
 }

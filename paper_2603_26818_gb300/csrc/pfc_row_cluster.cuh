@@ -25,7 +25,9 @@ __device__ __forceinline__ void cluster_sync_relaxed() {
     asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
 }
 
-template <typename R, int CS>
+// LM = log2 M, the row transform length, fixed at compile time (the planner uses this kernel
+// for nx = 4096 only).
+template <typename R, int CS, int LM>
 __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
     k_row_cube_cl(const Geom g, const RowArgs<R> a) {
     using V = typename VT<R>::V;
@@ -37,7 +39,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
     const int h = (int)cl.block_rank();
     const int tid = threadIdx.x, nt = blockDim.x;
     const int field = blockIdx.y;
-    const int M = g.M, lM = g.lM, hM = M >> 1;
+    const int M = g.M, hM = M >> 1;
     const int grp = blockIdx.x / CS;
     const R mean = a.mean ? (R)a.mean[field] : (R)0;
     // smem: RPC rows | one scratch row per row in flight (ping-pong transforms) | split
@@ -121,11 +123,11 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
             V v[8];
             // ping-pong through this row group's scratch row
             const RowAddr sc{(RPC + gidx) * g.rs};
-            if (grouped) fft_run_pp<+1>(v, sm, ad, sc, lM, j, act, false, true, a.st, nbar);
-            else fft_run_pp<+1>(v, sm, ad, sc, lM, j, act, false, true, a.st);
+            if (grouped) fft_run_pp_t<+1, LM>(v, sm, ad, sc, j, act, false, true, a.st, nbar);
+            else fft_run_pp_t<+1, LM>(v, sm, ad, sc, j, act, false, true, a.st, BlockBarrier());
             cube_shifted(v, mean);
-            if (grouped) fft_run_pp<-1>(v, sm, ad, sc, lM, j, act, true, false, a.st, nbar);
-            else fft_run_pp<-1>(v, sm, ad, sc, lM, j, act, true, false, a.st);
+            if (grouped) fft_run_pp_t<-1, LM>(v, sm, ad, sc, j, act, true, false, a.st, nbar);
+            else fft_run_pp_t<-1, LM>(v, sm, ad, sc, j, act, true, false, a.st, BlockBarrier());
         }
     }
     cl.sync();
@@ -180,7 +182,8 @@ namespace pfc {
 // and D (y-part and real-transform processing) and the row transforms touch only the block's
 // own rows. The real parts of the kx = 0 and nx/2 columns are gathered in block 0, which does
 // the Hermitian projection (project_edge_columns) for the group.
-template <typename R>
+// LM = log2 M fixed at compile time (the planner uses this kernel for nx = 512 only).
+template <typename R, int LM>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 2)
     k_row_cube_cl3(const Geom g, const RowArgs<R> a) {
     using V = typename VT<R>::V;
@@ -276,9 +279,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 2)
             const bool act = r < rows;
             const RowAddr ad{r * g.rs};
             V v[8];
-            fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st);
+            fft_run_t<+1, LM>(v, sm, ad, j, act, false, true, a.st, BlockBarrier());
             cube_shifted(v, mean);
-            fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.st);
+            fft_run_t<-1, LM>(v, sm, ad, j, act, true, false, a.st, BlockBarrier());
         }
     }
     __syncthreads();
