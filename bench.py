@@ -254,10 +254,10 @@ def kernel_source_hash():
 
 def kernel_names(info):
     """Names (as ncu prints them, without arguments) of the row and line kernels a plan runs."""
-    row = "k_row_cube_cl<float, 2>" if info.get("row_cluster") == 2 else "k_row<float, ROW_CUBE>"
+    row = "k_row_cube_cl<float, 2, 11>" if info.get("row_cluster") == 2 else "k_row<float, ROW_CUBE>"
     ly = info["Qy"].bit_length() - 1
     fixed = info["Qz"] == 1 and info["threads_line"] <= 512 and 6 <= ly <= 10
-    line = f"k_line<float, LINE_STEP, 512, {ly}>" if fixed else "k_line<float, LINE_STEP>"
+    line = f"k_line<float, LINE_STEP, 512, {ly}, 0>" if fixed else "k_line<float, LINE_STEP>"
     return {"row": row, "line": line}
 
 

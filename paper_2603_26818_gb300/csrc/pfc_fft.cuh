@@ -146,6 +146,16 @@ struct NamedBarrier {
     int id, n;
     __device__ __forceinline__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 };
+// The barrier of the n threads that transform one row: a warp barrier when the row lies within
+// one warp (n <= 32, rows of n threads starting at multiples of n), else barrier id over n
+// threads (id 0 with n = the block: __syncthreads).
+struct RowBarrier {
+    int id, n;
+    __device__ __forceinline__ void sync() const {
+        if (n <= 32) __syncwarp();
+        else asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+    }
+};
 
 template <typename V> struct StageTw {
     const V *t8, *t4, *t2;

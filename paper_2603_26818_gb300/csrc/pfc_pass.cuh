@@ -473,25 +473,24 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_row(const Geom 
     // ---- per-row transforms ----
     const int Tr = M >> 3;
     const int RB = nt / Tr;
-    // groups of Tr threads, each with its own barrier, take rows gidx, gidx + RB, ...
+    // groups of Tr threads take rows gidx, gidx + RB, ...; a group syncs on its own warp (Tr <=
+    // 32), on its own named barrier, or (more groups than barriers, or ragged rounds) on the block
     const bool grouped = Tr >= 32 && RB <= 15 && rows % RB == 0;
     const int gidx = tid / Tr;
-    const NamedBarrier nbar{1 + gidx, Tr};
+    const RowBarrier nbar = Tr <= 32 ? RowBarrier{0, Tr} : grouped ? RowBarrier{1 + gidx, Tr} : RowBarrier{0, nt};
     for (int rb = 0; rb < rows; rb += RB) {
         const int r = rb + gidx, j = tid % Tr;
         const bool act = r < rows;
         const RowAddr ad{r * g.rs};
         V v[8];
         if (MODE == ROW_CUBE) {
-            if (grouped) fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st, nbar);
-            else fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st);
+            fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st, nbar);
             cube_shifted(v, mean);
-            if (grouped) fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.st, nbar);
-            else fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.st);
+            fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.st, nbar);
         } else if (MODE == ROW_FWD) {
-            fft_run<-1>(v, sm, ad, lM, j, act, false, false, a.st);
+            fft_run<-1>(v, sm, ad, lM, j, act, false, false, a.st, nbar);
         } else {   // ROW_INV, ROW_ADJ_MIX
-            fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st);
+            fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st, nbar);
             if (act) {
                 const int gi = r / P, pr = r % P;
                 const int grp = grp0 + gi;

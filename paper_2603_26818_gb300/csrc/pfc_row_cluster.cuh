@@ -279,9 +279,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 2)
             const bool act = r < rows;
             const RowAddr ad{r * g.rs};
             V v[8];
-            fft_run_t<+1, LM>(v, sm, ad, j, act, false, true, a.st, BlockBarrier());
+            const RowBarrier rbar = Tr <= 32 ? RowBarrier{0, Tr} : RowBarrier{0, nt};
+            fft_run_t<+1, LM>(v, sm, ad, j, act, false, true, a.st, rbar);
             cube_shifted(v, mean);
-            fft_run_t<-1, LM>(v, sm, ad, j, act, true, false, a.st, BlockBarrier());
+            fft_run_t<-1, LM>(v, sm, ad, j, act, true, false, a.st, rbar);
         }
     }
     __syncthreads();
