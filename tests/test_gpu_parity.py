@@ -18,6 +18,8 @@ pytestmark = pytest.mark.gpu
 
 ONE = (0, -0.25, 0.0, 0.0)
 TWO = (1, -0.3, 0.05, math.sqrt(4.0 / 3.0))
+# the paper's FCC operator of Eq. (5): two-mode with R1 = 0, q2^2 = 4/3 (eps = -0.25)
+PAPER_FCC = (1, -0.25, 0.0, math.sqrt(4.0 / 3.0))
 TOL_FFT = {"fp64": 1e-13, "fp32": 2e-6}
 
 
@@ -102,6 +104,8 @@ def test_config1_128_one_mode_steps(prec, tol1, tol100):
     ((512, 16, 16), TWO, 0.1, 5),
     ((4096, 16), ONE, 0.5, 10),
     ((64, 128), TWO, 0.1, 20),
+    ((32, 32, 32), PAPER_FCC, 0.1, 10),
+    ((128, 256), PAPER_FCC, 0.1, 10),
 ])
 def test_steps_match_oracle(shape, op, dt, nsteps, prec, tol):
     dx = math.pi / 4
