@@ -1,0 +1,91 @@
+"""Host logic of the tile planner (plan_tiles in csrc/pfc_host.h), compiled as a small host
+program: every plan for the supported shapes keeps the invariants the kernels rely on."""
+import itertools
+import json
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SMEM_MAX = 232448
+
+
+@pytest.fixture(scope="module")
+def planner(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path_factory.mktemp("planner") / "plan_dump")
+    r = subprocess.run([nvcc, "-std=c++17", "-O1", "-o", exe, os.path.join(ROOT, "tests", "host", "plan_dump.cu")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+
+    def run(cases):
+        args = [str(v) for c in cases for v in c]
+        out = subprocess.run([exe, *args], capture_output=True, text=True, check=True).stdout
+        return [json.loads(l) for l in out.splitlines()]
+    return run
+
+
+def _cases():
+    dims = [16, 32, 64, 128, 256, 512, 1024, 2048, 4096]
+    cases = []
+    for nx, ny in itertools.product(dims, dims):
+        for vb in (8, 16):
+            cases.append((nx, ny, 1, vb, 2, 1))
+    for n in (16, 32, 64, 128, 256, 512):
+        for vb in (8, 16):
+            for ntile in (2, 3):
+                cases.append((n, n, n, vb, ntile, 1))
+    cases += [(512, 256, 256, 8, 2, 1), (4096, 16, 16, 8, 2, 1), (16, 16, 4096, 8, 2, 1), (64, 64, 1, 8, 2, 400)]
+    return cases
+
+
+def test_plans_keep_the_kernel_invariants(planner):
+    plans = planner(_cases())
+    assert len(plans) == len(_cases())
+    for p in plans:
+        if not p["ok"]:
+            # only grids whose row group or tiles cannot fit: FP64 512^3 and larger
+            assert p["vb"] == 16 and p["nz"] >= 512
+            continue
+        nx, ny, nz, vb = p["nx"], p["ny"], p["nz"], p["vb"]
+        M = nx // 2
+        assert p["M"] == M
+        assert p["P"] == p["Py"] * p["Pz"] and p["Q"] == p["Qy"] * p["Qz"]
+        assert p["Py"] * p["Qy"] == ny and p["Pz"] * p["Qz"] == nz
+        assert p["Py"] in (1, 2, 4, 8) and p["Pz"] in (1, 2, 4, 8)
+        assert p["Qy"] == 1 or p["Qy"] >= 8
+        assert p["Qz"] == 1 or p["Qz"] >= 8
+        assert nz > 1 or p["Pz"] == 1
+        # X' rows: every bin, a whole number of tiles, 16-byte aligned rows
+        assert p["xs"] >= M + 1 and p["xs"] % p["W"] == 0 and p["ncg"] * p["W"] == p["xs"]
+        assert (p["xs"] * vb) % 16 == 0
+        assert p["nhalf"] == p["P"] * p["Q"] * p["xs"]
+        # line tiles: one padding row per 8 tile rows, 8 elements per thread
+        assert p["tsz"] == (p["Q"] + p["Q"] // 8) * p["W"]
+        assert p["nt_line"] * 8 == p["Q"] * p["W"]
+        assert p["nt_line"] <= (1024 if vb == 8 else 512)
+        assert p["smem_line"] == p["ntile"] * p["tsz"] * vb <= SMEM_MAX
+        # row blocks: rows of M + 1 bins (stride a multiple of 16 for the XOR swizzle)
+        assert p["rs"] >= M + 1 and p["rs"] % 16 == 0
+        assert p["nt_row"] <= 512 and p["nt_row"] % max(1, M // 8) == 0
+        assert p["smem_row"] <= SMEM_MAX
+        assert p["Q"] % p["gpc"] == 0
+        # clustered psi^3 rows: FP32 only, at the row lengths the kernels are compiled for
+        if p["row_cs"]:
+            assert vb == 8 and p["row_cs"] == 2 and p["gpc"] == 1
+            assert (p["Pz"] == 1 and p["Py"] == 8 and M == 2048) or (p["Pz"] == 8 and M == 256)
+            assert p["smem_row_cs"] <= SMEM_MAX // 2   # two blocks per SM
+            assert p["nt_row_cs"] <= 512
+
+
+def test_bench_and_config_plans(planner):
+    p, q, single, batch = planner([(4096, 4096, 1, 8, 2, 1), (512, 512, 512, 8, 2, 1),
+                                   (64, 64, 1, 8, 2, 1), (64, 64, 1, 8, 2, 400)])
+    assert (p["Py"], p["Qy"], p["W"], p["nt_line"], p["row_cs"]) == (8, 512, 4, 256, 2)
+    assert (q["Py"], q["Pz"], q["W"], q["row_cs"]) == (8, 8, 2, 2)
+    # a small grid alone keeps one row block per SM; as a batch class it packs row groups
+    assert single["gpc"] == 1 and batch["gpc"] > 1
