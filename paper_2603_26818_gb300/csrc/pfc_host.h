@@ -202,7 +202,8 @@ inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, s
         // 3D: the group's 8 Py rows split by z_p halves over a cluster of two blocks
         t.row_cs = 2;
         t.nt_row_cs = std::min(512, 4 * g.Py * Tr);
-        t.smem_row_cs = (size_t)round_up((int64_t)4 * g.Py * row_bytes + (int64_t)g.P * vb + g.P * vb, 16);
+        t.smem_row_cs = (size_t)round_up((int64_t)4 * g.Py * row_bytes + (int64_t)g.P * vb + g.P * vb +
+                                             2 * (int64_t)g.P * vb, 16);
     }
     return true;
 }

@@ -223,7 +223,7 @@ __device__ __forceinline__ void row_pair_b(const Geom &g, typename VT<R>::V *sm,
         }
     }
     if (FROM_GLOBAL && proj && k0) {
-        // Hermitian projection (see project_edge_columns) done here when the thread holds every
+        // Hermitian projection (see project_edge_columns_par) done here when the thread holds every
         // row of the kx = 0 and kx = M columns (Pz == 1): X' = DFT_P(real parts) / P. a and b are
         // reused: the pre-processing above no longer needs them.
 #pragma unroll
@@ -278,42 +278,43 @@ __device__ void row_phase_b(const Geom &g, typename VT<R>::V *sm, R *edge,
 // never sees and which the update multiplies by 1/D(k) > 1 at the linearly unstable
 // wavenumbers, so without projection it grows until it overflows. This writes the saved real
 // parts of both columns back to X' through the forward P-part (X' = DFT_P(row values) / P).
+// Spread over threads: the y-part of every (group, column, z_p), then the z-part, twiddle and
+// store of every (group, column, k_py), through S (2 gpc P complex values of shared memory).
+// Called by every thread of the block (it contains a barrier).
 template <typename R>
-__device__ void project_edge_columns(const Geom &g, const R *edge, int grp0,
-                                     const typename VT<R>::V *stw,
-                                     typename VT<R>::V *__restrict__ xout) {
+__device__ void project_edge_columns_par(const Geom &g, const R *edge, int grp0,
+                                         const typename VT<R>::V *stw, typename VT<R>::V *__restrict__ xout,
+                                         typename VT<R>::V *S) {
     using V = typename VT<R>::V;
-    const int P = g.P;
+    const int P = g.P, Py = g.Py, Pz = g.Pz;
     const R invP = (R)1 / (R)P;
-    for (int t = threadIdx.x; t < 2 * g.gpc; t += blockDim.x) {
-        const int gi = t >> 1, c = t & 1, k = c ? g.M : 0, grp = grp0 + gi;
-        V vals[64];
-        for (int pr = 0; pr < P; ++pr) vals[pr] = V{edge[(gi * 2 + c) * P + pr], (R)0};
+    for (int t = threadIdx.x; t < 2 * g.gpc * Pz; t += blockDim.x) {
+        const int gc = t / Pz, zp = t % Pz;   // gc = 2 gi + c
         V tt[8];
-        if (g.Py > 1) {
-            for (int zp = 0; zp < g.Pz; ++zp) {
 #pragma unroll
-                for (int b = 0; b < 8; ++b) if (b < g.Py) tt[b] = vals[zp * g.Py + b];
-                dft_small<-1>(tt, g.Py);
+        for (int b = 0; b < 8; ++b)
+            if (b < Py) tt[b] = V{edge[gc * P + zp * Py + b], (R)0};
+        dft_small<-1>(tt, Py);
 #pragma unroll
-                for (int b = 0; b < 8; ++b) if (b < g.Py) vals[zp * g.Py + b] = tt[b];
+        for (int b = 0; b < 8; ++b)
+            if (b < Py) S[gc * P + zp * Py + b] = tt[b];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * g.gpc * Py; t += blockDim.x) {
+        const int gc = t / Py, kpy = t % Py, gi = gc >> 1, k = (gc & 1) ? g.M : 0, grp = grp0 + gi;
+        V tt[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+            if (a < Pz) tt[a] = S[gc * P + a * Py + kpy];
+        dft_small<-1>(tt, Pz);
+#pragma unroll
+        for (int kpz = 0; kpz < 8; ++kpz) {
+            if (kpz < Pz) {
+                V x = tt[kpz];
+                if (P > 1) x = cmul(x, stw[gi * P + kpz * Py + kpy]);
+                xout[(size_t)((kpz * Py + kpy) * g.Q + grp) * g.xs + k] = cscale(x, invP);
             }
         }
-        if (g.Pz > 1) {
-            for (int kpy = 0; kpy < g.Py; ++kpy) {
-#pragma unroll
-                for (int a = 0; a < 8; ++a) if (a < g.Pz) tt[a] = vals[a * g.Py + kpy];
-                dft_small<-1>(tt, g.Pz);
-#pragma unroll
-                for (int a = 0; a < 8; ++a) if (a < g.Pz) vals[a * g.Py + kpy] = tt[a];
-            }
-        }
-        for (int kpz = 0; kpz < g.Pz; ++kpz)
-            for (int kpy = 0; kpy < g.Py; ++kpy) {
-                V x = vals[kpz * g.Py + kpy];
-                if (P > 1) x = cmul(x, stw[gi * P + kpz * g.Py + kpy]);
-                xout[(size_t)((kpz * g.Py + kpy) * g.Q + grp) * g.xs + k] = cscale(x, invP);
-            }
     }
 }
 
@@ -531,7 +532,8 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_row(const Geom 
     // the edge values were saved in phase B in their own smem area; nothing waits on this
     if (MODE == ROW_CUBE && g.Pz > 1) {   // (Pz == 1 projects in phase B)
         V *xw = reinterpret_cast<V *>(a.proj) + (size_t)field * g.nhalf;
-        project_edge_columns<R>(g, edge, grp0, stw, xw);
+        __syncthreads();   // phase E has read the rows; they serve as the projection's scratch
+        project_edge_columns_par<R>(g, edge, grp0, stw, xw, sm);
     }
 }
 

@@ -90,7 +90,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
                 }
                 if (k0 && a.proj) {
                     // Hermitian projection of the kx = 0 and nx/2 columns (see
-                    // project_edge_columns): X' = DFT_P(real parts of the row values) / P
+                    // project_edge_columns_par): X' = DFT_P(real parts of the row values) / P
 #pragma unroll
                     for (int yy = 0; yy < ROWCL_PY; ++yy) {
                         va[yy].y = (R)0;
@@ -181,7 +181,7 @@ namespace pfc {
 // distributed shared memory, the partner's; the items are split between the blocks. Phases B
 // and D (y-part and real-transform processing) and the row transforms touch only the block's
 // own rows. The real parts of the kx = 0 and nx/2 columns are gathered in block 0, which does
-// the Hermitian projection (project_edge_columns) for the group.
+// the Hermitian projection (project_edge_columns_par) for the group.
 // LM = log2 M fixed at compile time (the planner uses this kernel for nx = 512 only).
 template <typename R, int LM>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 2)
@@ -200,7 +200,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 2)
     const int rows = ZPB * Py;
     const R mean = a.mean ? (R)a.mean[field] : (R)0;
     // smem: rows (z_p local, k_py or y_p) | split twiddles of the group (P) | edge values (2 P,
-    // used in block 0)
+    // used in block 0) | the projection's scratch (2 P complex, block 0)
     V *stw = sm + rows * g.rs;
     R *edge = reinterpret_cast<R *>(stw + P);
     for (int t = tid; t < P; t += nt) stw[t] = split_twiddle(g, a.tw, grp, t / Py, t % Py);
@@ -321,7 +321,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 2)
     // that follows phase D)
     if (h == 0 && a.proj) {
         V *xw = reinterpret_cast<V *>(a.proj) + (size_t)field * g.nhalf;
-        project_edge_columns<R>(g, edge, grp, stw, xw);
+        project_edge_columns_par<R>(g, edge, grp, stw, xw, reinterpret_cast<V *>(edge + 2 * P));
     }
     cluster_sync_relaxed();
 }
