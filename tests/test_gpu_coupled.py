@@ -82,3 +82,20 @@ def test_coupled_long_single_call_matches_oracle():
     got = x.cpu().numpy()
     assert np.isfinite(got).all()
     assert rel(got[0], rp) <= 1e-9 and rel(got[1], rc) <= 1e-9
+
+
+@pytest.mark.parametrize("shape,opc,dt", [((4096, 4096), OPC, 0.5), ((256, 256, 512), OPC2, 0.1)])
+def test_coupled_pair_on_the_clustered_row_passes(shape, opc, dt):
+    """Two fields through the clustered psi^3 row passes (2D rows of 4096, 3D rows of 512 with
+    Py = Pz = 8): the second field runs as the second row of the launch grid."""
+    from paper_2603_26818_gb300 import binding
+    alpha, nsteps = 0.1, 2
+    p0, c0 = _pair(shape, 67)
+    pl = _plan(shape, dt, [OPP, opc], "fp32", alpha)
+    assert pl.info()["row_cluster"] == 2
+    x = torch.from_numpy(np.stack([p0, c0])).to(device="cuda", dtype=torch.float32)
+    pl.step(x, nsteps)
+    got = x.double().cpu().numpy()
+    pl.close()
+    rp, rc = oracle.step2(p0, c0, math.pi / 4, dt, OPP, opc, alpha, nsteps)
+    assert rel(got[0], rp) <= 1e-5 and rel(got[1], rc) <= 1e-5
