@@ -115,3 +115,23 @@ def test_adjoint_config_256_cubed_r_gradient_matches_finite_differences():
     assert gr == pytest.approx(fd, rel=1e-6)
     assert np.isfinite(g).all()
     p.close()
+
+
+@pytest.mark.parametrize("shape,op,dt", [((4096, 4096), ONE, 0.5), ((256, 256, 512), TWO, 0.1)])
+def test_adjoint_step_on_the_clustered_row_passes(shape, op, dt):
+    """FP32 adjoint step of plans whose psi^3 row pass runs on two-block clusters (2D rows of
+    4096, 3D rows of 512) against the oracle's adjoint step."""
+    psi = inputs.uniform_state(shape, -0.25, 0.2, seed=53)
+    lam = inputs.uniform_state(shape, 0.0, 1.0, seed=54)
+    ref_lam, ref_dr = oracle.step_adjoint(psi, lam, math.pi / 4, dt, op)
+    p = _plan(shape, dt, op, "fp32")
+    assert p.info()["row_cluster"] == 2
+    pd = torch.from_numpy(psi).to(device="cuda", dtype=torch.float32)
+    ld = torch.from_numpy(lam).to(device="cuda", dtype=torch.float32)
+    out = torch.empty_like(ld)
+    dr = torch.zeros(1, dtype=torch.float64, device="cuda")
+    p.step_adjoint(pd, ld, out, dr)
+    torch.cuda.synchronize()
+    assert rel(out.double().cpu().numpy(), ref_lam) <= 2e-5
+    assert abs(float(dr) - ref_dr) <= 2e-4 * max(1.0, abs(ref_dr))
+    p.close()
