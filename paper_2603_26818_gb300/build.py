@@ -58,7 +58,7 @@ def _link(out, objs, extra):
 # translation units of libpfc.so: host plan logic, the kernels of each precision, and the
 # allocation-free step
 LIB_UNITS = ["pfc_api.cu", "pfc_batch.cu", "pfc_kern_f32.cu", "pfc_kern_f64.cu", "pfc_line_fixed_f32.cu",
-             "pfc_line_fixed_f64.cu", "pfc_noalloc.cu"]
+             "pfc_line_fixed_f64.cu", "pfc_row_fixed_f32.cu", "pfc_row_fixed_f64.cu", "pfc_noalloc.cu"]
 
 
 def build(force: bool = False) -> str:

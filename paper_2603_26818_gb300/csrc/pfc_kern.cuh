@@ -22,6 +22,10 @@ template <typename R> void launch_row(const LaunchCfg &c, int mode, const RowArg
             return;
         }
     }
+    if (mode == ROW_CUBE && c.g.lM >= ROW_FIXED_MIN && c.g.lM <= ROW_FIXED_MAX) {
+        launch_row_cube_fixed<R>(c, a, nf);
+        return;
+    }
     dim3 grid(c.g.Q / c.g.gpc, nf);
     if (mode == ROW_CUBE) k_row<R, ROW_CUBE><<<grid, c.nt_row, c.smem_row, c.stream>>>(c.g, a);
     else if (mode == ROW_FWD) k_row<R, ROW_FWD><<<grid, c.nt_row, c.smem_row, c.stream>>>(c.g, a);
@@ -73,6 +77,7 @@ template <typename R> cudaError_t set_smem_attrs(const LaunchCfg &c) {
         if (c.row_cs == 2 && c.g.Pz > 1 &&
             (e = allow_smem(k_row_cube_cl3<R, 8>, c.smem_row_cs)) != cudaSuccess) return e;
     }
+    if ((e = set_smem_attrs_row_fixed<R>(c)) != cudaSuccess) return e;
     return set_smem_attrs_fixed<R>(c);
 }
 

@@ -62,12 +62,19 @@ template <typename R> inline bool line_fixed_fits(const LaunchCfg &c) {
     return sizeof(R) == 4 && nt <= 1024 && ly == 6 && lz == 6;
 }
 template <typename R> void launch_line_step_fixed(const LaunchCfg &c, const LineArgs<R> &a, int nf);
+// The psi^3 row pass with its row length M = 2^lM fixed at compile time, lM in [ROW_FIXED_MIN,
+// ROW_FIXED_MAX] (compiled in pfc_row_fixed_f32.cu / pfc_row_fixed_f64.cu).
+constexpr int ROW_FIXED_MIN = 5, ROW_FIXED_MAX = 10;
+template <typename R> void launch_row_cube_fixed(const LaunchCfg &c, const RowArgs<R> &a, int nf);
+template <typename R> cudaError_t set_smem_attrs_row_fixed(const LaunchCfg &c);
 template <typename R> cudaError_t set_smem_attrs_fixed(const LaunchCfg &c);
 
 #define PFC_DECLARE_LAUNCH(R)                                                                   \
     extern template void launch_row<R>(const LaunchCfg &, int, const RowArgs<R> &, int);        \
     extern template void launch_line<R>(const LaunchCfg &, int, const LineArgs<R> &, int);      \
     extern template void launch_line_step_fixed<R>(const LaunchCfg &, const LineArgs<R> &, int); \
+    extern template void launch_row_cube_fixed<R>(const LaunchCfg &, const RowArgs<R> &, int);   \
+    extern template cudaError_t set_smem_attrs_row_fixed<R>(const LaunchCfg &);                 \
     extern template cudaError_t set_smem_attrs_fixed<R>(const LaunchCfg &);                     \
     extern template cudaError_t set_smem_attrs<R>(const LaunchCfg &);                           \
     extern template void launch_line_adj<R>(const LaunchCfg &, const AdjArgs<R> &);             \

@@ -422,7 +422,18 @@ __device__ __forceinline__ void cube_shifted(V (&v)[8], R mean) {
 //   ROW_INV   X' -> real psi = scale ((row inverse of X') + mean)
 // grid = (row groups / gpc, nfields); block = threads (a multiple of M/8).
 // ------------------------------------------------------------------------------------------
-template <typename R, int MODE>
+// row transform of a row pass: length 2^LM fixed at compile time when LM > 0 (a kernel with one
+// transform length is a fraction of the size of the all-lengths one: small rows are bound by
+// instruction fetch otherwise), else the plan's length
+template <int S, int LM, typename V, typename Bar>
+__device__ __forceinline__ void row_fft(V (&v)[8], V *sm, const RowAddr &ad, int lM, int j, bool act,
+                                        bool in_regs, bool out_regs, const StageTw<V> &tw, const Bar &bar) {
+    if constexpr (LM > 0) fft_run_t<S, LM>(v, sm, ad, j, act, in_regs, out_regs, tw, bar);
+    else fft_run<S>(v, sm, ad, lM, j, act, in_regs, out_regs, tw, bar);
+}
+
+// LM > 0: the kernel only serves plans with M = 2^LM.
+template <typename R, int MODE, int LM = 0>
 __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_row(const Geom g, const RowArgs<R> a) {
     using V = typename VT<R>::V;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -485,13 +496,13 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_row(const Geom 
         const RowAddr ad{r * g.rs};
         V v[8];
         if (MODE == ROW_CUBE) {
-            fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st, nbar);
+            row_fft<+1, LM>(v, sm, ad, lM, j, act, false, true, a.st, nbar);
             cube_shifted(v, mean);
-            fft_run<-1>(v, sm, ad, lM, j, act, true, false, a.st, nbar);
+            row_fft<-1, LM>(v, sm, ad, lM, j, act, true, false, a.st, nbar);
         } else if (MODE == ROW_FWD) {
-            fft_run<-1>(v, sm, ad, lM, j, act, false, false, a.st, nbar);
+            row_fft<-1, LM>(v, sm, ad, lM, j, act, false, false, a.st, nbar);
         } else {   // ROW_INV, ROW_ADJ_MIX
-            fft_run<+1>(v, sm, ad, lM, j, act, false, true, a.st, nbar);
+            row_fft<+1, LM>(v, sm, ad, lM, j, act, false, true, a.st, nbar);
             if (act) {
                 const int gi = r / P, pr = r % P;
                 const int grp = grp0 + gi;
