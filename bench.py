@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / cuFFT context timings")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="--config 4a/4b: keep the planner's tiles instead of autotuning them")
     ap.add_argument("--config", choices=sorted(CONFIGS), default=None,
                     help="time one of the other workloads instead of the 4096^2 headline (1 GPU)")
     return ap.parse_args()
@@ -73,11 +75,11 @@ CONFIGS = {
     "4a": dict(desc="1024 batched 2D one-mode domains, nx, ny from {64,128,256,512}, r~U[-0.4,-0.1], "
                     "mean~U[-0.4,-0.2] (seed 4), noise 0.01, dt=0.5, FP32-mixed; 20 time steps per bench "
                     "step (graph of per-size-class branches)",
-               kind="batch", prec="fp32", dt=0.5, inner=20, sweeps=5),
+               kind="batch", prec="fp32", dt=0.5, inner=20, sweeps=5, autotune=True),
     "4b": dict(desc="coupled density/composition pair 256^3 FP32-mixed, alpha=0.1, one-mode r=-0.25 "
                     "for both, means -0.25/-0.2, noise 0.01 (seeds 5, 6), dt=0.5; 10 time steps per "
                     "bench step", kind="pair", dims=(256, 256, 256), prec="fp32", dt=0.5, inner=10,
-               sweeps=10),
+               sweeps=10, autotune=True),
     "5": dict(desc="adjoint step, 3D one-mode 256^3 FP32-mixed, dx=pi/4, dt=0.5, r=-0.25, "
                    "psi0=-0.25+U[-0.01,0.01] (seed 6); 10 adjoint steps per bench step",
               kind="adjoint", dims=(256, 256, 256), prec="fp32", op=(0, -0.25, 0.0, 0.0), dt=0.5,
@@ -108,6 +110,10 @@ def run_config(args):
         state = torch.from_numpy(np.concatenate(parts)).to(device=dev, dtype=dtype)
         npts = state.numel()
         run = lambda: obj.step(state, c["inner"])
+        if c.get("autotune") and not args.no_autotune:
+            # tiles of every size class chosen by measurement (untimed)
+            extra["autotune"] = {"candidates": 6, "trial_steps": 8,
+                                 "ms_per_step_sum_of_classes": obj.autotune(6, 8)}
     elif c["kind"] == "pair":
         shape = c["dims"]
         p0 = inputs.uniform_state(shape, -0.25, 0.01, seed=5)
@@ -117,6 +123,9 @@ def run_config(args):
         state = torch.from_numpy(np.stack([p0, c0])).to(device=dev, dtype=dtype)
         npts = p0.size
         run = lambda: obj.step(state, c["inner"])
+        if c.get("autotune") and not args.no_autotune:
+            extra["autotune"] = {"candidates": 6, "trial_steps": 8, "ms_per_step": obj.autotune(6, 8)}
+        extra["plan"] = obj.info()
     else:
         shape = c["dims"]
         seed = {"1": 1, "3": 3}.get(args.config, 6)
@@ -247,11 +256,17 @@ def hbm_peak():
     return 6800.0, "fallback"
 
 
+# device code of the library: the kernel headers and the translation units that instantiate the
+# kernels (the host-only plan, batch and allocation-free units choose launches, not kernel code;
+# the tiling a counter was taken on is checked separately, see ncu_traffic)
+KERNEL_UNITS = ("pfc_kern_", "pfc_line_fixed_", "pfc_row_fixed_")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2603_26818_gb300", "csrc")
     for n in sorted(os.listdir(csrc)):
-        if n.endswith((".cu", ".cuh")) and not n.startswith(("cufft", "peak_probe")):
+        if n.endswith(".cuh") or (n.endswith(".cu") and n.startswith(KERNEL_UNITS)):
             h.update(open(os.path.join(csrc, n), "rb").read())
     return h.hexdigest()[:16]
 
@@ -265,8 +280,9 @@ def kernel_names(info):
     return {"row": row, "line": line}
 
 
-def ncu_traffic(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
+def ncu_traffic(kernel_key, plan_info=None):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel
+    source and (when the summary records it) on the same tiling as plan_info."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -275,7 +291,12 @@ def ncu_traffic(kernel_key):
     if t.get("source_hash") != kernel_source_hash():
         return None
     k = t.get("kernels", {}).get(kernel_key)
-    return None if k is None else k.get("dram_bytes_per_launch_full_size")
+    if k is None:
+        return None
+    if plan_info is not None and "plan" in k:
+        if any(plan_info.get(f) != v for f, v in k["plan"].items()):
+            return None
+    return k.get("dram_bytes_per_launch_full_size")
 
 
 # ------------------------------------------------------------------------------- oracle
@@ -444,7 +465,7 @@ def run_ours(args):
     achieved = alg[dom] / dur / 1e9
     key = kernel_names(plan.info())[dom]
     roof = {"bound": "hbm", "kernel": key, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": ncu_traffic(key),
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": ncu_traffic(key, plan.info()),
             "algorithmic_bytes_per_launch": alg[dom], "avg_launch_ms": dur * 1e3,
             "per_kernel_ms_per_step": {k: prof[k] / INNER for k in ("row", "line")},
             "per_kernel_gbs": {k: alg[k] / (prof[k] * 1e-3 / INNER) / 1e9 for k in ("row", "line")},

@@ -130,6 +130,26 @@ pfc_status pfc_sync(pfc_plan *plan);
  *   scratch_bytes = device bytes the plan owns. */
 pfc_status pfc_plan_info(pfc_plan *plan, int32_t *tiles, int64_t *scratch_bytes);
 
+/* Autotuner: choose the plan's tiling by measurement. The candidates are the valid tilings of
+ * the grid (the split of the y/z transforms between the row and line passes, the line tile
+ * width, and, where the grid has one, the clustered psi^3 row pass on or off), in the
+ * planner's order with its own choice first; at most max_candidates (>= 1) of them are timed,
+ * each on pfc_step of trial_steps (>= 1) steps of a zero field (a fixed point of the step) in
+ * a scratch array, and the fastest is kept. The results of later calls do not depend on the
+ * tiling beyond rounding; pfc_plan_info reports the choice. Line blocks stay within the
+ * planner's limits, so every call the plan supported stays supported.
+ *   cache_path  NULL, or a text file of one JSON object per line, keyed by grid, precision,
+ *               field count and device name: an entry for this plan is applied without
+ *               timing (the last one wins); otherwise the choice is appended to the file.
+ *   best_ms_out host, may be NULL: ms per step of the chosen tiling (from the cache entry
+ *               when one was applied).
+ * Synchronises. Allocates a real array of the grid for the duration of the call, and larger
+ * plan scratch when the chosen tiling pads kx further; the adjoint's third half spectrum is
+ * released (the next pfc_step_adjoint allocates it again). Errors: INVALID_ARG,
+ * OUT_OF_MEMORY, CUDA; on an error the planner's tiling is restored. */
+pfc_status pfc_plan_autotune(pfc_plan *plan, int max_candidates, int trial_steps,
+                             const char *cache_path, double *best_ms_out);
+
 /* Measurement support. Runs exactly the work of pfc_step(plan, state, nsteps) but records a
  * CUDA event on the plan's stream between consecutive kernel launches (no CUDA graph), then
  * synchronises and returns the summed event time per kernel kind in ms_out[4] (host):
@@ -183,6 +203,13 @@ pfc_status pfc_batch_destroy(pfc_batch *batch);
 
 /* Advance every domain of the packed device state by nsteps. */
 pfc_status pfc_batch_step(pfc_batch *batch, void *packed_state, int64_t nsteps);
+
+/* Autotune the tiling of every size class as pfc_plan_autotune does, each class timed alone on
+ * trial_steps of its steps on zero fields; *best_ms_out (host, may be NULL) = the sum over
+ * classes of the chosen ms per step. The step graph is captured again at the next
+ * pfc_batch_step. Synchronises. Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+pfc_status pfc_batch_autotune(pfc_batch *batch, int max_candidates, int trial_steps,
+                              double *best_ms_out);
 
 /* Per-domain mass (mean), out_host[ndomains]. Synchronises. */
 pfc_status pfc_batch_mass(pfc_batch *batch, const void *packed_state, double *out_host);

@@ -24,7 +24,7 @@ PFC_ONE_MODE, PFC_TWO_MODE = 0, 1
 # every extern "C" symbol of include/pfc.h
 EXPORTS = ["pfc_plan_create", "pfc_plan_destroy", "pfc_step", "pfc_fft_r2c", "pfc_fft_c2r",
            "pfc_mass", "pfc_energy", "pfc_step_adjoint", "pfc_set_r", "pfc_sync", "pfc_plan_info",
-           "pfc_profile_steps", "pfc_step_noalloc",
+           "pfc_profile_steps", "pfc_step_noalloc", "pfc_plan_autotune", "pfc_batch_autotune",
            "pfc_status_string", "pfc_last_error", "pfc_batch_create", "pfc_batch_destroy",
            "pfc_batch_step", "pfc_batch_mass"]
 
@@ -68,6 +68,8 @@ def load_library(path: str = LIB_PATH):
         "pfc_sync": [vp],
         "pfc_plan_info": [vp, P(ctypes.c_int32), P(i64)],
         "pfc_profile_steps": [vp, vp, i64, P(dbl), P(i64)],
+        "pfc_plan_autotune": [vp, cint, cint, ctypes.c_char_p, P(dbl)],
+        "pfc_batch_autotune": [vp, cint, cint, P(dbl)],
         "pfc_step_noalloc": [cint, P(i64), dbl, dbl, P(pfc_op), cint, vp, i64, vp],
         "pfc_batch_create": [P(vp), cint, P(i64), P(dbl), dbl, dbl, cint, vp],
         "pfc_batch_destroy": [vp],
@@ -214,6 +216,14 @@ class Plan:
                                                ctypes.byref(nl)))
         return dict(zip(["row", "line", "entry", "exit"], list(ms))), nl.value
 
+    def autotune(self, max_candidates: int = 8, trial_steps: int = 20, cache: str = None) -> float:
+        """pfc_plan_autotune: time up to max_candidates tilings and keep the fastest; returns its
+        ms per step. cache: optional path of the JSON-lines cache file."""
+        ms = ctypes.c_double()
+        check(load_library().pfc_plan_autotune(self._h, int(max_candidates), int(trial_steps),
+                                               cache.encode() if cache else None, ctypes.byref(ms)))
+        return ms.value
+
     def info(self):
         tiles = (ctypes.c_int32 * 9)()
         sb = ctypes.c_int64()
@@ -275,6 +285,13 @@ class Batch:
     def step(self, state: torch.Tensor, nsteps: int = 1) -> torch.Tensor:
         check(load_library().pfc_batch_step(self._h, ctypes.c_void_p(self._ptr(state)), int(nsteps)))
         return state
+
+    def autotune(self, max_candidates: int = 8, trial_steps: int = 20) -> float:
+        """pfc_batch_autotune: tile every size class by measurement; returns the summed ms per step."""
+        ms = ctypes.c_double()
+        check(load_library().pfc_batch_autotune(self._h, int(max_candidates), int(trial_steps),
+                                                ctypes.byref(ms)))
+        return ms.value
 
     def mass(self, state: torch.Tensor):
         out = (ctypes.c_double * self.nd)()

@@ -47,6 +47,9 @@ struct pfc_plan {
     double *d_mean = nullptr, *d_part = nullptr, *d_out = nullptr;
     int *d_status = nullptr;
     size_t scratch = 0;
+    size_t half_cap = 0;          // bytes allocated for each of X and C
+    size_t adj_bytes = 0;         // bytes of A and d_adjpart
+    int ntile = 2;                // line-pass tiles (3 for a two-field plan)
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
     bool destroyed = false;
@@ -309,7 +312,8 @@ pfc_status adjoint_impl(pfc_plan *p, const void *psi_n, const void *lam_next, vo
         PFC_CUDA(cudaMalloc(&p->A, half_bytes));
         PFC_CUDA(cudaMemset(p->A, 0, half_bytes));
         PFC_CUDA(cudaMalloc(&p->d_adjpart, (size_t)nblk * sizeof(double)));
-        p->scratch += half_bytes + (size_t)nblk * sizeof(double);
+        p->adj_bytes = half_bytes + (size_t)nblk * sizeof(double);
+        p->scratch += p->adj_bytes;
     }
     const R scale_x = (R)(1.0 / ((double)g.P * (double)g.M));
     RowArgs<R> f1 = row_args<R>(p);          // Psi' = X' form of psi_n
@@ -409,6 +413,123 @@ pfc_status profile_impl(pfc_plan *p, void *state, int64_t nsteps, double *ms, in
     return PFC_OK;
 }
 
+// Switch a plan to the tiling t: X' and C' grow when t pads kx further (contents cleared),
+// the adjoint's arrays are released (its next call allocates them for t), kernel shared-memory
+// limits are raised, and the captured graph is dropped.
+pfc_status apply_tiles(pfc_plan *p, const Tiles &t) {
+    const size_t need = (size_t)t.g.nhalf * p->nfields * vbytes(p);
+    PFC_CUDA(cudaStreamSynchronize(p->stream));
+    if (p->graph) {
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    if (p->A) {
+        cudaFree(p->A);
+        cudaFree(p->d_adjpart);
+        p->A = nullptr;
+        p->d_adjpart = nullptr;
+        p->scratch -= p->adj_bytes;
+        p->adj_bytes = 0;
+    }
+    if (need > p->half_cap) {
+        cudaFree(p->X);
+        cudaFree(p->C);
+        p->X = p->C = nullptr;
+        p->scratch -= 2 * p->half_cap;
+        p->half_cap = 0;
+        PFC_CUDA(cudaMalloc(&p->X, need));
+        PFC_CUDA(cudaMalloc(&p->C, need));
+        p->half_cap = need;
+        p->scratch += 2 * need;
+    }
+    PFC_CUDA(cudaMemsetAsync(p->X, 0, p->half_cap, p->stream));
+    PFC_CUDA(cudaMemsetAsync(p->C, 0, p->half_cap, p->stream));
+    p->t = t;
+    PFC_CUDA(p->prec == PFC_FP64 ? raise_smem_attrs<double>(cfg(p)) : raise_smem_attrs<float>(cfg(p)));
+    return PFC_OK;
+}
+
+// ms per step of pfc_step(state, nsteps) on the current tiling: one untimed call (which also
+// captures the graph), then the faster of two timed calls.
+pfc_status time_steps(pfc_plan *p, void *state, int nsteps, double *ms) {
+    cudaEvent_t e0, e1;
+    PFC_CUDA(cudaEventCreate(&e0));
+    cudaError_t err = cudaEventCreate(&e1);
+    if (err != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(PFC_ERR_CUDA, std::string("autotune events: ") + cudaGetErrorString(err));
+    }
+    pfc_status st = pfc_step(p, state, nsteps);
+    double best = 1e300;
+    for (int rep = 0; rep < 2 && st == PFC_OK; ++rep) {
+        float t = 0.f;
+        if ((err = cudaEventRecord(e0, p->stream)) != cudaSuccess) break;
+        if ((st = pfc_step(p, state, nsteps)) != PFC_OK) break;
+        if ((err = cudaEventRecord(e1, p->stream)) != cudaSuccess) break;
+        if ((err = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        if ((err = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) break;
+        best = std::min(best, (double)t / nsteps);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PFC_OK) return st;
+    if (err != cudaSuccess) return fail(PFC_ERR_CUDA, std::string("autotune timing: ") + cudaGetErrorString(err));
+    *ms = best;
+    return PFC_OK;
+}
+
+// Key of an autotune cache entry: the grid, precision, field count and device.
+std::string tune_key(const pfc_plan *p) {
+    int dev = 0;
+    cudaDeviceProp prop{};
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+        std::snprintf(prop.name, sizeof(prop.name), "unknown");
+    for (char *c = prop.name; *c; ++c)
+        if (*c == ' ' || *c == '"') *c = '_';
+    char buf[384];
+    std::snprintf(buf, sizeof(buf), "%dx%dx%d prec%d fields%d %s", p->nz, p->ny, p->nx, p->prec, p->nfields,
+                  prop.name);
+    return buf;
+}
+
+// Cache file: one JSON object per line,
+//   {"key": "<nz>x<ny>x<nx> prec<p> fields<f> <device>", "Py": .., "Pz": .., "W": .., "cluster": .., "ms_per_step": ..}
+bool cache_lookup(const char *path, const std::string &key, TileChoice &c, double &ms) {
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        char k[512];
+        TileChoice t;
+        double m = 0;
+        if (std::sscanf(line, "{\"key\": \"%511[^\"]\", \"Py\": %d, \"Pz\": %d, \"W\": %d, \"cluster\": %d, "
+                              "\"ms_per_step\": %lf}", k, &t.Py, &t.Pz, &t.W, &t.cluster, &m) == 6 && key == k) {
+            c = t;   // the last entry for a key wins
+            ms = m;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void cache_store(const char *path, const std::string &key, const TileChoice &c, double ms) {
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "{\"key\": \"%s\", \"Py\": %d, \"Pz\": %d, \"W\": %d, \"cluster\": %d, \"ms_per_step\": %.6f}\n",
+                 key.c_str(), c.Py, c.Pz, c.W, c.cluster, ms);
+    std::fclose(f);
+}
+
+size_t smem_optin() {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return 0;
+    return (size_t)optin;
+}
+
 }  // namespace
 
 pfc_status pfc::set_error(pfc_status s, const std::string &msg) {
@@ -489,7 +610,7 @@ pfc_status pfc_plan_create(pfc_plan **out, int ndim, const int64_t *dims, double
         return fail(PFC_ERR_UNSUPPORTED, "no pass tiling fits shared memory for this grid and precision");
     }
     const Geom &g = p->t.g;
-    e = p->prec == PFC_FP64 ? set_smem_attrs<double>(cfg(p)) : set_smem_attrs<float>(cfg(p));
+    e = p->prec == PFC_FP64 ? raise_smem_attrs<double>(cfg(p)) : raise_smem_attrs<float>(cfg(p));
     if (e != cudaSuccess) { delete p; return fail(PFC_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e)); }
 
     const size_t half_bytes = (size_t)g.nhalf * nfields * vbytes(p);
@@ -508,6 +629,8 @@ pfc_status pfc_plan_create(pfc_plan **out, int ndim, const int64_t *dims, double
     if ((e = cudaMalloc(&p->d_part, RED_BLOCKS * sizeof(double))) != cudaSuccess) return cleanup(e);
     if ((e = cudaMalloc(&p->d_out, 8 * sizeof(double))) != cudaSuccess) return cleanup(e);
     if ((e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) return cleanup(e);
+    p->half_cap = half_bytes;
+    p->ntile = nfields == 2 ? 3 : 2;
     p->scratch = 2 * half_bytes + (ntab + nst) * vbytes(p) + (16 + RED_BLOCKS) * sizeof(double) + sizeof(int);
 
     std::vector<double> tw, st;
@@ -619,6 +742,78 @@ pfc_status pfc_plan_info(pfc_plan *p, int32_t *tiles, int64_t *scratch_bytes) {
         std::memcpy(tiles, v, sizeof(v));
     }
     if (scratch_bytes) *scratch_bytes = (int64_t)p->scratch;
+    return PFC_OK;
+}
+
+pfc_status pfc_plan_autotune(pfc_plan *p, int max_candidates, int trial_steps, const char *cache_path,
+                             double *best_ms_out) {
+    if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
+    if (max_candidates < 1 || trial_steps < 1) return fail(PFC_ERR_INVALID_ARG, "max_candidates and trial_steps must be >= 1");
+    const size_t smem_max = smem_optin();
+    if (!smem_max) return fail(PFC_ERR_CUDA, "device query failed");
+    const std::string key = tune_key(p);
+    const Tiles before = p->t;
+    if (cache_path) {
+        TileChoice c;
+        double ms = 0;
+        Tiles t;
+        if (cache_lookup(cache_path, key, c, ms) &&
+            plan_tiles_as(t, c, p->nx, p->ny, p->nz, vbytes(p), p->ntile, smem_max) &&
+            (p->nfields == 1 || t.nt_line <= 512)) {
+            pfc_status st = apply_tiles(p, t);
+            if (st != PFC_OK) return st;
+            if (best_ms_out) *best_ms_out = ms;
+            return PFC_OK;
+        }
+    }
+    // candidates in the planner's order (its own choice first), each also without the clustered
+    // row pass where it has one; line blocks no larger than the planner's (or 512 threads), so
+    // that every call the plan supported (the adjoint, the coupled pass) stays supported
+    const int max_line = std::max(512, before.nt_line);
+    std::vector<std::pair<TileChoice, Tiles>> cand;
+    for (const TileChoice &c0 : tile_candidates(p->nx, p->ny, p->nz, vbytes(p), p->ntile, smem_max)) {
+        for (int cl = 1; cl >= 0 && (int)cand.size() < max_candidates; --cl) {
+            TileChoice c = c0;
+            c.cluster = cl;
+            Tiles t;
+            if (!plan_tiles_as(t, c, p->nx, p->ny, p->nz, vbytes(p), p->ntile, smem_max)) break;
+            if (t.nt_line > max_line || (p->nfields == 2 && t.nt_line > 512)) break;
+            cand.push_back({c, t});
+            if (t.row_cs == 0) break;   // no clustered variant to compare against
+        }
+        if ((int)cand.size() >= max_candidates) break;
+    }
+    if (cand.empty()) return fail(PFC_ERR_UNSUPPORTED, "no tiling to try");
+    const size_t rbytes = p->prec == PFC_FP64 ? 8 : 4;
+    void *tmp = nullptr;
+    PFC_CUDA(cudaMalloc(&tmp, (size_t)p->t.g.nreal * p->nfields * rbytes));
+    // a zero field is a fixed point of the step: the timed work is the real work on finite data
+    cudaError_t e = cudaMemsetAsync(tmp, 0, (size_t)p->t.g.nreal * p->nfields * rbytes, p->stream);
+    if (e != cudaSuccess) {
+        cudaFree(tmp);
+        return fail(PFC_ERR_CUDA, std::string("autotune state: ") + cudaGetErrorString(e));
+    }
+    int best = -1;
+    double best_ms = 1e300;
+    pfc_status st = PFC_OK;
+    for (size_t i = 0; i < cand.size(); ++i) {
+        if ((st = apply_tiles(p, cand[i].second)) != PFC_OK) break;
+        double ms = 0;
+        if ((st = time_steps(p, tmp, trial_steps, &ms)) != PFC_OK) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = (int)i;
+        }
+    }
+    cudaFree(tmp);
+    if (st != PFC_OK) {
+        const std::string msg = pfc_last_error();
+        apply_tiles(p, before);
+        return fail(st, "autotune: " + msg);
+    }
+    if ((st = apply_tiles(p, cand[best].second)) != PFC_OK) return st;
+    if (cache_path) cache_store(cache_path, key, cand[best].first, best_ms);
+    if (best_ms_out) *best_ms_out = best_ms;
     return PFC_OK;
 }
 

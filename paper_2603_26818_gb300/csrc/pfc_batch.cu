@@ -28,6 +28,7 @@ struct BatchClass {
     void *X = nullptr, *C = nullptr, *r = nullptr;
     int64_t *moff = nullptr;    // device: member offsets into the packed state
     cudaStream_t s = nullptr;
+    size_t cap = 0;             // bytes allocated for each of X and C
 };
 
 }  // namespace
@@ -167,6 +168,72 @@ template <typename R> pfc_status batch_step_impl(pfc_batch *b, void *state, int6
     return PFC_OK;
 }
 
+// Autotune one class: time up to max_candidates tilings (the planner's order, its own choice
+// first) on trial_steps class steps of zero fields (a fixed point of the step), keep the fastest.
+template <typename R>
+pfc_status tune_class(pfc_batch *b, BatchClass &c, int max_candidates, int trial_steps, size_t smem_max,
+                      double *ms_out) {
+    const size_t vb = sizeof(R) * 2;
+    const int nm = (int)c.members.size();
+    std::vector<Tiles> cand;
+    for (const TileChoice &tc : tile_candidates(c.nx, c.ny, 1, vb, 2, smem_max)) {
+        Tiles t;
+        if (!plan_tiles_as(t, tc, c.nx, c.ny, 1, vb, 2, smem_max, nm) || t.nt_line > 512) continue;
+        t.g.ltab = BATCH_LTAB;
+        cand.push_back(t);
+        if ((int)cand.size() >= max_candidates) break;
+    }
+    if (cand.empty()) return set_error(PFC_ERR_UNSUPPORTED, "no tiling to try for a domain size");
+    cudaEvent_t e0, e1;
+    PFC_BCUDA(cudaEventCreate(&e0));
+    PFC_BCUDA(cudaEventCreate(&e1));
+    auto use = [&](const Tiles &t) -> cudaError_t {
+        const size_t need = (size_t)t.g.nhalf * vb * nm;
+        cudaError_t e = cudaStreamSynchronize(b->stream);
+        if (e == cudaSuccess && need > c.cap) {
+            cudaFree(c.X);
+            cudaFree(c.C);
+            c.X = c.C = nullptr;
+            c.cap = 0;
+            if ((e = cudaMalloc(&c.X, need)) == cudaSuccess && (e = cudaMalloc(&c.C, need)) == cudaSuccess)
+                c.cap = need;
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(c.X, 0, c.cap, b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c.C, 0, c.cap, b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_mean + c.cbase, 0, nm * sizeof(double), b->stream);
+        const LaunchCfg lc{t.g, t.nt_row, t.nt_line, t.smem_row, t.smem_line, b->stream};
+        if (e == cudaSuccess) e = raise_smem_attrs<R>(lc);
+        c.t = t;
+        return e;
+    };
+    cudaError_t e = cudaSuccess;
+    int best = -1;
+    double best_ms = 1e300;
+    for (size_t i = 0; i < cand.size() && e == cudaSuccess; ++i) {
+        if ((e = use(cand[i])) != cudaSuccess) break;
+        for (int k = 0; k < trial_steps; ++k) enqueue_class_step<R>(b, c, b->stream);
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+            float t = 0.f;
+            e = cudaEventRecord(e0, b->stream);
+            for (int k = 0; k < trial_steps; ++k) enqueue_class_step<R>(b, c, b->stream);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e == cudaSuccess && (double)t / trial_steps < best_ms) {
+                best_ms = (double)t / trial_steps;
+                best = (int)i;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e == cudaSuccess) e = use(cand[best]);
+    if (e != cudaSuccess) return set_error(PFC_ERR_CUDA, std::string("batch autotune: ") + cudaGetErrorString(e));
+    *ms_out = best_ms;
+    return PFC_OK;
+}
+
 void free_batch(pfc_batch *b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -248,6 +315,7 @@ pfc_status pfc_batch_create(pfc_batch **out, int nd, const int64_t *dims_host, c
         const size_t half = (size_t)c.t.g.nhalf * vb * nm;
         b->cls.push_back(c);
         BatchClass &cc = b->cls.back();
+        cc.cap = half;
         if ((e = cudaMalloc(&cc.X, half)) != cudaSuccess || (e = cudaMalloc(&cc.C, half)) != cudaSuccess ||
             (e = cudaMemset(cc.X, 0, half)) != cudaSuccess || (e = cudaMemset(cc.C, 0, half)) != cudaSuccess ||
             (e = cudaMalloc(&cc.moff, nm * sizeof(int64_t))) != cudaSuccess ||
@@ -294,7 +362,7 @@ pfc_status pfc_batch_create(pfc_batch **out, int nd, const int64_t *dims_host, c
     }
     if (e != cudaSuccess) return bail(PFC_ERR_CUDA, std::string("batch tables: ") + cudaGetErrorString(e));
     const LaunchCfg mx{b->cls[0].t.g, 0, 0, b->smem_row, b->smem_line, b->stream};
-    e = precision == PFC_FP64 ? set_smem_attrs<double>(mx) : set_smem_attrs<float>(mx);
+    e = precision == PFC_FP64 ? raise_smem_attrs<double>(mx) : raise_smem_attrs<float>(mx);
     if (e != cudaSuccess) return bail(PFC_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
     *out = b;
     return PFC_OK;
@@ -315,6 +383,34 @@ pfc_status pfc_batch_step(pfc_batch *b, void *packed_state, int64_t nsteps) {
     if (nsteps == 0) return PFC_OK;
     return b->prec == PFC_FP64 ? batch_step_impl<double>(b, packed_state, nsteps)
                                : batch_step_impl<float>(b, packed_state, nsteps);
+}
+
+pfc_status pfc_batch_autotune(pfc_batch *b, int max_candidates, int trial_steps, double *best_ms_out) {
+    if (!b) return set_error(PFC_ERR_INVALID_ARG, "invalid batch");
+    if (max_candidates < 1 || trial_steps < 1)
+        return set_error(PFC_ERR_INVALID_ARG, "max_candidates and trial_steps must be >= 1");
+    int dev = 0, optin = 0;
+    PFC_BCUDA(cudaGetDevice(&dev));
+    PFC_BCUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    PFC_BCUDA(cudaStreamSynchronize(b->stream));
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    double total = 0;
+    b->smem_row = b->smem_line = 0;
+    for (BatchClass &c : b->cls) {
+        double ms = 0;
+        pfc_status st = b->prec == PFC_FP64 ? tune_class<double>(b, c, max_candidates, trial_steps, (size_t)optin, &ms)
+                                            : tune_class<float>(b, c, max_candidates, trial_steps, (size_t)optin, &ms);
+        if (st != PFC_OK) return st;
+        total += ms;
+        b->smem_row = std::max(b->smem_row, c.t.smem_row);
+        b->smem_line = std::max(b->smem_line, c.t.smem_line);
+    }
+    PFC_BCUDA(cudaStreamSynchronize(b->stream));
+    if (best_ms_out) *best_ms_out = total;
+    return PFC_OK;
 }
 
 pfc_status pfc_batch_mass(pfc_batch *b, const void *packed_state, double *out_host) {

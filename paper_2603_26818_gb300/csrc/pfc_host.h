@@ -8,7 +8,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/pfc.h"
@@ -90,73 +92,95 @@ struct Tiles {
     size_t smem_row_cs = 0;
 };
 
-// Choose the split of the y/z transforms between the passes and the tile widths.
-//   row pass:  gpc groups of P = Py Pz rows of M + 1 elements (stride rounded up to 16)
-//   line pass: ntile tiles of Q W complex values (Q = ny nz / P), W columns each, one padding
-//              row after every 8 tile rows
-// Preference: 32-byte tile rows, line blocks of at most 512 threads nearest to 256, then the
-// smallest P (see the score below).
-// instances: grids of this shape stepped by the same launches (the members of a batch class)
-inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, size_t smem_max,
-                       int instances = 1) {
-    const int max_threads = vb == 8 ? 1024 : 512;   // line pass blocks
-    // row blocks of at most 512 threads: two blocks (64 registers a thread) fit an SM, so one
-    // block's memory phases overlap the other's transforms (256^3 FP32 row pass 212 -> 162 us
-    // against 1024-thread blocks)
-    const int max_row_threads = 512;
+// A tiling of a grid: the split of the y/z transforms between the passes (Py, Pz), the line
+// tile width W, and whether the psi^3 row pass may run on clusters where a cluster kernel
+// exists for the grid (cluster = 0 keeps it on single blocks).
+struct TileChoice {
+    int Py = 0, Pz = 0, W = 0;
+    int cluster = 1;
+};
+
+inline Geom grid_geom(int nx, int ny, int nz) {
     Geom g{};
     g.nx = nx; g.ny = ny; g.nz = nz; g.M = nx / 2;
     g.lnx = ilog2(nx); g.lny = ilog2(ny); g.lnz = ilog2(nz); g.lM = g.lnx - 1;
     g.ltab = std::max(g.lnx, std::max(g.lny, g.lnz));
     g.rs = (int)round_up(g.M + 1, 16);   // row_swz keeps each aligned block of 16
-    const size_t row_bytes = (size_t)g.rs * vb;
-    // PFC_TILE="Py,Pz,W" forces a tiling (used to compare tilings; rejected if it does not fit)
-    int fpy = 0, fpz = 0, fw = 0;
-    if (const char *env = std::getenv("PFC_TILE")) std::sscanf(env, "%d,%d,%d", &fpy, &fpz, &fw);
-    long best_score = LONG_MIN;
-    Geom best{};
+    return g;
+}
+
+// Score of the tiling (Py, Pz, W) of grid g, or LONG_MIN when it breaks a kernel limit or does
+// not fit shared memory:
+//   row pass:  gpc groups of P = Py Pz rows of M + 1 elements (stride rounded up to 16)
+//   line pass: ntile tiles of Q W complex values (Q = ny nz / P), W columns each, one padding
+//              row after every 8 tile rows
+// Preference: 32-byte tile rows (one DRAM sector per tile row), then line blocks of at most 512
+// threads nearest to 256 (several small blocks per SM interleave their load, transform and
+// store phases), then the smallest P. At 4096^2 FP32, 32-byte rows in 256-thread blocks
+// measured fastest, ahead of 64-byte rows or 512 threads. limit_w: tile rows of at most 64
+// bytes (lifted for a width forced by PFC_TILE).
+inline long tile_score(const Geom &g, int Py, int Pz, int W, size_t vb, int ntile, size_t smem_max,
+                       bool limit_w) {
+    const int max_threads = vb == 8 ? 1024 : 512;   // line pass blocks
+    const int ny = g.ny, nz = g.nz;
+    if (!is_pow2(Py) || Py > 8 || !is_pow2(Pz) || Pz > 8 || !is_pow2(W) || W > 16) return LONG_MIN;
+    if ((Py > 1 && ny / Py < 8) || ny % Py) return LONG_MIN;
+    if ((nz == 1 && Pz > 1) || (Pz > 1 && nz / Pz < 8) || nz % Pz) return LONG_MIN;
+    const int Qy = ny / Py, Qz = nz / Pz;
+    if ((Qy < 8 && Qy != 1) || (Qz < 8 && Qz != 1)) return LONG_MIN;
+    const int P = Py * Pz, Q = Qy * Qz;
+    if ((size_t)P * ((size_t)g.rs * vb + vb) > smem_max) return LONG_MIN;
+    if (limit_w && (size_t)W * vb > 64) return LONG_MIN;
+    if (W > g.M + 1 && W > 1) return LONG_MIN;
+    const int64_t QW = (int64_t)Q * W;
+    if (QW < 8 || QW / 8 > max_threads) return LONG_MIN;
+    const size_t tile = (size_t)(Q + Q / 8) * W;
+    if ((size_t)ntile * tile * vb > smem_max) return LONG_MIN;
+    const size_t wb = (size_t)W * vb;
+    const long pref = wb == 32 ? 5 : wb == 64 ? 4 : wb == 16 ? 3 : wb == 128 ? 2 : 1;
+    const int lnt = ilog2((int)(QW / 8));
+    return pref * 1000000 - (QW / 8 > 512 ? 200000 : 0) - (long)std::abs(lnt - 8) * 1000 - P;
+}
+
+// Every valid tiling (Py, Pz, W) of the grid, best score first; ties keep the order Py, Pz
+// ascending, W descending. force: fields > 0 are fixed (a forced W lifts the 64-byte limit).
+inline std::vector<TileChoice> tile_candidates(int nx, int ny, int nz, size_t vb, int ntile, size_t smem_max,
+                                               const TileChoice &force = TileChoice{}) {
+    const Geom g = grid_geom(nx, ny, nz);
+    std::vector<std::pair<long, TileChoice>> all;
     for (int Py = 1; Py <= 8; Py *= 2) {
-        if (Py > 1 && ny / Py < 8) continue;
-        if (ny % Py) continue;
-        if (fpy && Py != fpy) continue;
+        if (force.Py > 0 && Py != force.Py) continue;
         for (int Pz = 1; Pz <= 8; Pz *= 2) {
-            if (nz == 1 && Pz > 1) continue;
-            if (Pz > 1 && nz / Pz < 8) continue;
-            if (nz % Pz) continue;
-            if (fpz && Pz != fpz) continue;
-            const int Qy = ny / Py, Qz = nz / Pz;
-            if (Qy < 8 && Qy != 1) continue;
-            if (Qz < 8 && Qz != 1) continue;
-            const int P = Py * Pz, Q = Qy * Qz;
-            if ((size_t)P * (row_bytes + vb) > smem_max) continue;
+            if (force.Pz > 0 && Pz != force.Pz) continue;
             for (int W = 16; W >= 1; W /= 2) {
-                if (fw && W != fw) continue;
-                if (!fw && (size_t)W * vb > 64) continue;   // 64-byte tile rows at most
-                if (W > g.M + 1 && W > 1) continue;
-                const int64_t QW = (int64_t)Q * W;
-                if (QW < 8 || QW / 8 > max_threads) continue;
-                const size_t tile = (size_t)(Q + Q / 8) * W;   // one padding row per 8 rows
-                if ((size_t)ntile * tile * vb > smem_max) continue;
-                // 32-byte tile rows first (one DRAM sector per tile row), then blocks of at most
-                // 512 threads, nearest to 256 (several small blocks per SM interleave their load,
-                // transform and store phases), then the smallest P. At 4096^2 FP32, 32-byte rows
-                // in 256-thread blocks measured fastest, ahead of 64-byte rows or 512 threads.
-                const size_t wb = (size_t)W * vb;
-                const long pref = wb == 32 ? 5 : wb == 64 ? 4 : wb == 16 ? 3 : wb == 128 ? 2 : 1;
-                const int lnt = ilog2((int)(QW / 8));
-                const long score = pref * 1000000 - (QW / 8 > 512 ? 200000 : 0) -
-                                   (long)std::abs(lnt - 8) * 1000 - P;
-                if (score > best_score) {
-                    best_score = score;
-                    best = g;
-                    best.Py = Py; best.Pz = Pz; best.Qy = Qy; best.Qz = Qz;
-                    best.W = W;
-                }
+                if (force.W > 0 && W != force.W) continue;
+                const long s = tile_score(g, Py, Pz, W, vb, ntile, smem_max, force.W <= 0);
+                if (s == LONG_MIN) continue;
+                TileChoice c;
+                c.Py = Py; c.Pz = Pz; c.W = W; c.cluster = force.cluster;
+                all.push_back({s, c});
             }
         }
     }
-    if (best_score == LONG_MIN) return false;
-    g = best;
+    std::stable_sort(all.begin(), all.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    std::vector<TileChoice> out;
+    for (auto &e : all) out.push_back(e.second);
+    return out;
+}
+
+// The plan of one tiling (Py, Pz, W all set): derived sizes, row groups per CTA, block sizes,
+// shared memory, and the clustered psi^3 row pass where one exists for the grid.
+// instances: grids of this shape stepped by the same launches (the members of a batch class)
+inline bool plan_tiles_as(Tiles &t, const TileChoice &c, int nx, int ny, int nz, size_t vb, int ntile,
+                          size_t smem_max, int instances = 1) {
+    Geom g = grid_geom(nx, ny, nz);
+    if (tile_score(g, c.Py, c.Pz, c.W, vb, ntile, smem_max, false) == LONG_MIN) return false;
+    // row blocks of at most 512 threads: two blocks (64 registers a thread) fit an SM, so one
+    // block's memory phases overlap the other's transforms (256^3 FP32 row pass 212 -> 162 us
+    // against 1024-thread blocks)
+    const int max_row_threads = 512;
+    const size_t row_bytes = (size_t)g.rs * vb;
+    g.Py = c.Py; g.Pz = c.Pz; g.Qy = ny / c.Py; g.Qz = nz / c.Pz; g.W = c.W;
     g.lPy = ilog2(g.Py); g.lPz = ilog2(g.Pz); g.lQy = ilog2(g.Qy); g.lQz = ilog2(g.Qz);
     g.P = g.Py * g.Pz; g.Q = g.Qy * g.Qz; g.lQ = ilog2(g.Q);
     g.lW = ilog2(g.W);
@@ -188,8 +212,10 @@ inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, s
     // 2D (Pz = 1, Py = 8) four rows per block, 3D (Pz = 8) four z_p rows of Py each
     // (PFC_ROW_CLUSTER=0 turns this off).
     t.row_cs = 0;
+    t.nt_row_cs = 0;
+    t.smem_row_cs = 0;
     const char *rc = std::getenv("PFC_ROW_CLUSTER");
-    const bool rc_on = !(rc && rc[0] == '0');
+    const bool rc_on = c.cluster != 0 && !(rc && rc[0] == '0');
     // (the cluster kernels are compiled for these row lengths only: M = 2048 in 2D, 256 in 3D)
     if (rc_on && vb == 8 && g.Pz == 1 && g.Py == 8 && gpc == 1 && 2 * (size_t)rows * row_bytes > smem_max &&
         g.M == 2048) {
@@ -206,6 +232,34 @@ inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, s
                                              2 * (int64_t)g.P * vb, 16);
     }
     return true;
+}
+
+// The planner's tiling: the best-scoring candidate. PFC_TILE="Py,Pz,W" forces a tiling (used to
+// compare tilings; rejected if it does not fit).
+inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, size_t smem_max,
+                       int instances = 1) {
+    TileChoice force;
+    if (const char *env = std::getenv("PFC_TILE")) std::sscanf(env, "%d,%d,%d", &force.Py, &force.Pz, &force.W);
+    const std::vector<TileChoice> c = tile_candidates(nx, ny, nz, vb, ntile, smem_max, force);
+    return !c.empty() && plan_tiles_as(t, c[0], nx, ny, nz, vb, ntile, smem_max, instances);
+}
+
+// A kernel's shared-memory limit is an attribute of the function, shared by every plan of the
+// process: plans (and batches, and the allocation-free step) only ever raise it to the largest
+// size any of them launches with, so a plan created later with smaller tiles cannot make an
+// earlier plan's launches exceed the limit.
+template <typename R> cudaError_t raise_smem_attrs(const LaunchCfg &c) {
+    static std::mutex mu;
+    static size_t row = 0, line = 0, cs2 = 0, cs3 = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    LaunchCfg m = c;
+    m.smem_row = row = std::max(row, c.smem_row);
+    m.smem_line = line = std::max(line, c.smem_line);
+    if (c.row_cs == 2) {
+        size_t &cs = c.g.Pz == 1 ? cs2 : cs3;
+        m.smem_row_cs = cs = std::max(cs, c.smem_row_cs);
+    }
+    return set_smem_attrs<R>(m);
 }
 
 // Per-stage twiddle tables (see StageTw): entries for R = 8, 4, 2 and Ns = 8, 64, 512.

@@ -182,7 +182,7 @@ extern "C" pfc_status pfc_step_noalloc(int ndim, const int64_t *dims, double dx,
     pfc_status s = device_setup(dev, &base);
     if (s != PFC_OK) return s;
     const LaunchCfg c{t.g, t.nt_row, t.nt_line, t.smem_row, t.smem_line, reinterpret_cast<cudaStream_t>(stream)};
-    e = precision == PFC_FP64 ? set_smem_attrs<double>(c) : set_smem_attrs<float>(c);
+    e = precision == PFC_FP64 ? raise_smem_attrs<double>(c) : raise_smem_attrs<float>(c);
     if (e != cudaSuccess) return set_error(PFC_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
     return precision == PFC_FP64 ? run<double>(c, base, *op, dx, dt, state, nsteps)
                                  : run<float>(c, base, *op, dx, dt, state, nsteps);

@@ -77,6 +77,8 @@ def test_host_side_validation(lib):
     assert _create(lib, (128, 128), ops=[binding.make_op(0, -0.25), binding.make_op(0, -0.2)],
                    nfields=2, coupling=5.0) == 3
     assert lib.pfc_step(None, None, 1) == 1
+    assert lib.pfc_plan_autotune(None, 4, 20, None, None) == 1
+    assert lib.pfc_batch_autotune(None, 4, 20, None) == 1
     assert lib.pfc_plan_destroy(None) == 0
 
 

@@ -22,9 +22,14 @@ def planner(tmp_path_factory):
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-2000:]
 
-    def run(cases):
+    def run(cases, all_candidates=False):
         args = [str(v) for c in cases for v in c]
-        out = subprocess.run([exe, *args], capture_output=True, text=True, check=True).stdout
+        env = dict(os.environ)
+        env.pop("PFC_TILE", None)
+        env.pop("PFC_ROW_CLUSTER", None)
+        if all_candidates:
+            env["PLAN_DUMP_ALL"] = "1"
+        out = subprocess.run([exe, *args], capture_output=True, text=True, check=True, env=env).stdout
         return [json.loads(l) for l in out.splitlines()]
     return run
 
@@ -43,6 +48,38 @@ def _cases():
     return cases
 
 
+def _check_plan(p):
+    nx, ny, nz, vb = p["nx"], p["ny"], p["nz"], p["vb"]
+    M = nx // 2
+    assert p["M"] == M
+    assert p["P"] == p["Py"] * p["Pz"] and p["Q"] == p["Qy"] * p["Qz"]
+    assert p["Py"] * p["Qy"] == ny and p["Pz"] * p["Qz"] == nz
+    assert p["Py"] in (1, 2, 4, 8) and p["Pz"] in (1, 2, 4, 8)
+    assert p["Qy"] == 1 or p["Qy"] >= 8
+    assert p["Qz"] == 1 or p["Qz"] >= 8
+    assert nz > 1 or p["Pz"] == 1
+    # X' rows: every bin, a whole number of tiles, 16-byte aligned rows
+    assert p["xs"] >= M + 1 and p["xs"] % p["W"] == 0 and p["ncg"] * p["W"] == p["xs"]
+    assert (p["xs"] * vb) % 16 == 0
+    assert p["nhalf"] == p["P"] * p["Q"] * p["xs"]
+    # line tiles: one padding row per 8 tile rows, 8 elements per thread
+    assert p["tsz"] == (p["Q"] + p["Q"] // 8) * p["W"]
+    assert p["nt_line"] * 8 == p["Q"] * p["W"]
+    assert p["nt_line"] <= (1024 if vb == 8 else 512)
+    assert p["smem_line"] == p["ntile"] * p["tsz"] * vb <= SMEM_MAX
+    # row blocks: rows of M + 1 bins (stride a multiple of 16 for the XOR swizzle)
+    assert p["rs"] >= M + 1 and p["rs"] % 16 == 0
+    assert p["nt_row"] <= 512 and p["nt_row"] % max(1, M // 8) == 0
+    assert p["smem_row"] <= SMEM_MAX
+    assert p["Q"] % p["gpc"] == 0
+    # clustered psi^3 rows: FP32 only, at the row lengths the kernels are compiled for
+    if p["row_cs"]:
+        assert vb == 8 and p["row_cs"] == 2 and p["gpc"] == 1
+        assert (p["Pz"] == 1 and p["Py"] == 8 and M == 2048) or (p["Pz"] == 8 and M == 256)
+        assert p["smem_row_cs"] <= SMEM_MAX // 2   # two blocks per SM
+        assert p["nt_row_cs"] <= 512
+
+
 def test_plans_keep_the_kernel_invariants(planner):
     plans = planner(_cases())
     assert len(plans) == len(_cases())
@@ -51,35 +88,29 @@ def test_plans_keep_the_kernel_invariants(planner):
             # only grids whose row group or tiles cannot fit: FP64 512^3 and larger
             assert p["vb"] == 16 and p["nz"] >= 512
             continue
-        nx, ny, nz, vb = p["nx"], p["ny"], p["nz"], p["vb"]
-        M = nx // 2
-        assert p["M"] == M
-        assert p["P"] == p["Py"] * p["Pz"] and p["Q"] == p["Qy"] * p["Qz"]
-        assert p["Py"] * p["Qy"] == ny and p["Pz"] * p["Qz"] == nz
-        assert p["Py"] in (1, 2, 4, 8) and p["Pz"] in (1, 2, 4, 8)
-        assert p["Qy"] == 1 or p["Qy"] >= 8
-        assert p["Qz"] == 1 or p["Qz"] >= 8
-        assert nz > 1 or p["Pz"] == 1
-        # X' rows: every bin, a whole number of tiles, 16-byte aligned rows
-        assert p["xs"] >= M + 1 and p["xs"] % p["W"] == 0 and p["ncg"] * p["W"] == p["xs"]
-        assert (p["xs"] * vb) % 16 == 0
-        assert p["nhalf"] == p["P"] * p["Q"] * p["xs"]
-        # line tiles: one padding row per 8 tile rows, 8 elements per thread
-        assert p["tsz"] == (p["Q"] + p["Q"] // 8) * p["W"]
-        assert p["nt_line"] * 8 == p["Q"] * p["W"]
-        assert p["nt_line"] <= (1024 if vb == 8 else 512)
-        assert p["smem_line"] == p["ntile"] * p["tsz"] * vb <= SMEM_MAX
-        # row blocks: rows of M + 1 bins (stride a multiple of 16 for the XOR swizzle)
-        assert p["rs"] >= M + 1 and p["rs"] % 16 == 0
-        assert p["nt_row"] <= 512 and p["nt_row"] % max(1, M // 8) == 0
-        assert p["smem_row"] <= SMEM_MAX
-        assert p["Q"] % p["gpc"] == 0
-        # clustered psi^3 rows: FP32 only, at the row lengths the kernels are compiled for
-        if p["row_cs"]:
-            assert vb == 8 and p["row_cs"] == 2 and p["gpc"] == 1
-            assert (p["Pz"] == 1 and p["Py"] == 8 and M == 2048) or (p["Pz"] == 8 and M == 256)
-            assert p["smem_row_cs"] <= SMEM_MAX // 2   # two blocks per SM
-            assert p["nt_row_cs"] <= 512
+        _check_plan(p)
+
+
+def test_every_autotune_candidate_keeps_the_kernel_invariants(planner):
+    """The autotuner times tilings other than the planner's: each must satisfy the same
+    invariants, and the first candidate must be the planner's own choice."""
+    cases = [c for c in _cases() if c[0] * c[1] * c[2] <= 512 ** 3]
+    chosen = {tuple(c): p for c, p in zip(cases, planner(cases))}
+    allc = planner(cases, all_candidates=True)
+    assert allc
+    seen_first = set()
+    for p in allc:
+        assert p["ok"], p
+        _check_plan(p)
+        key = (p["nx"], p["ny"], p["nz"], p["vb"], p["ntile"])
+        if p["cand"] == 0 and key not in seen_first:
+            seen_first.add(key)
+            ref = [q for c, q in chosen.items() if c[:5] == key][0]
+            for k in ("Py", "Pz", "W", "row_cs"):
+                assert p[k] == ref[k], (key, k)
+    # the clustered grids also offer the single-block row pass
+    c4096 = [p for p in planner([(4096, 4096, 1, 8, 2, 1)], all_candidates=True) if p["cand"] == 0]
+    assert [p["row_cs"] for p in c4096] == [2, 0]
 
 
 def test_bench_and_config_plans(planner):
