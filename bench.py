@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / cuFFT context timings")
     ap.add_argument("--no-autotune", action="store_true",
                     help="--config 4a/4b: keep the planner's tiles instead of autotuning them")
+    ap.add_argument("--autotune", action="store_true",
+                    help="autotune the plan's tiles before timing (--config 1/3, and the headline)")
     ap.add_argument("--config", choices=sorted(CONFIGS), default=None,
                     help="time one of the other workloads instead of the 4096^2 headline (1 GPU)")
     return ap.parse_args()
@@ -114,6 +116,9 @@ def run_config(args):
             # tiles of every size class chosen by measurement (untimed)
             extra["autotune"] = {"candidates": 6, "trial_steps": 8,
                                  "ms_per_step_sum_of_classes": obj.autotune(6, 8)}
+        extra["classes"] = [[k[f] for f in ("ny", "nx", "members", "Py", "W", "gpc", "threads_line")]
+                            for k in obj.info()]
+        extra["classes_fields"] = ["ny", "nx", "members", "Py", "W", "gpc", "threads_line"]
     elif c["kind"] == "pair":
         shape = c["dims"]
         p0 = inputs.uniform_state(shape, -0.25, 0.01, seed=5)
@@ -134,6 +139,9 @@ def run_config(args):
         obj = binding.Plan(shape, DX, c["dt"], [binding.make_op(*c["op"])], precision=prec)
         state = torch.from_numpy(psi0).to(device=dev, dtype=dtype)
         npts = psi0.size
+        if args.autotune and c["kind"] == "plan":
+            extra["autotune"] = {"candidates": 8, "trial_steps": c["inner"],
+                                 "ms_per_step": obj.autotune(8, c["inner"])}
         extra["plan"] = obj.info()
         if c["kind"] == "plan":
             run = lambda: obj.step(state, c["inner"])
@@ -409,6 +417,7 @@ def run_ours(args):
     psi0 = make_input()
     op = binding.make_op(0, R_OP)
     plan = binding.Plan((NY, NX), DX, DT, [op], precision="fp32")
+    tuned_ms = plan.autotune(8, INNER) if args.autotune else None
     state = torch.from_numpy(psi0).to(device=dev, dtype=torch.float32)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     npts = NY * NX
@@ -477,7 +486,9 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "grid": [NY, NX], "time_steps_per_step": INNER,
                        "precision": "fp32-mixed", "parallelism": f"replicas{world}",
                        "l2": "512 MiB buffer written between timed steps",
-                       "plan": plan.info()},
+                       "plan": plan.info(),
+                       "tiles": ({"autotuned": True, "ms_per_step": tuned_ms} if args.autotune
+                                 else "planner")},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_call * args.steps,
             "clocks": clk.summary()}
 

@@ -211,6 +211,12 @@ pfc_status pfc_batch_step(pfc_batch *batch, void *packed_state, int64_t nsteps);
 pfc_status pfc_batch_autotune(pfc_batch *batch, int max_candidates, int trial_steps,
                               double *best_ms_out);
 
+/* Size classes of the batch and their tiles (host out-params): *nclasses = number of classes;
+ * for class i < max_classes, classes_out[9 i .. 9 i + 8] = {ny, nx, members, Py, W,
+ * row_groups_per_cta, threads_row, threads_line, Qy}. classes_out may be NULL when
+ * max_classes is 0. */
+pfc_status pfc_batch_info(pfc_batch *batch, int32_t *classes_out, int max_classes, int32_t *nclasses);
+
 /* Per-domain mass (mean), out_host[ndomains]. Synchronises. */
 pfc_status pfc_batch_mass(pfc_batch *batch, const void *packed_state, double *out_host);
 

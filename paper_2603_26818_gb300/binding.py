@@ -25,6 +25,7 @@ PFC_ONE_MODE, PFC_TWO_MODE = 0, 1
 EXPORTS = ["pfc_plan_create", "pfc_plan_destroy", "pfc_step", "pfc_fft_r2c", "pfc_fft_c2r",
            "pfc_mass", "pfc_energy", "pfc_step_adjoint", "pfc_set_r", "pfc_sync", "pfc_plan_info",
            "pfc_profile_steps", "pfc_step_noalloc", "pfc_plan_autotune", "pfc_batch_autotune",
+           "pfc_batch_info",
            "pfc_status_string", "pfc_last_error", "pfc_batch_create", "pfc_batch_destroy",
            "pfc_batch_step", "pfc_batch_mass"]
 
@@ -70,6 +71,7 @@ def load_library(path: str = LIB_PATH):
         "pfc_profile_steps": [vp, vp, i64, P(dbl), P(i64)],
         "pfc_plan_autotune": [vp, cint, cint, ctypes.c_char_p, P(dbl)],
         "pfc_batch_autotune": [vp, cint, cint, P(dbl)],
+        "pfc_batch_info": [vp, P(ctypes.c_int32), cint, P(ctypes.c_int32)],
         "pfc_step_noalloc": [cint, P(i64), dbl, dbl, P(pfc_op), cint, vp, i64, vp],
         "pfc_batch_create": [P(vp), cint, P(i64), P(dbl), dbl, dbl, cint, vp],
         "pfc_batch_destroy": [vp],
@@ -292,6 +294,16 @@ class Batch:
         check(load_library().pfc_batch_autotune(self._h, int(max_candidates), int(trial_steps),
                                                 ctypes.byref(ms)))
         return ms.value
+
+    def info(self):
+        """pfc_batch_info: one dict per size class with its tiles."""
+        lib = load_library()
+        n = ctypes.c_int32()
+        check(lib.pfc_batch_info(self._h, None, 0, ctypes.byref(n)))
+        buf = (ctypes.c_int32 * (9 * n.value))()
+        check(lib.pfc_batch_info(self._h, buf, n.value, ctypes.byref(n)))
+        keys = ["ny", "nx", "members", "Py", "W", "gpc", "threads_row", "threads_line", "Qy"]
+        return [dict(zip(keys, list(buf[9 * i:9 * i + 9]))) for i in range(n.value)]
 
     def mass(self, state: torch.Tensor):
         out = (ctypes.c_double * self.nd)()

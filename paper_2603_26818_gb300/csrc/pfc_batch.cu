@@ -413,6 +413,19 @@ pfc_status pfc_batch_autotune(pfc_batch *b, int max_candidates, int trial_steps,
     return PFC_OK;
 }
 
+pfc_status pfc_batch_info(pfc_batch *b, int32_t *classes_out, int max_classes, int32_t *nclasses) {
+    if (!b || !nclasses) return set_error(PFC_ERR_INVALID_ARG, "null pointer argument");
+    if (max_classes < 0 || (max_classes > 0 && !classes_out)) return set_error(PFC_ERR_INVALID_ARG, "bad class buffer");
+    *nclasses = (int32_t)b->cls.size();
+    for (int i = 0; i < (int)b->cls.size() && i < max_classes; ++i) {
+        const BatchClass &c = b->cls[i];
+        const int32_t v[9] = {c.ny, c.nx, (int32_t)c.members.size(), c.t.g.Py, c.t.g.W, c.t.g.gpc,
+                              c.t.nt_row, c.t.nt_line, c.t.g.Qy};
+        std::memcpy(classes_out + 9 * i, v, sizeof(v));
+    }
+    return PFC_OK;
+}
+
 pfc_status pfc_batch_mass(pfc_batch *b, const void *packed_state, double *out_host) {
     if (!b || !packed_state || !out_host) return set_error(PFC_ERR_INVALID_ARG, "null pointer argument");
     if (b->prec == PFC_FP64)
