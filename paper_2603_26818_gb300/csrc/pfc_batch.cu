@@ -176,7 +176,7 @@ pfc_status tune_class(pfc_batch *b, BatchClass &c, int max_candidates, int trial
     const size_t vb = sizeof(R) * 2;
     const int nm = (int)c.members.size();
     std::vector<Tiles> cand;
-    for (const TileChoice &tc : tile_candidates(c.nx, c.ny, 1, vb, 2, smem_max)) {
+    for (const TileChoice &tc : tile_candidates(c.nx, c.ny, 1, vb, 2, smem_max, TileChoice{}, nm)) {
         Tiles t;
         if (!plan_tiles_as(t, tc, c.nx, c.ny, 1, vb, 2, smem_max, nm) || t.nt_line > 512) continue;
         t.g.ltab = BATCH_LTAB;

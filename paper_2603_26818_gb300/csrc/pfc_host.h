@@ -115,12 +115,12 @@ inline Geom grid_geom(int nx, int ny, int nz) {
 //   line pass: ntile tiles of Q W complex values (Q = ny nz / P), W columns each, one padding
 //              row after every 8 tile rows
 // Preference: 32-byte tile rows (one DRAM sector per tile row), then line blocks of at most 512
-// threads nearest to 256 (several small blocks per SM interleave their load, transform and
-// store phases), then the smallest P. At 4096^2 FP32, 32-byte rows in 256-thread blocks
+// threads nearest to 2^lnt_target (several small blocks per SM interleave their load, transform
+// and store phases), then the smallest P. At 4096^2 FP32, 32-byte rows in 256-thread blocks
 // measured fastest, ahead of 64-byte rows or 512 threads. limit_w: tile rows of at most 64
 // bytes (lifted for a width forced by PFC_TILE).
 inline long tile_score(const Geom &g, int Py, int Pz, int W, size_t vb, int ntile, size_t smem_max,
-                       bool limit_w) {
+                       bool limit_w, int lnt_target = 8) {
     const int max_threads = vb == 8 ? 1024 : 512;   // line pass blocks
     const int ny = g.ny, nz = g.nz;
     if (!is_pow2(Py) || Py > 8 || !is_pow2(Pz) || Pz > 8 || !is_pow2(W) || W > 16) return LONG_MIN;
@@ -139,13 +139,20 @@ inline long tile_score(const Geom &g, int Py, int Pz, int W, size_t vb, int ntil
     const size_t wb = (size_t)W * vb;
     const long pref = wb == 32 ? 5 : wb == 64 ? 4 : wb == 16 ? 3 : wb == 128 ? 2 : 1;
     const int lnt = ilog2((int)(QW / 8));
-    return pref * 1000000 - (QW / 8 > 512 ? 200000 : 0) - (long)std::abs(lnt - 8) * 1000 - P;
+    return pref * 1000000 - (QW / 8 > 512 ? 200000 : 0) - (long)std::abs(lnt - lnt_target) * 1000 - P;
 }
+
+// Line-block size the planner aims at (log2 threads). A grid alone: 256 threads. The members of
+// a batch class (many grids stepped by the same launches, so parallelism comes from the members):
+// 32 threads. On the 1024-domain ensemble ({64..512}^2, FP32) the autotuner's choices for the 16
+// classes had line blocks of 8 to 64 threads, and timed 1.39x the step of the 256-thread rule.
+inline int line_target(int instances) { return instances >= 8 ? 5 : 8; }
 
 // Every valid tiling (Py, Pz, W) of the grid, best score first; ties keep the order Py, Pz
 // ascending, W descending. force: fields > 0 are fixed (a forced W lifts the 64-byte limit).
+// instances: as for plan_tiles_as (sets the line-block size aimed at).
 inline std::vector<TileChoice> tile_candidates(int nx, int ny, int nz, size_t vb, int ntile, size_t smem_max,
-                                               const TileChoice &force = TileChoice{}) {
+                                               const TileChoice &force = TileChoice{}, int instances = 1) {
     const Geom g = grid_geom(nx, ny, nz);
     std::vector<std::pair<long, TileChoice>> all;
     for (int Py = 1; Py <= 8; Py *= 2) {
@@ -154,7 +161,7 @@ inline std::vector<TileChoice> tile_candidates(int nx, int ny, int nz, size_t vb
             if (force.Pz > 0 && Pz != force.Pz) continue;
             for (int W = 16; W >= 1; W /= 2) {
                 if (force.W > 0 && W != force.W) continue;
-                const long s = tile_score(g, Py, Pz, W, vb, ntile, smem_max, force.W <= 0);
+                const long s = tile_score(g, Py, Pz, W, vb, ntile, smem_max, force.W <= 0, line_target(instances));
                 if (s == LONG_MIN) continue;
                 TileChoice c;
                 c.Py = Py; c.Pz = Pz; c.W = W; c.cluster = force.cluster;
@@ -240,7 +247,7 @@ inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, s
                        int instances = 1) {
     TileChoice force;
     if (const char *env = std::getenv("PFC_TILE")) std::sscanf(env, "%d,%d,%d", &force.Py, &force.Pz, &force.W);
-    const std::vector<TileChoice> c = tile_candidates(nx, ny, nz, vb, ntile, smem_max, force);
+    const std::vector<TileChoice> c = tile_candidates(nx, ny, nz, vb, ntile, smem_max, force, instances);
     return !c.empty() && plan_tiles_as(t, c[0], nx, ny, nz, vb, ntile, smem_max, instances);
 }
 

@@ -9,16 +9,16 @@
 
 #include "../../paper_2603_26818_gb300/csrc/pfc_host.h"
 
-static void print_plan(const pfc::Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, int cand) {
+static void print_plan(const pfc::Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, int inst, int cand) {
     const pfc::Geom &g = t.g;
     std::printf("{\"nx\": %d, \"ny\": %d, \"nz\": %d, \"vb\": %zu, \"ntile\": %d, \"ok\": true, \"M\": %d, "
                 "\"Py\": %d, \"Pz\": %d, \"Qy\": %d, \"Qz\": %d, \"P\": %d, \"Q\": %d, \"W\": %d, \"xs\": %d, "
                 "\"ncg\": %d, \"tsz\": %d, \"rs\": %d, \"gpc\": %d, \"nt_row\": %d, \"nt_line\": %d, "
                 "\"smem_row\": %zu, \"smem_line\": %zu, \"row_cs\": %d, \"nt_row_cs\": %d, "
-                "\"smem_row_cs\": %zu, \"nhalf\": %lld, \"cand\": %d}\n",
+                "\"smem_row_cs\": %zu, \"nhalf\": %lld, \"inst\": %d, \"cand\": %d}\n",
                 nx, ny, nz, vb, ntile, g.M, g.Py, g.Pz, g.Qy, g.Qz, g.P, g.Q, g.W, g.xs, g.ncg, g.tsz, g.rs,
                 g.gpc, t.nt_row, t.nt_line, t.smem_row, t.smem_line, t.row_cs, t.nt_row_cs, t.smem_row_cs,
-                (long long)g.nhalf, cand);
+                (long long)g.nhalf, inst, cand);
 }
 
 int main(int argc, char **argv) {
@@ -29,7 +29,7 @@ int main(int argc, char **argv) {
         const int ntile = std::atoi(argv[i + 4]), inst = std::atoi(argv[i + 5]);
         if (std::getenv("PLAN_DUMP_ALL")) {
             int rank = 0;
-            for (const pfc::TileChoice &c0 : pfc::tile_candidates(nx, ny, nz, vb, ntile, smem_max)) {
+            for (const pfc::TileChoice &c0 : pfc::tile_candidates(nx, ny, nz, vb, ntile, smem_max, pfc::TileChoice{}, inst)) {
                 for (int cl = 1; cl >= 0; --cl) {
                     pfc::TileChoice c = c0;
                     c.cluster = cl;
@@ -39,7 +39,7 @@ int main(int argc, char **argv) {
                                     nx, ny, nz, vb, rank);
                         break;
                     }
-                    print_plan(t, nx, ny, nz, vb, ntile, rank);
+                    print_plan(t, nx, ny, nz, vb, ntile, inst, rank);
                     if (t.row_cs == 0) break;
                 }
                 ++rank;
@@ -51,7 +51,7 @@ int main(int argc, char **argv) {
             std::printf("{\"nx\": %d, \"ny\": %d, \"nz\": %d, \"vb\": %zu, \"ok\": false}\n", nx, ny, nz, vb);
             continue;
         }
-        print_plan(t, nx, ny, nz, vb, ntile, -1);
+        print_plan(t, nx, ny, nz, vb, ntile, inst, -1);
     }
     return 0;
 }

@@ -102,10 +102,10 @@ def test_every_autotune_candidate_keeps_the_kernel_invariants(planner):
     for p in allc:
         assert p["ok"], p
         _check_plan(p)
-        key = (p["nx"], p["ny"], p["nz"], p["vb"], p["ntile"])
+        key = (p["nx"], p["ny"], p["nz"], p["vb"], p["ntile"], p["inst"])
         if p["cand"] == 0 and key not in seen_first:
             seen_first.add(key)
-            ref = [q for c, q in chosen.items() if c[:5] == key][0]
+            ref = chosen[key]
             for k in ("Py", "Pz", "W", "row_cs"):
                 assert p[k] == ref[k], (key, k)
     # the clustered grids also offer the single-block row pass
