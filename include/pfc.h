@@ -138,9 +138,10 @@ pfc_status pfc_plan_info(pfc_plan *plan, int32_t *tiles, int64_t *scratch_bytes)
  * a scratch array, and the fastest is kept. The results of later calls do not depend on the
  * tiling beyond rounding; pfc_plan_info reports the choice. Line blocks stay within the
  * planner's limits, so every call the plan supported stays supported.
- *   cache_path  NULL, or a text file of one JSON object per line, keyed by grid, precision,
- *               field count and device name: an entry for this plan is applied without
- *               timing (the last one wins); otherwise the choice is appended to the file.
+ *   cache_path  a text file of one JSON object per line, keyed by grid, precision, field
+ *               count and device name: an entry for this plan is applied without timing (the
+ *               last one wins); otherwise the choice is appended to the file. NULL: the file
+ *               named by the environment variable PFC_AUTOTUNE_CACHE, or no cache if unset.
  *   best_ms_out host, may be NULL: ms per step of the chosen tiling (from the cache entry
  *               when one was applied).
  * Synchronises. Allocates a real array of the grid for the duration of the call, and larger

@@ -753,6 +753,8 @@ pfc_status pfc_plan_autotune(pfc_plan *p, int max_candidates, int trial_steps, c
     if (!smem_max) return fail(PFC_ERR_CUDA, "device query failed");
     const std::string key = tune_key(p);
     const Tiles before = p->t;
+    if (!cache_path) cache_path = std::getenv("PFC_AUTOTUNE_CACHE");
+    if (cache_path && !cache_path[0]) cache_path = nullptr;
     if (cache_path) {
         TileChoice c;
         double ms = 0;

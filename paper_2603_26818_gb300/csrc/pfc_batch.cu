@@ -186,7 +186,10 @@ pfc_status tune_class(pfc_batch *b, BatchClass &c, int max_candidates, int trial
     if (cand.empty()) return set_error(PFC_ERR_UNSUPPORTED, "no tiling to try for a domain size");
     cudaEvent_t e0, e1;
     PFC_BCUDA(cudaEventCreate(&e0));
-    PFC_BCUDA(cudaEventCreate(&e1));
+    if (cudaError_t e1err = cudaEventCreate(&e1); e1err != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return set_error(PFC_ERR_CUDA, std::string("batch autotune events: ") + cudaGetErrorString(e1err));
+    }
     auto use = [&](const Tiles &t) -> cudaError_t {
         const size_t need = (size_t)t.g.nhalf * vb * nm;
         cudaError_t e = cudaStreamSynchronize(b->stream);

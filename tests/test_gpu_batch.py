@@ -69,11 +69,13 @@ def test_batch_matches_single_plans_and_graph_path_matches_direct_steps():
 
 
 def test_full_ensemble_1024_domains_fp32():
-    """1024 domains of {64..512}^2 (about 5.9e7 points), 200 steps, FP32-mixed: a sample of
-    domains against single-domain FP64 plans, and every domain's mass conserved."""
+    """1024 domains of {64..512}^2 (about 5.9e7 points), 200 steps, FP32-mixed on autotuned
+    tiles: a sample of domains against single-domain FP64 plans, and every domain's mass
+    conserved."""
     from paper_2603_26818_gb300 import binding
     draws = inputs.batch_draws(1024, seed=4)
     b = _batch(draws, "fp32")
+    b.autotune(6, 8)          # the tiles the bench times this workload on
     x, parts = _state(b, draws, 1000, torch.float32)
     b.step(x, 200)
     assert bool(torch.isfinite(x).all())
