@@ -432,15 +432,20 @@ pfc_status apply_tiles(pfc_plan *p, const Tiles &t) {
         p->adj_bytes = 0;
     }
     if (need > p->half_cap) {
+        // the new arrays first: on failure the plan keeps its arrays and tiling
+        void *x = nullptr, *c = nullptr;
+        PFC_CUDA(cudaMalloc(&x, need));
+        if (cudaError_t e = cudaMalloc(&c, need); e != cudaSuccess) {
+            cudaFree(x);
+            return fail(e == cudaErrorMemoryAllocation ? PFC_ERR_OUT_OF_MEMORY : PFC_ERR_CUDA,
+                        std::string("autotune scratch: ") + cudaGetErrorString(e));
+        }
         cudaFree(p->X);
         cudaFree(p->C);
-        p->X = p->C = nullptr;
-        p->scratch -= 2 * p->half_cap;
-        p->half_cap = 0;
-        PFC_CUDA(cudaMalloc(&p->X, need));
-        PFC_CUDA(cudaMalloc(&p->C, need));
+        p->X = x;
+        p->C = c;
+        p->scratch += 2 * (need - p->half_cap);
         p->half_cap = need;
-        p->scratch += 2 * need;
     }
     PFC_CUDA(cudaMemsetAsync(p->X, 0, p->half_cap, p->stream));
     PFC_CUDA(cudaMemsetAsync(p->C, 0, p->half_cap, p->stream));

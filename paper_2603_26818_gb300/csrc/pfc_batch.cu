@@ -190,23 +190,29 @@ pfc_status tune_class(pfc_batch *b, BatchClass &c, int max_candidates, int trial
         cudaEventDestroy(e0);
         return set_error(PFC_ERR_CUDA, std::string("batch autotune events: ") + cudaGetErrorString(e1err));
     }
+    // switch the class to tiling t; on failure the class keeps its arrays and tiling
     auto use = [&](const Tiles &t) -> cudaError_t {
         const size_t need = (size_t)t.g.nhalf * vb * nm;
         cudaError_t e = cudaStreamSynchronize(b->stream);
         if (e == cudaSuccess && need > c.cap) {
+            void *x = nullptr, *y = nullptr;
+            if ((e = cudaMalloc(&x, need)) != cudaSuccess) return e;
+            if ((e = cudaMalloc(&y, need)) != cudaSuccess) {
+                cudaFree(x);
+                return e;
+            }
             cudaFree(c.X);
             cudaFree(c.C);
-            c.X = c.C = nullptr;
-            c.cap = 0;
-            if ((e = cudaMalloc(&c.X, need)) == cudaSuccess && (e = cudaMalloc(&c.C, need)) == cudaSuccess)
-                c.cap = need;
+            c.X = x;
+            c.C = y;
+            c.cap = need;
         }
         if (e == cudaSuccess) e = cudaMemsetAsync(c.X, 0, c.cap, b->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(c.C, 0, c.cap, b->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(b->d_mean + c.cbase, 0, nm * sizeof(double), b->stream);
         const LaunchCfg lc{t.g, t.nt_row, t.nt_line, t.smem_row, t.smem_line, b->stream};
         if (e == cudaSuccess) e = raise_smem_attrs<R>(lc);
-        c.t = t;
+        if (e == cudaSuccess) c.t = t;
         return e;
     };
     cudaError_t e = cudaSuccess;
