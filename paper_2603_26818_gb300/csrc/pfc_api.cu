@@ -497,36 +497,6 @@ std::string tune_key(const pfc_plan *p) {
     return buf;
 }
 
-// Cache file: one JSON object per line,
-//   {"key": "<nz>x<ny>x<nx> prec<p> fields<f> <device>", "Py": .., "Pz": .., "W": .., "cluster": .., "ms_per_step": ..}
-bool cache_lookup(const char *path, const std::string &key, TileChoice &c, double &ms) {
-    FILE *f = std::fopen(path, "r");
-    if (!f) return false;
-    char line[1024];
-    bool found = false;
-    while (std::fgets(line, sizeof(line), f)) {
-        char k[512];
-        TileChoice t;
-        double m = 0;
-        if (std::sscanf(line, "{\"key\": \"%511[^\"]\", \"Py\": %d, \"Pz\": %d, \"W\": %d, \"cluster\": %d, "
-                              "\"ms_per_step\": %lf}", k, &t.Py, &t.Pz, &t.W, &t.cluster, &m) == 6 && key == k) {
-            c = t;   // the last entry for a key wins
-            ms = m;
-            found = true;
-        }
-    }
-    std::fclose(f);
-    return found;
-}
-
-void cache_store(const char *path, const std::string &key, const TileChoice &c, double ms) {
-    FILE *f = std::fopen(path, "a");
-    if (!f) return;
-    std::fprintf(f, "{\"key\": \"%s\", \"Py\": %d, \"Pz\": %d, \"W\": %d, \"cluster\": %d, \"ms_per_step\": %.6f}\n",
-                 key.c_str(), c.Py, c.Pz, c.W, c.cluster, ms);
-    std::fclose(f);
-}
-
 size_t smem_optin() {
     int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -764,7 +734,7 @@ pfc_status pfc_plan_autotune(pfc_plan *p, int max_candidates, int trial_steps, c
         TileChoice c;
         double ms = 0;
         Tiles t;
-        if (cache_lookup(cache_path, key, c, ms) &&
+        if (tune_cache_lookup(cache_path, key, c, ms) &&
             plan_tiles_as(t, c, p->nx, p->ny, p->nz, vbytes(p), p->ntile, smem_max) &&
             (p->nfields == 1 || t.nt_line <= 512)) {
             pfc_status st = apply_tiles(p, t);
@@ -819,7 +789,7 @@ pfc_status pfc_plan_autotune(pfc_plan *p, int max_candidates, int trial_steps, c
         return fail(st, "autotune: " + msg);
     }
     if ((st = apply_tiles(p, cand[best].second)) != PFC_OK) return st;
-    if (cache_path) cache_store(cache_path, key, cand[best].first, best_ms);
+    if (cache_path) tune_cache_store(cache_path, key, cand[best].first, best_ms);
     if (best_ms_out) *best_ms_out = best_ms;
     return PFC_OK;
 }

@@ -251,6 +251,37 @@ inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, s
     return !c.empty() && plan_tiles_as(t, c[0], nx, ny, nz, vb, ntile, smem_max, instances);
 }
 
+// Autotune cache file: one JSON object per line,
+//   {"key": "<nz>x<ny>x<nx> prec<p> fields<f> <device>", "Py": .., "Pz": .., "W": .., "cluster": .., "ms_per_step": ..}
+// Lookup returns the last entry for the key; lines in any other form are skipped.
+inline bool tune_cache_lookup(const char *path, const std::string &key, TileChoice &c, double &ms) {
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        char k[512];
+        TileChoice t;
+        double m = 0;
+        if (std::sscanf(line, "{\"key\": \"%511[^\"]\", \"Py\": %d, \"Pz\": %d, \"W\": %d, \"cluster\": %d, "
+                              "\"ms_per_step\": %lf}", k, &t.Py, &t.Pz, &t.W, &t.cluster, &m) == 6 && key == k) {
+            c = t;
+            ms = m;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+inline void tune_cache_store(const char *path, const std::string &key, const TileChoice &c, double ms) {
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "{\"key\": \"%s\", \"Py\": %d, \"Pz\": %d, \"W\": %d, \"cluster\": %d, \"ms_per_step\": %.6f}\n",
+                 key.c_str(), c.Py, c.Pz, c.W, c.cluster, ms);
+    std::fclose(f);
+}
+
 // A kernel's shared-memory limit is an attribute of the function, shared by every plan of the
 // process: plans (and batches, and the allocation-free step) only ever raise it to the largest
 // size any of them launches with, so a plan created later with smaller tiles cannot make an

@@ -120,3 +120,28 @@ def test_bench_and_config_plans(planner):
     assert (q["Py"], q["Pz"], q["W"], q["row_cs"]) == (8, 8, 2, 2)
     # a small grid alone keeps one row block per SM; as a batch class it packs row groups
     assert single["gpc"] == 1 and batch["gpc"] > 1
+
+
+def test_autotune_cache_file_round_trip(tmp_path):
+    """The autotune cache (host code): entries are valid JSON lines, a lookup finds the last entry
+    for its key, other keys and malformed lines are skipped."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path / "tune_cache")
+    r = subprocess.run([nvcc, "-std=c++17", "-O1", "-o", exe, os.path.join(ROOT, "tests", "host", "tune_cache.cu")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    path = tmp_path / "tiles.jsonl"
+    path.write_text("not json\n{\"key\": \"other\"}\n")
+    out = subprocess.run([exe, str(path)], capture_output=True, text=True, check=True).stdout
+    a, b, c = [json.loads(l) for l in out.splitlines()]
+    assert a["found"] and (a["Py"], a["Pz"], a["W"], a["cluster"]) == (8, 1, 2, 1) and a["ms"] == 0.16
+    assert b["found"] and (b["Py"], b["Pz"], b["W"], b["cluster"]) == (2, 2, 8, 0)
+    assert not c["found"]
+    entries = [json.loads(l) for l in path.read_text().splitlines()[2:]]
+    assert [e["key"] for e in entries] == ["1x4096x4096 prec1 fields1 NVIDIA_GB300",
+                                           "256x256x256 prec1 fields2 NVIDIA_GB300",
+                                           "1x4096x4096 prec1 fields1 NVIDIA_GB300"]
+    assert entries[1] == {"key": "256x256x256 prec1 fields2 NVIDIA_GB300", "Py": 2, "Pz": 2, "W": 8,
+                          "cluster": 0, "ms_per_step": 0.556376}
