@@ -185,9 +185,9 @@ const char *pfc_status_string(pfc_status status);
 const char *pfc_last_error(void);
 
 /* ---------------------------------------------------------------------------------- */
-/* Batched ensemble: many independent 2D one-mode domains of uneven sizes stepped by one */
-/* launch per pass (a work list over all domains), the whole nsteps loop captured once  */
-/* in a CUDA graph.                                                                      */
+/* Batched ensemble: many independent 2D one-mode domains of uneven sizes. Domains of    */
+/* one size form a class stepped by one launch per pass (a member index per block);      */
+/* every class is a branch of a CUDA graph captured once and replayed.                   */
 /* ---------------------------------------------------------------------------------- */
 typedef struct pfc_batch pfc_batch;
 
