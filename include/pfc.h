@@ -98,7 +98,10 @@ pfc_status pfc_fft_r2c(pfc_plan *plan, const void *in_real, void *out_half);
  * of the kx = 0 and kx = nx/2 bins are ignored. in_half is not modified. */
 pfc_status pfc_fft_c2r(pfc_plan *plan, const void *in_half, void *out_real);
 
-/* Mass: the mean density of each field, out_host[nfields] (host), FP64 accumulation.
+/* Mass: the mean density of each field, out_host[nfields] (host), FP64 accumulation; the
+ * k = 0 Fourier coefficient divided by N. Eq. (6) puts the whole right-hand side under a
+ * Laplacian, so the k = 0 mode is multiplied by k^2 = 0 in the update of Listing 1 and the mass
+ * of each field is a constant of the motion (pfc_step carries it exactly in FP64).
  * Synchronises. Errors: NONFINITE if the state holds NaN or Inf. */
 pfc_status pfc_mass(pfc_plan *plan, const void *state, double *out_host);
 
@@ -163,20 +166,25 @@ pfc_status pfc_profile_steps(pfc_plan *plan, void *state, int64_t nsteps, double
  * it exists for callers that cannot call cudaMalloc, such as a process whose device memory is
  * already held by another allocator (a framework's caching allocator, a fixed budget) or a
  * latency-sensitive loop that cannot afford the device-wide synchronisation of cudaMalloc and
- * cudaFree. Same arithmetic as pfc_step on a single field; no plan is needed and nothing is
- * allocated: the work arrays live in one file-scope device array of 24 MiB that every GPU
- * loading libpfc.so holds until the process exits.
+ * cudaFree. Same arithmetic as pfc_step on a single field (the same kernels and tiling as a
+ * plan of the grid); no plan is needed and nothing is allocated: the work arrays live in one
+ * file-scope device array of 24 MiB that every GPU loading libpfc.so holds until the process
+ * exits.
  *   ndim, dims, dx, dt, op, precision  as for pfc_plan_create (one field).
  *   state   device real array, advanced in place by nsteps steps (stream ordered on stream).
  *   stream  cudaStream_t (NULL = legacy default stream).
+ * The call synchronises stream once, after the FP64 mean of the input state, to read the
+ * status word: a state holding NaN or Inf returns PFC_ERR_NONFINITE and is left unchanged.
+ * The steps that follow are stream ordered (not synchronised).
  * Limit: the two padded half spectra of the grid must fit the array beside its 0.3 MiB of
  * tables, e.g. 2D 1024x1024 in FP64 or 1024x2048 in FP32-mixed, 3D 128^3 in FP32-mixed or
  * 64^3 in FP64 (2048^2 FP32-mixed and 128^3 FP64 do not fit); a larger grid returns
  * PFC_ERR_UNSUPPORTED before any device work (use pfc_plan_create).
- * The first call on a device takes the array's device address and writes its twiddle tables
- * with synchronous copies, so make it before any stream capture. All calls share the array
- * and find the previous call's contents there: each call clears what must start at zero,
- * and calls that overlap on the GPU (other streams or threads) race. */
+ * The first call on a device (and the first after a device reset) writes the array's twiddle
+ * tables with synchronous copies. The host-side checks of a problem (stability, tiling, size)
+ * are done on its first call and remembered. All calls share the array and find the previous
+ * call's contents there: each call clears what must start at zero, and calls that overlap on
+ * the GPU (other streams or threads) race. */
 pfc_status pfc_step_noalloc(int ndim, const int64_t *dims, double dx, double dt, const pfc_op *op,
                             int precision, void *state, int64_t nsteps, void *stream);
 

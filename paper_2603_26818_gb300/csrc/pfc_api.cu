@@ -95,13 +95,7 @@ template <typename R> LineArgs<R> line_args(const pfc_plan *p) {
     return a;
 }
 
-LaunchCfg cfg(const pfc_plan *p) {
-    LaunchCfg c{p->t.g, p->t.nt_row, p->t.nt_line, p->t.smem_row, p->t.smem_line, p->stream};
-    c.row_cs = p->t.row_cs;
-    c.nt_row_cs = p->t.nt_row_cs;
-    c.smem_row_cs = p->t.smem_row_cs;
-    return c;
-}
+LaunchCfg cfg(const pfc_plan *p) { return launch_cfg(p->t, p->stream); }
 
 template <typename R> void launch_row_m(const pfc_plan *p, int mode, const RowArgs<R> &a, int nf) {
     launch_row<R>(cfg(p), mode, a, nf);

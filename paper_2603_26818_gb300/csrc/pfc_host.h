@@ -241,6 +241,15 @@ inline bool plan_tiles_as(Tiles &t, const TileChoice &c, int nx, int ny, int nz,
     return true;
 }
 
+// The launch configuration of a tiling on a stream (the clustered row pass included).
+inline LaunchCfg launch_cfg(const Tiles &t, cudaStream_t stream) {
+    LaunchCfg c{t.g, t.nt_row, t.nt_line, t.smem_row, t.smem_line, stream};
+    c.row_cs = t.row_cs;
+    c.nt_row_cs = t.nt_row_cs;
+    c.smem_row_cs = t.smem_row_cs;
+    return c;
+}
+
 // The planner's tiling: the best-scoring candidate. PFC_TILE="Py,Pz,W" forces a tiling (used to
 // compare tilings; rejected if it does not fit).
 inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, size_t smem_max,

@@ -92,3 +92,36 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
             binding.load_library(str(tmp_path / "missing.so"))
     finally:
         binding._lib = saved
+
+
+def _noalloc(lib, dims, dx=0.785, dt=0.5, op=None, prec=0, state=16, nsteps=1):
+    """pfc_step_noalloc with a fake (aligned, never dereferenced) state pointer: every call here
+    must be rejected on the host before any device work."""
+    from paper_2603_26818_gb300 import binding
+    op = op if op is not None else binding.make_op(0, -0.25)
+    d = (ctypes.c_int64 * len(dims))(*dims) if dims is not None else None
+    return lib.pfc_step_noalloc(len(dims) if dims else 2, d, dx, dt,
+                                ctypes.byref(op) if op is not False else None, prec,
+                                ctypes.c_void_p(state) if state else None, nsteps, None)
+
+
+def test_noalloc_host_side_rejections(lib):
+    from paper_2603_26818_gb300 import binding
+    assert _noalloc(lib, None) == 1                                      # null dims
+    assert _noalloc(lib, (128, 128), state=0) == 1                       # null state
+    assert _noalloc(lib, (128, 128), op=False) == 1                      # null operator
+    assert _noalloc(lib, (128,)) == 1                                    # ndim 1
+    assert _noalloc(lib, (128, 128), dx=-1.0) == 1
+    assert _noalloc(lib, (128, 128), dt=float("inf")) == 1
+    assert _noalloc(lib, (128, 128), prec=3) == 1
+    assert _noalloc(lib, (128, 128), nsteps=-1) == 1
+    assert _noalloc(lib, (128, 128), state=8) == 1                       # not 16-byte aligned
+    assert _noalloc(lib, (128, 128), op=binding.make_op(0, float("nan"))) == 1
+    assert b"finite" in lib.pfc_last_error()
+    assert _noalloc(lib, (128, 128), op=binding.make_op(1, -0.3, float("inf"), 1.1)) == 1
+    assert _noalloc(lib, (96, 128)) == 2                                 # not a power of two
+    # grids whose two half spectra alone exceed the 24 MiB array
+    assert _noalloc(lib, (2048, 2048), prec=1) == 2
+    assert b"24 MiB" in lib.pfc_last_error()
+    assert _noalloc(lib, (128, 128, 128), prec=0) == 2
+    assert _noalloc(lib, (128, 128), nsteps=0) == 0                      # no work, no device

@@ -80,3 +80,53 @@ def test_noalloc_size_limit(shape, prec, fits):
     torch.cuda.synchronize()
     assert rel(x, before) <= TOL[prec]
     plan.close()
+
+
+def test_noalloc_matches_the_oracle():
+    """Against the FP64 oracle directly (not only against pfc_step), FP64 and FP32-mixed."""
+    import oracle
+    shape, dx, dt, op = (64, 128), math.pi / 4, 0.5, (0, -0.25, 0.0, 0.0)
+    psi0 = inputs.uniform_state(shape, -0.25, 0.05, seed=31)
+    ref = oracle.step(psi0, dx, dt, op, 12)
+    for prec, dtype, tol in (("fp64", torch.float64, 1e-12), ("fp32", torch.float32, 1e-5)):
+        x = torch.from_numpy(psi0).to(device="cuda", dtype=dtype)
+        assert _noalloc(shape, dx, dt, op, prec, x, 12) == 0
+        torch.cuda.synchronize()
+        got = x.double().cpu().numpy()
+        assert float(np.linalg.norm(got - ref) / np.linalg.norm(ref)) <= tol
+
+
+def test_noalloc_on_the_clustered_row_pass(monkeypatch):
+    """A tiling with the psi^3 row pass on two-block clusters (Py = 8 rows of nx = 4096, FP32):
+    the allocation-free step takes the same launches as the plan. The time step is unique to
+    this test, so the tiling is not one remembered from another call."""
+    from paper_2603_26818_gb300 import binding
+    monkeypatch.setenv("PFC_TILE", "8,1,4")
+    shape, dx, dt, op = (512, 4096), math.pi / 4, 0.4375, (0, -0.25, 0.0, 0.0)
+    psi0 = inputs.uniform_state(shape, -0.25, 0.05, seed=37)
+    plan = binding.Plan(shape, dx, dt, [binding.make_op(*op)], precision="fp32")
+    assert plan.info()["row_cluster"] == 2
+    ref = torch.from_numpy(psi0).to(device="cuda", dtype=torch.float32)
+    got = ref.clone()
+    for nsteps in (3, 4):
+        plan.step(ref, nsteps)
+        assert _noalloc(shape, dx, dt, op, "fp32", got, nsteps) == 0
+        torch.cuda.synchronize()
+        assert rel(got, ref) <= TOL["fp32"]
+    plan.close()
+
+
+def test_noalloc_rejects_a_nonfinite_state():
+    """NaN in the state: PFC_ERR_NONFINITE, and the state is left as it was."""
+    from paper_2603_26818_gb300 import binding
+    shape = (64, 64)
+    x = torch.from_numpy(inputs.uniform_state(shape, -0.25, 0.05, seed=41)).to(device="cuda")
+    x[5, 7] = float("nan")
+    before = x.clone()
+    rc = _noalloc(shape, math.pi / 4, 0.5, (0, -0.25, 0.0, 0.0), "fp64", x, 3)
+    assert rc == 6 and b"NaN" in binding.load_library().pfc_last_error()
+    torch.cuda.synchronize()
+    assert torch.equal(torch.nan_to_num(x, nan=7.0), torch.nan_to_num(before, nan=7.0))
+    # a finite state afterwards runs normally (the status word is cleared per call)
+    y = torch.from_numpy(inputs.uniform_state(shape, -0.25, 0.05, seed=43)).to(device="cuda")
+    assert _noalloc(shape, math.pi / 4, 0.5, (0, -0.25, 0.0, 0.0), "fp64", y, 3) == 0
