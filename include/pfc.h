@@ -74,7 +74,14 @@ typedef struct pfc_plan pfc_plan;
  *   precision PFC_FP64 (all FP64) or PFC_FP32_MIXED (FP32 data and butterflies, twiddles
  *             generated in FP64 and rounded, FP64 reductions, the k = 0 mode carried in FP64).
  *   stream    cudaStream_t the plan issues all its work on (NULL = legacy default stream).
- * Allocates the plan's device scratch (about 2 * nfields half-spectra) with cudaMalloc.
+ * Pass schedule: a step is a row pass (x transforms, psi^3, the first part of the y/z
+ * transforms) and a line pass (the rest of the y/z transforms and the update), 5 sweeps of a
+ * half spectrum, when a group of rows and two line tiles fit one SM's shared memory. Larger
+ * grids (FP64 512^3, 3D grids from 1024^3 up) take the three-pass schedule: a middle pass takes
+ * over a third part of the y/z transforms (9 sweeps a step). Two-field plans need the two-pass
+ * schedule (UNSUPPORTED otherwise).
+ * Allocates the plan's device scratch with cudaMalloc: 2 * nfields half spectra, and a third
+ * for a three-pass plan.
  * Errors: INVALID_ARG, UNSUPPORTED, UNSTABLE_OPERATOR, OUT_OF_MEMORY, CUDA. */
 pfc_status pfc_plan_create(pfc_plan **out, int ndim, const int64_t *dims, double dx, double dt,
                            const pfc_op *ops, int nfields, const double *coupling,
@@ -128,8 +135,11 @@ pfc_status pfc_set_r(pfc_plan *plan, int field, double r);
 pfc_status pfc_sync(pfc_plan *plan);
 
 /* Tile choice and memory of a plan (host out-params).
- *   tiles[9] = {Py, Pz, Qy, Qz, W, row_groups_per_cta, threads_row, threads_line,
- *               row_cluster}   (row_cluster: blocks per cluster of the psi^3 row pass, 0 = none)
+ *   tiles[11] = {Py, Pz, Qy, Qz, W, row_groups_per_cta, threads_row, threads_line,
+ *                row_cluster, Ry, Rz}
+ *     row_cluster: blocks per cluster of the psi^3 row pass, 0 = none.
+ *     Ry, Rz: the middle pass of the three-pass schedule (1, 1 = the two-pass schedule); the
+ *     y length is Py Ry Qy and the z length Pz Rz Qz.
  *   scratch_bytes = device bytes the plan owns. */
 pfc_status pfc_plan_info(pfc_plan *plan, int32_t *tiles, int64_t *scratch_bytes);
 
@@ -156,8 +166,9 @@ pfc_status pfc_plan_autotune(pfc_plan *plan, int max_candidates, int trial_steps
 
 /* Measurement support. Runs exactly the work of pfc_step(plan, state, nsteps) but records a
  * CUDA event on the plan's stream between consecutive kernel launches (no CUDA graph), then
- * synchronises and returns the summed event time per kernel kind in ms_out[4] (host):
- *   {row pass forming psi^3, line pass with the update, entry conversion, exit conversion}
+ * synchronises and returns the summed event time per kernel kind in ms_out[5] (host):
+ *   {row pass forming psi^3, line pass with the update, entry conversion, exit conversion,
+ *    middle passes of a three-pass plan (0 for two-pass plans)}
  * and the number of kernel launches in *launches (host). */
 pfc_status pfc_profile_steps(pfc_plan *plan, void *state, int64_t nsteps, double *ms_out,
                              int64_t *launches);

@@ -210,13 +210,13 @@ class Plan:
         check(load_library().pfc_sync(self._h))
 
     def profile_steps(self, state: torch.Tensor, nsteps: int):
-        """pfc_profile_steps: ms per kernel kind {row, line, entry, exit} and the launch count."""
+        """pfc_profile_steps: ms per kernel kind {row, line, entry, exit, mid} and the launch count."""
         p = self._check_real(state, "state")
-        ms = (ctypes.c_double * 4)()
+        ms = (ctypes.c_double * 5)()
         nl = ctypes.c_int64()
         check(load_library().pfc_profile_steps(self._h, ctypes.c_void_p(p), int(nsteps), ms,
                                                ctypes.byref(nl)))
-        return dict(zip(["row", "line", "entry", "exit"], list(ms))), nl.value
+        return dict(zip(["row", "line", "entry", "exit", "mid"], list(ms))), nl.value
 
     def autotune(self, max_candidates: int = 8, trial_steps: int = 20, cache: str = None) -> float:
         """pfc_plan_autotune: time up to max_candidates tilings and keep the fastest; returns its
@@ -227,10 +227,10 @@ class Plan:
         return ms.value
 
     def info(self):
-        tiles = (ctypes.c_int32 * 9)()
+        tiles = (ctypes.c_int32 * 11)()
         sb = ctypes.c_int64()
         check(load_library().pfc_plan_info(self._h, tiles, ctypes.byref(sb)))
-        keys = ["Py", "Pz", "Qy", "Qz", "W", "gpc", "threads_row", "threads_line", "row_cluster"]
+        keys = ["Py", "Pz", "Qy", "Qz", "W", "gpc", "threads_row", "threads_line", "row_cluster", "Ry", "Rz"]
         d = dict(zip(keys, list(tiles)))
         d["scratch_bytes"] = sb.value
         return d

@@ -43,7 +43,9 @@ __global__ void __launch_bounds__(512) k_line_adj(const Geom g, const AdjArgs<R>
     const PadTileAddr ady = tile_y(g, mp);
     const TileAddr adz = tile_z(g, mp);
     const bool two_axes = g.Qz > 1;
-    const int kpy = kp % g.Py, kpz = kp / g.Py;
+    int kpy, kpz;
+    line_kp(g, kp, kpy, kpz);
+    const int lsy = g.lPy + g.lRy, lsz = g.lPz + g.lRz;
     V v[8];
 
 
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(512) k_line_adj(const Geom g, const AdjArgs<R>
     auto mult = [&](int m, R &ca, R &cb) {
         const int kqy = two_axes ? mp.yq : mp.jy + m * mp.ny8;
         const int kqz = two_axes ? mp.jz + m * mp.nz8 : 0;
-        const int ky = kpy + (kqy << g.lPy), kz = kpz + (kqz << g.lPz);
+        const int ky = kpy + (kqy << lsy), kz = kpz + (kqz << lsz);
         const int my = ky <= (g.ny >> 1) ? ky : ky - g.ny;
         const int mz = kz <= (g.nz >> 1) ? kz : kz - g.nz;
         const R fy = a.up.cy * (R)my, fz = a.up.cz * (R)mz;

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -42,12 +43,14 @@ struct pfc_plan {
     cudaStream_t stream = nullptr;
     Tiles t{};
     void *X = nullptr, *C = nullptr, *tw = nullptr, *stw = nullptr;
+    void *Y = nullptr;            // three-pass plans: the state in the row-pass form (P-part only)
     void *A = nullptr;            // third half spectrum, allocated by the first adjoint call
     double *d_adjpart = nullptr;  // adjoint line-pass partial sums (one per block)
     double *d_mean = nullptr, *d_part = nullptr, *d_out = nullptr;
     int *d_status = nullptr;
     size_t scratch = 0;
     size_t half_cap = 0;          // bytes allocated for each of X and C
+    size_t y_cap = 0;             // bytes allocated for Y
     size_t adj_bytes = 0;         // bytes of A and d_adjpart
     int ntile = 2;                // line-pass tiles (3 for a two-field plan)
     cudaGraphExec_t graph = nullptr;
@@ -100,6 +103,19 @@ LaunchCfg cfg(const pfc_plan *p) { return launch_cfg(p->t, p->stream); }
 template <typename R> void launch_row_m(const pfc_plan *p, int mode, const RowArgs<R> &a, int nf) {
     launch_row<R>(cfg(p), mode, a, nf);
 }
+// Middle pass of a three-pass plan: dir -1 forward (row-pass form -> line form), +1 inverse
+// (unnormalised); edges: only the kx = 0 and nx/2 columns.
+template <typename R>
+void launch_mid_m(const pfc_plan *p, int dir, const void *in, void *out, double scale, bool edges) {
+    MidArgs<R> a{};
+    a.in = in;
+    a.out = out;
+    a.scale = (R)scale;
+    a.tw = reinterpret_cast<const typename VT<R>::V *>(p->tw);
+    a.edges = edges ? 1 : 0;
+    launch_mid<R>(cfg(p), dir, a);
+}
+bool three_pass(const pfc_plan *p) { return p->t.g.R > 1; }
 template <typename R> void launch_line_m(const pfc_plan *p, int mode, const LineArgs<R> &a, int nf) {
     launch_line<R>(cfg(p), mode, a, nf);
 }
@@ -136,15 +152,60 @@ template <typename R> void launch_update(pfc_plan *p) {
     launch_line_m<R>(p, LINE_STEP, la, 1);
 }
 
-// One step on the carried state X' (row pass + line pass).
-template <typename R> void enqueue_one_step(pfc_plan *p) {
+// The psi^3 row pass of one step. Two-pass plans: X' -> C', edge columns projected in X'.
+// Three-pass plans carry X'' (P and R parts done): the middle pass takes it back to the
+// row-pass form in Y, the row pass writes C' and projects Y's edge columns, and the middle pass
+// takes C' forward in place and the projected edge columns of Y forward into X'' (scale 1/R,
+// the scale of the carried state). Sweeps: 2 + 2 + 2 (+ the edge columns) before the line pass.
+template <typename R> void enqueue_cube(pfc_plan *p, int mark_mid = -1, int mark_row = -1,
+                                        const std::function<void(int)> &mark = nullptr) {
+    const bool three = three_pass(p);
+    if (three) {
+        if (mark) mark(mark_mid);
+        launch_mid_m<R>(p, +1, p->X, p->Y, 1.0, false);
+    }
     RowArgs<R> ra = row_args<R>(p);
-    ra.in = p->X;
+    ra.in = three ? p->Y : p->X;
     ra.out = p->C;
-    ra.proj = p->X;
+    ra.proj = three ? p->Y : p->X;
     ra.mean = p->d_mean;
+    if (mark) mark(mark_row);
     launch_row_m<R>(p, ROW_CUBE, ra, p->nfields);
+    if (three) {
+        if (mark) mark(mark_mid);
+        launch_mid_m<R>(p, -1, p->C, p->C, 1.0, false);
+        launch_mid_m<R>(p, -1, p->Y, p->X, 1.0 / p->t.g.R, true);
+    }
+}
+
+// One step on the carried state (row pass (+ middle passes) + line pass).
+template <typename R> void enqueue_one_step(pfc_plan *p) {
+    enqueue_cube<R>(p);
     launch_update<R>(p);
+}
+
+// Entry: real state -> carried state (X' or, three-pass, X'' = middle forward of X' / R).
+template <typename R> void enqueue_entry(pfc_plan *p, const void *state) {
+    const Geom &g = p->t.g;
+    launch_means<R>(p, state);
+    RowArgs<R> ra = row_args<R>(p);
+    ra.in = state;
+    ra.out = p->X;
+    ra.mean = p->d_mean;
+    ra.scale = (R)(1.0 / ((double)g.P * (double)g.M));
+    launch_row_m<R>(p, ROW_FWD, ra, p->nfields);
+    if (three_pass(p)) launch_mid_m<R>(p, -1, p->X, p->X, 1.0 / g.R, false);
+}
+
+// Exit: carried state -> real state.
+template <typename R> void enqueue_exit(pfc_plan *p, void *state) {
+    const bool three = three_pass(p);
+    if (three) launch_mid_m<R>(p, +1, p->X, p->Y, 1.0, false);
+    RowArgs<R> rb = row_args<R>(p);
+    rb.in = three ? p->Y : p->X;
+    rb.out = state;
+    rb.mean = p->d_mean;
+    launch_row_m<R>(p, ROW_INV, rb, p->nfields);
 }
 
 template <typename R> pfc_status run_steps(pfc_plan *p, int64_t nsteps) {
@@ -179,22 +240,11 @@ template <typename R> pfc_status run_steps(pfc_plan *p, int64_t nsteps) {
 }
 
 template <typename R> pfc_status step_impl(pfc_plan *p, void *state, int64_t nsteps) {
-    const Geom &g = p->t.g;
-    launch_means<R>(p, state);
-    RowArgs<R> ra = row_args<R>(p);
-    ra.in = state;
-    ra.out = p->X;
-    ra.mean = p->d_mean;
-    ra.scale = (R)(1.0 / ((double)g.P * (double)g.M));
-    launch_row_m<R>(p, ROW_FWD, ra, p->nfields);
+    enqueue_entry<R>(p, state);
     PFC_CUDA(cudaGetLastError());
     pfc_status s = run_steps<R>(p, nsteps);
     if (s != PFC_OK) return s;
-    RowArgs<R> rb = row_args<R>(p);
-    rb.in = p->X;
-    rb.out = state;
-    rb.mean = p->d_mean;
-    launch_row_m<R>(p, ROW_INV, rb, p->nfields);
+    enqueue_exit<R>(p, state);
     PFC_CUDA(cudaGetLastError());
     return PFC_OK;
 }
@@ -204,6 +254,7 @@ template <typename R> pfc_status r2c_impl(pfc_plan *p, const void *in, void *out
     ra.in = in;
     ra.out = p->X;
     launch_row_m<R>(p, ROW_FWD, ra, p->nfields);
+    if (three_pass(p)) launch_mid_m<R>(p, -1, p->X, p->X, 1.0, false);
     LineArgs<R> la = line_args<R>(p);
     la.x = p->X;
     la.std_out = out;
@@ -219,6 +270,7 @@ template <typename R> pfc_status c2r_impl(pfc_plan *p, const void *in, void *out
     la.std_in = in;
     la.scale = (R)(2.0 / (double)g.nreal);
     launch_line_m<R>(p, LINE_INV, la, p->nfields);
+    if (three_pass(p)) launch_mid_m<R>(p, +1, p->X, p->X, 1.0, false);
     RowArgs<R> ra = row_args<R>(p);
     ra.in = p->X;
     ra.out = out;
@@ -263,6 +315,7 @@ template <typename R> pfc_status energy_impl(pfc_plan *p, const void *state, dou
         ra.out = p->X;
         ra.mean = p->d_mean + f;
         launch_row_m<R>(p, ROW_FWD, ra, 1);
+        if (three_pass(p)) launch_mid_m<R>(p, -1, p->X, p->X, 1.0, false);
         LineArgs<R> la = line_args<R>(p);
         la.x = p->X;
         la.std_out = p->C;
@@ -294,14 +347,17 @@ template <typename R> pfc_status energy_impl(pfc_plan *p, const void *state, dou
 bool plan_ok(const pfc_plan *p) { return p && !p->destroyed; }
 
 // Adjoint of one step: lam_out = A lam_next - 3 psi_n^2 B lam_next, *dr += <lam_next, d psi'/dr>.
+// Three-pass plans run the same chain with the middle pass between the row-pass form (in Y) and
+// the line form of each array.
 template <typename R>
 pfc_status adjoint_impl(pfc_plan *p, const void *psi_n, const void *lam_next, void *lam_out, double *dr) {
     const Geom &g = p->t.g;
+    const bool three = three_pass(p);
     if (p->nfields != 1) return fail(PFC_ERR_UNSUPPORTED, "the adjoint step is built for single-field plans");
     if (p->t.nt_line > 512) return fail(PFC_ERR_UNSUPPORTED, "the adjoint line pass needs tiles of at most 512 threads");
     if (psi_n == lam_out) return fail(PFC_ERR_INVALID_ARG, "lam_out must not alias psi_n");
     const size_t half_bytes = (size_t)g.nhalf * vbytes(p);
-    const int nblk = g.ncg * g.P;
+    const int nblk = g.ncg * g.P * g.R;
     if (!p->A) {
         PFC_CUDA(cudaMalloc(&p->A, half_bytes));
         PFC_CUDA(cudaMemset(p->A, 0, half_bytes));
@@ -310,37 +366,46 @@ pfc_status adjoint_impl(pfc_plan *p, const void *psi_n, const void *lam_next, vo
         p->scratch += p->adj_bytes;
     }
     const R scale_x = (R)(1.0 / ((double)g.P * (double)g.M));
+    const double inv_r = 1.0 / g.R;
+    void *rowform = three ? p->Y : p->A;     // psi_n in the row-pass form
     RowArgs<R> f1 = row_args<R>(p);          // Psi' = X' form of psi_n
     f1.in = psi_n;
-    f1.out = p->A;
+    f1.out = rowform;
     f1.scale = scale_x;
     launch_row_m<R>(p, ROW_FWD, f1, 1);
     RowArgs<R> f2 = row_args<R>(p);          // C' = F_p(psi_n^3)
-    f2.in = p->A;
+    f2.in = rowform;
     f2.out = p->C;
-    f2.proj = p->A;
+    f2.proj = rowform;
     launch_row_m<R>(p, ROW_CUBE, f2, 1);
+    if (three) {
+        launch_mid_m<R>(p, -1, p->C, p->C, 1.0, false);
+        launch_mid_m<R>(p, -1, p->Y, p->A, inv_r, false);
+    }
     RowArgs<R> f3 = row_args<R>(p);          // Lam' = X' form of lam_next
     f3.in = lam_next;
     f3.out = p->X;
     f3.scale = scale_x;
     launch_row_m<R>(p, ROW_FWD, f3, 1);
+    if (three) launch_mid_m<R>(p, -1, p->X, p->X, inv_r, false);
     AdjArgs<R> aa{};
     aa.lam = p->X;
     aa.psi = p->A;
     aa.c = p->C;
     aa.partials = p->d_adjpart;
     aa.up = line_args<R>(p).up;
-    aa.PM = (R)((double)g.P * (double)g.M);
+    aa.PM = (R)((double)g.P * (double)g.M * (double)g.R);
     aa.st = stage_tw<R>(p);
     launch_line_adj<R>(cfg(p), aa);
     launch_finish(p->stream, p->d_adjpart, nblk, 1.0 / (2.0 * g.Q), dr, true);
+    if (three) launch_mid_m<R>(p, +1, p->X, p->Y, 1.0, false);
     RowArgs<R> i1 = row_args<R>(p);          // lam_out = U
-    i1.in = p->X;
+    i1.in = three ? p->Y : p->X;
     i1.out = lam_out;
     launch_row_m<R>(p, ROW_INV, i1, 1);
+    if (three) launch_mid_m<R>(p, +1, p->A, p->Y, 1.0, false);
     RowArgs<R> i2 = row_args<R>(p);          // lam_out -= 3 psi_n^2 V
-    i2.in = p->A;
+    i2.in = three ? p->Y : p->A;
     i2.out = lam_out;
     i2.aux = psi_n;
     launch_row_m<R>(p, ROW_ADJ_MIX, i2, 1);
@@ -348,10 +413,10 @@ pfc_status adjoint_impl(pfc_plan *p, const void *psi_n, const void *lam_next, vo
     return PFC_OK;
 }
 
-// pfc_step with an event between consecutive launches; kinds: 0 row, 1 line, 2 entry, 3 exit.
+// pfc_step with an event between consecutive launches; kinds: 0 row, 1 line, 2 entry, 3 exit,
+// 4 middle passes.
 template <typename R>
 pfc_status profile_impl(pfc_plan *p, void *state, int64_t nsteps, double *ms, int64_t *launches) {
-    const Geom &g = p->t.g;
     std::vector<cudaEvent_t> ev;
     std::vector<int> kind;
     auto mark = [&](int k) -> cudaError_t {
@@ -363,38 +428,26 @@ pfc_status profile_impl(pfc_plan *p, void *state, int64_t nsteps, double *ms, in
         return cudaEventRecord(e, p->stream);
     };
     int64_t nl = 0;
+    const bool three = three_pass(p);
     cudaError_t err = mark(2);
-    launch_means<R>(p, state);
-    RowArgs<R> ra = row_args<R>(p);
-    ra.in = state;
-    ra.out = p->X;
-    ra.mean = p->d_mean;
-    ra.scale = (R)(1.0 / ((double)g.P * (double)g.M));
-    launch_row_m<R>(p, ROW_FWD, ra, p->nfields);
-    nl += 2 * p->nfields + 1;
+    enqueue_entry<R>(p, state);
+    nl += 2 * p->nfields + 1 + (three ? 1 : 0);
+    auto mk = [&](int k) {
+        if (err == cudaSuccess) err = mark(k);
+    };
     for (int64_t s = 0; s < nsteps && err == cudaSuccess; ++s) {
-        RowArgs<R> rc = row_args<R>(p);
-        rc.in = p->X;
-        rc.out = p->C;
-        rc.proj = p->X;
-        rc.mean = p->d_mean;
-        if ((err = mark(0)) != cudaSuccess) break;
-        launch_row_m<R>(p, ROW_CUBE, rc, p->nfields);
-        if ((err = mark(1)) != cudaSuccess) break;
+        enqueue_cube<R>(p, 4, 0, mk);
+        mk(1);
         launch_update<R>(p);
-        nl += 2;
+        nl += 2 + (three ? 3 : 0);
     }
-    if (err == cudaSuccess) err = mark(3);
-    RowArgs<R> rb = row_args<R>(p);
-    rb.in = p->X;
-    rb.out = state;
-    rb.mean = p->d_mean;
-    launch_row_m<R>(p, ROW_INV, rb, p->nfields);
-    nl += 1;
-    if (err == cudaSuccess) err = mark(-1);
+    mk(3);
+    enqueue_exit<R>(p, state);
+    nl += 1 + (three ? 1 : 0);
+    mk(-1);
     if (err == cudaSuccess) err = cudaGetLastError();
     if (err == cudaSuccess) err = cudaStreamSynchronize(p->stream);
-    double acc[4] = {0, 0, 0, 0};
+    double acc[5] = {0, 0, 0, 0, 0};
     for (size_t i = 0; err == cudaSuccess && i + 1 < ev.size(); ++i) {
         float t = 0.f;
         err = cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
@@ -413,6 +466,12 @@ pfc_status profile_impl(pfc_plan *p, void *state, int64_t nsteps, double *ms, in
 pfc_status apply_tiles(pfc_plan *p, const Tiles &t) {
     const size_t need = (size_t)t.g.nhalf * p->nfields * vbytes(p);
     PFC_CUDA(cudaStreamSynchronize(p->stream));
+    if (t.g.R > 1 && !p->Y) {
+        // a three-pass tiling needs the row-pass form of the state as well (allocated on demand)
+        PFC_CUDA(cudaMalloc(&p->Y, std::max(need, p->half_cap)));
+        p->scratch += std::max(need, p->half_cap);
+        p->y_cap = std::max(need, p->half_cap);
+    }
     if (p->graph) {
         cudaGraphExecDestroy(p->graph);
         p->graph = nullptr;
@@ -440,6 +499,14 @@ pfc_status apply_tiles(pfc_plan *p, const Tiles &t) {
         p->C = c;
         p->scratch += 2 * (need - p->half_cap);
         p->half_cap = need;
+    }
+    if (p->Y && p->y_cap < p->half_cap) {
+        void *y = nullptr;
+        PFC_CUDA(cudaMalloc(&y, p->half_cap));
+        cudaFree(p->Y);
+        p->Y = y;
+        p->scratch += p->half_cap - p->y_cap;
+        p->y_cap = p->half_cap;
     }
     PFC_CUDA(cudaMemsetAsync(p->X, 0, p->half_cap, p->stream));
     PFC_CUDA(cudaMemsetAsync(p->C, 0, p->half_cap, p->stream));
@@ -574,7 +641,7 @@ pfc_status pfc_plan_create(pfc_plan **out, int ndim, const int64_t *dims, double
     const size_t smem_max = (size_t)optin;
     // the line pass holds two tiles, a two-field plan's three (see k_line_step2)
     if (!plan_tiles(p->t, p->nx, p->ny, p->nz, vbytes(p), nfields == 2 ? 3 : 2, smem_max) ||
-        (nfields == 2 && p->t.nt_line > 512)) {
+        (nfields == 2 && (p->t.nt_line > 512 || p->t.g.R > 1))) {
         delete p;
         return fail(PFC_ERR_UNSUPPORTED, "no pass tiling fits shared memory for this grid and precision");
     }
@@ -591,6 +658,10 @@ pfc_status pfc_plan_create(pfc_plan **out, int ndim, const int64_t *dims, double
     };
     if ((e = cudaMalloc(&p->X, half_bytes)) != cudaSuccess) return cleanup(e);
     if ((e = cudaMalloc(&p->C, half_bytes)) != cudaSuccess) return cleanup(e);
+    if (g.R > 1) {
+        if ((e = cudaMalloc(&p->Y, half_bytes)) != cudaSuccess) return cleanup(e);
+        p->y_cap = half_bytes;
+    }
     if ((e = cudaMalloc(&p->tw, ntab * vbytes(p))) != cudaSuccess) return cleanup(e);
     const int64_t nst = STW_TOTAL;
     if ((e = cudaMalloc(&p->stw, nst * vbytes(p))) != cudaSuccess) return cleanup(e);
@@ -600,7 +671,8 @@ pfc_status pfc_plan_create(pfc_plan **out, int ndim, const int64_t *dims, double
     if ((e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) return cleanup(e);
     p->half_cap = half_bytes;
     p->ntile = nfields == 2 ? 3 : 2;
-    p->scratch = 2 * half_bytes + (ntab + nst) * vbytes(p) + (16 + RED_BLOCKS) * sizeof(double) + sizeof(int);
+    p->scratch = (g.R > 1 ? 3 : 2) * half_bytes + (ntab + nst) * vbytes(p) + (16 + RED_BLOCKS) * sizeof(double) +
+                 sizeof(int);
 
     std::vector<double> tw, st;
     twiddle_tables(ntab, tw, st);
@@ -625,7 +697,7 @@ pfc_status pfc_plan_destroy(pfc_plan *p) {
     if (p->destroyed) return fail(PFC_ERR_INVALID_ARG, "plan already destroyed");
     cudaStreamSynchronize(p->stream);
     if (p->graph) cudaGraphExecDestroy(p->graph);
-    cudaFree(p->X); cudaFree(p->C); cudaFree(p->tw); cudaFree(p->stw);
+    cudaFree(p->X); cudaFree(p->C); cudaFree(p->Y); cudaFree(p->tw); cudaFree(p->stw);
     cudaFree(p->A); cudaFree(p->d_adjpart);
     cudaFree(p->d_mean); cudaFree(p->d_part); cudaFree(p->d_out); cudaFree(p->d_status);
     p->destroyed = true;
@@ -707,7 +779,8 @@ pfc_status pfc_plan_info(pfc_plan *p, int32_t *tiles, int64_t *scratch_bytes) {
     if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
     const Geom &g = p->t.g;
     if (tiles) {
-        const int32_t v[9] = {g.Py, g.Pz, g.Qy, g.Qz, g.W, g.gpc, p->t.nt_row, p->t.nt_line, p->t.row_cs};
+        const int32_t v[11] = {g.Py, g.Pz, g.Qy, g.Qz, g.W, g.gpc, p->t.nt_row, p->t.nt_line, p->t.row_cs,
+                               g.Ry, g.Rz};
         std::memcpy(tiles, v, sizeof(v));
     }
     if (scratch_bytes) *scratch_bytes = (int64_t)p->scratch;
@@ -742,7 +815,18 @@ pfc_status pfc_plan_autotune(pfc_plan *p, int max_candidates, int trial_steps, c
     // that every call the plan supported (the adjoint, the coupled pass) stays supported
     const int max_line = std::max(512, before.nt_line);
     std::vector<std::pair<TileChoice, Tiles>> cand;
-    for (const TileChoice &c0 : tile_candidates(p->nx, p->ny, p->nz, vbytes(p), p->ntile, smem_max)) {
+    // the pass schedule is a choice too: two-pass tilings first (5 sweeps a step), then, for
+    // single-field plans, up to two three-pass tilings (9 sweeps, but line tiles R times shorter)
+    std::vector<TileChoice> choices = tile_candidates(p->nx, p->ny, p->nz, vbytes(p), p->ntile, smem_max);
+    if (p->nfields == 1 && before.g.R == 1) {
+        std::vector<TileChoice> three =
+            tile_candidates(p->nx, p->ny, p->nz, vbytes(p), p->ntile, smem_max, TileChoice{}, 1, SCHED_THREE);
+        const int keep = std::min<int>(2, (int)three.size());
+        const int room = std::max(0, max_candidates - keep);
+        if ((int)choices.size() > room) choices.resize(room);
+        choices.insert(choices.end(), three.begin(), three.begin() + keep);
+    }
+    for (const TileChoice &c0 : choices) {
         for (int cl = 1; cl >= 0 && (int)cand.size() < max_candidates; --cl) {
             TileChoice c = c0;
             c.cluster = cl;

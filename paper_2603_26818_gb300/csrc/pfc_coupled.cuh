@@ -39,7 +39,9 @@ __global__ void __launch_bounds__(512, 1) k_line_step2(const Geom g, const Step2
     const PadTileAddr ady = tile_y(g, mp);
     const TileAddr adz = tile_z(g, mp);
     const bool two_axes = g.Qz > 1;
-    const int kpy = kp % g.Py, kpz = kp / g.Py;
+    int kpy, kpz;
+    line_kp(g, kp, kpy, kpz);
+    const int lsy = g.lPy + g.lRy, lsz = g.lPz + g.lRz;
     V v[8];
 
     const int kx = cg * g.W + mp.w;
@@ -50,8 +52,8 @@ __global__ void __launch_bounds__(512, 1) k_line_step2(const Geom g, const Step2
     do {                                                                                      \
         const int kqy_ = two_axes ? mp.yq : mp.jy + (m) * mp.ny8;                             \
         const int kqz_ = two_axes ? mp.jz + (m) * mp.nz8 : 0;                                 \
-        ky = kpy + (kqy_ << g.lPy);                                                           \
-        kz = kpz + (kqz_ << g.lPz);                                                           \
+        ky = kpy + (kqy_ << lsy);                                                           \
+        kz = kpz + (kqz_ << lsz);                                                           \
         const int my_ = ky <= (g.ny >> 1) ? ky : ky - g.ny;                                   \
         const int mz_ = kz <= (g.nz >> 1) ? kz : kz - g.nz;                                   \
         const R fy_ = a.up.cy * (R)my_, fz_ = a.up.cz * (R)mz_;                               \

@@ -92,13 +92,19 @@ struct Tiles {
     size_t smem_row_cs = 0;
 };
 
-// A tiling of a grid: the split of the y/z transforms between the passes (Py, Pz), the line
-// tile width W, and whether the psi^3 row pass may run on clusters where a cluster kernel
+// A tiling of a grid: the split of the y/z transforms between the passes (Py, Pz, and Ry, Rz
+// for the middle pass of the three-pass schedule; Ry = Rz = 1 is the two-pass schedule), the
+// line tile width W, and whether the psi^3 row pass may run on clusters where a cluster kernel
 // exists for the grid (cluster = 0 keeps it on single blocks).
 struct TileChoice {
     int Py = 0, Pz = 0, W = 0;
     int cluster = 1;
+    int Ry = 1, Rz = 1;
 };
+
+// Which schedules tile_candidates may return: the two-pass ones, the three-pass ones, or the
+// two-pass ones when the grid has any and the three-pass ones otherwise.
+enum { SCHED_TWO = 2, SCHED_THREE = 3, SCHED_AUTO = 0 };
 
 inline Geom grid_geom(int nx, int ny, int nz) {
     Geom g{};
@@ -106,6 +112,8 @@ inline Geom grid_geom(int nx, int ny, int nz) {
     g.lnx = ilog2(nx); g.lny = ilog2(ny); g.lnz = ilog2(nz); g.lM = g.lnx - 1;
     g.ltab = std::max(g.lnx, std::max(g.lny, g.lnz));
     g.rs = (int)round_up(g.M + 1, 16);   // row_swz keeps each aligned block of 16
+    g.Ry = g.Rz = g.R = 1;
+    g.lRy = g.lRz = g.lR = 0;
     return g;
 }
 
@@ -119,15 +127,23 @@ inline Geom grid_geom(int nx, int ny, int nz) {
 // and store phases), then the smallest P. At 4096^2 FP32, 32-byte rows in 256-thread blocks
 // measured fastest, ahead of 64-byte rows or 512 threads. limit_w: tile rows of at most 64
 // bytes (lifted for a width forced by PFC_TILE).
+//
+// Three-pass tilings (Ry Rz > 1; the middle pass takes the Ry x Rz-point sums, each at most 8):
+// the line tile is Q = ny nz / (P R) long. They cost 9 sweeps a step instead of 5, so the planner
+// takes them only for grids with no two-pass tiling; among them the same preferences apply,
+// then the smallest R.
 inline long tile_score(const Geom &g, int Py, int Pz, int W, size_t vb, int ntile, size_t smem_max,
-                       bool limit_w, int lnt_target = 8) {
+                       bool limit_w, int lnt_target = 8, int Ry = 1, int Rz = 1) {
     const int max_threads = vb == 8 ? 1024 : 512;   // line pass blocks
     const int ny = g.ny, nz = g.nz;
     if (!is_pow2(Py) || Py > 8 || !is_pow2(Pz) || Pz > 8 || !is_pow2(W) || W > 16) return LONG_MIN;
-    if ((Py > 1 && ny / Py < 8) || ny % Py) return LONG_MIN;
-    if ((nz == 1 && Pz > 1) || (Pz > 1 && nz / Pz < 8) || nz % Pz) return LONG_MIN;
-    const int Qy = ny / Py, Qz = nz / Pz;
+    if (!is_pow2(Ry) || Ry > 8 || !is_pow2(Rz) || Rz > 8 || (nz == 1 && Rz > 1)) return LONG_MIN;
+    const int three = Ry * Rz > 1;
+    if ((Py > 1 && ny / Py < 8) || ny % (Py * Ry)) return LONG_MIN;
+    if ((nz == 1 && Pz > 1) || (Pz > 1 && nz / Pz < 8) || nz % (Pz * Rz)) return LONG_MIN;
+    const int Qy = ny / (Py * Ry), Qz = nz / (Pz * Rz);
     if ((Qy < 8 && Qy != 1) || (Qz < 8 && Qz != 1)) return LONG_MIN;
+    if (three && (Qy < 8 || (nz > 1 && Qz < 8))) return LONG_MIN;
     const int P = Py * Pz, Q = Qy * Qz;
     if ((size_t)P * ((size_t)g.rs * vb + vb) > smem_max) return LONG_MIN;
     if (limit_w && (size_t)W * vb > 64) return LONG_MIN;
@@ -139,7 +155,8 @@ inline long tile_score(const Geom &g, int Py, int Pz, int W, size_t vb, int ntil
     const size_t wb = (size_t)W * vb;
     const long pref = wb == 32 ? 5 : wb == 64 ? 4 : wb == 16 ? 3 : wb == 128 ? 2 : 1;
     const int lnt = ilog2((int)(QW / 8));
-    return pref * 1000000 - (QW / 8 > 512 ? 200000 : 0) - (long)std::abs(lnt - lnt_target) * 1000 - P;
+    return pref * 1000000 - (QW / 8 > 512 ? 200000 : 0) - (long)std::abs(lnt - lnt_target) * 1000 -
+           P - 100 * (Ry * Rz - 1);
 }
 
 // Line-block size the planner aims at (log2 threads). A grid alone: 256 threads. The members of
@@ -151,28 +168,46 @@ inline int line_target(int instances) { return instances >= 8 ? 5 : 8; }
 // Every valid tiling (Py, Pz, W) of the grid, best score first; ties keep the order Py, Pz
 // ascending, W descending. force: fields > 0 are fixed (a forced W lifts the 64-byte limit).
 // instances: as for plan_tiles_as (sets the line-block size aimed at).
+// sched: SCHED_TWO, SCHED_THREE or SCHED_AUTO (a forced Ry or Rz > 1 selects SCHED_THREE).
 inline std::vector<TileChoice> tile_candidates(int nx, int ny, int nz, size_t vb, int ntile, size_t smem_max,
-                                               const TileChoice &force = TileChoice{}, int instances = 1) {
+                                               const TileChoice &force = TileChoice{}, int instances = 1,
+                                               int sched = SCHED_AUTO) {
     const Geom g = grid_geom(nx, ny, nz);
-    std::vector<std::pair<long, TileChoice>> all;
-    for (int Py = 1; Py <= 8; Py *= 2) {
-        if (force.Py > 0 && Py != force.Py) continue;
-        for (int Pz = 1; Pz <= 8; Pz *= 2) {
-            if (force.Pz > 0 && Pz != force.Pz) continue;
-            for (int W = 16; W >= 1; W /= 2) {
-                if (force.W > 0 && W != force.W) continue;
-                const long s = tile_score(g, Py, Pz, W, vb, ntile, smem_max, force.W <= 0, line_target(instances));
-                if (s == LONG_MIN) continue;
-                TileChoice c;
-                c.Py = Py; c.Pz = Pz; c.W = W; c.cluster = force.cluster;
-                all.push_back({s, c});
+    if (force.Ry > 1 || force.Rz > 1) sched = SCHED_THREE;
+    auto collect = [&](bool three) {
+        std::vector<std::pair<long, TileChoice>> all;
+        for (int Py = 1; Py <= 8; Py *= 2) {
+            if (force.Py > 0 && Py != force.Py) continue;
+            for (int Pz = 1; Pz <= 8; Pz *= 2) {
+                if (force.Pz > 0 && Pz != force.Pz) continue;
+                for (int Ry = 1; Ry <= (three ? 8 : 1); Ry *= 2) {
+                    if (three && force.Ry > 1 && Ry != force.Ry) continue;
+                    for (int Rz = 1; Rz <= (three ? 8 : 1); Rz *= 2) {
+                        if (three && force.Rz > 1 && Rz != force.Rz) continue;
+                        if (three && Ry * Rz == 1) continue;
+                        for (int W = 16; W >= 1; W /= 2) {
+                            if (force.W > 0 && W != force.W) continue;
+                            const long s = tile_score(g, Py, Pz, W, vb, ntile, smem_max, force.W <= 0,
+                                                      line_target(instances), Ry, Rz);
+                            if (s == LONG_MIN) continue;
+                            TileChoice c;
+                            c.Py = Py; c.Pz = Pz; c.W = W; c.cluster = force.cluster;
+                            c.Ry = Ry; c.Rz = Rz;
+                            all.push_back({s, c});
+                        }
+                    }
+                }
             }
         }
-    }
-    std::stable_sort(all.begin(), all.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
-    std::vector<TileChoice> out;
-    for (auto &e : all) out.push_back(e.second);
-    return out;
+        std::stable_sort(all.begin(), all.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+        std::vector<TileChoice> out;
+        for (auto &e : all) out.push_back(e.second);
+        return out;
+    };
+    if (sched == SCHED_THREE) return collect(true);
+    std::vector<TileChoice> two = collect(false);
+    if (sched == SCHED_TWO || !two.empty()) return two;
+    return collect(true);
 }
 
 // The plan of one tiling (Py, Pz, W all set): derived sizes, row groups per CTA, block sizes,
@@ -181,15 +216,19 @@ inline std::vector<TileChoice> tile_candidates(int nx, int ny, int nz, size_t vb
 inline bool plan_tiles_as(Tiles &t, const TileChoice &c, int nx, int ny, int nz, size_t vb, int ntile,
                           size_t smem_max, int instances = 1) {
     Geom g = grid_geom(nx, ny, nz);
-    if (tile_score(g, c.Py, c.Pz, c.W, vb, ntile, smem_max, false) == LONG_MIN) return false;
+    const int Ry = std::max(c.Ry, 1), Rz = std::max(c.Rz, 1);
+    if (tile_score(g, c.Py, c.Pz, c.W, vb, ntile, smem_max, false, 8, Ry, Rz) == LONG_MIN) return false;
     // row blocks of at most 512 threads: two blocks (64 registers a thread) fit an SM, so one
     // block's memory phases overlap the other's transforms (256^3 FP32 row pass 212 -> 162 us
     // against 1024-thread blocks)
     const int max_row_threads = 512;
     const size_t row_bytes = (size_t)g.rs * vb;
-    g.Py = c.Py; g.Pz = c.Pz; g.Qy = ny / c.Py; g.Qz = nz / c.Pz; g.W = c.W;
+    g.Py = c.Py; g.Pz = c.Pz; g.Ry = Ry; g.Rz = Rz;
+    g.Qy = ny / (c.Py * Ry); g.Qz = nz / (c.Pz * Rz); g.W = c.W;
     g.lPy = ilog2(g.Py); g.lPz = ilog2(g.Pz); g.lQy = ilog2(g.Qy); g.lQz = ilog2(g.Qz);
+    g.lRy = ilog2(Ry); g.lRz = ilog2(Rz);
     g.P = g.Py * g.Pz; g.Q = g.Qy * g.Qz; g.lQ = ilog2(g.Q);
+    g.R = Ry * Rz; g.lR = ilog2(g.R); g.QR = g.R * g.Q;
     g.lW = ilog2(g.W);
     g.tsz = (g.Q + g.Q / 8) * g.W;
     g.xs = (int)round_up(g.M + 1, std::max(g.W, 2));
@@ -198,12 +237,12 @@ inline bool plan_tiles_as(Tiles &t, const TileChoice &c, int nx, int ny, int nz,
     // row pass keeps at least one block per SM (a small grid alone has few groups)
     const int Tr = g.M / 8;
     int gpc = 1;
-    while (gpc * 2 <= g.Q && (size_t)(gpc * 2) * g.P * (row_bytes + vb) <= smem_max &&
-           gpc * g.P * Tr < 256 && (int64_t)g.Q * instances / (gpc * 2) >= 152)
+    while (gpc * 2 <= g.QR && (size_t)(gpc * 2) * g.P * (row_bytes + vb) <= smem_max &&
+           gpc * g.P * Tr < 256 && (int64_t)g.QR * instances / (gpc * 2) >= 152)
         gpc *= 2;
     g.gpc = gpc;
     g.nreal = (int64_t)nx * ny * nz;
-    g.nhalf = (int64_t)g.P * g.Q * g.xs;
+    g.nhalf = (int64_t)g.P * g.QR * g.xs;
     g.nstd = (int64_t)ny * nz * (g.M + 1);
     const int rows = gpc * g.P;
     t.nt_row = std::min(max_row_threads, std::max(Tr, rows * Tr));
@@ -250,19 +289,23 @@ inline LaunchCfg launch_cfg(const Tiles &t, cudaStream_t stream) {
     return c;
 }
 
-// The planner's tiling: the best-scoring candidate. PFC_TILE="Py,Pz,W" forces a tiling (used to
-// compare tilings; rejected if it does not fit).
+// The planner's tiling: the best-scoring candidate. PFC_TILE="Py,Pz,W" forces a tiling and
+// "Py,Pz,W,Ry,Rz" a three-pass one (used to compare tilings and to test the three-pass
+// schedule on small grids; rejected if it does not fit).
 inline bool plan_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int ntile, size_t smem_max,
                        int instances = 1) {
     TileChoice force;
-    if (const char *env = std::getenv("PFC_TILE")) std::sscanf(env, "%d,%d,%d", &force.Py, &force.Pz, &force.W);
+    if (const char *env = std::getenv("PFC_TILE"))
+        std::sscanf(env, "%d,%d,%d,%d,%d", &force.Py, &force.Pz, &force.W, &force.Ry, &force.Rz);
     const std::vector<TileChoice> c = tile_candidates(nx, ny, nz, vb, ntile, smem_max, force, instances);
     return !c.empty() && plan_tiles_as(t, c[0], nx, ny, nz, vb, ntile, smem_max, instances);
 }
 
 // Autotune cache file: one JSON object per line,
-//   {"key": "<nz>x<ny>x<nx> prec<p> fields<f> <device>", "Py": .., "Pz": .., "W": .., "cluster": .., "ms_per_step": ..}
-// Lookup returns the last entry for the key; lines in any other form are skipped.
+//   {"key": "<nz>x<ny>x<nx> prec<p> fields<f> <device>", "Py": .., "Pz": .., "W": .., "cluster": ..,
+//    "Ry": .., "Rz": .., "ms_per_step": ..}
+// (entries without Ry and Rz are two-pass tilings). Lookup returns the last entry for the key;
+// lines in any other form are skipped.
 inline bool tune_cache_lookup(const char *path, const std::string &key, TileChoice &c, double &ms) {
     FILE *f = std::fopen(path, "r");
     if (!f) return false;
@@ -272,8 +315,16 @@ inline bool tune_cache_lookup(const char *path, const std::string &key, TileChoi
         char k[512];
         TileChoice t;
         double m = 0;
-        if (std::sscanf(line, "{\"key\": \"%511[^\"]\", \"Py\": %d, \"Pz\": %d, \"W\": %d, \"cluster\": %d, "
-                              "\"ms_per_step\": %lf}", k, &t.Py, &t.Pz, &t.W, &t.cluster, &m) == 6 && key == k) {
+        const bool full = std::sscanf(line, "{\"key\": \"%511[^\"]\", \"Py\": %d, \"Pz\": %d, \"W\": %d, "
+                                            "\"cluster\": %d, \"Ry\": %d, \"Rz\": %d, \"ms_per_step\": %lf}",
+                                      k, &t.Py, &t.Pz, &t.W, &t.cluster, &t.Ry, &t.Rz, &m) == 8;
+        bool ok = full;
+        if (!full) {
+            t = TileChoice{};
+            ok = std::sscanf(line, "{\"key\": \"%511[^\"]\", \"Py\": %d, \"Pz\": %d, \"W\": %d, \"cluster\": %d, "
+                                   "\"ms_per_step\": %lf}", k, &t.Py, &t.Pz, &t.W, &t.cluster, &m) == 6;
+        }
+        if (ok && key == k) {
             c = t;
             ms = m;
             found = true;
@@ -286,8 +337,9 @@ inline bool tune_cache_lookup(const char *path, const std::string &key, TileChoi
 inline void tune_cache_store(const char *path, const std::string &key, const TileChoice &c, double ms) {
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "{\"key\": \"%s\", \"Py\": %d, \"Pz\": %d, \"W\": %d, \"cluster\": %d, \"ms_per_step\": %.6f}\n",
-                 key.c_str(), c.Py, c.Pz, c.W, c.cluster, ms);
+    std::fprintf(f, "{\"key\": \"%s\", \"Py\": %d, \"Pz\": %d, \"W\": %d, \"cluster\": %d, \"Ry\": %d, "
+                    "\"Rz\": %d, \"ms_per_step\": %.6f}\n",
+                 key.c_str(), c.Py, c.Pz, c.W, c.cluster, std::max(c.Ry, 1), std::max(c.Rz, 1), ms);
     std::fclose(f);
 }
 

@@ -16,9 +16,9 @@ template <typename R> void launch_row(const LaunchCfg &c, int mode, const RowArg
     if constexpr (sizeof(R) == 4) {
         if (mode == ROW_CUBE && c.row_cs == 2) {
             if (c.g.Pz == 1)
-                k_row_cube_cl<R, 2, 11><<<dim3(2 * c.g.Q, nf), c.nt_row_cs, c.smem_row_cs, c.stream>>>(c.g, a);
+                k_row_cube_cl<R, 2, 11><<<dim3(2 * c.g.QR, nf), c.nt_row_cs, c.smem_row_cs, c.stream>>>(c.g, a);
             else
-                k_row_cube_cl3<R, 8><<<dim3(2 * c.g.Q, nf), c.nt_row_cs, c.smem_row_cs, c.stream>>>(c.g, a);
+                k_row_cube_cl3<R, 8><<<dim3(2 * c.g.QR, nf), c.nt_row_cs, c.smem_row_cs, c.stream>>>(c.g, a);
             return;
         }
     }
@@ -26,7 +26,7 @@ template <typename R> void launch_row(const LaunchCfg &c, int mode, const RowArg
         launch_row_cube_fixed<R>(c, a, nf);
         return;
     }
-    dim3 grid(c.g.Q / c.g.gpc, nf);
+    dim3 grid(c.g.QR / c.g.gpc, nf);
     if (mode == ROW_CUBE) k_row<R, ROW_CUBE><<<grid, c.nt_row, c.smem_row, c.stream>>>(c.g, a);
     else if (mode == ROW_FWD) k_row<R, ROW_FWD><<<grid, c.nt_row, c.smem_row, c.stream>>>(c.g, a);
     else if (mode == ROW_INV) k_row<R, ROW_INV><<<grid, c.nt_row, c.smem_row, c.stream>>>(c.g, a);
@@ -35,7 +35,7 @@ template <typename R> void launch_row(const LaunchCfg &c, int mode, const RowArg
 
 template <typename R, int MAXT>
 static void launch_line_t(const LaunchCfg &c, int mode, const LineArgs<R> &a, int nf) {
-    dim3 grid(c.g.ncg, c.g.P, nf);
+    dim3 grid(c.g.ncg, c.g.P * c.g.R, nf);
     if (mode == LINE_STEP) k_line<R, LINE_STEP, MAXT><<<grid, c.nt_line, c.smem_line, c.stream>>>(c.g, a);
     else if (mode == LINE_FWD) k_line<R, LINE_FWD, MAXT><<<grid, c.nt_line, c.smem_line, c.stream>>>(c.g, a);
     else k_line<R, LINE_INV, MAXT><<<grid, c.nt_line, c.smem_line, c.stream>>>(c.g, a);
@@ -82,13 +82,19 @@ template <typename R> cudaError_t set_smem_attrs(const LaunchCfg &c) {
 }
 
 template <typename R> void launch_line_adj(const LaunchCfg &c, const AdjArgs<R> &a) {
-    dim3 grid(c.g.ncg, c.g.P);
+    dim3 grid(c.g.ncg, c.g.P * c.g.R);
     k_line_adj<R><<<grid, c.nt_line, c.smem_line, c.stream>>>(c.g, a);
 }
 
 template <typename R> void launch_line_step2(const LaunchCfg &c, const Step2Args<R> &a) {
-    dim3 grid(c.g.ncg, c.g.P);
+    dim3 grid(c.g.ncg, c.g.P * c.g.R);
     k_line_step2<R><<<grid, c.nt_line, c.smem_line, c.stream>>>(c.g, a);
+}
+
+template <typename R> void launch_mid(const LaunchCfg &c, int dir, const MidArgs<R> &a) {
+    const dim3 grid(a.edges ? 1 : (c.g.xs + MID_CW - 1) / MID_CW, c.g.Q, c.g.P);
+    if (dir < 0) k_mid<R, -1><<<grid, MID_THREADS, 0, c.stream>>>(c.g, a);
+    else k_mid<R, +1><<<grid, MID_THREADS, 0, c.stream>>>(c.g, a);
 }
 
 template <typename R>
@@ -118,6 +124,7 @@ void launch_reduce_spec(cudaStream_t s, const Geom &g, OpDev op, double dx, cons
     template cudaError_t set_smem_attrs<R>(const LaunchCfg &);                             \
     template void launch_line_adj<R>(const LaunchCfg &, const AdjArgs<R> &);               \
     template void launch_line_step2<R>(const LaunchCfg &, const Step2Args<R> &);           \
+    template void launch_mid<R>(const LaunchCfg &, int, const MidArgs<R> &);               \
     template void launch_batch_mean<R>(cudaStream_t, const R *, const int64_t *,           \
                                        const int64_t *, int, double *, int *);             \
     template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t,  \

@@ -8,6 +8,7 @@
 
 #include "pfc_adjoint.cuh"
 #include "pfc_coupled.cuh"
+#include "pfc_mid.cuh"
 
 namespace pfc {
 
@@ -47,6 +48,8 @@ void launch_batch_mean(cudaStream_t s, const R *base, const int64_t *off, const 
 template <typename R> void launch_line_adj(const LaunchCfg &c, const AdjArgs<R> &a);
 // coupled two-field line pass (blocks of nt_line <= 512 threads, smem_line for three tiles)
 template <typename R> void launch_line_step2(const LaunchCfg &c, const Step2Args<R> &a);
+// middle pass of a three-pass plan (g.R > 1): dir -1 forward, +1 inverse (pfc_mid.cuh)
+template <typename R> void launch_mid(const LaunchCfg &c, int dir, const MidArgs<R> &a);
 
 // The update pass (LINE_STEP) with its transform lengths fixed at compile time, compiled in
 // pfc_line_fixed_f32.cu / pfc_line_fixed_f64.cu: one-axis tiles (Qz = 1) with Qy = 2^6 .. 2^10
@@ -79,6 +82,7 @@ template <typename R> cudaError_t set_smem_attrs_fixed(const LaunchCfg &c);
     extern template cudaError_t set_smem_attrs<R>(const LaunchCfg &);                           \
     extern template void launch_line_adj<R>(const LaunchCfg &, const AdjArgs<R> &);             \
     extern template void launch_line_step2<R>(const LaunchCfg &, const Step2Args<R> &);         \
+    extern template void launch_mid<R>(const LaunchCfg &, int, const MidArgs<R> &);             \
     extern template void launch_batch_mean<R>(cudaStream_t, const R *, const int64_t *,         \
                                               const int64_t *, int, double *, int *);           \
     extern template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t, \

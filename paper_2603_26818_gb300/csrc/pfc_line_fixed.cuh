@@ -8,7 +8,7 @@ namespace pfc {
 
 template <typename R, int MAXT, int LY, int LZ>
 static void launch_fixed_t(const LaunchCfg &c, const LineArgs<R> &a, int nf) {
-    dim3 grid(c.g.ncg, c.g.P, nf);
+    dim3 grid(c.g.ncg, c.g.P * c.g.R, nf);
     k_line<R, LINE_STEP, MAXT, LY, LZ><<<grid, c.nt_line, c.smem_line, c.stream>>>(c.g, a);
 }
 

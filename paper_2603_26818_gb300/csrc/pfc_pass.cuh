@@ -21,6 +21,17 @@
 //
 // Scaling: X' = F_p(psi - mean) / (P M) with M = nx/2, so the row-pass inverse chain returns
 // psi - mean exactly; the update multipliers fold the remaining 1/N.
+//
+// Three-pass form (grids whose row groups and line tiles cannot both fit shared memory): the
+// y (and z) length is split in three, n = P R Q,
+//   y = y_q + Q (y_r + R y_p),  ky = k_p + P (k_r + R k_q),
+//   Yhat = sum_{y_q} W_Q^{y_q k_q} W_{RQ}^{y_q k_r} sum_{y_r} W_R^{y_r k_r}
+//          [ W_n^{(y_q + Q y_r) k_p} sum_{y_p} x W_P^{y_p k_p} ].
+// The row pass is the two-pass row pass with R Q groups (group (r, q) holds the rows
+// y_q + Q y_r + Q R y_p); a middle pass (pfc_mid.cuh) owns the R-point sums and the twiddle
+// W_{RQ}^{y_q k_r}; the line pass owns the Q-point sums of one (k_p, k_r). Rows of X' are
+// [k_p][r][q] in both forms (r = y_r + Ry z_r before the middle pass, k_ry + Ry k_rz after it),
+// so a line tile is still contiguous. With R = 1 everything reduces to the two-pass form.
 #pragma once
 
 #include "pfc_fft.cuh"
@@ -33,6 +44,8 @@ struct Geom {
     int xs;                          // complex stride of X'/C' rows (multiple of W)
     int Py, Pz, Qy, Qz, lPy, lPz, lQy, lQz;
     int P, Q, lQ;
+    int Ry, Rz, R, lRy, lRz, lR;     // middle-pass split (1 in the two-pass form)
+    int QR;                          // row groups = R Q
     int ltab;                        // full twiddle table has 2^ltab entries
     int W, lW, ncg;                  // line pass: columns per tile, column groups
     int tsz;                         // line pass tile size in elements, (Q + Q/8) W (see tile_y)
@@ -91,13 +104,39 @@ template <typename R> struct LineArgs {
 // ------------------------------------------------------------------------------------------
 // Helpers
 // ------------------------------------------------------------------------------------------
-// Split twiddle W_ny^{y_q k_py} W_nz^{z_q k_pz} of row group grp (forward sign).
+// Row group grp = r Q + q (q = z_q Qy + y_q, r = y_r + Ry z_r) -> the y and z offsets of its
+// rows, yo = y_q + Qy y_r and zo = z_q + Qz z_r; its rows are y = yo + Qy Ry y_p,
+// z = zo + Qz Rz z_p.
+__device__ __forceinline__ void grp_yz(const Geom &g, int grp, int &zo, int &yo) {
+    const int q = grp & (g.Q - 1), r = grp >> g.lQ;
+    yo = (q & (g.Qy - 1)) + g.Qy * (r & (g.Ry - 1));
+    zo = (q >> g.lQy) + g.Qz * (r >> g.lRy);
+}
+
+// Row of row group grp for (z_p, y_p) in the caller's real array (z, y).
+__device__ __forceinline__ void grp_row(const Geom &g, int grp, int zp, int yp, int &z, int &y) {
+    int zo, yo;
+    grp_yz(g, grp, zo, yo);
+    z = zo + g.Qz * g.Rz * zp;
+    y = yo + g.Qy * g.Ry * yp;
+}
+
+// Line tile kp = k_p R + k_r -> the low parts of its wavenumber indices, ky = kpy + Py Ry k_qy,
+// kz = kpz + Pz Rz k_qz.
+__device__ __forceinline__ void line_kp(const Geom &g, int kp, int &kpy, int &kpz) {
+    const int p = kp >> g.lR, r = kp & (g.R - 1);
+    kpy = (p & (g.Py - 1)) + g.Py * (r & (g.Ry - 1));
+    kpz = (p >> g.lPy) + g.Pz * (r >> g.lRy);
+}
+
+// Split twiddle W_ny^{yo k_py} W_nz^{zo k_pz} of row group grp (forward sign).
 template <typename V>
 __device__ __forceinline__ V split_twiddle(const Geom &g, const V *__restrict__ tw, int grp,
                                            int kpz, int kpy) {
-    const int zq = grp >> g.lQy, yq = grp & (g.Qy - 1);
-    V t = __ldg(&tw[(yq * kpy) << (g.ltab - g.lny)]);
-    if (g.Pz > 1) t = cmul(t, __ldg(&tw[(zq * kpz) << (g.ltab - g.lnz)]));
+    int zo, yo;
+    grp_yz(g, grp, zo, yo);
+    V t = __ldg(&tw[(yo * kpy) << (g.ltab - g.lny)]);
+    if (g.Pz > 1) t = cmul(t, __ldg(&tw[(zo * kpz) << (g.ltab - g.lnz)]));
     return t;
 }
 
@@ -168,7 +207,7 @@ __device__ void row_phase_a(const Geom &g, typename VT<R>::V *sm, const typename
 #pragma unroll
         for (int a = 0; a < 8; ++a)
             if (a < g.Pz)
-                t[a] = ctw<+1>(X[(size_t)((a * g.Py + kpy) * g.Q + grp) * g.xs + k],
+                t[a] = ctw<+1>(X[(size_t)((a * g.Py + kpy) * g.QR + grp) * g.xs + k],
                                stw[gi * P + a * g.Py + kpy]);
         dft_small<+1>(t, g.Pz);
 #pragma unroll
@@ -194,7 +233,7 @@ __device__ __forceinline__ void row_pair_b(const Geom &g, typename VT<R>::V *sm,
     for (int yy = 0; yy < 8; ++yy) {
         if (yy < g.Py) {
             if (FROM_GLOBAL) {
-                const V *src = X + (size_t)(yy * g.Q + grp) * g.xs;
+                const V *src = X + (size_t)(yy * g.QR + grp) * g.xs;
                 const V w = stw[gi * P + yy];
                 a[yy] = ctw<+1>(__ldcg(&src[ca]), w);
                 b[yy] = ctw<+1>(__ldcg(&src[cb]), w);
@@ -237,7 +276,7 @@ __device__ __forceinline__ void row_pair_b(const Geom &g, typename VT<R>::V *sm,
 #pragma unroll
         for (int yy = 0; yy < 8; ++yy) {
             if (yy < g.Py) {
-                V *dst = proj + (size_t)(yy * g.Q + grp) * g.xs;
+                V *dst = proj + (size_t)(yy * g.QR + grp) * g.xs;
                 dst[0] = cscale(cmul(a[yy], stw[gi * P + yy]), invP);
                 dst[g.M] = cscale(cmul(b[yy], stw[gi * P + yy]), invP);
             }
@@ -312,7 +351,7 @@ __device__ void project_edge_columns_par(const Geom &g, const R *edge, int grp0,
             if (kpz < Pz) {
                 V x = tt[kpz];
                 if (P > 1) x = cmul(x, stw[gi * P + kpz * Py + kpy]);
-                xout[(size_t)((kpz * Py + kpy) * g.Q + grp) * g.xs + k] = cscale(x, invP);
+                xout[(size_t)((kpz * Py + kpy) * g.QR + grp) * g.xs + k] = cscale(x, invP);
             }
         }
     }
@@ -344,7 +383,7 @@ __device__ __forceinline__ void row_pair_d(const Geom &g, typename VT<R>::V *sm,
         if (yy < g.Py) {
             if (g.Pz == 1) {
                 const V t = stw[gi * P + yy];
-                V *dst = out + (size_t)(yy * g.Q + grp) * g.xs;
+                V *dst = out + (size_t)(yy * g.QR + grp) * g.xs;
                 __stcg(&dst[ca], cscale(cmul(a[yy], t), scale));
                 if (cb != ca) __stcg(&dst[cb], cscale(cmul(b[yy], t), scale));
             } else {
@@ -400,7 +439,7 @@ __device__ void row_phase_e(const Geom &g, const typename VT<R>::V *sm, typename
 #pragma unroll
         for (int a = 0; a < 8; ++a)
             if (a < g.Pz)
-                out[(size_t)((a * g.Py + kpy) * g.Q + grp) * g.xs + k] =
+                out[(size_t)((a * g.Py + kpy) * g.QR + grp) * g.xs + k] =
                     cscale(cmul(t[a], stw[gi * P + a * g.Py + kpy]), scale);
     }
 }
@@ -459,9 +498,8 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_row(const Geom 
             const int i = e & (M - 1), r = e >> lM;
             const int gi = r / P, pr = r % P;
             const int grp = grp0 + gi;
-            const int zq = grp >> g.lQy, yq = grp & (g.Qy - 1);
-            const int zp = pr >> g.lPy, yp = pr & (g.Py - 1);
-            const int z = zq + g.Qz * zp, y = yq + g.Qy * yp;
+            int z, y;
+            grp_row(g, grp, pr >> g.lPy, pr & (g.Py - 1), z, y);
             V v = in[((size_t)z * g.ny + y) * M + i];
             v.x -= mean;
             v.y -= mean;
@@ -506,9 +544,8 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_row(const Geom 
             if (act) {
                 const int gi = r / P, pr = r % P;
                 const int grp = grp0 + gi;
-                const int zq = grp >> g.lQy, yq = grp & (g.Qy - 1);
-                const int zp = pr >> g.lPy, yp = pr & (g.Py - 1);
-                const int z = zq + g.Qz * zp, y = yq + g.Qy * yp;
+                int z, y;
+                grp_row(g, grp, pr >> g.lPy, pr & (g.Py - 1), z, y);
                 V *out = reinterpret_cast<V *>(a.out) +
                          (a.moff ? (size_t)(a.moff[field] / 2) : (size_t)field * (g.nreal / 2)) +
                          ((size_t)z * g.ny + y) * M;
@@ -655,7 +692,9 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
     const PadTileAddr ady = tile_y(g, mp);
     const TileAddr adz = tile_z(g, mp);
     const bool two_axes = LZ > 0 || (LY == 0 && g.Qz > 1);
-    const int kpy = kp % g.Py, kpz = kp / g.Py;
+    int kpy, kpz;
+    line_kp(g, kp, kpy, kpz);
+    const int lsy = g.lPy + g.lRy, lsz = g.lPz + g.lRz;   // ky = kpy + (k_qy << lsy), kz likewise
     V vt[8], vc[8];
 
     if (MODE == LINE_STEP) {
@@ -684,7 +723,7 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
             for (int m = 0; m < 8; ++m) {
                 const int kqy = two_axes ? mp.yq : mp.jy + m * mp.ny8;
                 const int kqz = two_axes ? mp.jz + m * mp.nz8 : 0;
-                const int ky = kpy + (kqy << g.lPy), kz = kpz + (kqz << g.lPz);
+                const int ky = kpy + (kqy << lsy), kz = kpz + (kqz << lsz);
                 O[((size_t)kz * g.ny + ky) * (g.M + 1) + kx] = cscale(vt[m], a.scale);
             }
         }
@@ -704,7 +743,7 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
             const V c = Cs[tile_slot(mp, two_axes, ady, adz, m)];
             const int kqy = two_axes ? mp.yq : mp.jy + m * mp.ny8;
             const int kqz = two_axes ? mp.jz + m * mp.nz8 : 0;
-            const int ky = kpy + (kqy << g.lPy), kz = kpz + (kqz << g.lPz);
+            const int ky = kpy + (kqy << lsy), kz = kpz + (kqz << lsz);
             const int my = ky <= (g.ny >> 1) ? ky : ky - g.ny;
             const int mz = kz <= (g.nz >> 1) ? kz : kz - g.nz;
             const R fy = cy * (R)my, fz = cz * (R)mz;
@@ -725,7 +764,7 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
         for (int m = 0; m < 8; ++m) {
             const int kqy = two_axes ? mp.yq : mp.jy + m * mp.ny8;
             const int kqz = two_axes ? mp.jz + m * mp.nz8 : 0;
-            const int ky = kpy + (kqy << g.lPy), kz = kpz + (kqz << g.lPz);
+            const int ky = kpy + (kqy << lsy), kz = kpz + (kqz << lsz);
             vt[m] = kx <= g.M ? I[((size_t)kz * g.ny + ky) * (g.M + 1) + kx] : V{(R)0, (R)0};
         }
     }

@@ -72,7 +72,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
                 V va[ROWCL_PY], vb[ROWCL_PY];
 #pragma unroll
                 for (int yy = 0; yy < ROWCL_PY; ++yy) {
-                    const V *src = X + (size_t)(yy * g.Q + grp) * g.xs;
+                    const V *src = X + (size_t)(yy * g.QR + grp) * g.xs;
                     const V w = stw[yy];
                     va[yy] = ctw<+1>(__ldcg(&src[ca]), w);
                     vb[yy] = ctw<+1>(__ldcg(&src[cb]), w);
@@ -101,7 +101,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
                     const R invP = (R)1 / (R)ROWCL_PY;
 #pragma unroll
                     for (int yy = 0; yy < ROWCL_PY; ++yy) {
-                        V *dst = pw + (size_t)(yy * g.Q + grp) * g.xs;
+                        V *dst = pw + (size_t)(yy * g.QR + grp) * g.xs;
                         dst[0] = cscale(cmul(va[yy], stw[yy]), invP);
                         dst[M] = cscale(cmul(vb[yy], stw[yy]), invP);
                     }
@@ -157,7 +157,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
 #pragma unroll
                 for (int yy = 0; yy < ROWCL_PY; ++yy) {
                     const V t = stw[yy];
-                    V *dst = out + (size_t)(yy * g.Q + grp) * g.xs;
+                    V *dst = out + (size_t)(yy * g.QR + grp) * g.xs;
                     __stcg(&dst[ca], cscale(cmul(va[yy], t), a.scale));
                     if (cb != ca) __stcg(&dst[cb], cscale(cmul(vb[yy], t), a.scale));
                 }
@@ -223,7 +223,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 2)
             V t[PZ];
 #pragma unroll
             for (int zz = 0; zz < PZ; ++zz)
-                t[zz] = ctw<+1>(__ldcg(&X[(size_t)((zz * Py + kpy) * g.Q + grp) * g.xs + k]), stw[zz * Py + kpy]);
+                t[zz] = ctw<+1>(__ldcg(&X[(size_t)((zz * Py + kpy) * g.QR + grp) * g.xs + k]), stw[zz * Py + kpy]);
             dft8<+1>(t);
 #pragma unroll
             for (int zz = 0; zz < PZ; ++zz)
@@ -313,7 +313,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 2)
             dft8<-1>(t);
 #pragma unroll
             for (int zz = 0; zz < PZ; ++zz)
-                __stcg(&out[(size_t)((zz * Py + kpy) * g.Q + grp) * g.xs + k],
+                __stcg(&out[(size_t)((zz * Py + kpy) * g.QR + grp) * g.xs + k],
                        cscale(cmul(t[zz], stw[zz * Py + kpy]), a.scale));
         }
     }

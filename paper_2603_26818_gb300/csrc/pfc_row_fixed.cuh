@@ -8,7 +8,7 @@ namespace pfc {
 
 template <typename R, int LM>
 static void launch_row_fixed_t(const LaunchCfg &c, const RowArgs<R> &a, int nf) {
-    dim3 grid(c.g.Q / c.g.gpc, nf);
+    dim3 grid(c.g.QR / c.g.gpc, nf);
     k_row<R, ROW_CUBE, LM><<<grid, c.nt_row, c.smem_row, c.stream>>>(c.g, a);
 }
 

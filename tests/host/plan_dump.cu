@@ -3,7 +3,7 @@
 //   plan_dump NX NY NZ VB NTILE INSTANCES [NX NY NZ VB NTILE INSTANCES ...]
 // With PLAN_DUMP_ALL set it prints instead every candidate tiling the autotuner may time
 // (tile_candidates, each with the clustered row pass on and, where it applies, off), with its
-// rank in "cand".
+// rank in "cand"; PLAN_DUMP_SCHED=3 lists the three-pass candidates instead.
 #include <cstdio>
 #include <cstdlib>
 
@@ -15,10 +15,11 @@ static void print_plan(const pfc::Tiles &t, int nx, int ny, int nz, size_t vb, i
                 "\"Py\": %d, \"Pz\": %d, \"Qy\": %d, \"Qz\": %d, \"P\": %d, \"Q\": %d, \"W\": %d, \"xs\": %d, "
                 "\"ncg\": %d, \"tsz\": %d, \"rs\": %d, \"gpc\": %d, \"nt_row\": %d, \"nt_line\": %d, "
                 "\"smem_row\": %zu, \"smem_line\": %zu, \"row_cs\": %d, \"nt_row_cs\": %d, "
-                "\"smem_row_cs\": %zu, \"nhalf\": %lld, \"inst\": %d, \"cand\": %d}\n",
+                "\"smem_row_cs\": %zu, \"nhalf\": %lld, \"inst\": %d, \"cand\": %d, \"Ry\": %d, \"Rz\": %d, "
+                "\"R\": %d, \"QR\": %d}\n",
                 nx, ny, nz, vb, ntile, g.M, g.Py, g.Pz, g.Qy, g.Qz, g.P, g.Q, g.W, g.xs, g.ncg, g.tsz, g.rs,
                 g.gpc, t.nt_row, t.nt_line, t.smem_row, t.smem_line, t.row_cs, t.nt_row_cs, t.smem_row_cs,
-                (long long)g.nhalf, inst, cand);
+                (long long)g.nhalf, inst, cand, g.Ry, g.Rz, g.R, g.QR);
 }
 
 int main(int argc, char **argv) {
@@ -29,7 +30,10 @@ int main(int argc, char **argv) {
         const int ntile = std::atoi(argv[i + 4]), inst = std::atoi(argv[i + 5]);
         if (std::getenv("PLAN_DUMP_ALL")) {
             int rank = 0;
-            for (const pfc::TileChoice &c0 : pfc::tile_candidates(nx, ny, nz, vb, ntile, smem_max, pfc::TileChoice{}, inst)) {
+            const char *sc = std::getenv("PLAN_DUMP_SCHED");
+            const int sched = sc ? std::atoi(sc) : pfc::SCHED_AUTO;
+            for (const pfc::TileChoice &c0 :
+                 pfc::tile_candidates(nx, ny, nz, vb, ntile, smem_max, pfc::TileChoice{}, inst, sched)) {
                 for (int cl = 1; cl >= 0; --cl) {
                     pfc::TileChoice c = c0;
                     c.cluster = cl;

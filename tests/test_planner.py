@@ -22,13 +22,15 @@ def planner(tmp_path_factory):
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-2000:]
 
-    def run(cases, all_candidates=False):
+    def run(cases, all_candidates=False, sched=None):
         args = [str(v) for c in cases for v in c]
         env = dict(os.environ)
         env.pop("PFC_TILE", None)
         env.pop("PFC_ROW_CLUSTER", None)
         if all_candidates:
             env["PLAN_DUMP_ALL"] = "1"
+        if sched is not None:
+            env["PLAN_DUMP_SCHED"] = str(sched)
         out = subprocess.run([exe, *args], capture_output=True, text=True, check=True, env=env).stdout
         return [json.loads(l) for l in out.splitlines()]
     return run
@@ -45,6 +47,10 @@ def _cases():
             for ntile in (2, 3):
                 cases.append((n, n, n, vb, ntile, 1))
     cases += [(512, 256, 256, 8, 2, 1), (4096, 16, 16, 8, 2, 1), (16, 16, 4096, 8, 2, 1), (64, 64, 1, 8, 2, 400)]
+    # grids beyond the two-pass tilings (three-pass schedule)
+    cases += [(1024, 1024, 1024, 8, 2, 1), (1024, 1024, 1024, 16, 2, 1), (2048, 2048, 2048, 8, 2, 1),
+              (2048, 2048, 2048, 16, 2, 1), (4096, 4096, 4096, 8, 2, 1), (4096, 1024, 1024, 8, 2, 1),
+              (1024, 2048, 2048, 8, 2, 1)]
     return cases
 
 
@@ -53,15 +59,19 @@ def _check_plan(p):
     M = nx // 2
     assert p["M"] == M
     assert p["P"] == p["Py"] * p["Pz"] and p["Q"] == p["Qy"] * p["Qz"]
-    assert p["Py"] * p["Qy"] == ny and p["Pz"] * p["Qz"] == nz
+    assert p["R"] == p["Ry"] * p["Rz"] and p["QR"] == p["R"] * p["Q"]
+    assert p["Py"] * p["Ry"] * p["Qy"] == ny and p["Pz"] * p["Rz"] * p["Qz"] == nz
     assert p["Py"] in (1, 2, 4, 8) and p["Pz"] in (1, 2, 4, 8)
+    assert p["Ry"] in (1, 2, 4, 8) and p["Rz"] in (1, 2, 4, 8)
     assert p["Qy"] == 1 or p["Qy"] >= 8
     assert p["Qz"] == 1 or p["Qz"] >= 8
-    assert nz > 1 or p["Pz"] == 1
+    assert nz > 1 or (p["Pz"] == 1 and p["Rz"] == 1)
+    if p["R"] > 1:   # three-pass line tiles have both axes of at least 8 (one in 2D)
+        assert p["Qy"] >= 8 and (nz == 1 or p["Qz"] >= 8)
     # X' rows: every bin, a whole number of tiles, 16-byte aligned rows
     assert p["xs"] >= M + 1 and p["xs"] % p["W"] == 0 and p["ncg"] * p["W"] == p["xs"]
     assert (p["xs"] * vb) % 16 == 0
-    assert p["nhalf"] == p["P"] * p["Q"] * p["xs"]
+    assert p["nhalf"] == p["P"] * p["QR"] * p["xs"]
     # line tiles: one padding row per 8 tile rows, 8 elements per thread
     assert p["tsz"] == (p["Q"] + p["Q"] // 8) * p["W"]
     assert p["nt_line"] * 8 == p["Q"] * p["W"]
@@ -71,7 +81,7 @@ def _check_plan(p):
     assert p["rs"] >= M + 1 and p["rs"] % 16 == 0
     assert p["nt_row"] <= 512 and p["nt_row"] % max(1, M // 8) == 0
     assert p["smem_row"] <= SMEM_MAX
-    assert p["Q"] % p["gpc"] == 0
+    assert p["QR"] % p["gpc"] == 0
     # clustered psi^3 rows: FP32 only, at the row lengths the kernels are compiled for
     if p["row_cs"]:
         assert vb == 8 and p["row_cs"] == 2 and p["gpc"] == 1
@@ -84,11 +94,16 @@ def test_plans_keep_the_kernel_invariants(planner):
     plans = planner(_cases())
     assert len(plans) == len(_cases())
     for p in plans:
-        if not p["ok"]:
-            # only grids whose row group or tiles cannot fit: FP64 512^3 and larger
-            assert p["vb"] == 16 and p["nz"] >= 512
+        # every grid has a plan: two-pass where a row group and two line tiles fit, else
+        # three-pass; only grids whose arrays exceed the GPU's 288 GB anyway have none (the
+        # middle pass takes at most 8 x 8 points)
+        if (p["nx"], p["ny"], p["nz"], p["vb"]) in ((2048, 2048, 2048, 16), (4096, 4096, 4096, 8)):
+            assert not p["ok"]
             continue
+        assert p["ok"], p
         _check_plan(p)
+        if p["R"] > 1:
+            assert (p["vb"] == 16 and p["nz"] >= 512) or p["nz"] >= 1024 or p["nx"] * p["ny"] * p["nz"] >= 2 ** 30
 
 
 def test_every_autotune_candidate_keeps_the_kernel_invariants(planner):
@@ -144,4 +159,21 @@ def test_autotune_cache_file_round_trip(tmp_path):
                                            "256x256x256 prec1 fields2 NVIDIA_GB300",
                                            "1x4096x4096 prec1 fields1 NVIDIA_GB300"]
     assert entries[1] == {"key": "256x256x256 prec1 fields2 NVIDIA_GB300", "Py": 2, "Pz": 2, "W": 8,
-                          "cluster": 0, "ms_per_step": 0.556376}
+                          "cluster": 0, "Ry": 1, "Rz": 1, "ms_per_step": 0.556376}
+
+
+def test_three_pass_plans(planner):
+    """Grids with no two-pass tiling get three-pass plans; a two-pass grid keeps its plan and also
+    lists three-pass candidates for the autotuner."""
+    f64_512, f32_1024, f32_2048 = planner([(512, 512, 512, 16, 2, 1), (1024, 1024, 1024, 8, 2, 1),
+                                           (2048, 2048, 2048, 8, 2, 1)])
+    for p in (f64_512, f32_1024, f32_2048):
+        assert p["ok"] and p["R"] > 1
+        _check_plan(p)
+    assert f32_2048["nt_line"] <= 1024
+    # 512^3 FP32 has a two-pass plan; its three-pass candidates all keep the invariants
+    three = planner([(512, 512, 512, 8, 2, 1), (256, 256, 256, 16, 2, 1), (64, 128, 1, 8, 2, 1)],
+                    all_candidates=True, sched=3)
+    assert three and all(p["ok"] and p["R"] > 1 for p in three)
+    for p in three:
+        _check_plan(p)
