@@ -89,7 +89,25 @@ CONFIGS = {
     "5d": dict(desc="adjoint step, 3D one-mode 256^3 FP64, as config 5; 5 adjoint steps per bench step",
                kind="adjoint", dims=(256, 256, 256), prec="fp64", op=(0, -0.25, 0.0, 0.0), dt=0.5,
                inner=5, sweeps=17),
+    "3d64": dict(desc="3D two-mode 512^3 FP64 (three-pass schedule), as config 3; 4 time steps per bench step",
+                 kind="plan", dims=(512, 512, 512), prec="fp64", op=(1, -0.3, 0.05, math.sqrt(4.0 / 3.0)),
+                 dt=0.1, inner=4, sweeps=9),
+    "L": dict(desc="the largest power-of-two 3D one-mode grid whose FP32-mixed plan and state fit the GPU's "
+                   "free memory (2048^3 on a GB300), dx=pi/4, dt=0.5, r=-0.25, psi0=-0.25+U[-0.01,0.01] "
+                   "(torch generator, seed 8), three-pass schedule; 3 time steps per bench step",
+              kind="largest", prec="fp32", op=(0, -0.25, 0.0, 0.0), dt=0.5, inner=3, sweeps=9),
 }
+
+# Bytes of a plan's real state, its scratch (3 half spectra for a three-pass plan) and slack, per
+# grid point, FP32-mixed: the largest cube is chosen from the free memory with this.
+BYTES_PER_POINT_FP32_THREE_PASS = 4 + 3 * 4 + 1
+
+
+def largest_cube(free_bytes):
+    n = 256
+    while (2 * n) ** 3 * BYTES_PER_POINT_FP32_THREE_PASS <= free_bytes and 2 * n <= 4096:
+        n *= 2
+    return n
 
 
 def run_config(args):
@@ -131,10 +149,21 @@ def run_config(args):
         if c.get("autotune") and not args.no_autotune:
             extra["autotune"] = {"candidates": 6, "trial_steps": 8, "ms_per_step": obj.autotune(6, 8)}
         extra["plan"] = obj.info()
+    elif c["kind"] == "largest":
+        torch.cuda.empty_cache()
+        n = largest_cube(torch.cuda.mem_get_info()[0])
+        shape = (n, n, n)
+        obj = binding.Plan(shape, DX, c["dt"], [binding.make_op(*c["op"])], precision=prec)
+        state = seeded_uniform_state(shape, -0.25, 0.01, 8, dtype, dev)
+        npts = state.numel()
+        extra["plan"] = obj.info()
+        extra["grid"] = list(shape)
+        extra["chosen_from_free_bytes"] = True
+        run = lambda: obj.step(state, c["inner"])
     else:
         shape = c["dims"]
-        seed = {"1": 1, "3": 3}.get(args.config, 6)
-        mean, amp = {"1": (-0.25, 0.01), "3": (-0.35, 0.02)}.get(args.config, (-0.25, 0.01))
+        seed = {"1": 1, "3": 3, "3d64": 3}.get(args.config, 6)
+        mean, amp = {"1": (-0.25, 0.01), "3": (-0.35, 0.02), "3d64": (-0.35, 0.02)}.get(args.config, (-0.25, 0.01))
         psi0 = inputs.uniform_state(shape, mean, amp, seed=seed)
         obj = binding.Plan(shape, DX, c["dt"], [binding.make_op(*c["op"])], precision=prec)
         state = torch.from_numpy(psi0).to(device=dev, dtype=dtype)
@@ -182,10 +211,168 @@ def run_config(args):
             "roofline": {"bound": "hbm", "model_bytes_per_point_step": bpp, "achieved": gbs, "peak": peak,
                          "unit": "GB/s", "frac": gbs / peak, "peak_kind": peak_kind, "traffic": None},
             "clocks": clk.summary()}
-    if c["kind"] == "plan":
+    if c["kind"] in ("plan", "largest"):
         prof, _ = obj.profile_steps(state, c["inner"])
-        line["roofline"]["per_kernel_ms_per_step"] = {k: prof[k] / c["inner"] for k in ("row", "line")}
+        line["roofline"]["per_kernel_ms_per_step"] = {k: prof[k] / c["inner"] for k in ("row", "line", "mid")}
     print(json.dumps(line), flush=True)
+
+
+def seeded_uniform_state(shape, mean, amp, seed, dtype, dev):
+    """mean + U[-amp, amp] drawn on the device by a seeded torch generator (for grids too large to
+    draw on the host)."""
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    x = torch.empty(shape, dtype=dtype, device=dev)
+    x.uniform_(mean - amp, mean + amp, generator=g)
+    return x
+
+
+def time_plan(torch, plan, state, inner, steps, warmup, flush):
+    """ms per time step of plan.step(state, inner), L2 flushed between timed calls, CUDA events."""
+    for _ in range(warmup):
+        plan.step(state, inner)
+    torch.cuda.synchronize()
+    total = 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0.record()
+        plan.step(state, inner)
+        e1.record()
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / (steps * inner)
+
+
+def other_grids(torch, dev, flush):
+    """Rates of the 512^3 two-mode grid (FP32-mixed, two-pass) and of the largest FP32 cube that
+    fits the free memory (three-pass), with per-kernel times and HBM fractions."""
+    from paper_2603_26818_gb300 import binding, inputs
+    peak, _ = hbm_peak()
+    out = {}
+    two = binding.make_op(1, -0.3, 0.05, math.sqrt(4.0 / 3.0))
+    psi0 = inputs.uniform_state((512, 512, 512), -0.35, 0.02, seed=3)
+    p = binding.Plan((512, 512, 512), DX, 0.1, [two], precision="fp32")
+    x = torch.from_numpy(psi0).to(device=dev, dtype=torch.float32)
+    ms = time_plan(torch, p, x, 10, 5, 3, flush)
+    prof, _ = p.profile_steps(x, 10)
+    npts = 512 ** 3
+    half = 512 * 512 * 257 * 8
+    out["512cube_two_mode_fp32"] = {
+        "grid_point_steps_per_s": npts / (ms * 1e-3), "ms_per_time_step": ms, "plan": p.info(),
+        "hbm_frac_at_20_B_per_pt": 20 * npts / (ms * 1e-3) / 1e9 / peak,
+        "per_kernel_ms_per_step": {k: prof[k] / 10 for k in ("row", "line")},
+        "per_kernel_frac": {"row": 2 * half / (prof["row"] / 10 * 1e-3) / 1e9 / peak,
+                            "line": 3 * half / (prof["line"] / 10 * 1e-3) / 1e9 / peak}}
+    p.close()
+    del x
+    torch.cuda.empty_cache()
+    n = largest_cube(torch.cuda.mem_get_info()[0])
+    shape = (n, n, n)
+    p = binding.Plan(shape, DX, 0.5, [binding.make_op(0, -0.25)], precision="fp32")
+    x = seeded_uniform_state(shape, -0.25, 0.01, 8, torch.float32, dev)
+    ms = time_plan(torch, p, x, 3, 3, 2, flush)
+    prof, _ = p.profile_steps(x, 3)
+    info = p.info()
+    npts = n ** 3
+    sweeps = 9 if info["Ry"] * info["Rz"] > 1 else 5
+    half = n * n * (n // 2 + 1) * 8
+    out["largest_cube_fp32"] = {
+        "grid": [n, n, n], "grid_point_steps_per_s": npts / (ms * 1e-3), "ms_per_time_step": ms,
+        "plan": info, "sweeps_per_step": sweeps,
+        "hbm_frac_at_model_bytes": sweeps * 4 * npts / (ms * 1e-3) / 1e9 / peak,
+        "per_kernel_ms_per_step": {k: prof[k] / 3 for k in ("row", "line", "mid")},
+        "per_kernel_frac": {"row": 2 * half / (prof["row"] / 3 * 1e-3) / 1e9 / peak,
+                            "line": 3 * half / (prof["line"] / 3 * 1e-3) / 1e9 / peak,
+                            "mid": 6 * half / max(prof["mid"] / 3 * 1e-3, 1e-12) / 1e9 / peak},
+        "state": "psi0 = -0.25 + U[-0.01, 0.01] from a seeded torch generator (seed 8)"}
+    p.close()
+    del x
+    torch.cuda.empty_cache()
+    return out
+
+
+def precision_report(torch, dev):
+    """FP32-mixed against the FP64 path, per workload: relative L2 errors after each workload's
+    full length (the FP64 paths are pinned to the oracle by the test suite)."""
+    import numpy as np
+    from paper_2603_26818_gb300 import binding, inputs
+    from paper_2603_26818_gb300.autograd import rollout
+    out = {}
+
+    def relerr(a, b):
+        return float((a.double() - b.double()).norm() / b.double().norm())
+
+    # 512^3 two-mode, 500 steps (the FP64 plan is three-pass)
+    two = binding.make_op(1, -0.3, 0.05, math.sqrt(4.0 / 3.0))
+    psi0 = inputs.uniform_state((512, 512, 512), -0.35, 0.02, seed=3)
+    res = {}
+    for prec, dt_ in (("fp64", torch.float64), ("fp32", torch.float32)):
+        p = binding.Plan((512, 512, 512), DX, 0.1, [two], precision=prec)
+        x = torch.from_numpy(psi0).to(device=dev, dtype=dt_)
+        p.step(x, 500)
+        res[prec] = (x, p.mass(x)[0])
+        p.close()
+    a, b = res["fp32"][0], res["fp64"][0]
+    m0 = float(psi0.astype(np.float32).astype(np.float64).mean())
+    out["3_512cube_two_mode_500_steps"] = {
+        "rel_l2_fp32_vs_fp64": relerr(a, b),
+        "rel_l2_of_fluctuation": float((a.double() - b).norm() / (b - b.mean()).norm()),
+        "mass_drift_rel_fp32": abs(res["fp32"][1] - m0) / abs(m0)}
+    del res, a, b
+    torch.cuda.empty_cache()
+    # 1024-domain ensemble, 200 steps, every domain; coupled pair 256^3, 200 steps
+    draws = inputs.batch_draws(1024, seed=4)
+    parts = np.concatenate([inputs.uniform_state((ny, nx), m, 0.01, seed=1000 + i).ravel()
+                            for i, (ny, nx, r, m) in enumerate(draws)])
+    xs = {}
+    for prec, dt_ in (("fp64", torch.float64), ("fp32", torch.float32)):
+        bt = binding.Batch([(d[0], d[1]) for d in draws], [d[2] for d in draws], DX, 0.5, precision=prec)
+        x = torch.from_numpy(parts).to(device=dev, dtype=dt_)
+        bt.step(x, 200)
+        xs[prec] = (bt, x)
+    errs = []
+    for d in range(len(draws)):
+        errs.append(relerr(xs["fp32"][0].view(xs["fp32"][1], d), xs["fp64"][0].view(xs["fp64"][1], d)))
+    for bt, _ in xs.values():
+        bt.close()
+    errs = np.array(errs)
+    out["4a_ensemble_1024_domains_200_steps"] = {
+        "rel_l2_max_over_domains": float(errs.max()), "rel_l2_median": float(np.median(errs)),
+        "domains_above_1e-5": int((errs > 1e-5).sum())}
+    p0 = inputs.uniform_state((256, 256, 256), -0.25, 0.01, seed=5)
+    c0 = inputs.uniform_state((256, 256, 256), -0.2, 0.01, seed=6)
+    ops = [binding.make_op(0, -0.25), binding.make_op(0, -0.25)]
+    xs = {}
+    for prec, dt_ in (("fp64", torch.float64), ("fp32", torch.float32)):
+        p = binding.Plan((256, 256, 256), DX, 0.5, ops, precision=prec, coupling=0.1)
+        x = torch.from_numpy(np.stack([p0, c0])).to(device=dev, dtype=dt_)
+        p.step(x, 200)
+        xs[prec] = x
+        p.close()
+    out["4b_coupled_pair_256cube_200_steps"] = {
+        "rel_l2_psi": relerr(xs["fp32"][0], xs["fp64"][0]), "rel_l2_c": relerr(xs["fp32"][1], xs["fp64"][1])}
+    del xs
+    # adjoint: 256^3 one-mode, 200 steps, checkpoints every 20, gradients FP32 vs FP64
+    shape = (256, 256, 256)
+    psi0 = inputs.uniform_state(shape, -0.25, 0.01, seed=6)
+    grads = {}
+    for prec, dt_ in (("fp64", torch.float64), ("fp32", torch.float32)):
+        p = binding.Plan(shape, DX, 0.5, [binding.make_op(0, -0.25)], precision=prec)
+        p.set_r(-0.2)
+        tg = torch.from_numpy(psi0).to(device=dev, dtype=dt_)
+        p.step(tg, 200)
+        x0 = torch.from_numpy(psi0).to(device=dev, dtype=dt_).requires_grad_(True)
+        rt = torch.tensor(-0.25, dtype=torch.float64, requires_grad=True)
+        loss = 0.5 * ((rollout(x0, rt, p, 200, 20) - tg) ** 2).sum()
+        loss.backward()
+        grads[prec] = (x0.grad.detach(), float(rt.grad))
+        p.close()
+    out["5_adjoint_256cube_200_steps"] = {
+        "rel_l2_grad_psi0": relerr(grads["fp32"][0], grads["fp64"][0]),
+        "rel_err_grad_r": abs(grads["fp32"][1] - grads["fp64"][1]) / abs(grads["fp64"][1])}
+    return out
 
 
 def make_input():
@@ -523,6 +710,14 @@ def run_ours(args):
             "rel_l2_of_fluctuation": float((a.double() - b).norm() / fl),
             "mass_drift_rel_fp32": abs(plan.mass(a)[0] - m0) / abs(m0),
             "mass_drift_rel_fp64": abs(p64.mass(b)[0] - m0) / abs(m0)}
+        del a, b, x64
+        p64.close()
+        torch.cuda.empty_cache()
+        # the other grids' rates (512^3, the largest cube that fits) and the other workloads'
+        # FP32-mixed precision
+        extras["other_grids"] = other_grids(torch, dev, flush)
+        extras["precision_per_config"] = {"2_4096sq_polycrystal_1000_steps": extras["precision_1000_steps"],
+                                          **precision_report(torch, dev)}
         # ALU view: the transform flops of a step (5 log2 N per point for one r2c and one c2r,
         # plus ~20 pointwise) against the measured plain-FMA rates; the FP64 path is bound there
         peaks = fma_peaks()
@@ -536,7 +731,6 @@ def run_ours(args):
                 "fp64_frac": extras["ours_fp64"] * fpp / 1e12 / peaks["fp64_tflops"],
                 "peak_kind": "measured (libpfc_probe.so: 8 independent FMA chains per thread)"}
         line["context"] = extras
-        p64.close()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(psi0, 32)

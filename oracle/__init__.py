@@ -10,6 +10,8 @@ every number is computed in C). Arrays are numpy float64 / complex128, row-major
 Parity status of each function (what pins it is in ``tests/test_oracle_pins.py``):
   dft, fft_radix2, fft_mixed, rfftn, irfftn   pinned (numpy.fft, naive DFT, closed forms)
   step, mass, energy                          pinned (closed forms, invariants, symmetries)
+  step_scheme                                 pinned (scheme 0 = step, S = 0 reduction, scalar
+                                              recurrences of one small mode, convergence order)
   step2, energy2                              pinned (alpha=0 reduction, Cramer, mass)
   step_tangent, step_adjoint, adjoint_run     pinned (dot-product test, finite differences)
 """
@@ -58,6 +60,7 @@ def _load():
     lib.orc_lin_op.argtypes = [cint, dbl, dbl, dbl, dbl]
     lib.orc_lin_op.restype = dbl
     lib.orc_step.argtypes = [i64, i64, i64, dbl, dbl, cint, dbl, dbl, dbl, p, i64]
+    lib.orc_step_scheme.argtypes = [i64, i64, i64, dbl, dbl, cint, dbl, dbl, dbl, cint, dbl, p, i64]
     lib.orc_mass.argtypes = [i64, p]
     lib.orc_mass.restype = dbl
     lib.orc_energy.argtypes = [i64, i64, i64, dbl, cint, dbl, dbl, dbl, p]
@@ -158,6 +161,20 @@ def step(psi, dx: float, dt: float, op, nsteps: int = 1) -> np.ndarray:
     y = _f64(psi).copy()
     nz, ny, nx = _dims3(y.shape)
     _load().orc_step(nz, ny, nx, float(dx), float(dt), *_op_args(op), _ptr(y), int(nsteps))
+    return y
+
+
+SEMI_IMPLICIT, STABILIZED, SBDF2 = 0, 1, 2
+
+
+def step_scheme(psi, dx: float, dt: float, op, scheme: int, S: float = 0.0, nsteps: int = 1) -> np.ndarray:
+    """psi after nsteps steps of an alternative integrator (0 semi-implicit, 1 stabilised with
+    constant S, 2 second-order BDF with extrapolated nonlinearity started by one step of 0);
+    the nsteps steps are one run."""
+    y = _f64(psi).copy()
+    nz, ny, nx = _dims3(y.shape)
+    _load().orc_step_scheme(nz, ny, nx, float(dx), float(dt), *_op_args(op), int(scheme), float(S),
+                            _ptr(y), int(nsteps))
     return y
 
 

@@ -284,6 +284,53 @@ void orc_step(int64_t nz, int64_t ny, int64_t nx, double dx, double dt,
     free(ph); free(nh); free(cube);
 }
 
+/* Alternative time integrators of the same spectral system. The paper integrates with the
+ * semi-implicit scheme above and notes that other time-integration schemes can be used. Each
+ * Fourier mode obeys d/dt psi_hat = -k^2 (Lk psi_hat + N_hat), N = psi^3 (Eq. (6)); one step of
+ *   scheme 0  semi-implicit Euler (orc_step);
+ *   scheme 1  stabilised semi-implicit Euler with a constant S: S psi is added to the implicit
+ *             linear part and taken away from the explicit part,
+ *               psi_hat <- ((1 + dt k^2 S) psi_hat - dt k^2 N_hat) / (1 + dt k^2 (Lk + S));
+ *   scheme 2  second-order semi-implicit backward differentiation: BDF2 for the linear part
+ *             and the nonlinear part extrapolated to t_{n+1} from t_n and t_{n-1},
+ *               (3 psi_hat^{n+1} - 4 psi_hat^n + psi_hat^{n-1}) / (2 dt)
+ *                   = -k^2 (Lk psi_hat^{n+1} + 2 N_hat^n - N_hat^{n-1}),
+ *             the first step of a call being one step of scheme 0 (the call's nsteps steps are
+ *             one run: the two previous levels are carried inside the call only). */
+void orc_step_scheme(int64_t nz, int64_t ny, int64_t nx, double dx, double dt, int kind, double r,
+                     double R1, double q2, int scheme, double S, double *psi, int64_t nsteps)
+{
+    int64_t n = nz * ny * nx, nxh = nx / 2 + 1, h = nz * ny * nxh;
+    cplx *ph = malloc(sizeof(cplx) * h), *nh = malloc(sizeof(cplx) * h);
+    cplx *ph_old = malloc(sizeof(cplx) * h), *nh_old = malloc(sizeof(cplx) * h);
+    double *cube = malloc(sizeof(double) * n);
+    for (int64_t s = 0; s < nsteps; ++s) {
+        orc_rfftn(nz, ny, nx, psi, ph);
+        for (int64_t j = 0; j < n; ++j) cube[j] = psi[j] * psi[j] * psi[j];
+        orc_rfftn(nz, ny, nx, cube, nh);
+        for (int64_t iz = 0; iz < nz; ++iz)
+            for (int64_t iy = 0; iy < ny; ++iy)
+                for (int64_t ik = 0; ik < nxh; ++ik) {
+                    int64_t idx = (iz * ny + iy) * nxh + ik;
+                    double k2 = ksq(iz, iy, ik, nz, ny, nx, dx);
+                    double lk = orc_lin_op(kind, r, R1, q2, k2);
+                    cplx next;
+                    if (scheme == 1)
+                        next = ((1.0 + dt * k2 * S) * ph[idx] - dt * k2 * nh[idx]) / (1.0 + dt * k2 * (lk + S));
+                    else if (scheme == 2 && s > 0)
+                        next = (4.0 * ph[idx] - ph_old[idx] - 2.0 * dt * k2 * (2.0 * nh[idx] - nh_old[idx])) /
+                               (3.0 + 2.0 * dt * k2 * lk);
+                    else
+                        next = (ph[idx] - dt * k2 * nh[idx]) / (1.0 + dt * k2 * lk);
+                    ph_old[idx] = ph[idx];
+                    nh_old[idx] = nh[idx];
+                    ph[idx] = next;
+                }
+        orc_irfftn(nz, ny, nx, ph, psi);
+    }
+    free(ph); free(nh); free(ph_old); free(nh_old); free(cube);
+}
+
 /* Mass: the mean density (1/N) sum_j psi_j, i.e. psi_hat(k=0)/N. */
 double orc_mass(int64_t n, const double *psi)
 {

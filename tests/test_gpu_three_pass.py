@@ -187,7 +187,11 @@ def _modes_check(shape, prec, nsteps, op=ONE, dt=0.5, mean=-0.25, amp=1e-6, nmod
     rng = np.random.default_rng(seed)
     modes = []
     for _ in range(nmodes):
-        m = [int(rng.integers(1, min(n // 4, 40))) * (1 if rng.random() < 0.5 else -1) for n in shape]
+        # |q| per axis at most ~0.6 (|q|^2 <= ~1.1 in 3D): modes near the PFC band, not damped to
+        # nothing in three steps (a mode at |q|^2 ~ 10 shrinks by ~500 a step, and its relative
+        # error would then measure rounding of a vanishing amplitude)
+        mmax = [max(2, min(40, int(0.6 * n * DX / (2 * math.pi)))) for n in shape]
+        m = [int(rng.integers(1, mm + 1)) * (1 if rng.random() < 0.5 else -1) for mm in mmax]
         phase = float(rng.random() * 2 * math.pi)
         q2 = sum((2 * math.pi * mi / (n * DX)) ** 2 for mi, n in zip(m, shape))
         g = (1 - 3 * mean * mean * dt * q2) / (1 + dt * q2 * oracle.lin_op(op, q2))
