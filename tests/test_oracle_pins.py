@@ -352,3 +352,72 @@ def test_oracle_regression_fixture():
     assert oracle.energy(out, math.pi / 4, op) == pytest.approx(gold["energy"], rel=1e-12)
     np.testing.assert_allclose(out.ravel()[gold["sample_idx"]], gold["sample_val"], rtol=1e-11,
                                atol=1e-14)
+
+
+# ---------------------------------------------------------------------------------------------
+# Alternative time integrators (step_scheme): 0 semi-implicit, 1 stabilised, 2 second-order BDF
+# ---------------------------------------------------------------------------------------------
+def test_scheme_zero_and_unstabilised_scheme_one_are_the_semi_implicit_step():
+    psi = inputs.uniform_state((16, 32), -0.25, 0.1, seed=61)
+    ref = oracle.step(psi, math.pi / 4, 0.5, ONE, 7)
+    np.testing.assert_array_equal(oracle.step_scheme(psi, math.pi / 4, 0.5, ONE, 0, 0.0, 7), ref)
+    np.testing.assert_array_equal(oracle.step_scheme(psi, math.pi / 4, 0.5, ONE, 1, 0.0, 7), ref)
+    # the second-order scheme's first step is a semi-implicit step
+    np.testing.assert_array_equal(oracle.step_scheme(psi, math.pi / 4, 0.5, ONE, 2, 0.0, 1),
+                                  oracle.step(psi, math.pi / 4, 0.5, ONE, 1))
+
+
+def _linear_recurrence(scheme, S, op, mean, q2, dt, nsteps, a0=1.0):
+    """Amplitude of one small mode after nsteps steps, from the scalar recurrence each scheme
+    reduces to when psi^3 is linearised about the mean (N_hat = 3 mean^2 psi_hat)."""
+    kind, r, R1, qq = op
+    lk = r + (1 - q2) ** 2 if kind == 0 else r + (1 - q2) ** 2 * (R1 + (qq * qq - q2) ** 2)
+    c = 3.0 * mean * mean
+    a_prev, a = a0, a0
+    for s in range(nsteps):
+        if scheme == 1:
+            nxt = ((1 + dt * q2 * S) * a - dt * q2 * c * a) / (1 + dt * q2 * (lk + S))
+        elif scheme == 2 and s > 0:
+            nxt = (4 * a - a_prev - 2 * dt * q2 * c * (2 * a - a_prev)) / (3 + 2 * dt * q2 * lk)
+        else:
+            nxt = (a - dt * q2 * c * a) / (1 + dt * q2 * lk)
+        a_prev, a = a, nxt
+    return a
+
+
+@pytest.mark.parametrize("scheme,S", [(1, 0.5), (1, 2.0), (2, 0.0)])
+@pytest.mark.parametrize("op", [ONE, TWO], ids=["one-mode", "two-mode"])
+@pytest.mark.parametrize("shape,m", [((32, 32), (0, 5)), ((32, 64), (3, 7)), ((16, 16, 16), (13, 2, 0))])
+def test_scheme_single_mode_matches_its_scalar_recurrence(scheme, S, op, shape, m):
+    dx, dt, nsteps, mean = math.pi / 4, 0.5, 12, -0.25
+    _, q2 = mode_field(shape, dx, mean, 0.0, m)
+    amp = _linear_recurrence(scheme, S, op, mean, q2, dt, nsteps)
+    delta = 1e-6 / max(1.0, abs(amp))
+    psi, _ = mode_field(shape, dx, mean, delta, m)
+    out = oracle.step_scheme(psi, dx, dt, op, scheme, S, nsteps)
+    assert mode_amplitude(out, m) == pytest.approx(delta * amp, rel=2e-9)
+
+
+@pytest.mark.parametrize("scheme,S", [(1, 1.0), (2, 0.0)])
+def test_schemes_conserve_mass(scheme, S):
+    psi = inputs.uniform_state((24, 32), -0.25, 0.05, seed=62)
+    out = oracle.step_scheme(psi, math.pi / 4, 0.5, ONE, scheme, S, 20)
+    assert abs(oracle.mass(out) - oracle.mass(psi)) <= 1e-15
+
+
+@pytest.mark.parametrize("scheme,S,order", [(0, 0.0, 1), (1, 0.5, 1), (2, 0.0, 2)])
+def test_schemes_converge_at_their_order(scheme, S, order):
+    """Error at t = 4 against a run with 1/32 of the step: halving dt divides it by 2^order.
+    Smooth initial data (three low modes): a noisy start has a stiff initial layer that the
+    first-order starting step of scheme 2 resolves only to first order."""
+    y, x = np.meshgrid(np.arange(16), np.arange(16), indexing="ij")
+    psi = (-0.3 + 0.1 * np.cos(2 * np.pi * 2 * x / 16) + 0.07 * np.cos(2 * np.pi * (2 * y + 2 * x) / 16 + 0.3)
+           + 0.05 * np.sin(2 * np.pi * 3 * y / 16))
+    op, T = (oracle.ONE_MODE, -0.1, 0.0, 0.0), 4.0
+    ref = oracle.step_scheme(psi, math.pi / 4, 0.2 / 32, op, scheme, S, int(round(T / (0.2 / 32))))
+    errs = []
+    for dt in (0.2, 0.1, 0.05):
+        out = oracle.step_scheme(psi, math.pi / 4, dt, op, scheme, S, int(round(T / dt)))
+        errs.append(np.linalg.norm(out - ref))
+    for a, b in zip(errs, errs[1:]):
+        assert 2 ** order * 0.8 <= a / b <= 2 ** order * 1.25
