@@ -52,6 +52,9 @@ typedef enum { PFC_FP64 = 0, PFC_FP32_MIXED = 1 } pfc_precision;
 
 typedef enum { PFC_ONE_MODE = 0, PFC_TWO_MODE = 1 } pfc_op_kind;
 
+/* Time integrators of pfc_set_integrator. */
+typedef enum { PFC_SEMI_IMPLICIT = 0, PFC_STABILIZED = 1, PFC_SBDF2 = 2 } pfc_integrator;
+
 /* Linear PFC symbol Lk(k) (Eq. (5)-(6)); kind is a pfc_op_kind. R1 and q2 are read only for
  * PFC_TWO_MODE. */
 typedef struct {
@@ -129,6 +132,27 @@ pfc_status pfc_step_adjoint(pfc_plan *plan, const void *psi_n, const void *lam_n
 
 /* Change r of field `field` (0-based); re-checks operator stability. */
 pfc_status pfc_set_r(pfc_plan *plan, int field, double r);
+
+/* Time integrator of pfc_step (single-field plans; a new plan uses PFC_SEMI_IMPLICIT). The paper
+ * integrates with the semi-implicit scheme (Listing 1) and notes that other time-integration
+ * schemes can be used; in Fourier space each mode obeys d/dt psi_hat = -k^2 (Lk psi_hat + N_hat),
+ * N = psi^3 (Eq. (6)), and one step is
+ *   PFC_SEMI_IMPLICIT  psi_hat <- (psi_hat - dt k^2 N_hat) / (1 + dt k^2 Lk)              (S unused)
+ *   PFC_STABILIZED     psi_hat <- ((1 + dt k^2 S) psi_hat - dt k^2 N_hat) / (1 + dt k^2 (Lk + S)):
+ *                      S psi moved from the explicit to the implicit part (S >= 0; S = 0 is the
+ *                      semi-implicit step); first order
+ *   PFC_SBDF2          (3 psi_hat^{n+1} - 4 psi_hat^n + psi_hat^{n-1}) / (2 dt)
+ *                          = -k^2 (Lk psi_hat^{n+1} + 2 N_hat^n - N_hat^{n-1}):
+ *                      second-order backward differentiation with the nonlinear term extrapolated
+ *                      (S unused). It carries two time levels inside one pfc_step call, whose
+ *                      first step is a semi-implicit step: a call of nsteps steps is one run
+ *                      (the levels do not persist between calls). Allocates two more half spectra.
+ * Passes: the same two (or three) passes per step; PFC_SBDF2's line pass reads the previous
+ * level's X' and C' too (7 sweeps a step in the two-pass schedule). Re-checks that the scheme's
+ * implicit factor is positive. pfc_step_adjoint stays the adjoint of the semi-implicit step
+ * (UNSUPPORTED under another scheme). Errors: INVALID_ARG, UNSUPPORTED (two-field plans),
+ * UNSTABLE_OPERATOR, OUT_OF_MEMORY, CUDA. */
+pfc_status pfc_set_integrator(pfc_plan *plan, int scheme, double S);
 
 /* Synchronise the plan's stream and return the latched device status (TIMEOUT, NONFINITE),
  * clearing it. */

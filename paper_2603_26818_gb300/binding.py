@@ -20,12 +20,14 @@ STATUS_NAMES = {0: "PFC_OK", 1: "PFC_ERR_INVALID_ARG", 2: "PFC_ERR_UNSUPPORTED",
                 6: "PFC_ERR_NONFINITE", 7: "PFC_ERR_TIMEOUT"}
 PFC_FP64, PFC_FP32_MIXED = 0, 1
 PFC_ONE_MODE, PFC_TWO_MODE = 0, 1
+PFC_SEMI_IMPLICIT, PFC_STABILIZED, PFC_SBDF2 = 0, 1, 2
 
 # every extern "C" symbol of include/pfc.h
 EXPORTS = ["pfc_plan_create", "pfc_plan_destroy", "pfc_step", "pfc_fft_r2c", "pfc_fft_c2r",
            "pfc_mass", "pfc_energy", "pfc_step_adjoint", "pfc_set_r", "pfc_sync", "pfc_plan_info",
            "pfc_profile_steps", "pfc_step_noalloc", "pfc_plan_autotune", "pfc_batch_autotune",
            "pfc_batch_info",
+           "pfc_set_integrator",
            "pfc_status_string", "pfc_last_error", "pfc_batch_create", "pfc_batch_destroy",
            "pfc_batch_step", "pfc_batch_mass"]
 
@@ -66,6 +68,7 @@ def load_library(path: str = LIB_PATH):
         "pfc_energy": [vp, vp, P(dbl)],
         "pfc_step_adjoint": [vp, vp, vp, vp, vp],
         "pfc_set_r": [vp, cint, dbl],
+        "pfc_set_integrator": [vp, cint, dbl],
         "pfc_sync": [vp],
         "pfc_plan_info": [vp, P(ctypes.c_int32), P(i64)],
         "pfc_profile_steps": [vp, vp, i64, P(dbl), P(i64)],
@@ -205,6 +208,10 @@ class Plan:
 
     def set_r(self, r: float, field: int = 0):
         check(load_library().pfc_set_r(self._h, int(field), float(r)))
+
+    def set_integrator(self, scheme: int, S: float = 0.0):
+        """pfc_set_integrator: PFC_SEMI_IMPLICIT, PFC_STABILIZED (constant S) or PFC_SBDF2."""
+        check(load_library().pfc_set_integrator(self._h, int(scheme), float(S)))
 
     def sync(self):
         check(load_library().pfc_sync(self._h))

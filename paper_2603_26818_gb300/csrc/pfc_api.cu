@@ -44,6 +44,9 @@ struct pfc_plan {
     Tiles t{};
     void *X = nullptr, *C = nullptr, *tw = nullptr, *stw = nullptr;
     void *Y = nullptr;            // three-pass plans: the state in the row-pass form (P-part only)
+    int scheme = PFC_SEMI_IMPLICIT;   // time integrator (pfc_set_integrator)
+    double stab = 0.0;            // its stabilisation constant S
+    void *X2 = nullptr, *C2 = nullptr;   // the second time level of the second-order scheme
     void *A = nullptr;            // third half spectrum, allocated by the first adjoint call
     double *d_adjpart = nullptr;  // adjoint line-pass partial sums (one per block)
     double *d_mean = nullptr, *d_part = nullptr, *d_out = nullptr;
@@ -51,6 +54,7 @@ struct pfc_plan {
     size_t scratch = 0;
     size_t half_cap = 0;          // bytes allocated for each of X and C
     size_t y_cap = 0;             // bytes allocated for Y
+    size_t lv_cap = 0;            // bytes allocated for each of X2 and C2
     size_t adj_bytes = 0;         // bytes of A and d_adjpart
     int ntile = 2;                // line-pass tiles (3 for a two-field plan)
     cudaGraphExec_t graph = nullptr;
@@ -130,8 +134,26 @@ template <typename R> void launch_means(pfc_plan *p, const void *state) {
     }
 }
 
-// The line pass of one step: per field, or the coupled 2x2 solve for a two-field plan.
-template <typename R> void launch_update(pfc_plan *p) {
+// The buffers of step s (0-based within one pfc_step call). The second-order scheme carries two
+// time levels, X'/C' of step s - 1 and s: step s reads level s from lv[s % 2] and level s - 1 from
+// lv[(s + 1) % 2], and writes level s + 1 over level s - 1. The other schemes work in place.
+struct StepBufs {
+    void *x, *c, *xprev, *cprev, *xout;
+};
+StepBufs step_bufs(const pfc_plan *p, int64_t s) {
+    if (p->scheme != PFC_SBDF2) return StepBufs{p->X, p->C, nullptr, nullptr, p->X};
+    void *xs[2] = {p->X, p->X2}, *cs[2] = {p->C, p->C2};
+    const int cur = (int)(s & 1), oth = 1 - cur;
+    return StepBufs{xs[cur], cs[cur], s > 0 ? xs[oth] : nullptr, s > 0 ? cs[oth] : nullptr, xs[oth]};
+}
+// where the carried state is after nsteps steps of a call
+void *final_state(const pfc_plan *p, int64_t nsteps) {
+    return p->scheme == PFC_SBDF2 && (nsteps & 1) ? p->X2 : p->X;
+}
+
+// The line pass of one step: per field, or the coupled 2x2 solve for a two-field plan; the
+// alternative integrators (single field) on the LINE_SCHEME pass.
+template <typename R> void launch_update(pfc_plan *p, const StepBufs &b) {
     LineArgs<R> la = line_args<R>(p);
     if (p->nfields == 2) {
         using V = typename VT<R>::V;
@@ -147,41 +169,67 @@ template <typename R> void launch_update(pfc_plan *p) {
         launch_line_step2<R>(cfg(p), a2);
         return;
     }
-    la.x = p->X;
-    la.c = p->C;
-    launch_line_m<R>(p, LINE_STEP, la, 1);
+    la.x = b.x;
+    la.c = b.c;
+    if (p->scheme == PFC_SEMI_IMPLICIT) {
+        launch_line_m<R>(p, LINE_STEP, la, 1);
+        return;
+    }
+    la.xout = b.xout;
+    la.up.d0 = (R)1;
+    la.up.d1 = (R)1;
+    la.up.S = (R)0;
+    la.up.xw0 = la.up.cw0 = (R)1;
+    la.up.xw1 = la.up.cw1 = (R)0;
+    if (p->scheme == PFC_STABILIZED) {
+        la.up.S = (R)p->stab;
+    } else if (b.xprev) {
+        // (3 X^{n+1} - 4 X^n + X^{n-1}) / (2 dt) = -k^2 (Lk X^{n+1} + 2 N^n - N^{n-1})
+        la.xprev = b.xprev;
+        la.cprev = b.cprev;
+        la.up.d0 = (R)3;
+        la.up.d1 = (R)2;
+        la.up.xw0 = (R)4;
+        la.up.xw1 = (R)-1;
+        la.up.cw0 = (R)2;
+        la.up.cw1 = (R)-1;
+    }   // else: the second-order scheme's first step, a semi-implicit step written to xout
+    launch_line_m<R>(p, LINE_SCHEME, la, 1);
 }
 
-// The psi^3 row pass of one step. Two-pass plans: X' -> C', edge columns projected in X'.
-// Three-pass plans carry X'' (P and R parts done): the middle pass takes it back to the
-// row-pass form in Y, the row pass writes C' and projects Y's edge columns, and the middle pass
-// takes C' forward in place and the projected edge columns of Y forward into X'' (scale 1/R,
-// the scale of the carried state). Sweeps: 2 + 2 + 2 (+ the edge columns) before the line pass.
-template <typename R> void enqueue_cube(pfc_plan *p, int mark_mid = -1, int mark_row = -1,
+// The psi^3 row pass of one step on the carried state x, writing c. Two-pass plans: X' -> C',
+// edge columns projected in X'. Three-pass plans carry X'' (P and R parts done): the middle
+// pass takes it back to the row-pass form in Y, the row pass writes C' and projects Y's edge
+// columns, and the middle pass takes C' forward in place and the projected edge columns of Y
+// forward into X'' (scale 1/R, the scale of the carried state). Sweeps: 2 + 2 + 2 (+ the edge
+// columns) before the line pass.
+template <typename R> void enqueue_cube(pfc_plan *p, void *x, void *c, int mark_mid = -1, int mark_row = -1,
                                         const std::function<void(int)> &mark = nullptr) {
     const bool three = three_pass(p);
     if (three) {
         if (mark) mark(mark_mid);
-        launch_mid_m<R>(p, +1, p->X, p->Y, 1.0, false);
+        launch_mid_m<R>(p, +1, x, p->Y, 1.0, false);
     }
     RowArgs<R> ra = row_args<R>(p);
-    ra.in = three ? p->Y : p->X;
-    ra.out = p->C;
-    ra.proj = three ? p->Y : p->X;
+    ra.in = three ? p->Y : x;
+    ra.out = c;
+    ra.proj = three ? p->Y : x;
     ra.mean = p->d_mean;
     if (mark) mark(mark_row);
     launch_row_m<R>(p, ROW_CUBE, ra, p->nfields);
     if (three) {
         if (mark) mark(mark_mid);
-        launch_mid_m<R>(p, -1, p->C, p->C, 1.0, false);
-        launch_mid_m<R>(p, -1, p->Y, p->X, 1.0 / p->t.g.R, true);
+        launch_mid_m<R>(p, -1, c, c, 1.0, false);
+        launch_mid_m<R>(p, -1, p->Y, x, 1.0 / p->t.g.R, true);
     }
 }
 
-// One step on the carried state (row pass (+ middle passes) + line pass).
-template <typename R> void enqueue_one_step(pfc_plan *p) {
-    enqueue_cube<R>(p);
-    launch_update<R>(p);
+// Step s of a call (row pass (+ middle passes) + line pass).
+template <typename R> void enqueue_step(pfc_plan *p, int64_t s, const std::function<void(int)> &mark = nullptr) {
+    const StepBufs b = step_bufs(p, s);
+    enqueue_cube<R>(p, b.x, b.c, 4, 0, mark);
+    if (mark) mark(1);
+    launch_update<R>(p, b);
 }
 
 // Entry: real state -> carried state (X' or, three-pass, X'' = middle forward of X' / R).
@@ -197,19 +245,24 @@ template <typename R> void enqueue_entry(pfc_plan *p, const void *state) {
     if (three_pass(p)) launch_mid_m<R>(p, -1, p->X, p->X, 1.0 / g.R, false);
 }
 
-// Exit: carried state -> real state.
-template <typename R> void enqueue_exit(pfc_plan *p, void *state) {
+// Exit: carried state x -> real state.
+template <typename R> void enqueue_exit(pfc_plan *p, void *x, void *state) {
     const bool three = three_pass(p);
-    if (three) launch_mid_m<R>(p, +1, p->X, p->Y, 1.0, false);
+    if (three) launch_mid_m<R>(p, +1, x, p->Y, 1.0, false);
     RowArgs<R> rb = row_args<R>(p);
-    rb.in = three ? p->Y : p->X;
+    rb.in = three ? p->Y : x;
     rb.out = state;
     rb.mean = p->d_mean;
     launch_row_m<R>(p, ROW_INV, rb, p->nfields);
 }
 
+// nsteps steps: the second-order scheme's starting step directly, then chunks of GRAPH_CHUNK
+// steps through one captured graph (an even chunk, so every chunk starts at the same parity of
+// the time levels), then the remainder directly.
 template <typename R> pfc_status run_steps(pfc_plan *p, int64_t nsteps) {
-    if (nsteps >= GRAPH_CHUNK && !p->graph) {
+    int64_t done = 0;
+    if (p->scheme == PFC_SBDF2) enqueue_step<R>(p, done++);
+    if (nsteps - done >= GRAPH_CHUNK && !p->graph) {
         cudaStream_t cap;
         PFC_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaStream_t saved = p->stream;
@@ -217,7 +270,7 @@ template <typename R> pfc_status run_steps(pfc_plan *p, int64_t nsteps) {
         cudaGraph_t graph;
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            for (int s = 0; s < GRAPH_CHUNK; ++s) enqueue_one_step<R>(p);
+            for (int s = 0; s < GRAPH_CHUNK; ++s) enqueue_step<R>(p, done + s);
             e = cudaStreamEndCapture(cap, &graph);
         }
         p->stream = saved;
@@ -229,12 +282,11 @@ template <typename R> pfc_status run_steps(pfc_plan *p, int64_t nsteps) {
         if (e != cudaSuccess) return fail(PFC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
         p->graph_steps = GRAPH_CHUNK;
     }
-    int64_t done = 0;
     if (p->graph) {
         for (; done + p->graph_steps <= nsteps; done += p->graph_steps)
             PFC_CUDA(cudaGraphLaunch(p->graph, p->stream));
     }
-    for (; done < nsteps; ++done) enqueue_one_step<R>(p);
+    for (; done < nsteps; ++done) enqueue_step<R>(p, done);
     PFC_CUDA(cudaGetLastError());
     return PFC_OK;
 }
@@ -244,7 +296,7 @@ template <typename R> pfc_status step_impl(pfc_plan *p, void *state, int64_t nst
     PFC_CUDA(cudaGetLastError());
     pfc_status s = run_steps<R>(p, nsteps);
     if (s != PFC_OK) return s;
-    enqueue_exit<R>(p, state);
+    enqueue_exit<R>(p, final_state(p, nsteps), state);
     PFC_CUDA(cudaGetLastError());
     return PFC_OK;
 }
@@ -354,6 +406,8 @@ pfc_status adjoint_impl(pfc_plan *p, const void *psi_n, const void *lam_next, vo
     const Geom &g = p->t.g;
     const bool three = three_pass(p);
     if (p->nfields != 1) return fail(PFC_ERR_UNSUPPORTED, "the adjoint step is built for single-field plans");
+    if (p->scheme != PFC_SEMI_IMPLICIT)
+        return fail(PFC_ERR_UNSUPPORTED, "the adjoint step is the adjoint of the semi-implicit step");
     if (p->t.nt_line > 512) return fail(PFC_ERR_UNSUPPORTED, "the adjoint line pass needs tiles of at most 512 threads");
     if (psi_n == lam_out) return fail(PFC_ERR_INVALID_ARG, "lam_out must not alias psi_n");
     const size_t half_bytes = (size_t)g.nhalf * vbytes(p);
@@ -436,13 +490,11 @@ pfc_status profile_impl(pfc_plan *p, void *state, int64_t nsteps, double *ms, in
         if (err == cudaSuccess) err = mark(k);
     };
     for (int64_t s = 0; s < nsteps && err == cudaSuccess; ++s) {
-        enqueue_cube<R>(p, 4, 0, mk);
-        mk(1);
-        launch_update<R>(p);
+        enqueue_step<R>(p, s, mk);
         nl += 2 + (three ? 3 : 0);
     }
     mk(3);
-    enqueue_exit<R>(p, state);
+    enqueue_exit<R>(p, final_state(p, nsteps), state);
     nl += 1 + (three ? 1 : 0);
     mk(-1);
     if (err == cudaSuccess) err = cudaGetLastError();
@@ -499,6 +551,21 @@ pfc_status apply_tiles(pfc_plan *p, const Tiles &t) {
         p->C = c;
         p->scratch += 2 * (need - p->half_cap);
         p->half_cap = need;
+    }
+    if (p->X2 && p->lv_cap < p->half_cap) {
+        void *x = nullptr, *c = nullptr;
+        PFC_CUDA(cudaMalloc(&x, p->half_cap));
+        if (cudaError_t e = cudaMalloc(&c, p->half_cap); e != cudaSuccess) {
+            cudaFree(x);
+            return fail(e == cudaErrorMemoryAllocation ? PFC_ERR_OUT_OF_MEMORY : PFC_ERR_CUDA,
+                        std::string("time levels: ") + cudaGetErrorString(e));
+        }
+        cudaFree(p->X2);
+        cudaFree(p->C2);
+        p->X2 = x;
+        p->C2 = c;
+        p->scratch += 2 * (p->half_cap - p->lv_cap);
+        p->lv_cap = p->half_cap;
     }
     if (p->Y && p->y_cap < p->half_cap) {
         void *y = nullptr;
@@ -697,7 +764,7 @@ pfc_status pfc_plan_destroy(pfc_plan *p) {
     if (p->destroyed) return fail(PFC_ERR_INVALID_ARG, "plan already destroyed");
     cudaStreamSynchronize(p->stream);
     if (p->graph) cudaGraphExecDestroy(p->graph);
-    cudaFree(p->X); cudaFree(p->C); cudaFree(p->Y); cudaFree(p->tw); cudaFree(p->stw);
+    cudaFree(p->X); cudaFree(p->C); cudaFree(p->Y); cudaFree(p->X2); cudaFree(p->C2); cudaFree(p->tw); cudaFree(p->stw);
     cudaFree(p->A); cudaFree(p->d_adjpart);
     cudaFree(p->d_mean); cudaFree(p->d_part); cudaFree(p->d_out); cudaFree(p->d_status);
     p->destroyed = true;
@@ -766,6 +833,43 @@ pfc_status pfc_set_r(pfc_plan *p, int field, double r) {
         return fail(PFC_ERR_UNSTABLE_OPERATOR, "1 + dt k^2 Lk(k) is not positive on the grid");
     cudaStreamSynchronize(p->stream);
     p->ops[field].r = r;
+    if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+    return PFC_OK;
+}
+
+pfc_status pfc_set_integrator(pfc_plan *p, int scheme, double S) {
+    if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
+    if (scheme != PFC_SEMI_IMPLICIT && scheme != PFC_STABILIZED && scheme != PFC_SBDF2)
+        return fail(PFC_ERR_INVALID_ARG, "unknown integrator");
+    if (!std::isfinite(S) || S < 0) return fail(PFC_ERR_INVALID_ARG, "S must be finite and >= 0");
+    if (scheme != PFC_SEMI_IMPLICIT && p->nfields != 1)
+        return fail(PFC_ERR_UNSUPPORTED, "the alternative integrators are built for single-field plans");
+    // the implicit factor of the scheme must stay positive: 1 + dt k^2 (Lk + S) (stabilised, Lk
+    // shifted by S), 3 + 2 dt k^2 Lk (second order, the semi-implicit factor at dt 2/3)
+    pfc_op op = p->ops[0];
+    double dt = p->dt;
+    if (scheme == PFC_STABILIZED) op.r += S;
+    if (scheme == PFC_SBDF2) dt = 2.0 * p->dt / 3.0;
+    const double kmax = M_PI / p->dx;
+    if (min_implicit(&op, 1, 0.0, dt, kmax * kmax * p->ndim) <= 0.0 ||
+        (scheme == PFC_SBDF2 && min_implicit(p->ops, 1, 0.0, p->dt, kmax * kmax * p->ndim) <= 0.0))
+        return fail(PFC_ERR_UNSTABLE_OPERATOR, "the scheme's implicit factor is not positive on the grid");
+    PFC_CUDA(cudaStreamSynchronize(p->stream));
+    if (scheme == PFC_SBDF2 && !p->X2) {
+        PFC_CUDA(cudaMalloc(&p->X2, p->half_cap));
+        if (cudaError_t e = cudaMalloc(&p->C2, p->half_cap); e != cudaSuccess) {
+            cudaFree(p->X2);
+            p->X2 = nullptr;
+            return fail(e == cudaErrorMemoryAllocation ? PFC_ERR_OUT_OF_MEMORY : PFC_ERR_CUDA,
+                        std::string("time levels: ") + cudaGetErrorString(e));
+        }
+        PFC_CUDA(cudaMemset(p->X2, 0, p->half_cap));
+        PFC_CUDA(cudaMemset(p->C2, 0, p->half_cap));
+        p->lv_cap = p->half_cap;
+        p->scratch += 2 * p->half_cap;
+    }
+    p->scheme = scheme;
+    p->stab = scheme == PFC_STABILIZED ? S : 0.0;
     if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
     return PFC_OK;
 }

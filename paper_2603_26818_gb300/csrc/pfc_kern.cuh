@@ -37,6 +37,7 @@ template <typename R, int MAXT>
 static void launch_line_t(const LaunchCfg &c, int mode, const LineArgs<R> &a, int nf) {
     dim3 grid(c.g.ncg, c.g.P * c.g.R, nf);
     if (mode == LINE_STEP) k_line<R, LINE_STEP, MAXT><<<grid, c.nt_line, c.smem_line, c.stream>>>(c.g, a);
+    else if (mode == LINE_SCHEME) k_line<R, LINE_SCHEME, MAXT><<<grid, c.nt_line, c.smem_line, c.stream>>>(c.g, a);
     else if (mode == LINE_FWD) k_line<R, LINE_FWD, MAXT><<<grid, c.nt_line, c.smem_line, c.stream>>>(c.g, a);
     else k_line<R, LINE_INV, MAXT><<<grid, c.nt_line, c.smem_line, c.stream>>>(c.g, a);
 }
@@ -64,10 +65,12 @@ template <typename R> cudaError_t set_smem_attrs(const LaunchCfg &c) {
     if ((e = allow_smem(k_line_adj<R>, c.smem_line)) != cudaSuccess) return e;
     if ((e = allow_smem(k_line_step2<R>, c.smem_line)) != cudaSuccess) return e;
     if ((e = allow_smem(k_line<R, LINE_STEP, 512>, c.smem_line)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_line<R, LINE_SCHEME, 512>, c.smem_line)) != cudaSuccess) return e;
     if ((e = allow_smem(k_line<R, LINE_FWD, 512>, c.smem_line)) != cudaSuccess) return e;
     if ((e = allow_smem(k_line<R, LINE_INV, 512>, c.smem_line)) != cudaSuccess) return e;
     if constexpr (sizeof(R) == 4) {
         if ((e = allow_smem(k_line<R, LINE_STEP, 1024>, c.smem_line)) != cudaSuccess) return e;
+        if ((e = allow_smem(k_line<R, LINE_SCHEME, 1024>, c.smem_line)) != cudaSuccess) return e;
         if ((e = allow_smem(k_line<R, LINE_FWD, 1024>, c.smem_line)) != cudaSuccess) return e;
         if ((e = allow_smem(k_line<R, LINE_INV, 1024>, c.smem_line)) != cudaSuccess) return e;
     }

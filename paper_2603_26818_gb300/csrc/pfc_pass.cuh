@@ -62,7 +62,7 @@ struct OpDev {
 };
 
 enum { ROW_CUBE = 0, ROW_FWD = 1, ROW_INV = 2, ROW_ADJ_MIX = 3 };
-enum { LINE_STEP = 0, LINE_FWD = 1, LINE_INV = 2 };
+enum { LINE_STEP = 0, LINE_FWD = 1, LINE_INV = 2, LINE_SCHEME = 3 };
 enum { STATUS_NONFINITE = 1, STATUS_TIMEOUT = 2 };
 
 template <typename R> struct RowArgs {
@@ -88,11 +88,18 @@ template <typename R> struct UpdR {
     R cx, cy, cz;         // 2 pi / (n dx) per axis
     R invQ, inv_halfN;    // 1/Q and 2/N
     OpR<R> op[2];         // per field
+    // LINE_SCHEME: psi_hat' = (1 + dt k^2 S) inv X - d1 dt k^2 inv C, inv = 1 / (d0 + d1 dt k^2 (Lk + S)),
+    // X and C the combinations xw0 X + xw1 Xprev and cw0 C + cw1 Cprev (Xprev, Cprev may be null)
+    R d0, d1, S;
+    R xw0, xw1, cw0, cw1;
 };
 
 template <typename R> struct LineArgs {
-    void *x;              // X' (in/out)
+    void *x;              // X' (in/out; LINE_SCHEME: in)
     const void *c;        // C'
+    const void *xprev;    // LINE_SCHEME: the previous level's X' and C' (null: not used)
+    const void *cprev;
+    void *xout;           // LINE_SCHEME: output X' (may equal x or xprev)
     const void *std_in;   // LINE_INV input (standard half spectrum)
     void *std_out;        // LINE_FWD output (standard half spectrum)
     R scale;              // LINE_INV / LINE_FWD output scale
@@ -697,18 +704,38 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
     const int lsy = g.lPy + g.lRy, lsz = g.lPz + g.lRz;   // ky = kpy + (k_qy << lsy), kz likewise
     V vt[8], vc[8];
 
-    if (MODE == LINE_STEP) {
+    if (MODE == LINE_STEP || MODE == LINE_SCHEME) {
         // C' first, completely into smem (natural order), so that only one register set is live
         const V *C = reinterpret_cast<const V *>(a.c) + (size_t)field * g.nhalf;
 #pragma unroll
         for (int m = 0; m < 8; ++m) vc[m] = __ldcg(&C[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)]);
+        if constexpr (MODE == LINE_SCHEME) {
+            if (a.cprev) {
+                const V *Cp = reinterpret_cast<const V *>(a.cprev) + (size_t)field * g.nhalf;
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const V u = __ldcg(&Cp[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)]);
+                    vc[m] = V{a.up.cw0 * vc[m].x + a.up.cw1 * u.x, a.up.cw0 * vc[m].y + a.up.cw1 * u.y};
+                }
+            }
+        }
         line_yfft<-1, LY>(vc, Cs, ady, g, mp.jy, true, false, a.st);
         if (two_axes) line_zfft<-1, LZ>(vc, Cs, adz, g, mp.jz, false, false, a.st);
     }
-    if (MODE == LINE_STEP || MODE == LINE_FWD) {
+    if (MODE == LINE_STEP || MODE == LINE_FWD || MODE == LINE_SCHEME) {
         const V *X = reinterpret_cast<const V *>(a.x) + (size_t)field * g.nhalf;
 #pragma unroll
         for (int m = 0; m < 8; ++m) vt[m] = __ldcg(&X[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)]);
+        if constexpr (MODE == LINE_SCHEME) {
+            if (a.xprev) {
+                const V *Xp = reinterpret_cast<const V *>(a.xprev) + (size_t)field * g.nhalf;
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const V u = __ldcg(&Xp[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)]);
+                    vt[m] = V{a.up.xw0 * vt[m].x + a.up.xw1 * u.x, a.up.xw0 * vt[m].y + a.up.xw1 * u.y};
+                }
+            }
+        }
         line_yfft<-1, LY>(vt, T, ady, g, mp.jy, true, !two_axes, a.st);
         if (two_axes) line_zfft<-1, LZ>(vt, T, adz, g, mp.jz, false, true, a.st);
     }
@@ -730,7 +757,7 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
         return;
     }
 
-    if (MODE == LINE_STEP) {
+    if (MODE == LINE_STEP || MODE == LINE_SCHEME) {
         OpR<R> op = field == 0 ? a.up.op[0] : a.up.op[1];
         if (a.rmem) op.r = a.rmem[field];
         const R invQ = a.up.invQ, inv_halfN = a.up.inv_halfN, dt = a.up.dt;
@@ -749,8 +776,17 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
             const R fy = cy * (R)my, fz = cz * (R)mz;
             const R k2 = fx * fx + fy * fy + fz * fz;
             const R lk = lin_symbol<R>(op, k2);
-            const R inv = (R)1 / ((R)1 + dt * k2 * lk);
-            const R ca = inv * invQ, cb = dt * k2 * inv * inv_halfN;
+            R ca, cb;
+            if constexpr (MODE == LINE_SCHEME) {
+                const R dk = dt * k2;
+                const R inv = (R)1 / (a.up.d0 + a.up.d1 * dk * (lk + a.up.S));
+                ca = ((R)1 + dk * a.up.S) * inv * invQ;
+                cb = a.up.d1 * dk * inv * inv_halfN;
+            } else {
+                const R inv = (R)1 / ((R)1 + dt * k2 * lk);
+                ca = inv * invQ;
+                cb = dt * k2 * inv * inv_halfN;
+            }
             V t = V{ca * vt[m].x - cb * c.x, ca * vt[m].y - cb * c.y};
             if (kx == 0 && ky == 0 && kz == 0) t = V{(R)0, (R)0};
             vt[m] = t;
@@ -776,7 +812,7 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
     } else {
         line_yfft<+1, LY>(vt, T, ady, g, mp.jy, true, true, a.st);
     }
-    V *Xo = reinterpret_cast<V *>(a.x) + (size_t)field * g.nhalf;
+    V *Xo = reinterpret_cast<V *>(MODE == LINE_SCHEME ? a.xout : a.x) + (size_t)field * g.nhalf;
     const R sc = MODE == LINE_INV ? a.scale : (R)1;
 #pragma unroll
     for (int m = 0; m < 8; ++m)

@@ -80,6 +80,7 @@ def test_host_side_validation(lib):
     assert lib.pfc_plan_autotune(None, 4, 20, None, None) == 1
     assert lib.pfc_batch_autotune(None, 4, 20, None) == 1
     assert lib.pfc_batch_info(None, None, 0, None) == 1
+    assert lib.pfc_set_integrator(None, 2, 0.0) == 1
     assert lib.pfc_plan_destroy(None) == 0
 
 
