@@ -285,7 +285,7 @@ def other_grids(torch, dev, flush):
         "per_kernel_ms_per_step": {k: prof[k] / 3 for k in ("row", "line", "mid")},
         "per_kernel_frac": {"row": 2 * half / (prof["row"] / 3 * 1e-3) / 1e9 / peak,
                             "line": 3 * half / (prof["line"] / 3 * 1e-3) / 1e9 / peak,
-                            "mid": 6 * half / max(prof["mid"] / 3 * 1e-3, 1e-12) / 1e9 / peak},
+                            "mid": 4 * half / max(prof["mid"] / 3 * 1e-3, 1e-12) / 1e9 / peak},
         "state": "psi0 = -0.25 + U[-0.01, 0.01] from a seeded torch generator (seed 8)"}
     p.close()
     del x
@@ -295,7 +295,10 @@ def other_grids(torch, dev, flush):
 
 def precision_report(torch, dev):
     """FP32-mixed against the FP64 path, per workload: relative L2 errors after each workload's
-    full length (the FP64 paths are pinned to the oracle by the test suite)."""
+    full length (the FP64 paths are pinned to the oracle by the test suite). Both runs start from
+    the same FP32-representable state, so the figure is the FP32 path's arithmetic; where the
+    workload's own FP64 draws differ visibly from their FP32 rounding (small fluctuations about a
+    large mean, linearly unstable), the error against the FP64 draws is reported beside it."""
     import numpy as np
     from paper_2603_26818_gb300 import binding, inputs
     from paper_2603_26818_gb300.autograd import rollout
@@ -308,9 +311,10 @@ def precision_report(torch, dev):
     two = binding.make_op(1, -0.3, 0.05, math.sqrt(4.0 / 3.0))
     psi0 = inputs.uniform_state((512, 512, 512), -0.35, 0.02, seed=3)
     res = {}
-    for prec, dt_ in (("fp64", torch.float64), ("fp32", torch.float32)):
+    x0 = torch.from_numpy(psi0).to(device=dev, dtype=torch.float32)
+    for prec in ("fp64", "fp32"):
         p = binding.Plan((512, 512, 512), DX, 0.1, [two], precision=prec)
-        x = torch.from_numpy(psi0).to(device=dev, dtype=dt_)
+        x = x0.double() if prec == "fp64" else x0.clone()
         p.step(x, 500)
         res[prec] = (x, p.mass(x)[0])
         p.close()
@@ -326,28 +330,30 @@ def precision_report(torch, dev):
     draws = inputs.batch_draws(1024, seed=4)
     parts = np.concatenate([inputs.uniform_state((ny, nx), m, 0.01, seed=1000 + i).ravel()
                             for i, (ny, nx, r, m) in enumerate(draws)])
-    xs = {}
-    for prec, dt_ in (("fp64", torch.float64), ("fp32", torch.float32)):
-        bt = binding.Batch([(d[0], d[1]) for d in draws], [d[2] for d in draws], DX, 0.5, precision=prec)
-        x = torch.from_numpy(parts).to(device=dev, dtype=dt_)
-        bt.step(x, 200)
-        xs[prec] = (bt, x)
-    errs = []
-    for d in range(len(draws)):
-        errs.append(relerr(xs["fp32"][0].view(xs["fp32"][1], d), xs["fp64"][0].view(xs["fp64"][1], d)))
-    for bt, _ in xs.values():
-        bt.close()
-    errs = np.array(errs)
+    b32 = binding.Batch([(d[0], d[1]) for d in draws], [d[2] for d in draws], DX, 0.5, precision="fp32")
+    b64 = binding.Batch([(d[0], d[1]) for d in draws], [d[2] for d in draws], DX, 0.5, precision="fp64")
+    x = torch.from_numpy(parts).to(device=dev, dtype=torch.float32)
+    y = x.double()
+    yin = torch.from_numpy(parts).to(device=dev)
+    for bt, z in ((b32, x), (b64, y), (b64, yin)):
+        bt.step(z, 200)
+    errs = np.array([relerr(b32.view(x, d), b64.view(y, d)) for d in range(len(draws))])
+    errs_in = np.array([relerr(b32.view(x, d), b64.view(yin, d)) for d in range(len(draws))])
+    b32.close()
+    b64.close()
     out["4a_ensemble_1024_domains_200_steps"] = {
         "rel_l2_max_over_domains": float(errs.max()), "rel_l2_median": float(np.median(errs)),
-        "domains_above_1e-5": int((errs > 1e-5).sum())}
+        "domains_above_1e-5": int((errs > 1e-5).sum()),
+        "against_fp64_draws": {"rel_l2_max_over_domains": float(errs_in.max()),
+                               "domains_above_1e-5": int((errs_in > 1e-5).sum())}}
     p0 = inputs.uniform_state((256, 256, 256), -0.25, 0.01, seed=5)
     c0 = inputs.uniform_state((256, 256, 256), -0.2, 0.01, seed=6)
     ops = [binding.make_op(0, -0.25), binding.make_op(0, -0.25)]
     xs = {}
-    for prec, dt_ in (("fp64", torch.float64), ("fp32", torch.float32)):
+    x0 = torch.from_numpy(np.stack([p0, c0])).to(device=dev, dtype=torch.float32)
+    for prec in ("fp64", "fp32"):
         p = binding.Plan((256, 256, 256), DX, 0.5, ops, precision=prec, coupling=0.1)
-        x = torch.from_numpy(np.stack([p0, c0])).to(device=dev, dtype=dt_)
+        x = x0.double() if prec == "fp64" else x0.clone()
         p.step(x, 200)
         xs[prec] = x
         p.close()
@@ -356,13 +362,17 @@ def precision_report(torch, dev):
     del xs
     # adjoint: 256^3 one-mode, 200 steps, checkpoints every 20, gradients FP32 vs FP64
     shape = (256, 256, 256)
-    psi0 = inputs.uniform_state(shape, -0.25, 0.01, seed=6)
+    psi0 = inputs.uniform_state(shape, -0.25, 0.01, seed=6).astype(np.float32).astype(np.float64)
+    p = binding.Plan(shape, DX, 0.5, [binding.make_op(0, -0.25)], precision="fp64")
+    p.set_r(-0.2)
+    tg64 = torch.from_numpy(psi0).to(device=dev)
+    p.step(tg64, 200)
+    p.close()
+    tg64 = tg64.float().double()   # one target for both precisions
     grads = {}
     for prec, dt_ in (("fp64", torch.float64), ("fp32", torch.float32)):
         p = binding.Plan(shape, DX, 0.5, [binding.make_op(0, -0.25)], precision=prec)
-        p.set_r(-0.2)
-        tg = torch.from_numpy(psi0).to(device=dev, dtype=dt_)
-        p.step(tg, 200)
+        tg = tg64.to(dt_)
         x0 = torch.from_numpy(psi0).to(device=dev, dtype=dt_).requires_grad_(True)
         rt = torch.tensor(-0.25, dtype=torch.float64, requires_grad=True)
         loss = 0.5 * ((rollout(x0, rt, p, 200, 20) - tg) ** 2).sum()
@@ -698,19 +708,22 @@ def run_ours(args):
         extras["speedup_vs_plain_fp64"] = value / world / extras["cufft_plain_fp64"] if extras["cufft_plain_fp64"] else None
         # precision report: FP32-mixed vs our FP64 path after 1000 steps from psi0
         a = torch.from_numpy(psi0).to(device=dev, dtype=torch.float32)
-        b = torch.from_numpy(psi0).to(device=dev)
-        m0 = float(psi0.mean())
+        b = a.double()                      # the same FP32-representable start
+        bin_ = torch.from_numpy(psi0).to(device=dev)   # the FP64 draws
+        m0 = float(b.mean())
         plan.step(a, 1000)
         p64.step(b, 1000)
+        p64.step(bin_, 1000)
         torch.cuda.synchronize()
         diff = (a.double() - b).norm() / b.norm()
         fl = (b - b.mean()).norm()
         extras["precision_1000_steps"] = {
             "rel_l2_fp32_vs_fp64": float(diff),
             "rel_l2_of_fluctuation": float((a.double() - b).norm() / fl),
+            "rel_l2_against_fp64_draws": float((a.double() - bin_).norm() / bin_.norm()),
             "mass_drift_rel_fp32": abs(plan.mass(a)[0] - m0) / abs(m0),
             "mass_drift_rel_fp64": abs(p64.mass(b)[0] - m0) / abs(m0)}
-        del a, b, x64
+        del a, b, bin_, x64
         p64.close()
         torch.cuda.empty_cache()
         # the other grids' rates (512^3, the largest cube that fits) and the other workloads'

@@ -135,3 +135,56 @@ def test_adjoint_step_on_the_clustered_row_passes(shape, op, dt):
     assert rel(out.double().cpu().numpy(), ref_lam) <= 2e-5
     assert abs(float(dr) - ref_dr) <= 2e-4 * max(1.0, abs(ref_dr))
     p.close()
+
+
+def test_adjoint_config_256_cubed_psi0_gradient_matches_finite_differences():
+    """The same 256^3 FP64 workload: the initial-field gradient along a random direction v,
+    <dL/dpsi0, v>, against the fourth-order central difference of L(psi0 + h v)."""
+    shape, dt, nsteps, every = (256, 256, 256), 0.5, 200, 20
+    psi0 = inputs.uniform_state(shape, -0.25, 0.01, seed=6)
+    v = inputs.uniform_state(shape, 0.0, 1.0, seed=66)
+    p = _plan(shape, dt, ONE, "fp64")
+    p.set_r(-0.2)
+    tg = torch.from_numpy(psi0).cuda()
+    p.step(tg, nsteps)
+    p.set_r(-0.25)
+    loss, g, gr = _loss_and_grads(shape, dt, ONE, "fp64", nsteps, every, psi0, tg.cpu().numpy(), -0.25)
+    gv = float(np.dot(g.ravel(), v.ravel()))
+    x0 = torch.from_numpy(psi0).cuda()
+    vd = torch.from_numpy(v).cuda()
+
+    def L(h):
+        x = x0 + h * vd
+        p.step(x, nsteps)
+        return 0.5 * float(((x - tg) ** 2).sum())
+
+    h = 1e-5
+    fd = (8 * (L(h) - L(-h)) - (L(2 * h) - L(-2 * h))) / (12 * h)
+    print(f"256^3 FP64: <dL/dpsi0, v> adjoint {gv:.12e}, finite difference {fd:.12e}")
+    assert gv == pytest.approx(fd, rel=1e-6)
+    p.close()
+
+
+def test_adjoint_config_256_cubed_fp32_gradients_against_fp64():
+    """Config 5 in FP32-mixed: the rollout gradients (psi0 and r) against the FP64 ones on the
+    same workload. The step is linearly unstable (r + 3 mean^2 < 0), so rounding differences of
+    the FP32 forward run grow with the unstable modes over t = 100 before the adjoint carries
+    them back; the bound is the relative L2 the arithmetic gives (FP32 transforms ~1e-7 per step,
+    amplified along the unstable band), checked loosely and reported."""
+    shape, dt, nsteps, every = (256, 256, 256), 0.5, 200, 20
+    # one FP32-representable start and one target for both precisions
+    psi0 = inputs.uniform_state(shape, -0.25, 0.01, seed=6).astype(np.float32).astype(np.float64)
+    p = _plan(shape, dt, ONE, "fp64")
+    p.set_r(-0.2)
+    tg = torch.from_numpy(psi0).cuda()
+    p.step(tg, nsteps)
+    p.close()
+    target = tg.float().double().cpu().numpy()
+    res = {}
+    for prec in ("fp64", "fp32"):
+        res[prec] = _loss_and_grads(shape, dt, ONE, prec, nsteps, every, psi0, target, -0.25)
+    (l64, g64, r64), (l32, g32, r32) = res["fp64"], res["fp32"]
+    eg, er = rel(g32, g64), abs(r32 - r64) / abs(r64)
+    print(f"256^3 adjoint FP32 vs FP64: loss {l32:.6e} / {l64:.6e}, rel L2 dL/dpsi0 {eg:.3e}, rel dL/dr {er:.3e}")
+    assert np.isfinite(g32).all()
+    assert eg <= 1e-3 and er <= 1e-3

@@ -70,22 +70,31 @@ def test_batch_matches_single_plans_and_graph_path_matches_direct_steps():
 
 def test_full_ensemble_1024_domains_fp32():
     """1024 domains of {64..512}^2 (about 5.9e7 points), 200 steps, FP32-mixed on autotuned
-    tiles: a sample of domains against single-domain FP64 plans, and every domain's mass
-    conserved."""
-    from paper_2603_26818_gb300 import binding
+    tiles: every domain against the FP64 batch of the same ensemble (the FP64 batch is pinned to
+    the oracle and to single-domain plans above), and every domain's mass conserved."""
     draws = inputs.batch_draws(1024, seed=4)
     b = _batch(draws, "fp32")
     b.autotune(6, 8)          # the tiles the bench times this workload on
     x, parts = _state(b, draws, 1000, torch.float32)
+    y = x.double()            # the FP64 run starts from the same FP32-representable fields
+    yin, _ = _state(b, draws, 1000, torch.float64)   # and from the FP64 draws (input rounding included)
     b.step(x, 200)
     assert bool(torch.isfinite(x).all())
     ms = b.mass(x)
-    for d in range(0, 1024, 97):
-        ny, nx, r, m = draws[d]
-        p = binding.Plan((ny, nx), DX, 0.5, [binding.make_op(0, r)], precision="fp64")
-        z = torch.from_numpy(parts[d].reshape(ny, nx)).cuda()
-        p.step(z, 200)
-        assert rel(b.view(x, d).double().cpu().numpy(), z.cpu().numpy()) <= 1e-4
-        p.close()
+    b64 = _batch(draws, "fp64")
+    b64.step(y, 200)
+    b64.step(yin, 200)
+
+    def errs_to(ref):
+        return np.array([float((b.view(x, d).double() - b64.view(ref, d)).norm() / b64.view(ref, d).norm())
+                         for d in range(len(draws))])
+    errs, errs_in = errs_to(y), errs_to(yin)
+    worst = int(errs.argmax())
+    print(f"1024-domain ensemble, 200 steps, FP32 vs FP64 from the same start: max rel L2 {errs.max():.3e} "
+          f"(domain {worst}, {draws[worst]}), median {np.median(errs):.3e}; against the FP64 draws: max "
+          f"{errs_in.max():.3e}, above 1e-5: {int((errs_in > 1e-5).sum())}")
+    assert errs.max() <= 1e-5
     for d, p in enumerate(parts):
         assert abs(ms[d] - p.astype(np.float32).astype(np.float64).mean()) <= 1e-6 * abs(p.mean())
+    b.close()
+    b64.close()
