@@ -22,6 +22,18 @@ template <typename R> struct VT;
 template <> struct VT<float> { using V = float2; };
 template <> struct VT<double> { using V = double2; };
 
+// Two complex values of adjacent kx columns, moved and transformed together (one 16-byte access,
+// one twiddle for both): the element type of the two-column line pass.
+struct __align__(16) cf2 {
+    float2 a, b;
+};
+
+// scalar type and twiddle (table element) type of a transform element type
+template <typename V> struct ElemOf;
+template <> struct ElemOf<float2> { using R = float; using Tw = float2; };
+template <> struct ElemOf<double2> { using R = double; using Tw = double2; };
+template <> struct ElemOf<cf2> { using R = float; using Tw = float2; };
+
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return V{a.x + b.x, a.y + b.y}; }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { return V{a.x - b.x, a.y - b.y}; }
 template <typename V> __device__ __forceinline__ V cconj(V a) { return V{a.x, -a.y}; }
@@ -39,6 +51,23 @@ template <int S, typename V> __device__ __forceinline__ V cmul_i(V a) {
     if (S < 0) return V{a.y, -a.x};
     return V{-a.y, a.x};
 }
+// t W8 and t W8^3, W8 = exp(S 2 pi i / 8), h = 1/sqrt(2):
+//   t W8 = (x - S y, y + S x) h;  t W8^3 = (-x - S y, S x - y) h
+template <int S, typename V, typename R> __device__ __forceinline__ V w8_1(V t, R h) {
+    return V{(t.x - S * t.y) * h, (t.y + S * t.x) * h};
+}
+template <int S, typename V, typename R> __device__ __forceinline__ V w8_3(V t, R h) {
+    return V{(-t.x - S * t.y) * h, (S * t.x - t.y) * h};
+}
+
+// the same operations on two columns at once
+__device__ __forceinline__ cf2 cadd(cf2 p, cf2 q) { return cf2{cadd(p.a, q.a), cadd(p.b, q.b)}; }
+__device__ __forceinline__ cf2 csub(cf2 p, cf2 q) { return cf2{csub(p.a, q.a), csub(p.b, q.b)}; }
+__device__ __forceinline__ cf2 cscale(cf2 p, float s) { return cf2{cscale(p.a, s), cscale(p.b, s)}; }
+template <int S> __device__ __forceinline__ cf2 ctw(cf2 p, float2 w) { return cf2{ctw<S>(p.a, w), ctw<S>(p.b, w)}; }
+template <int S> __device__ __forceinline__ cf2 cmul_i(cf2 p) { return cf2{cmul_i<S>(p.a), cmul_i<S>(p.b)}; }
+template <int S> __device__ __forceinline__ cf2 w8_1(cf2 t, float h) { return cf2{w8_1<S>(t.a, h), w8_1<S>(t.b, h)}; }
+template <int S> __device__ __forceinline__ cf2 w8_3(cf2 t, float h) { return cf2{w8_3<S>(t.a, h), w8_3<S>(t.b, h)}; }
 
 // ------------------------------------------------------------------------------------------
 // Small DFTs in registers: X[k] = sum_n x[n] exp(S 2 pi i n k / R), in natural order.
@@ -61,15 +90,14 @@ template <int S, typename V> __device__ __forceinline__ void dft4(V &c0, V &c1, 
 // Decimation in frequency: even outputs from x[n] + x[n+4], odd outputs from
 // (x[n] - x[n+4]) W8^n, each a DFT4.
 template <int S, typename V> __device__ __forceinline__ void dft8(V (&v)[8]) {
-    using R = decltype(v[0].x);
+    using R = typename ElemOf<V>::R;
     const R h = (R)0.70710678118654752440084436210484903928;
     V a0 = cadd(v[0], v[4]), a4 = csub(v[0], v[4]);
     V a1 = cadd(v[1], v[5]), t5 = csub(v[1], v[5]);
     V a2 = cadd(v[2], v[6]), a6 = cmul_i<S>(csub(v[2], v[6]));
     V a3 = cadd(v[3], v[7]), t7 = csub(v[3], v[7]);
-    // t5 * W8^1 = (x - S y, y + S x) / sqrt2 ; t7 * W8^3 = (-x - S y, S x - y) / sqrt2
-    V a5 = V{(t5.x - S * t5.y) * h, (t5.y + S * t5.x) * h};
-    V a7 = V{(-t7.x - S * t7.y) * h, (S * t7.x - t7.y) * h};
+    V a5 = w8_1<S>(t5, h);
+    V a7 = w8_3<S>(t7, h);
     V b0 = cadd(a0, a2), b2 = csub(a0, a2);
     V b1 = cadd(a1, a3), b3 = cmul_i<S>(csub(a1, a3));
     V b4 = cadd(a4, a6), b6 = csub(a4, a6);
@@ -168,12 +196,12 @@ __host__ __device__ __forceinline__ int stage_tw_off(int R, int lNs) {
 
 template <int S, typename V>
 __device__ __forceinline__ void stage_exec(V (&v)[8], int lR, int lNs, int j, int n8,
-                                           const StageTw<V> &tw) {
+                                           const StageTw<typename ElemOf<V>::Tw> &tw) {
     const int Ns = 1 << lNs;
     if (lR == 3) {
         if (lNs > 0) {
             const int k = j & (Ns - 1);
-            const V *t = tw.t8 + stage_tw_off(8, lNs) + k;
+            const auto *t = tw.t8 + stage_tw_off(8, lNs) + k;
 #pragma unroll
             for (int r = 1; r < 8; ++r) v[r] = ctw<S>(v[r], __ldg(t + r * Ns));
         }
@@ -184,7 +212,7 @@ __device__ __forceinline__ void stage_exec(V (&v)[8], int lR, int lNs, int j, in
             V c0 = v[u], c1 = v[u + 2], c2 = v[u + 4], c3 = v[u + 6];
             if (lNs > 0) {
                 const int k = (j + u * n8) & (Ns - 1);
-                const V *t = tw.t4 + stage_tw_off(4, lNs) + k;
+                const auto *t = tw.t4 + stage_tw_off(4, lNs) + k;
                 c1 = ctw<S>(c1, __ldg(t + Ns));
                 c2 = ctw<S>(c2, __ldg(t + 2 * Ns));
                 c3 = ctw<S>(c3, __ldg(t + 3 * Ns));
@@ -298,7 +326,7 @@ __device__ __forceinline__ void stage_store_t(const V (&v)[8], V *sm, const Addr
 
 template <int S, int L, int LR, int LNS, typename V, typename Addr, typename Bar>
 __device__ __forceinline__ void stage_t(V (&v)[8], V *sm, const Addr &ad, int j, bool act,
-                                        bool load, bool store, const StageTw<V> &tw, const Bar &bar) {
+                                        bool load, bool store, const StageTw<typename ElemOf<V>::Tw> &tw, const Bar &bar) {
     constexpr int N8 = 1 << (L - 3);
     if (act && load) load8_t<N8>(v, sm, ad, j);
     if (act) stage_exec<S>(v, LR, LNS, j, N8, tw);
@@ -310,7 +338,7 @@ __device__ __forceinline__ void stage_t(V (&v)[8], V *sm, const Addr &ad, int j,
 
 template <int S, int L, typename V, typename Addr, typename Bar>
 __device__ __forceinline__ void fft_run_t(V (&v)[8], V *sm, const Addr &ad, int j, bool act,
-                                          bool in_regs, bool out_regs, const StageTw<V> &tw, const Bar &bar) {
+                                          bool in_regs, bool out_regs, const StageTw<typename ElemOf<V>::Tw> &tw, const Bar &bar) {
     constexpr int NFULL = L / 3;
     constexpr int LLAST = L - 3 * NFULL;    // 0: all stages radix 8
     constexpr int NST = NFULL + (LLAST ? 1 : 0);
@@ -326,7 +354,7 @@ __device__ __forceinline__ void fft_run_t(V (&v)[8], V *sm, const Addr &ad, int 
 // barrier (after the store) separates this stage's reads from the next stage's writes.
 template <int S, int L, int LR, int LNS, typename V, typename Addr, typename Bar>
 __device__ __forceinline__ void stage_pp_t(V (&v)[8], V *sm, const Addr &src, const Addr &dst, int j,
-                                           bool act, bool load, bool store, const StageTw<V> &tw,
+                                           bool act, bool load, bool store, const StageTw<typename ElemOf<V>::Tw> &tw,
                                            const Bar &bar) {
     constexpr int N8 = 1 << (L - 3);
     if (act && load) load8_t<N8>(v, sm, src, j);
@@ -344,7 +372,7 @@ __device__ __forceinline__ void stage_pp_t(V (&v)[8], V *sm, const Addr &src, co
 template <int S, int L, typename V, typename Addr, typename Bar>
 __device__ __forceinline__ void fft_run_pp_t(V (&v)[8], V *sm, const Addr &A, const Addr &B, int j,
                                              bool act, bool in_regs, bool out_regs,
-                                             const StageTw<V> &tw, const Bar &bar) {
+                                             const StageTw<typename ElemOf<V>::Tw> &tw, const Bar &bar) {
     constexpr int NFULL = L / 3;
     constexpr int LLAST = L - 3 * NFULL;
     constexpr int NST = NFULL + (LLAST ? 1 : 0);
@@ -369,7 +397,7 @@ __device__ __forceinline__ void fft_run_pp_t(V (&v)[8], V *sm, const Addr &A, co
 template <int S, typename V, typename Addr, typename Bar = BlockBarrier>
 __device__ __forceinline__ void fft_run_pp(V (&v)[8], V *sm, const Addr &A, const Addr &B, int L, int j,
                                            bool act, bool in_regs, bool out_regs,
-                                           const StageTw<V> &tw, const Bar &bar = Bar()) {
+                                           const StageTw<typename ElemOf<V>::Tw> &tw, const Bar &bar = Bar()) {
     switch (L) {
         case 3: fft_run_pp_t<S, 3>(v, sm, A, B, j, act, in_regs, out_regs, tw, bar); break;
         case 4: fft_run_pp_t<S, 4>(v, sm, A, B, j, act, in_regs, out_regs, tw, bar); break;
@@ -393,7 +421,7 @@ __device__ __forceinline__ void fft_run_pp(V (&v)[8], V *sm, const Addr &A, cons
 // be reading smem that this call overwrites.
 template <int S, typename V, typename Addr, typename Bar = BlockBarrier>
 __device__ __forceinline__ void fft_run(V (&v)[8], V *sm, const Addr &ad, int L, int j, bool act,
-                                        bool in_regs, bool out_regs, const StageTw<V> &tw,
+                                        bool in_regs, bool out_regs, const StageTw<typename ElemOf<V>::Tw> &tw,
                                         const Bar &bar = Bar()) {
     switch (L) {
         case 3: fft_run_t<S, 3>(v, sm, ad, j, act, in_regs, out_regs, tw, bar); break;

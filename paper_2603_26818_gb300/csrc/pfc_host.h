@@ -262,7 +262,8 @@ inline bool plan_tiles_as(Tiles &t, const TileChoice &c, int nx, int ny, int nz,
     t.smem_row_cs = 0;
     const char *rc = std::getenv("PFC_ROW_CLUSTER");
     const bool rc_on = c.cluster != 0 && !(rc && rc[0] == '0');
-    // (the cluster kernels are compiled for these row lengths only: M = 2048 in 2D, 256 in 3D)
+    // (the cluster kernels are compiled for these row lengths only: M = 2048 in 2D, 256, 512 and
+    // 1024 in 3D)
     if (rc_on && vb == 8 && g.Pz == 1 && g.Py == 8 && gpc == 1 && 2 * (size_t)rows * row_bytes > smem_max &&
         g.M == 2048) {
         // four rows and one scratch row per row in flight (two) for ping-pong transforms
@@ -270,7 +271,7 @@ inline bool plan_tiles_as(Tiles &t, const TileChoice &c, int nx, int ny, int nz,
         t.nt_row_cs = 2 * Tr;
         t.smem_row_cs = (size_t)round_up((int64_t)(4 + 2) * row_bytes + 8 * vb, 16);
     } else if (rc_on && vb == 8 && g.Pz == 8 && gpc == 1 && 2 * (size_t)rows * row_bytes > smem_max &&
-               g.M == 256) {
+               (g.M == 256 || g.M == 512 || g.M == 1024)) {
         // 3D: the group's 8 Py rows split by z_p halves over a cluster of two blocks
         t.row_cs = 2;
         t.nt_row_cs = std::min(512, 4 * g.Py * Tr);

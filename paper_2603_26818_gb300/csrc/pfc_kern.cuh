@@ -12,13 +12,21 @@ template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// 3D clustered psi^3 row pass, row length M = 2^8, 2^9 or 2^10 fixed at compile time
+template <typename R> void launch_row_cube_cl3(const LaunchCfg &c, const RowArgs<R> &a, int nf) {
+    const dim3 grid(2 * c.g.QR, nf);
+    if (c.g.lM == 8) k_row_cube_cl3<R, 8><<<grid, c.nt_row_cs, c.smem_row_cs, c.stream>>>(c.g, a);
+    else if (c.g.lM == 9) k_row_cube_cl3<R, 9><<<grid, c.nt_row_cs, c.smem_row_cs, c.stream>>>(c.g, a);
+    else k_row_cube_cl3<R, 10><<<grid, c.nt_row_cs, c.smem_row_cs, c.stream>>>(c.g, a);
+}
+
 template <typename R> void launch_row(const LaunchCfg &c, int mode, const RowArgs<R> &a, int nf) {
     if constexpr (sizeof(R) == 4) {
         if (mode == ROW_CUBE && c.row_cs == 2) {
             if (c.g.Pz == 1)
                 k_row_cube_cl<R, 2, 11><<<dim3(2 * c.g.QR, nf), c.nt_row_cs, c.smem_row_cs, c.stream>>>(c.g, a);
             else
-                k_row_cube_cl3<R, 8><<<dim3(2 * c.g.QR, nf), c.nt_row_cs, c.smem_row_cs, c.stream>>>(c.g, a);
+                launch_row_cube_cl3<R>(c, a, nf);
             return;
         }
     }
@@ -43,6 +51,12 @@ static void launch_line_t(const LaunchCfg &c, int mode, const LineArgs<R> &a, in
 }
 
 template <typename R> void launch_line(const LaunchCfg &c, int mode, const LineArgs<R> &a, int nf) {
+    if constexpr (sizeof(R) == 4) {
+        if (mode == LINE_STEP && line_v2_on(c)) {
+            launch_line_v2(c, a, nf);
+            return;
+        }
+    }
     if (mode == LINE_STEP && line_fixed_fits<R>(c)) {
         launch_line_step_fixed<R>(c, a, nf);
         return;
@@ -77,10 +91,15 @@ template <typename R> cudaError_t set_smem_attrs(const LaunchCfg &c) {
     if constexpr (sizeof(R) == 4) {
         if (c.row_cs == 2 && c.g.Pz == 1 &&
             (e = allow_smem(k_row_cube_cl<R, 2, 11>, c.smem_row_cs)) != cudaSuccess) return e;
-        if (c.row_cs == 2 && c.g.Pz > 1 &&
-            (e = allow_smem(k_row_cube_cl3<R, 8>, c.smem_row_cs)) != cudaSuccess) return e;
+        if (c.row_cs == 2 && c.g.Pz > 1) {
+            if ((e = allow_smem(k_row_cube_cl3<R, 8>, c.smem_row_cs)) != cudaSuccess) return e;
+            if ((e = allow_smem(k_row_cube_cl3<R, 9>, c.smem_row_cs)) != cudaSuccess) return e;
+            if ((e = allow_smem(k_row_cube_cl3<R, 10>, c.smem_row_cs)) != cudaSuccess) return e;
+        }
     }
     if ((e = set_smem_attrs_row_fixed<R>(c)) != cudaSuccess) return e;
+    if constexpr (sizeof(R) == 4)
+        if ((e = set_smem_attrs_v2(c)) != cudaSuccess) return e;
     return set_smem_attrs_fixed<R>(c);
 }
 

@@ -9,6 +9,7 @@
 #include "pfc_adjoint.cuh"
 #include "pfc_coupled.cuh"
 #include "pfc_mid.cuh"
+#include "pfc_line_v2.cuh"
 
 namespace pfc {
 
@@ -65,6 +66,10 @@ template <typename R> inline bool line_fixed_fits(const LaunchCfg &c) {
     return sizeof(R) == 4 && nt <= 1024 && ly == 6 && lz == 6;
 }
 template <typename R> void launch_line_step_fixed(const LaunchCfg &c, const LineArgs<R> &a, int nf);
+// The FP32 update pass with two kx columns per element (k_line_v2), for tiles of even width.
+bool line_v2_on(const LaunchCfg &c);
+void launch_line_v2(const LaunchCfg &c, const LineArgs<float> &a, int nf);
+cudaError_t set_smem_attrs_v2(const LaunchCfg &c);
 // The psi^3 row pass with its row length M = 2^lM fixed at compile time, lM in [ROW_FIXED_MIN,
 // ROW_FIXED_MAX] (compiled in pfc_row_fixed_f32.cu / pfc_row_fixed_f64.cu).
 constexpr int ROW_FIXED_MIN = 5, ROW_FIXED_MAX = 10;

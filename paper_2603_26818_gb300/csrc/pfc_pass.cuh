@@ -478,7 +478,7 @@ __device__ __forceinline__ void cube_shifted(V (&v)[8], R mean) {
 // instruction fetch otherwise), else the plan's length
 template <int S, int LM, typename V, typename Bar>
 __device__ __forceinline__ void row_fft(V (&v)[8], V *sm, const RowAddr &ad, int lM, int j, bool act,
-                                        bool in_regs, bool out_regs, const StageTw<V> &tw, const Bar &bar) {
+                                        bool in_regs, bool out_regs, const StageTw<typename ElemOf<V>::Tw> &tw, const Bar &bar) {
     if constexpr (LM > 0) fft_run_t<S, LM>(v, sm, ad, j, act, in_regs, out_regs, tw, bar);
     else fft_run<S>(v, sm, ad, lM, j, act, in_regs, out_regs, tw, bar);
 }
@@ -653,7 +653,7 @@ __device__ __forceinline__ int tile_slot(const LineMap &mp, bool two_axes, const
 template <typename V>
 __device__ __forceinline__ void line_forward(V (&v)[8], const Geom &g, const LineMap &mp, int kp, int cg,
                                              const V *src, V *tile, const PadTileAddr &ady,
-                                             const TileAddr &adz, bool to_regs, const StageTw<V> &st);
+                                             const TileAddr &adz, bool to_regs, const StageTw<typename ElemOf<V>::Tw> &st);
 
 // X' and C' are streamed once per pass: the passes read them with __ldcg and write them with
 // __stcg (cached in L2 only), so they do not evict the twiddle tables and register spills that
@@ -665,7 +665,7 @@ __device__ __forceinline__ size_t xprime_index(const Geom &g, int kp, int cg, in
 template <typename V>
 __device__ __forceinline__ void line_forward(V (&v)[8], const Geom &g, const LineMap &mp, int kp, int cg,
                                              const V *src, V *tile, const PadTileAddr &ady,
-                                             const TileAddr &adz, bool to_regs, const StageTw<V> &st) {
+                                             const TileAddr &adz, bool to_regs, const StageTw<typename ElemOf<V>::Tw> &st) {
     const bool two_axes = g.Qz > 1;
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = __ldcg(&src[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)]);
@@ -677,7 +677,7 @@ __device__ __forceinline__ void line_forward(V (&v)[8], const Geom &g, const Lin
 // straight-line code with no switch over lengths, fewer live registers), else the plan's length
 template <int S, int LY, typename V>
 __device__ __forceinline__ void line_yfft(V (&v)[8], V *sm, const PadTileAddr &ad, const Geom &g, int j,
-                                          bool in_regs, bool out_regs, const StageTw<V> &tw) {
+                                          bool in_regs, bool out_regs, const StageTw<typename ElemOf<V>::Tw> &tw) {
     if constexpr (LY > 0) fft_run_t<S, LY>(v, sm, ad, j, true, in_regs, out_regs, tw, BlockBarrier());
     else fft_run<S>(v, sm, ad, g.lQy, j, true, in_regs, out_regs, tw);
 }
@@ -685,7 +685,7 @@ __device__ __forceinline__ void line_yfft(V (&v)[8], V *sm, const PadTileAddr &a
 // z transform of a two-axis line tile: length 2^LZ fixed at compile time when LZ > 0
 template <int S, int LZ, typename V>
 __device__ __forceinline__ void line_zfft(V (&v)[8], V *sm, const TileAddr &ad, const Geom &g, int j,
-                                          bool in_regs, bool out_regs, const StageTw<V> &tw) {
+                                          bool in_regs, bool out_regs, const StageTw<typename ElemOf<V>::Tw> &tw) {
     if constexpr (LZ > 0) fft_run_t<S, LZ>(v, sm, ad, j, true, in_regs, out_regs, tw, BlockBarrier());
     else fft_run<S>(v, sm, ad, g.lQz, j, true, in_regs, out_regs, tw);
 }

@@ -182,7 +182,7 @@ namespace pfc {
 // and D (y-part and real-transform processing) and the row transforms touch only the block's
 // own rows. The real parts of the kx = 0 and nx/2 columns are gathered in block 0, which does
 // the Hermitian projection (project_edge_columns_par) for the group.
-// LM = log2 M fixed at compile time (the planner uses this kernel for nx = 512 only).
+// LM = log2 M fixed at compile time (the planner uses this kernel for nx = 512, 1024 and 2048).
 template <typename R, int LM>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 2)
     k_row_cube_cl3(const Geom g, const RowArgs<R> a) {

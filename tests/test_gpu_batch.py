@@ -70,31 +70,72 @@ def test_batch_matches_single_plans_and_graph_path_matches_direct_steps():
 
 def test_full_ensemble_1024_domains_fp32():
     """1024 domains of {64..512}^2 (about 5.9e7 points), 200 steps, FP32-mixed on autotuned
-    tiles: every domain against the FP64 batch of the same ensemble (the FP64 batch is pinned to
-    the oracle and to single-domain plans above), and every domain's mass conserved."""
+    tiles: every domain against the FP64 batch of the same ensemble from the same
+    FP32-representable start (the FP64 batch is pinned to the oracle and to single-domain plans
+    above), and every domain's mass conserved.
+
+    Bound: 1e-5 relative L2, except where the dynamics amplify rounding. Domains with
+    r + 3 mean^2 < 0 are linearly unstable (growth rate up to -(r + 3 mean^2) at k = 1) and
+    crystallise from the noise, so any perturbation of relative size eps32 grows with them. The
+    FP64 batch is therefore also run from the start perturbed by 6e-8 of its fluctuation (FP32
+    rounding size); a domain's FP32 error must stay within 1e-5 or within 10 times that FP64
+    sensitivity: the FP32 path is then as accurate as its precision allows there."""
     draws = inputs.batch_draws(1024, seed=4)
     b = _batch(draws, "fp32")
     b.autotune(6, 8)          # the tiles the bench times this workload on
     x, parts = _state(b, draws, 1000, torch.float32)
     y = x.double()            # the FP64 run starts from the same FP32-representable fields
-    yin, _ = _state(b, draws, 1000, torch.float64)   # and from the FP64 draws (input rounding included)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    u = torch.empty_like(y).uniform_(-1.0, 1.0, generator=g)
+    yp = y + 6e-8 * 0.01 * u  # a perturbation of FP32 rounding size of the 0.01 fluctuation
     b.step(x, 200)
     assert bool(torch.isfinite(x).all())
     ms = b.mass(x)
     b64 = _batch(draws, "fp64")
     b64.step(y, 200)
-    b64.step(yin, 200)
+    b64.step(yp, 200)
 
-    def errs_to(ref):
-        return np.array([float((b.view(x, d).double() - b64.view(ref, d)).norm() / b64.view(ref, d).norm())
+    def rel_to(a_state, a_batch, ref):
+        return np.array([float((a_batch.view(a_state, d).double() - b64.view(ref, d)).norm() / b64.view(ref, d).norm())
                          for d in range(len(draws))])
-    errs, errs_in = errs_to(y), errs_to(yin)
+    errs = rel_to(x, b, y)
+    sens = rel_to(yp, b64, y)
     worst = int(errs.argmax())
+    unstable = np.array([r + 3 * m * m < 0 for (_, _, r, m) in draws])
     print(f"1024-domain ensemble, 200 steps, FP32 vs FP64 from the same start: max rel L2 {errs.max():.3e} "
-          f"(domain {worst}, {draws[worst]}), median {np.median(errs):.3e}; against the FP64 draws: max "
-          f"{errs_in.max():.3e}, above 1e-5: {int((errs_in > 1e-5).sum())}")
-    assert errs.max() <= 1e-5
+          f"(domain {worst}, {draws[worst]}), median {np.median(errs):.3e}; above 1e-5: {int((errs > 1e-5).sum())} "
+          f"(all linearly unstable: {bool(unstable[errs > 1e-5].all())}); FP64 sensitivity to eps32 at the "
+          f"worst domain {sens[worst]:.3e}, max {sens.max():.3e}")
+    assert (errs[~unstable] <= 1e-5).all()
+    assert ((errs <= 1e-5) | (errs <= 10 * sens)).all()
     for d, p in enumerate(parts):
         assert abs(ms[d] - p.astype(np.float32).astype(np.float64).mean()) <= 1e-6 * abs(p.mean())
     b.close()
     b64.close()
+
+
+def test_error_versus_step_of_the_most_unstable_domain():
+    """The FP32-vs-FP64 error curve of the ensemble's most unstable domain, single-domain plans
+    from the same FP32-representable start (printed; reported in the design notes): it grows
+    with the unstable modes while the pattern forms, then levels off."""
+    from paper_2603_26818_gb300 import binding
+    draws = inputs.batch_draws(1024, seed=4)
+    d = int(np.argmin([r + 3 * m * m for (_, _, r, m) in draws]))
+    ny, nx, r, m = draws[d]
+    psi0 = inputs.uniform_state((ny, nx), m, 0.01, seed=1000 + d).astype(np.float32)
+    p32 = binding.Plan((ny, nx), DX, 0.5, [binding.make_op(0, r)], precision="fp32")
+    p64 = binding.Plan((ny, nx), DX, 0.5, [binding.make_op(0, r)], precision="fp64")
+    a = torch.from_numpy(psi0).cuda()
+    c = a.double()
+    curve, done = [], 0
+    for n in (1, 2, 5, 10, 20, 50, 100, 200):
+        p32.step(a, n - done)
+        p64.step(c, n - done)
+        done = n
+        curve.append((n, float((a.double() - c).norm() / c.norm())))
+    print(f"domain {d} {draws[d]}: r + 3 mean^2 = {r + 3 * m * m:.3f}; FP32 vs FP64 rel L2 by step: "
+          + ", ".join(f"{n}: {e:.2e}" for n, e in curve))
+    assert curve[0][1] <= 1e-6   # one step: the arithmetic alone
+    p32.close()
+    p64.close()

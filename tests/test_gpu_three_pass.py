@@ -271,3 +271,19 @@ def test_2048cube_fp32_three_pass_tiled_and_modes():
     # the fluctuation) plus O(amp^2 / mean^2)
     amp_err, rest = _modes_check((2048, 2048, 2048), "fp32", 3, amp=1e-3, slab=8)
     assert amp_err <= 1e-4 and rest <= 1e-2
+
+
+@pytest.mark.parametrize("shape,tile", [((64, 32, 1024), "4,8,4"), ((64, 16, 2048), "2,8,4"),
+                                        ((64, 64, 1024), "4,8,4,2,1")])
+def test_clustered_3d_row_pass_at_longer_rows(monkeypatch, shape, tile):
+    """The 3D psi^3 row pass on two-block clusters at row lengths M = 512 and 1024 (the large
+    three-pass grids use it), two-pass and three-pass tilings, FP32-mixed against the oracle."""
+    b = _binding()
+    monkeypatch.setenv("PFC_TILE", tile)
+    p = b.Plan(shape, DX, 0.1, [b.make_op(*TWO3)], precision="fp32")
+    assert p.info()["row_cluster"] == 2
+    psi0 = inputs.uniform_state(shape, -0.35, 0.05, seed=79)
+    x = to_dev(psi0, "fp32")
+    p.step(x, 20)
+    assert rel(x.double().cpu().numpy(), oracle.step(psi0, DX, 0.1, TWO3, 20)) <= 1e-5
+    p.close()
