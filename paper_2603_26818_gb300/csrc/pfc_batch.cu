@@ -6,6 +6,11 @@
 // from an offset table. The nsteps loop runs as a CUDA graph captured once per batch: every
 // size class gets its own branch (a forked stream), so classes proceed concurrently and each
 // class carries its own chain of row and line passes.
+//
+// Classes small enough for one block's shared memory (both extents <= 128, two half spectra in
+// the opt-in limit) are on-chip classes instead: one launch per call, one block per member, all
+// nsteps steps in shared memory (k_onchip, pfc_onchip.cuh), on the class's own stream beside the
+// graph. PFC_ONCHIP=0 keeps every class on the two-pass path (to compare the two).
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -29,6 +34,8 @@ struct BatchClass {
     int64_t *moff = nullptr;    // device: member offsets into the packed state
     cudaStream_t s = nullptr;
     size_t cap = 0;             // bytes allocated for each of X and C
+    bool onchip = false;        // stepped in shared memory by k_onchip (no X, C)
+    size_t smem_oc = 0;         // its shared memory per block
 };
 
 }  // namespace
@@ -44,6 +51,7 @@ struct pfc_batch {
     int *d_status = nullptr;
     void *tw = nullptr, *stw = nullptr;
     size_t smem_row = 0, smem_line = 0;
+    size_t smem_oc = 0;             // shared memory of the on-chip classes' launches (largest)
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t ev_fork = nullptr;
     std::vector<cudaEvent_t> ev_join;
@@ -112,6 +120,7 @@ template <typename R> pfc_status enqueue_steps(pfc_batch *b, cudaStream_t origin
     PFC_BCUDA(cudaEventRecord(b->ev_fork, origin));
     for (size_t i = 0; i < b->cls.size(); ++i) {
         BatchClass &c = b->cls[i];
+        if (c.onchip) continue;
         PFC_BCUDA(cudaStreamWaitEvent(c.s, b->ev_fork, 0));
         for (int64_t k = 0; k < nsteps; ++k) enqueue_class_step<R>(b, c, c.s);
         PFC_BCUDA(cudaEventRecord(b->ev_join[i], c.s));
@@ -125,6 +134,7 @@ template <typename R> pfc_status batch_step_impl(pfc_batch *b, void *state, int6
     launch_batch_mean<R>(b->stream, reinterpret_cast<const R *>(state), b->d_off, b->d_n, b->nd,
                          b->d_mean, b->d_status);
     for (BatchClass &c : b->cls) {
+        if (c.onchip) continue;
         RowArgs<R> ra = brow<R>(b, c);
         ra.in = state;
         ra.out = c.X;
@@ -132,6 +142,33 @@ template <typename R> pfc_status batch_step_impl(pfc_batch *b, void *state, int6
         launch_row<R>(bcfg(b, c, b->stream), ROW_FWD, ra, (int)c.members.size());
     }
     PFC_BCUDA(cudaGetLastError());
+    // on-chip classes: every step of the call in one launch per class, on the class's stream
+    bool any_onchip = false;
+    PFC_BCUDA(cudaEventRecord(b->ev_fork, b->stream));
+    for (size_t i = 0; i < b->cls.size(); ++i) {
+        BatchClass &c = b->cls[i];
+        if (!c.onchip) continue;
+        any_onchip = true;
+        PFC_BCUDA(cudaStreamWaitEvent(c.s, b->ev_fork, 0));
+        OnchipArgs<R> oa{};
+        oa.state = state;
+        oa.moff = c.moff;
+        oa.mean = b->d_mean + c.cbase;
+        oa.r = reinterpret_cast<const R *>(c.r);
+        oa.nsteps = nsteps;
+        const Geom &g = c.t.g;
+        const double two_pi = 6.28318530717958647692528676655900576839;
+        oa.up.dt = (R)b->dt;
+        oa.up.cx = (R)(two_pi / (g.nx * b->dx));
+        oa.up.cy = (R)(two_pi / (g.ny * b->dx));
+        oa.up.inv_halfN = (R)(2.0 / (double)g.nreal);
+        oa.up.op[0] = OpR<R>{PFC_ONE_MODE, (R)0, (R)0, (R)0};
+        oa.tw = reinterpret_cast<const typename VT<R>::V *>(b->tw);
+        oa.st = bstage<R>(b);
+        launch_onchip<R>(c.s, g, oa, (int)c.members.size(), c.smem_oc);
+        PFC_BCUDA(cudaGetLastError());
+        PFC_BCUDA(cudaEventRecord(b->ev_join[i], c.s));
+    }
     if (nsteps >= BATCH_GRAPH_CHUNK && !b->graph) {
         cudaStream_t cap;
         PFC_BCUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
@@ -159,11 +196,15 @@ template <typename R> pfc_status batch_step_impl(pfc_batch *b, void *state, int6
         if (st != PFC_OK) return st;
     }
     for (BatchClass &c : b->cls) {
+        if (c.onchip) continue;
         RowArgs<R> ra = brow<R>(b, c);
         ra.in = c.X;
         ra.out = state;
         launch_row<R>(bcfg(b, c, b->stream), ROW_INV, ra, (int)c.members.size());
     }
+    if (any_onchip)
+        for (size_t i = 0; i < b->cls.size(); ++i)
+            if (b->cls[i].onchip) PFC_BCUDA(cudaStreamWaitEvent(b->stream, b->ev_join[i], 0));
     PFC_BCUDA(cudaGetLastError());
     return PFC_OK;
 }
@@ -271,6 +312,8 @@ pfc_status pfc_batch_create(pfc_batch **out, int nd, const int64_t *dims_host, c
         return set_error(PFC_ERR_INVALID_ARG, "unknown precision");
     const double kmax = M_PI / dx;
     std::map<std::pair<int, int>, std::vector<int>> groups;
+    const char *oc_env = std::getenv("PFC_ONCHIP");
+    const bool onchip_on = !(oc_env && oc_env[0] == '0');
     for (int d = 0; d < nd; ++d) {
         const int64_t ny = dims_host[2 * d], nx = dims_host[2 * d + 1];
         if (!is_pow2(ny) || !is_pow2(nx) || ny < 16 || nx < 16 || ny > 512 || nx > 512)
@@ -308,8 +351,17 @@ pfc_status pfc_batch_create(pfc_batch **out, int nd, const int64_t *dims_host, c
         c.nx = kv.first.second;
         c.members = kv.second;
         c.cbase = slot;
-        if (!plan_tiles(c.t, c.nx, c.ny, 1, vb, 2, (size_t)optin, (int)c.members.size()))
+        c.onchip = onchip_on && c.ny <= ONCHIP_MAX && c.nx <= ONCHIP_MAX &&
+                   onchip_smem(c.ny, c.nx, vb) <= (size_t)optin;
+        if (c.onchip) {
+            c.t = Tiles{};
+            c.t.g = grid_geom(c.nx, c.ny, 1);
+            c.t.g.nreal = (int64_t)c.nx * c.ny;
+            c.smem_oc = onchip_smem(c.ny, c.nx, vb);
+            b->smem_oc = std::max(b->smem_oc, c.smem_oc);
+        } else if (!plan_tiles(c.t, c.nx, c.ny, 1, vb, 2, (size_t)optin, (int)c.members.size())) {
             return bail(PFC_ERR_UNSUPPORTED, "no pass tiling fits shared memory for a domain size");
+        }
         c.t.g.ltab = BATCH_LTAB;
         std::vector<int64_t> moff;
         std::vector<double> rr;
@@ -321,12 +373,12 @@ pfc_status pfc_batch_create(pfc_batch **out, int nd, const int64_t *dims_host, c
             rr.push_back(r_host[d]);
         }
         const size_t nm = c.members.size();
-        const size_t half = (size_t)c.t.g.nhalf * vb * nm;
+        const size_t half = c.onchip ? 0 : (size_t)c.t.g.nhalf * vb * nm;
         b->cls.push_back(c);
         BatchClass &cc = b->cls.back();
         cc.cap = half;
-        if ((e = cudaMalloc(&cc.X, half)) != cudaSuccess || (e = cudaMalloc(&cc.C, half)) != cudaSuccess ||
-            (e = cudaMemset(cc.X, 0, half)) != cudaSuccess || (e = cudaMemset(cc.C, 0, half)) != cudaSuccess ||
+        if ((!cc.onchip && ((e = cudaMalloc(&cc.X, half)) != cudaSuccess || (e = cudaMalloc(&cc.C, half)) != cudaSuccess ||
+                            (e = cudaMemset(cc.X, 0, half)) != cudaSuccess || (e = cudaMemset(cc.C, 0, half)) != cudaSuccess)) ||
             (e = cudaMalloc(&cc.moff, nm * sizeof(int64_t))) != cudaSuccess ||
             (e = cudaMemcpy(cc.moff, moff.data(), nm * sizeof(int64_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
             (e = cudaMalloc(&cc.r, nm * (vb / 2))) != cudaSuccess ||
@@ -342,6 +394,10 @@ pfc_status pfc_batch_create(pfc_batch **out, int nd, const int64_t *dims_host, c
         if (e != cudaSuccess) return bail(PFC_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e));
         b->smem_row = std::max(b->smem_row, cc.t.smem_row);
         b->smem_line = std::max(b->smem_line, cc.t.smem_line);
+    }
+    if (b->smem_oc) {
+        e = precision == PFC_FP64 ? set_smem_onchip<double>(b->smem_oc) : set_smem_onchip<float>(b->smem_oc);
+        if (e != cudaSuccess) return bail(PFC_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
     }
     if ((e = cudaMalloc(&b->d_off, nd * sizeof(int64_t))) != cudaSuccess ||
         (e = cudaMalloc(&b->d_n, nd * sizeof(int64_t))) != cudaSuccess ||
@@ -409,6 +465,7 @@ pfc_status pfc_batch_autotune(pfc_batch *b, int max_candidates, int trial_steps,
     double total = 0;
     b->smem_row = b->smem_line = 0;
     for (BatchClass &c : b->cls) {
+        if (c.onchip) continue;   // no tiling: stepped in shared memory
         double ms = 0;
         pfc_status st = b->prec == PFC_FP64 ? tune_class<double>(b, c, max_candidates, trial_steps, (size_t)optin, &ms)
                                             : tune_class<float>(b, c, max_candidates, trial_steps, (size_t)optin, &ms);
@@ -428,8 +485,10 @@ pfc_status pfc_batch_info(pfc_batch *b, int32_t *classes_out, int max_classes, i
     *nclasses = (int32_t)b->cls.size();
     for (int i = 0; i < (int)b->cls.size() && i < max_classes; ++i) {
         const BatchClass &c = b->cls[i];
-        const int32_t v[9] = {c.ny, c.nx, (int32_t)c.members.size(), c.t.g.Py, c.t.g.W, c.t.g.gpc,
-                              c.t.nt_row, c.t.nt_line, c.t.g.Qy};
+        const int32_t v[9] = {c.ny, c.nx, (int32_t)c.members.size(), c.onchip ? 0 : c.t.g.Py,
+                              c.onchip ? 0 : c.t.g.W, c.onchip ? 0 : c.t.g.gpc,
+                              c.onchip ? ONCHIP_THREADS : c.t.nt_row, c.onchip ? 0 : c.t.nt_line,
+                              c.onchip ? 0 : c.t.g.Qy};
         std::memcpy(classes_out + 9 * i, v, sizeof(v));
     }
     return PFC_OK;

@@ -120,6 +120,14 @@ template <typename R> void launch_mid(const LaunchCfg &c, int dir, const MidArgs
 }
 
 template <typename R>
+void launch_onchip(cudaStream_t s, const Geom &g, const OnchipArgs<R> &a, int members, size_t smem) {
+    k_onchip<R><<<members, ONCHIP_THREADS, smem, s>>>(g, a);
+}
+template <typename R> cudaError_t set_smem_onchip(size_t smem) {
+    return allow_smem(k_onchip<R>, smem);
+}
+
+template <typename R>
 void launch_batch_mean(cudaStream_t s, const R *base, const int64_t *off, const int64_t *n,
                        int members, double *mean, int *status) {
     k_batch_mean<R><<<members, RED_THREADS, 0, s>>>(base, off, n, mean, status);
@@ -147,6 +155,8 @@ void launch_reduce_spec(cudaStream_t s, const Geom &g, OpDev op, double dx, cons
     template void launch_line_adj<R>(const LaunchCfg &, const AdjArgs<R> &);               \
     template void launch_line_step2<R>(const LaunchCfg &, const Step2Args<R> &);           \
     template void launch_mid<R>(const LaunchCfg &, int, const MidArgs<R> &);               \
+    template void launch_onchip<R>(cudaStream_t, const Geom &, const OnchipArgs<R> &, int, size_t); \
+    template cudaError_t set_smem_onchip<R>(size_t);                                       \
     template void launch_batch_mean<R>(cudaStream_t, const R *, const int64_t *,           \
                                        const int64_t *, int, double *, int *);             \
     template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t,  \

@@ -10,6 +10,7 @@
 #include "pfc_coupled.cuh"
 #include "pfc_mid.cuh"
 #include "pfc_line_v2.cuh"
+#include "pfc_onchip.cuh"
 
 namespace pfc {
 
@@ -49,6 +50,10 @@ void launch_batch_mean(cudaStream_t s, const R *base, const int64_t *off, const 
 template <typename R> void launch_line_adj(const LaunchCfg &c, const AdjArgs<R> &a);
 // coupled two-field line pass (blocks of nt_line <= 512 threads, smem_line for three tiles)
 template <typename R> void launch_line_step2(const LaunchCfg &c, const Step2Args<R> &a);
+// on-chip steps of small batch domains (pfc_onchip.cuh): one block per member, smem bytes
+template <typename R>
+void launch_onchip(cudaStream_t s, const Geom &g, const OnchipArgs<R> &a, int members, size_t smem);
+template <typename R> cudaError_t set_smem_onchip(size_t smem);
 // middle pass of a three-pass plan (g.R > 1): dir -1 forward, +1 inverse (pfc_mid.cuh)
 template <typename R> void launch_mid(const LaunchCfg &c, int dir, const MidArgs<R> &a);
 
@@ -88,6 +93,8 @@ template <typename R> cudaError_t set_smem_attrs_fixed(const LaunchCfg &c);
     extern template void launch_line_adj<R>(const LaunchCfg &, const AdjArgs<R> &);             \
     extern template void launch_line_step2<R>(const LaunchCfg &, const Step2Args<R> &);         \
     extern template void launch_mid<R>(const LaunchCfg &, int, const MidArgs<R> &);             \
+    extern template void launch_onchip<R>(cudaStream_t, const Geom &, const OnchipArgs<R> &, int, size_t); \
+    extern template cudaError_t set_smem_onchip<R>(size_t);                                      \
     extern template void launch_batch_mean<R>(cudaStream_t, const R *, const int64_t *,         \
                                               const int64_t *, int, double *, int *);           \
     extern template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t, \

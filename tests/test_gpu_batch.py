@@ -139,3 +139,30 @@ def test_error_versus_step_of_the_most_unstable_domain():
     assert curve[0][1] <= 1e-6   # one step: the arithmetic alone
     p32.close()
     p64.close()
+
+
+def test_onchip_classes_match_the_two_pass_path(monkeypatch):
+    """Domains of at most 128 x 128 step in shared memory (one launch per call, every step on
+    chip); the same batch with PFC_ONCHIP=0 steps every class through the two-pass path: FP64
+    results agree to rounding, in both orders of calls (on-chip classes run beside the graph)."""
+    draws = [(64, 64, -0.3, -0.3), (128, 64, -0.25, -0.25), (64, 128, -0.2, -0.3), (16, 32, -0.35, -0.4),
+             (128, 128, -0.3, -0.28), (256, 64, -0.25, -0.25), (128, 256, -0.15, -0.3)]
+    b = _batch(draws, "fp64")
+    info = b.info()
+    onchip = {(c["ny"], c["nx"]) for c in info if c["Py"] == 0}
+    assert onchip == {(64, 64), (128, 64), (64, 128), (16, 32), (128, 128)}
+    x, parts = _state(b, draws, 300, torch.float64)
+    y = x.clone()
+    b.step(x, 21)
+    b.step(x, 7)
+    monkeypatch.setenv("PFC_ONCHIP", "0")
+    b2 = _batch(draws, "fp64")
+    assert all(c["Py"] > 0 for c in b2.info())
+    b2.step(y, 21)
+    b2.step(y, 7)
+    for d in range(len(draws)):
+        assert rel(b.view(x, d).cpu().numpy(), b2.view(y, d).cpu().numpy()) <= 1e-12
+    ref = oracle.step(parts[4].reshape(128, 128), DX, 0.5, (0, -0.3, 0.0, 0.0), 28)
+    assert rel(b.view(x, 4).cpu().numpy(), ref) <= 1e-11
+    b.close()
+    b2.close()
