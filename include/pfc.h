@@ -130,6 +130,26 @@ pfc_status pfc_energy(pfc_plan *plan, const void *state, double *out_host);
 pfc_status pfc_step_adjoint(pfc_plan *plan, const void *psi_n, const void *lam_next,
                             void *lam_out, double *dr_accum_dev);
 
+/* Recorded segments: the adjoint over several steps without leaving the plan's internal form.
+ * pfc_step_record advances state by nsteps >= 1 semi-implicit steps exactly like pfc_step and
+ * keeps, in the caller's device buffer record (pfc_record_bytes bytes, 256-byte aligned), the
+ * FP64 mean and each step's state and F(psi^3) in the plan's internal transformed layout.
+ * pfc_adjoint_segment then applies the adjoint of those nsteps steps, last to first (the same
+ * per-step adjoint as pfc_step_adjoint):
+ *     lam (device real array, in: dL/dpsi at the segment's end, out: dL/dpsi at its start),
+ *     *dr_accum_dev += sum over the steps of < lam_{n+1}, d psi_{n+1} / dr >.
+ * lam stays in the internal layout between the steps, and the state, its cube and the adjoint
+ * products are read from the record: 9 sweeps of a half spectrum per adjoint step instead of
+ * the 17 of a pfc_step_adjoint call. A record is valid for the plan's tiling and operator at the
+ * time it was written (pfc_plan_autotune and pfc_set_r invalidate it).
+ * Single-field two-pass plans with the semi-implicit integrator whose fused adjoint row pass
+ * fits shared memory (UNSUPPORTED otherwise, e.g. FP64 256^3: use pfc_step_adjoint).
+ * Stream ordered, not synchronised. Errors: INVALID_ARG, UNSUPPORTED, OUT_OF_MEMORY, CUDA. */
+pfc_status pfc_record_bytes(pfc_plan *plan, int64_t nsteps, int64_t *bytes_out);
+pfc_status pfc_step_record(pfc_plan *plan, void *state, int64_t nsteps, void *record);
+pfc_status pfc_adjoint_segment(pfc_plan *plan, const void *record, int64_t nsteps, void *lam,
+                               double *dr_accum_dev);
+
 /* Change r of field `field` (0-based); re-checks operator stability. */
 pfc_status pfc_set_r(pfc_plan *plan, int field, double r);
 

@@ -27,7 +27,7 @@ EXPORTS = ["pfc_plan_create", "pfc_plan_destroy", "pfc_step", "pfc_fft_r2c", "pf
            "pfc_mass", "pfc_energy", "pfc_step_adjoint", "pfc_set_r", "pfc_sync", "pfc_plan_info",
            "pfc_profile_steps", "pfc_step_noalloc", "pfc_plan_autotune", "pfc_batch_autotune",
            "pfc_batch_info",
-           "pfc_set_integrator",
+           "pfc_set_integrator", "pfc_record_bytes", "pfc_step_record", "pfc_adjoint_segment",
            "pfc_status_string", "pfc_last_error", "pfc_batch_create", "pfc_batch_destroy",
            "pfc_batch_step", "pfc_batch_mass"]
 
@@ -69,6 +69,9 @@ def load_library(path: str = LIB_PATH):
         "pfc_step_adjoint": [vp, vp, vp, vp, vp],
         "pfc_set_r": [vp, cint, dbl],
         "pfc_set_integrator": [vp, cint, dbl],
+        "pfc_record_bytes": [vp, i64, P(i64)],
+        "pfc_step_record": [vp, vp, i64, vp],
+        "pfc_adjoint_segment": [vp, vp, i64, vp, vp],
         "pfc_sync": [vp],
         "pfc_plan_info": [vp, P(ctypes.c_int32), P(i64)],
         "pfc_profile_steps": [vp, vp, i64, P(dbl), P(i64)],
@@ -205,6 +208,32 @@ class Plan:
         check(load_library().pfc_step_adjoint(self._h, ctypes.c_void_p(a), ctypes.c_void_p(b),
                                               ctypes.c_void_p(c), ctypes.c_void_p(d)))
         return lam_out
+
+    def record_bytes(self, nsteps: int):
+        """pfc_record_bytes: bytes of a recorded segment of nsteps steps, or None when the plan
+        has no fused adjoint (then use step_adjoint per step)."""
+        out = ctypes.c_int64()
+        st = load_library().pfc_record_bytes(self._h, int(nsteps), ctypes.byref(out))
+        if st == 2:
+            return None
+        check(st)
+        return out.value
+
+    def step_record(self, state: torch.Tensor, nsteps: int, record: torch.Tensor) -> torch.Tensor:
+        """pfc_step_record: nsteps steps of state, recording the segment into record (a uint8 CUDA
+        tensor of record_bytes(nsteps) bytes, 256-byte aligned)."""
+        p = self._check_real(state, "state")
+        check(load_library().pfc_step_record(self._h, ctypes.c_void_p(p), int(nsteps),
+                                             ctypes.c_void_p(_dev_ptr(record, torch.uint8, "record"))))
+        return state
+
+    def adjoint_segment(self, record: torch.Tensor, nsteps: int, lam: torch.Tensor, dr_accum: torch.Tensor):
+        """pfc_adjoint_segment: the adjoint of a recorded segment, lam in place."""
+        q = self._check_real(lam, "lam")
+        d = _dev_ptr(dr_accum, torch.float64, "dr_accum")
+        check(load_library().pfc_adjoint_segment(self._h, ctypes.c_void_p(_dev_ptr(record, torch.uint8, "record")),
+                                                 int(nsteps), ctypes.c_void_p(q), ctypes.c_void_p(d)))
+        return lam
 
     def set_r(self, r: float, field: int = 0):
         check(load_library().pfc_set_r(self._h, int(field), float(r)))

@@ -22,7 +22,8 @@ namespace pfc {
 
 template <typename R> struct AdjArgs {
     void *lam;            // in: Lam', out: U'
-    void *psi;            // in: Psi', out: V'
+    void *psi;            // in: Psi', out: V' (when vout is null)
+    void *vout;           // V' (null: over psi)
     const void *c;        // C'
     double *partials;     // one per block
     UpdR<R> up;
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(512) k_line_adj(const Geom g, const AdjArgs<R>
     }
     // 3. U' = inverse of the registers -> lam; V' = inverse of Cs -> psi
     V *U = reinterpret_cast<V *>(a.lam);
-    V *Vo = reinterpret_cast<V *>(a.psi);
+    V *Vo = reinterpret_cast<V *>(a.vout ? a.vout : a.psi);
     if (two_axes) {
         fft_run<+1>(v, T, adz, g.lQz, mp.jz, true, true, false, a.st);
         fft_run<+1>(v, T, ady, g.lQy, mp.jy, true, false, true, a.st);

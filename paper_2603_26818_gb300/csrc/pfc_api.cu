@@ -66,6 +66,8 @@ namespace {
 
 constexpr int GRAPH_CHUNK = 16;
 
+size_t smem_optin();   // the device's opt-in shared memory per block (0 when the query fails)
+
 size_t vbytes(const pfc_plan *p) { return p->prec == PFC_FP64 ? 16 : 8; }
 
 
@@ -463,6 +465,132 @@ pfc_status adjoint_impl(pfc_plan *p, const void *psi_n, const void *lam_next, vo
     i2.out = lam_out;
     i2.aux = psi_n;
     launch_row_m<R>(p, ROW_ADJ_MIX, i2, 1);
+    PFC_CUDA(cudaGetLastError());
+    return PFC_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Recorded segments and the fused adjoint (two-pass single-field semi-implicit plans)
+// ------------------------------------------------------------------------------------------
+// Record layout: a 256-byte header holding the FP64 mean, then the X' forms of the states of
+// steps 0 .. n (n + 1 half spectra; slot k + 1 is the line pass's output of step k), then the
+// C' forms F_p(psi_k^3) of steps 0 .. n - 1 (n half spectra).
+constexpr size_t REC_HEAD = 256;
+size_t record_bytes(const pfc_plan *p, int64_t n) {
+    return REC_HEAD + (size_t)(2 * n + 1) * (size_t)p->t.g.nhalf * vbytes(p);
+}
+
+// The fused adjoint row pass's geometry: the plan's, with fewer row groups per block when its
+// two row buffers need it; false when one group does not fit.
+bool adj2_geom(const pfc_plan *p, Geom &g, int &nt, size_t &smem) {
+    const size_t smax = smem_optin();
+    g = p->t.g;
+    while (g.gpc > 1 && row_adj2_smem(g, vbytes(p)) > smax) g.gpc /= 2;
+    smem = row_adj2_smem(g, vbytes(p));
+    const int Tr = g.M / 8, rows = g.gpc * g.P;
+    nt = std::min(512, std::max(Tr, rows * Tr));
+    if (nt < 32) nt = std::max(Tr, 32 / Tr * Tr);
+    return smem <= smax;
+}
+
+pfc_status segment_supported(const pfc_plan *p) {
+    if (p->nfields != 1) return fail(PFC_ERR_UNSUPPORTED, "recorded segments are built for single-field plans");
+    if (p->scheme != PFC_SEMI_IMPLICIT) return fail(PFC_ERR_UNSUPPORTED, "recorded segments follow the semi-implicit step");
+    if (three_pass(p)) return fail(PFC_ERR_UNSUPPORTED, "recorded segments are built for two-pass plans");
+    if (p->t.nt_line > 512) return fail(PFC_ERR_UNSUPPORTED, "the adjoint line pass needs tiles of at most 512 threads");
+    Geom g;
+    int nt;
+    size_t smem;
+    if (!adj2_geom(p, g, nt, smem)) return fail(PFC_ERR_UNSUPPORTED, "the fused adjoint row pass does not fit shared memory");
+    return PFC_OK;
+}
+
+template <typename R> pfc_status record_impl(pfc_plan *p, void *state, int64_t n, void *rec) {
+    using V = typename VT<R>::V;
+    const Geom &g = p->t.g;
+    V *slot = reinterpret_cast<V *>(static_cast<unsigned char *>(rec) + REC_HEAD);
+    V *cslot = slot + (size_t)(n + 1) * g.nhalf;
+    launch_means<R>(p, state);
+    RowArgs<R> ra = row_args<R>(p);
+    ra.in = state;
+    ra.out = slot;
+    ra.mean = p->d_mean;
+    ra.scale = (R)(1.0 / ((double)g.P * (double)g.M));
+    launch_row_m<R>(p, ROW_FWD, ra, 1);
+    for (int64_t k = 0; k < n; ++k) {
+        V *xk = slot + (size_t)k * g.nhalf;
+        RowArgs<R> rc = row_args<R>(p);
+        rc.in = xk;
+        rc.out = cslot + (size_t)k * g.nhalf;
+        rc.proj = xk;
+        rc.mean = p->d_mean;
+        launch_row_m<R>(p, ROW_CUBE, rc, 1);
+        LineArgs<R> la = line_args<R>(p);
+        la.x = xk;
+        la.c = rc.out;
+        la.xout = xk + g.nhalf;
+        launch_line_m<R>(p, LINE_STEP, la, 1);
+    }
+    RowArgs<R> rb = row_args<R>(p);
+    rb.in = slot + (size_t)n * g.nhalf;
+    rb.out = state;
+    rb.mean = p->d_mean;
+    launch_row_m<R>(p, ROW_INV, rb, 1);
+    PFC_CUDA(cudaMemcpyAsync(rec, p->d_mean, sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+    PFC_CUDA(cudaGetLastError());
+    return PFC_OK;
+}
+
+template <typename R> pfc_status segment_impl(pfc_plan *p, const void *rec, int64_t n, void *lam, double *dr) {
+    using V = typename VT<R>::V;
+    const Geom &g = p->t.g;
+    const size_t half_bytes = (size_t)g.nhalf * vbytes(p);
+    const int nblk = g.ncg * g.P * g.R;
+    if (!p->A) {
+        PFC_CUDA(cudaMalloc(&p->A, half_bytes));
+        PFC_CUDA(cudaMemset(p->A, 0, half_bytes));
+        PFC_CUDA(cudaMalloc(&p->d_adjpart, (size_t)nblk * sizeof(double)));
+        p->adj_bytes = half_bytes + (size_t)nblk * sizeof(double);
+        p->scratch += p->adj_bytes;
+    }
+    Geom g2;
+    int nt2;
+    size_t smem2;
+    adj2_geom(p, g2, nt2, smem2);
+    PFC_CUDA(set_smem_adj2<R>(smem2));
+    const V *slot = reinterpret_cast<const V *>(static_cast<const unsigned char *>(rec) + REC_HEAD);
+    const V *cslot = slot + (size_t)(n + 1) * g.nhalf;
+    const double *mean = static_cast<const double *>(rec);
+    RowArgs<R> f = row_args<R>(p);          // Lam' = X' form of lam (no mean)
+    f.in = lam;
+    f.out = p->X;
+    f.scale = (R)(1.0 / ((double)g.P * (double)g.M));
+    launch_row_m<R>(p, ROW_FWD, f, 1);
+    AdjArgs<R> aa{};
+    aa.lam = p->X;
+    aa.vout = p->A;
+    aa.partials = p->d_adjpart;
+    aa.up = line_args<R>(p).up;
+    aa.PM = (R)((double)g.P * (double)g.M);
+    aa.st = stage_tw<R>(p);
+    RowArgs<R> rr = row_args<R>(p);
+    rr.in = p->X;
+    rr.aux2 = p->A;
+    rr.out = p->X;
+    rr.mean = mean;
+    rr.scale = (R)(1.0 / ((double)g.P * (double)g.M));
+    for (int64_t k = n - 1; k >= 0; --k) {
+        aa.psi = const_cast<V *>(slot + (size_t)k * g.nhalf);
+        aa.c = cslot + (size_t)k * g.nhalf;
+        launch_line_adj<R>(cfg(p), aa);
+        launch_finish(p->stream, p->d_adjpart, nblk, 1.0 / (2.0 * g.Q), dr, true);
+        rr.aux3 = aa.psi;
+        launch_row_adj2<R>(p->stream, g2, nt2, smem2, rr);
+    }
+    RowArgs<R> i1 = row_args<R>(p);
+    i1.in = p->X;
+    i1.out = lam;
+    launch_row_m<R>(p, ROW_INV, i1, 1);
     PFC_CUDA(cudaGetLastError());
     return PFC_OK;
 }
@@ -872,6 +1000,37 @@ pfc_status pfc_set_integrator(pfc_plan *p, int scheme, double S) {
     p->stab = scheme == PFC_STABILIZED ? S : 0.0;
     if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
     return PFC_OK;
+}
+
+pfc_status pfc_record_bytes(pfc_plan *p, int64_t nsteps, int64_t *bytes_out) {
+    if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
+    if (nsteps < 1 || !bytes_out) return fail(PFC_ERR_INVALID_ARG, "nsteps must be >= 1 and bytes_out non-null");
+    pfc_status s = segment_supported(p);
+    if (s != PFC_OK) return s;
+    *bytes_out = (int64_t)record_bytes(p, nsteps);
+    return PFC_OK;
+}
+
+pfc_status pfc_step_record(pfc_plan *p, void *state, int64_t nsteps, void *record) {
+    if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
+    if (!state || !record || nsteps < 1) return fail(PFC_ERR_INVALID_ARG, "null array or nsteps < 1");
+    if ((reinterpret_cast<uintptr_t>(state) & 15) != 0 || (reinterpret_cast<uintptr_t>(record) & 255) != 0)
+        return fail(PFC_ERR_INVALID_ARG, "state must be 16-byte and record 256-byte aligned");
+    pfc_status s = segment_supported(p);
+    if (s != PFC_OK) return s;
+    return p->prec == PFC_FP64 ? record_impl<double>(p, state, nsteps, record)
+                               : record_impl<float>(p, state, nsteps, record);
+}
+
+pfc_status pfc_adjoint_segment(pfc_plan *p, const void *record, int64_t nsteps, void *lam, double *dr) {
+    if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
+    if (!record || !lam || !dr || nsteps < 1) return fail(PFC_ERR_INVALID_ARG, "null pointer or nsteps < 1");
+    if ((reinterpret_cast<uintptr_t>(lam) & 15) != 0 || (reinterpret_cast<uintptr_t>(record) & 255) != 0)
+        return fail(PFC_ERR_INVALID_ARG, "lam must be 16-byte and record 256-byte aligned");
+    pfc_status s = segment_supported(p);
+    if (s != PFC_OK) return s;
+    return p->prec == PFC_FP64 ? segment_impl<double>(p, record, nsteps, lam, dr)
+                               : segment_impl<float>(p, record, nsteps, lam, dr);
 }
 
 pfc_status pfc_sync(pfc_plan *p) {

@@ -126,6 +126,13 @@ void launch_onchip(cudaStream_t s, const Geom &g, const OnchipArgs<R> &a, int me
 template <typename R> cudaError_t set_smem_onchip(size_t smem) {
     return allow_smem(k_onchip<R>, smem);
 }
+template <typename R>
+void launch_row_adj2(cudaStream_t s, const Geom &g, int nt, size_t smem, const RowArgs<R> &a) {
+    k_row_adj2<R><<<g.QR / g.gpc, nt, smem, s>>>(g, a);
+}
+template <typename R> cudaError_t set_smem_adj2(size_t smem) {
+    return allow_smem(k_row_adj2<R>, smem);
+}
 
 template <typename R>
 void launch_batch_mean(cudaStream_t s, const R *base, const int64_t *off, const int64_t *n,
@@ -157,6 +164,8 @@ void launch_reduce_spec(cudaStream_t s, const Geom &g, OpDev op, double dx, cons
     template void launch_mid<R>(const LaunchCfg &, int, const MidArgs<R> &);               \
     template void launch_onchip<R>(cudaStream_t, const Geom &, const OnchipArgs<R> &, int, size_t); \
     template cudaError_t set_smem_onchip<R>(size_t);                                       \
+    template void launch_row_adj2<R>(cudaStream_t, const Geom &, int, size_t, const RowArgs<R> &); \
+    template cudaError_t set_smem_adj2<R>(size_t);                                         \
     template void launch_batch_mean<R>(cudaStream_t, const R *, const int64_t *,           \
                                        const int64_t *, int, double *, int *);             \
     template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t,  \

@@ -11,6 +11,7 @@
 #include "pfc_mid.cuh"
 #include "pfc_line_v2.cuh"
 #include "pfc_onchip.cuh"
+#include "pfc_adjoint_row.cuh"
 
 namespace pfc {
 
@@ -54,6 +55,10 @@ template <typename R> void launch_line_step2(const LaunchCfg &c, const Step2Args
 template <typename R>
 void launch_onchip(cudaStream_t s, const Geom &g, const OnchipArgs<R> &a, int members, size_t smem);
 template <typename R> cudaError_t set_smem_onchip(size_t smem);
+// fused adjoint row pass (pfc_adjoint_row.cuh) on geometry g (its gpc), nt threads, smem bytes
+template <typename R>
+void launch_row_adj2(cudaStream_t s, const Geom &g, int nt, size_t smem, const RowArgs<R> &a);
+template <typename R> cudaError_t set_smem_adj2(size_t smem);
 // middle pass of a three-pass plan (g.R > 1): dir -1 forward, +1 inverse (pfc_mid.cuh)
 template <typename R> void launch_mid(const LaunchCfg &c, int dir, const MidArgs<R> &a);
 
@@ -95,6 +100,8 @@ template <typename R> cudaError_t set_smem_attrs_fixed(const LaunchCfg &c);
     extern template void launch_mid<R>(const LaunchCfg &, int, const MidArgs<R> &);             \
     extern template void launch_onchip<R>(cudaStream_t, const Geom &, const OnchipArgs<R> &, int, size_t); \
     extern template cudaError_t set_smem_onchip<R>(size_t);                                      \
+    extern template void launch_row_adj2<R>(cudaStream_t, const Geom &, int, size_t, const RowArgs<R> &); \
+    extern template cudaError_t set_smem_adj2<R>(size_t);                                        \
     extern template void launch_batch_mean<R>(cudaStream_t, const R *, const int64_t *,         \
                                               const int64_t *, int, double *, int *);           \
     extern template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t, \

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_line_v2(const Geom g, const Geom gv
     } else {
         line_yfft<+1, LY>(vt, T, ady, gv, mp.jy, true, true, a.st);
     }
-    V *Xo = reinterpret_cast<V *>(a.x) + foff;
+    V *Xo = reinterpret_cast<V *>(a.xout ? a.xout : a.x) + foff;
 #pragma unroll
     for (int m = 0; m < 8; ++m) stcg2(&Xo[xprime_index(gv, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)], vt[m]);
 }

@@ -70,6 +70,8 @@ template <typename R> struct RowArgs {
     void *out;            // ROW_INV: real; else X' layout
     void *proj;           // ROW_CUBE: X' to receive the projected kx = 0 and nx/2 columns
     const void *aux;      // ROW_ADJ_MIX: real psi_n
+    const void *aux2;     // k_row_adj2: V' and Psi' (X' layout)
+    const void *aux3;
     const int64_t *moff;  // batched members: element offset of member m in the real arrays
     const double *mean;   // per field, may be null
     R scale;
@@ -99,7 +101,7 @@ template <typename R> struct LineArgs {
     const void *c;        // C'
     const void *xprev;    // LINE_SCHEME: the previous level's X' and C' (null: not used)
     const void *cprev;
-    void *xout;           // LINE_SCHEME: output X' (may equal x or xprev)
+    void *xout;           // LINE_STEP, LINE_SCHEME: output X' (null: x, in place; may equal xprev)
     const void *std_in;   // LINE_INV input (standard half spectrum)
     void *std_out;        // LINE_FWD output (standard half spectrum)
     R scale;              // LINE_INV / LINE_FWD output scale
@@ -817,7 +819,7 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
     } else {
         line_yfft<+1, LY>(vt, T, ady, g, mp.jy, true, true, a.st);
     }
-    V *Xo = reinterpret_cast<V *>(MODE == LINE_SCHEME ? a.xout : a.x) + (size_t)field * g.nhalf;
+    V *Xo = reinterpret_cast<V *>(MODE != LINE_INV && a.xout ? a.xout : a.x) + (size_t)field * g.nhalf;
     const R sc = MODE == LINE_INV ? a.scale : (R)1;
 #pragma unroll
     for (int m = 0; m < 8; ++m)

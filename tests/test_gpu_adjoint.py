@@ -188,3 +188,53 @@ def test_adjoint_config_256_cubed_fp32_gradients_against_fp64():
     print(f"256^3 adjoint FP32 vs FP64: loss {l32:.6e} / {l64:.6e}, rel L2 dL/dpsi0 {eg:.3e}, rel dL/dr {er:.3e}")
     assert np.isfinite(g32).all()
     assert eg <= 1e-3 and er <= 1e-3
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("shape,op,dt", [((64, 64), ONE, 0.5), ((16, 32, 32), TWO, 0.1), ((256, 128), ONE, 0.5),
+                                         ((32, 32, 64), ONE, 0.5)])
+def test_recorded_segment_adjoint_matches_step_by_step_adjoint(shape, op, dt, prec, tol):
+    """pfc_step_record + pfc_adjoint_segment (lam kept in the internal layout, the fused adjoint
+    row pass) against pfc_step applied step by step and pfc_step_adjoint applied in reverse."""
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    n = 7
+    p = _plan(shape, dt, op, prec)
+    nbytes = p.record_bytes(n)
+    assert nbytes is not None
+    psi0 = torch.from_numpy(inputs.uniform_state(shape, -0.25, 0.1, seed=57)).to(device="cuda", dtype=dtype)
+    lam0 = torch.from_numpy(inputs.uniform_state(shape, 0.0, 1.0, seed=58)).to(device="cuda", dtype=dtype)
+    # reference: the states step by step, the one-step adjoint in reverse
+    traj = [psi0.clone()]
+    for _ in range(n):
+        z = traj[-1].clone()
+        p.step(z, 1)
+        traj.append(z)
+    lam_ref = lam0.clone()
+    dr_ref = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for k in reversed(range(n)):
+        p.step_adjoint(traj[k], lam_ref, lam_ref, dr_ref)
+    # recorded segment
+    rec = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    x = psi0.clone()
+    p.step_record(x, n, rec)
+    lam = lam0.clone()
+    dr = torch.zeros(1, dtype=torch.float64, device="cuda")
+    p.adjoint_segment(rec, n, lam, dr)
+    torch.cuda.synchronize()
+    assert rel(x.double().cpu().numpy(), traj[-1].double().cpu().numpy()) <= (1e-14 if prec == "fp64" else 1e-6)
+    assert rel(lam.double().cpu().numpy(), lam_ref.double().cpu().numpy()) <= tol
+    assert float(dr) == pytest.approx(float(dr_ref), rel=tol * 10, abs=1e-12)
+    p.close()
+
+
+def test_segment_adjoint_is_unsupported_where_the_fused_row_pass_does_not_fit():
+    """Two-field plans and FP32 rows of 4096 (two row buffers of a group exceed shared memory)
+    report UNSUPPORTED, and the autograd rollout then falls back to the one-step adjoint."""
+    from paper_2603_26818_gb300 import binding
+    p = binding.Plan((32, 32), math.pi / 4, 0.5, [binding.make_op(*ONE), binding.make_op(*ONE)], precision="fp64",
+                     coupling=0.1)
+    assert p.record_bytes(4) is None
+    p.close()
+    q = _plan((256, 4096), 0.5, ONE, "fp32")
+    assert q.record_bytes(4) is None
+    q.close()
