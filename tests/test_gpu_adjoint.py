@@ -235,6 +235,6 @@ def test_segment_adjoint_is_unsupported_where_the_fused_row_pass_does_not_fit():
                      coupling=0.1)
     assert p.record_bytes(4) is None
     p.close()
-    q = _plan((256, 4096), 0.5, ONE, "fp32")
+    q = _plan((4096, 4096), 0.5, ONE, "fp32")
     assert q.record_bytes(4) is None
     q.close()
