@@ -89,6 +89,11 @@ CONFIGS = {
     "5d": dict(desc="adjoint step, 3D one-mode 256^3 FP64, as config 5; 5 adjoint steps per bench step",
                kind="adjoint", dims=(256, 256, 256), prec="fp64", op=(0, -0.25, 0.0, 0.0), dt=0.5,
                inner=5, sweeps=17),
+    "5s": dict(desc="adjoint over recorded segments, 3D one-mode 256^3 FP32-mixed, as config 5: per bench step "
+                    "the forward recompute of a 20-step segment with its record (pfc_step_record) and the "
+                    "fused adjoint over it (pfc_adjoint_segment); rate in rollout steps (forward + adjoint) x points",
+               kind="segment", dims=(256, 256, 256), prec="fp32", op=(0, -0.25, 0.0, 0.0), dt=0.5,
+               inner=20, sweeps=14),
     "3d64": dict(desc="3D two-mode 512^3 FP64 (three-pass schedule), as config 3; 4 time steps per bench step",
                  kind="plan", dims=(512, 512, 512), prec="fp64", op=(1, -0.3, 0.05, math.sqrt(4.0 / 3.0)),
                  dt=0.1, inner=4, sweeps=9),
@@ -174,6 +179,18 @@ def run_config(args):
         extra["plan"] = obj.info()
         if c["kind"] == "plan":
             run = lambda: obj.step(state, c["inner"])
+        elif c["kind"] == "segment":
+            nb = obj.record_bytes(c["inner"])
+            rec = torch.empty(nb, dtype=torch.uint8, device=dev)
+            lam = torch.ones_like(state) * 1e-3
+            dr = torch.zeros(1, dtype=torch.float64, device=dev)
+            x = state.clone()
+            extra["record_bytes"] = nb
+
+            def run():
+                x.copy_(state)
+                obj.step_record(x, c["inner"], rec)
+                obj.adjoint_segment(rec, c["inner"], lam, dr)
         else:
             lam = state.clone()
             lam_out = torch.empty_like(state)

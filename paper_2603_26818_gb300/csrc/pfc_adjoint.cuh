@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(512) k_line_adj(const Geom g, const AdjArgs<R>
         mult(m, ca, cb);
         const int pos = tile_slot(mp, two_axes, ady, adz, m);
         const V gv = Cs[pos];
-        acc += (double)(wk * (v[m].x * gv.x + v[m].y * gv.y));
+        // padding columns (kx > nx/2) take no part: their contents are whatever the arrays held
+        if (kx <= g.M) acc += (double)(wk * (v[m].x * gv.x + v[m].y * gv.y));
         Cs[pos] = V{cb * invQ * v[m].x, cb * invQ * v[m].y};
         v[m] = V{ca * invQ * v[m].x, ca * invQ * v[m].y};
     }
