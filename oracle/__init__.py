@@ -10,6 +10,10 @@ every number is computed in C). Arrays are numpy float64 / complex128, row-major
 Parity status of each function (what pins it is in ``tests/test_oracle_pins.py``):
   dft, fft_radix2, fft_mixed, rfftn, irfftn   pinned (numpy.fft, naive DFT, closed forms)
   step, mass, energy                          pinned (closed forms, invariants, symmetries)
+  hydro_step                                  pinned (reduction to step at rho = inf and v = 0,
+                                              viscous decay of a velocity mode, advected
+                                              density mode closed form, one-step mass with a
+                                              divergence-free velocity)
   step_scheme                                 pinned (scheme 0 = step, S = 0 reduction, scalar
                                               recurrences of one small mode, convergence order)
   step2, energy2                              pinned (alpha=0 reduction, Cramer, mass)
@@ -61,6 +65,7 @@ def _load():
     lib.orc_lin_op.restype = dbl
     lib.orc_step.argtypes = [i64, i64, i64, dbl, dbl, cint, dbl, dbl, dbl, p, i64]
     lib.orc_step_scheme.argtypes = [i64, i64, i64, dbl, dbl, cint, dbl, dbl, dbl, cint, dbl, p, i64]
+    lib.orc_hydro_step.argtypes = [i64, i64, i64, dbl, dbl, cint, dbl, dbl, dbl, dbl, dbl, dbl, p, p, i64]
     lib.orc_mass.argtypes = [i64, p]
     lib.orc_mass.restype = dbl
     lib.orc_energy.argtypes = [i64, i64, i64, dbl, cint, dbl, dbl, dbl, p]
@@ -176,6 +181,18 @@ def step_scheme(psi, dx: float, dt: float, op, scheme: int, S: float = 0.0, nste
     _load().orc_step_scheme(nz, ny, nx, float(dx), float(dt), *_op_args(op), int(scheme), float(S),
                             _ptr(y), int(nsteps))
     return y
+
+
+def hydro_step(psi, v, dx: float, dt: float, op, rho: float, gamma: float, a0: float, nsteps: int = 1):
+    """(psi, v) after nsteps steps of the hydrodynamic PFC model; v has shape (ndim,) + psi.shape
+    (x component first). Inputs are not modified."""
+    y = _f64(psi).copy()
+    w = _f64(v).copy()
+    nz, ny, nx = _dims3(y.shape)
+    assert w.shape == ((3 if nz > 1 else 2),) + y.shape
+    _load().orc_hydro_step(nz, ny, nx, float(dx), float(dt), *_op_args(op), float(rho), float(gamma), float(a0),
+                           _ptr(y), _ptr(w), int(nsteps))
+    return y, w
 
 
 def mass(psi) -> float:

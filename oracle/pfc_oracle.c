@@ -331,6 +331,102 @@ void orc_step_scheme(int64_t nz, int64_t ny, int64_t nx, double dx, double dt, i
     free(ph); free(nh); free(ph_old); free(nh_old); free(cube);
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* Hydrodynamic PFC (the paper's multiphysics example, Eq. (hpfc))                          */
+/* ------------------------------------------------------------------------------------ */
+
+/* i k_j of half-spectrum index (iz, iy, ikx) along axis j (0 x, 1 y, 2 z), zero at the Nyquist
+ * index of that axis (spectral first derivative of a real field). */
+static cplx deriv_mult(int j, int64_t iz, int64_t iy, int64_t ikx, int64_t nz, int64_t ny, int64_t nx, double dx)
+{
+    int64_t m = j == 0 ? ikx : (j == 1 ? iy : iz), n = j == 0 ? nx : (j == 1 ? ny : nz);
+    if (n > 1 && 2 * m == n) return 0;
+    return I * wavenumber(m, n, dx);
+}
+
+/* One or more steps of the hydrodynamic PFC model
+ *     d_t psi = lap(mu) - v . grad psi,      rho d_t v = Gamma lap v - < psi grad mu >,
+ *     mu = Lk psi + psi^3 (the variational derivative of the PFC energy, Eq. (5)),
+ * < . > the convolution with the normalised Gaussian of width a0, a multiplication by
+ * exp(-a0^2 k^2 / 2) in Fourier space. The update follows the paper's multi-field listing:
+ *     psi_hat' = (psi_hat - dt k^2 FFT(psi^3) - dt FFT(v . grad psi)) / (1 + dt k^2 Lk)
+ *     psi' = IFFT(psi_hat'),   mu_hat' = FFT(psi'^3) + Lk psi_hat'
+ *     v_hat_j' = (v_hat_j - (dt/rho) G FFT(psi' d_j mu')) / (1 + (dt/rho) Gamma k^2)
+ * (the density first, with the old velocity; the velocity with the new density). grad and d_j
+ * are spectral derivatives (deriv_mult). psi: real (nz, ny, nx); v: ndim real fields back to back
+ * (ndim = 2 when nz = 1, else 3), x component first. rho may be +inf (the velocity then stays
+ * put). */
+void orc_hydro_step(int64_t nz, int64_t ny, int64_t nx, double dx, double dt, int kind, double r,
+                    double R1, double q2, double rho, double gamma, double a0, double *psi, double *v,
+                    int64_t nsteps)
+{
+    int64_t n = nz * ny * nx, nxh = nx / 2 + 1, h = nz * ny * nxh;
+    int nd = nz > 1 ? 3 : 2;
+    cplx *ph = malloc(sizeof(cplx) * h), *nh = malloc(sizeof(cplx) * h), *wk = malloc(sizeof(cplx) * h);
+    cplx *mu = malloc(sizeof(cplx) * h), *fh = malloc(sizeof(cplx) * h);
+    double *t1 = malloc(sizeof(double) * n), *t2 = malloc(sizeof(double) * n);
+    double vf = dt / rho;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        orc_rfftn(nz, ny, nx, psi, ph);
+        for (int64_t i = 0; i < n; ++i) t1[i] = psi[i] * psi[i] * psi[i];
+        orc_rfftn(nz, ny, nx, t1, nh);
+        /* advection v . grad psi */
+        for (int64_t i = 0; i < n; ++i) t2[i] = 0;
+        for (int j = 0; j < nd; ++j) {
+            for (int64_t iz = 0; iz < nz; ++iz)
+                for (int64_t iy = 0; iy < ny; ++iy)
+                    for (int64_t ik = 0; ik < nxh; ++ik) {
+                        int64_t idx = (iz * ny + iy) * nxh + ik;
+                        wk[idx] = deriv_mult(j, iz, iy, ik, nz, ny, nx, dx) * ph[idx];
+                    }
+            orc_irfftn(nz, ny, nx, wk, t1);
+            for (int64_t i = 0; i < n; ++i) t2[i] += v[j * n + i] * t1[i];
+        }
+        orc_rfftn(nz, ny, nx, t2, fh);
+        for (int64_t iz = 0; iz < nz; ++iz)
+            for (int64_t iy = 0; iy < ny; ++iy)
+                for (int64_t ik = 0; ik < nxh; ++ik) {
+                    int64_t idx = (iz * ny + iy) * nxh + ik;
+                    double k2 = ksq(iz, iy, ik, nz, ny, nx, dx);
+                    double lk = orc_lin_op(kind, r, R1, q2, k2);
+                    ph[idx] = (ph[idx] - dt * k2 * nh[idx] - dt * fh[idx]) / (1.0 + dt * k2 * lk);
+                }
+        orc_irfftn(nz, ny, nx, ph, psi);
+        /* chemical potential of the new density */
+        for (int64_t i = 0; i < n; ++i) t1[i] = psi[i] * psi[i] * psi[i];
+        orc_rfftn(nz, ny, nx, t1, nh);
+        for (int64_t iz = 0; iz < nz; ++iz)
+            for (int64_t iy = 0; iy < ny; ++iy)
+                for (int64_t ik = 0; ik < nxh; ++ik) {
+                    int64_t idx = (iz * ny + iy) * nxh + ik;
+                    double k2 = ksq(iz, iy, ik, nz, ny, nx, dx);
+                    mu[idx] = nh[idx] + orc_lin_op(kind, r, R1, q2, k2) * ph[idx];
+                }
+        for (int j = 0; j < nd; ++j) {
+            for (int64_t iz = 0; iz < nz; ++iz)
+                for (int64_t iy = 0; iy < ny; ++iy)
+                    for (int64_t ik = 0; ik < nxh; ++ik) {
+                        int64_t idx = (iz * ny + iy) * nxh + ik;
+                        wk[idx] = deriv_mult(j, iz, iy, ik, nz, ny, nx, dx) * mu[idx];
+                    }
+            orc_irfftn(nz, ny, nx, wk, t1);
+            for (int64_t i = 0; i < n; ++i) t1[i] *= psi[i];
+            orc_rfftn(nz, ny, nx, t1, fh);
+            orc_rfftn(nz, ny, nx, v + j * n, wk);
+            for (int64_t iz = 0; iz < nz; ++iz)
+                for (int64_t iy = 0; iy < ny; ++iy)
+                    for (int64_t ik = 0; ik < nxh; ++ik) {
+                        int64_t idx = (iz * ny + iy) * nxh + ik;
+                        double k2 = ksq(iz, iy, ik, nz, ny, nx, dx);
+                        double g = exp(-0.5 * a0 * a0 * k2);
+                        wk[idx] = (wk[idx] - vf * g * fh[idx]) / (1.0 + vf * gamma * k2);
+                    }
+            orc_irfftn(nz, ny, nx, wk, v + j * n);
+        }
+    }
+    free(ph); free(nh); free(wk); free(mu); free(fh); free(t1); free(t2);
+}
+
 /* Mass: the mean density (1/N) sum_j psi_j, i.e. psi_hat(k=0)/N. */
 double orc_mass(int64_t n, const double *psi)
 {

@@ -421,3 +421,72 @@ def test_schemes_converge_at_their_order(scheme, S, order):
         errs.append(np.linalg.norm(out - ref))
     for a, b in zip(errs, errs[1:]):
         assert 2 ** order * 0.8 <= a / b <= 2 ** order * 1.25
+
+
+# ---------------------------------------------------------------------------------------------
+# Hydrodynamic PFC (hydro_step)
+# ---------------------------------------------------------------------------------------------
+HYD = dict(rho=1.0, gamma=1.0, a0=2 * math.pi)
+
+
+@pytest.mark.parametrize("shape", [(16, 32), (8, 16, 16)])
+def test_hydro_without_velocity_response_is_the_pfc_step(shape):
+    """rho = inf and v = 0: the velocity never moves and the density steps exactly like the
+    semi-implicit PFC step."""
+    psi = inputs.uniform_state(shape, -0.25, 0.1, seed=81)
+    v = np.zeros((len(shape),) + shape)
+    out, vo = oracle.hydro_step(psi, v, math.pi / 4, 0.5, ONE, math.inf, 1.0, 2 * math.pi, 6)
+    np.testing.assert_array_equal(out, oracle.step(psi, math.pi / 4, 0.5, ONE, 6))
+    np.testing.assert_array_equal(vo, v)
+
+
+@pytest.mark.parametrize("shape,m,j", [((16, 32), (3, 5), 0), ((16, 32), (2, 1), 1), ((8, 16, 16), (1, 2, 3), 2)])
+def test_hydro_velocity_mode_decays_viscously_on_a_uniform_density(shape, m, j):
+    """psi uniform (no chemical-potential gradient, no advection): a velocity mode decays by
+    1 / (1 + (dt/rho) Gamma k^2) per step and the density stays uniform."""
+    dx, dt, n = math.pi / 4, 0.5, 5
+    grids = np.meshgrid(*[np.arange(k) for k in shape], indexing="ij")
+    phase = sum(2 * np.pi * mi * g / k for mi, g, k in zip(m, grids, shape)) + 0.4
+    q2 = sum((2 * np.pi * (mi if mi <= k // 2 else mi - k) / (k * dx)) ** 2 for mi, k in zip(m, shape))
+    psi = np.full(shape, -0.3)
+    v = np.zeros((len(shape),) + shape)
+    v[j] = 0.2 * np.cos(phase)
+    out, vo = oracle.hydro_step(psi, v, dx, dt, ONE, HYD["rho"], 1.7, HYD["a0"], n)
+    f = (1.0 / (1.0 + dt / HYD["rho"] * 1.7 * q2)) ** n
+    np.testing.assert_allclose(vo[j], v[j] * f, atol=1e-14)
+    assert np.abs(np.delete(vo, j, axis=0)).max() <= 1e-15
+    np.testing.assert_allclose(out, psi, atol=1e-15)
+
+
+@pytest.mark.parametrize("shape,m", [((32, 32), (0, 5)), ((32, 64), (3, 7)), ((16, 16, 16), (1, 0, 2))])
+def test_hydro_advected_density_mode_closed_form(shape, m):
+    """A constant velocity V along x advects a small density mode: its complex amplitude is
+    multiplied by g = (1 - i dt q_x V - 3 mean^2 dt q^2) / (1 + dt q^2 Lk(q)) per step, to
+    O(delta^2) (the velocity the mode drives is O(delta) and advects it at O(delta^2))."""
+    dx, dt, n, mean, V = math.pi / 4, 0.5, 8, -0.25, 0.3
+    psi, q2 = mode_field(shape, dx, mean, 0.0, m)
+    qx = 2 * np.pi * m[-1] / (shape[-1] * dx)
+    kind, r, R1, qq = ONE
+    lk = r + (1 - q2) ** 2
+    g = (1 - 1j * dt * qx * V - 3 * mean * mean * dt * q2) / (1 + dt * q2 * lk)
+    delta = 1e-6 / max(1.0, abs(g) ** n)
+    psi, _ = mode_field(shape, dx, mean, delta, m)
+    v = np.zeros((len(shape),) + shape)
+    v[0] = V
+    out, _ = oracle.hydro_step(psi, v, dx, dt, ONE, HYD["rho"], HYD["gamma"], HYD["a0"], n)
+    amp = oracle.rfftn(out)[tuple(m)] * 2.0 / out.size
+    assert abs(amp - delta * g ** n) <= 2e-9 * abs(delta * g ** n)
+
+
+def test_hydro_one_step_mass_follows_the_divergence_of_v():
+    """The advection term v . grad psi conserves the mean density when div v = 0 (one step from
+    a shear flow) and does not otherwise."""
+    shape, dx, dt = (32, 32), math.pi / 4, 0.5
+    psi = inputs.uniform_state(shape, -0.25, 0.1, seed=82)
+    y, x = np.meshgrid(np.arange(32), np.arange(32), indexing="ij")
+    shear = np.stack([0.3 * np.sin(2 * np.pi * 2 * y / 32), np.zeros(shape)])
+    out, _ = oracle.hydro_step(psi, shear, dx, dt, ONE, **HYD)
+    assert abs(oracle.mass(out) - oracle.mass(psi)) <= 1e-15
+    compress = np.stack([0.3 * np.sin(2 * np.pi * 2 * x / 32), np.zeros(shape)])
+    out, _ = oracle.hydro_step(psi, compress, dx, dt, ONE, **HYD)
+    assert abs(oracle.mass(out) - oracle.mass(psi)) > 1e-6
