@@ -243,6 +243,30 @@ pfc_status pfc_profile_steps(pfc_plan *plan, void *state, int64_t nsteps, double
 pfc_status pfc_step_noalloc(int ndim, const int64_t *dims, double dx, double dt, const pfc_op *op,
                             int precision, void *state, int64_t nsteps, void *stream);
 
+/* ---------------------------------------------------------------------------------- */
+/* Hydrodynamic PFC: the paper's multiphysics example (Eq. (hpfc)), a density psi and a     */
+/* mesoscopic velocity v on one grid:                                                    */
+/*     d_t psi = lap(mu) - v . grad psi,      rho d_t v = Gamma lap v - < psi grad mu >,  */
+/*     mu = Lk psi + psi^3,  < . > the Gaussian average of width a0 (exp(-a0^2 k^2 / 2)).  */
+/* One step (the paper's multi-field listing): psi semi-implicit as in pfc_step with the    */
+/* advection term explicit (old velocity); then each velocity component implicit in the    */
+/* viscosity, forced by the averaged psi' d_j mu' of the new density. Spatial derivatives   */
+/* are spectral (i k_j, zero at the axis' Nyquist index).                                  */
+/* ---------------------------------------------------------------------------------- */
+typedef struct pfc_hydro pfc_hydro;
+
+/* ndim, dims, dx, dt, op, precision, stream as for pfc_plan_create (one field); rho > 0 (+inf:
+ * the velocity never changes), Gamma >= 0, a0 >= 0. Allocates a plan and six half spectra and
+ * two real fields of work arrays. Errors as pfc_plan_create. */
+pfc_status pfc_hydro_create(pfc_hydro **out, int ndim, const int64_t *dims, double dx, double dt,
+                            const pfc_op *op, double rho, double gamma, double a0, int precision,
+                            void *stream);
+/* Advance psi (device real field) and v (device, ndim real fields back to back, x component
+ * first) by nsteps steps, in place, stream ordered. The mean of psi is not carried separately
+ * (the advection term changes it where div v != 0). */
+pfc_status pfc_hydro_step(pfc_hydro *h, void *psi, void *v, int64_t nsteps);
+pfc_status pfc_hydro_destroy(pfc_hydro *h);
+
 /* Names of a status code and of the last error on this thread. Never NULL. */
 const char *pfc_status_string(pfc_status status);
 const char *pfc_last_error(void);

@@ -28,6 +28,7 @@ EXPORTS = ["pfc_plan_create", "pfc_plan_destroy", "pfc_step", "pfc_fft_r2c", "pf
            "pfc_profile_steps", "pfc_step_noalloc", "pfc_plan_autotune", "pfc_batch_autotune",
            "pfc_batch_info",
            "pfc_set_integrator", "pfc_record_bytes", "pfc_step_record", "pfc_adjoint_segment",
+           "pfc_hydro_create", "pfc_hydro_step", "pfc_hydro_destroy",
            "pfc_status_string", "pfc_last_error", "pfc_batch_create", "pfc_batch_destroy",
            "pfc_batch_step", "pfc_batch_mass"]
 
@@ -70,6 +71,9 @@ def load_library(path: str = LIB_PATH):
         "pfc_set_r": [vp, cint, dbl],
         "pfc_set_integrator": [vp, cint, dbl],
         "pfc_record_bytes": [vp, i64, P(i64)],
+        "pfc_hydro_create": [P(vp), cint, P(i64), dbl, dbl, P(pfc_op), dbl, dbl, dbl, cint, vp],
+        "pfc_hydro_step": [vp, vp, vp, i64],
+        "pfc_hydro_destroy": [vp],
         "pfc_step_record": [vp, vp, i64, vp],
         "pfc_adjoint_segment": [vp, vp, i64, vp, vp],
         "pfc_sync": [vp],
@@ -287,6 +291,42 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Hydro:
+    """A pfc_hydro: the hydrodynamic PFC model (density psi and velocity v) on one grid."""
+
+    def __init__(self, dims, dx, dt, op, rho=1.0, gamma=1.0, a0=0.0, precision="fp64", stream=None):
+        lib = load_library()
+        op = op if isinstance(op, pfc_op) else make_op(*op)
+        self.dims = tuple(int(d) for d in dims)
+        self.ndim = len(self.dims)
+        self.real_dtype = torch.float64 if precision == "fp64" else torch.float32
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        check(lib.pfc_hydro_create(ctypes.byref(h), self.ndim, (ctypes.c_int64 * self.ndim)(*self.dims), float(dx),
+                                   float(dt), ctypes.byref(op), float(rho), float(gamma), float(a0),
+                                   PFC_FP64 if precision == "fp64" else PFC_FP32_MIXED,
+                                   ctypes.c_void_p(_stream_handle(self._stream))))
+        self._h = h
+
+    def step(self, psi: torch.Tensor, v: torch.Tensor, nsteps: int = 1):
+        if tuple(psi.shape) != self.dims or tuple(v.shape) != (self.ndim,) + self.dims:
+            raise PfcError(1, f"psi must have shape {self.dims} and v {(self.ndim,) + self.dims}")
+        check(load_library().pfc_hydro_step(self._h, ctypes.c_void_p(_dev_ptr(psi, self.real_dtype, "psi")),
+                                            ctypes.c_void_p(_dev_ptr(v, self.real_dtype, "v")), int(nsteps)))
+        return psi, v
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            check(load_library().pfc_hydro_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

@@ -400,6 +400,81 @@ template <typename R> pfc_status energy_impl(pfc_plan *p, const void *state, dou
 
 bool plan_ok(const pfc_plan *p) { return p && !p->destroyed; }
 
+}  // namespace
+
+// The hydrodynamic PFC model on one grid: a single-field plan for the transforms and the
+// work arrays of one step.
+struct pfc_hydro {
+    pfc_plan *p = nullptr;
+    int ndim = 0;
+    double rho = 1, gamma = 1, a0 = 0;
+    void *Ps = nullptr, *Ns = nullptr, *Mu = nullptr, *Hw = nullptr, *Fh = nullptr, *Vh = nullptr;  // half spectra
+    void *T1 = nullptr, *T2 = nullptr;   // real fields
+};
+
+namespace {
+
+// One hydrodynamic step after another (the sequence of the oracle's hydro step): the density's
+// transforms, derivatives and update with the old velocity, then each velocity component's
+// update with the new density. 20 transforms of the grid a step in 3D (16 in 2D).
+template <typename R> pfc_status hydro_impl(pfc_hydro *h, void *psi, void *v, int64_t nsteps) {
+    pfc_plan *p = h->p;
+    const Geom &g = p->t.g;
+    const double two_pi = 6.28318530717958647692528676655900576839;
+    HydArgs<R> a{};
+    a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
+    a.cx = (R)(two_pi / (g.nx * p->dx));
+    a.cy = (R)(two_pi / (g.ny * p->dx));
+    a.cz = (R)(two_pi / (g.nz * p->dx));
+    a.dt = (R)p->dt;
+    a.vf = (R)(std::isinf(h->rho) ? 0.0 : p->dt / h->rho);
+    a.gamma = (R)h->gamma;
+    a.a0sq = (R)(h->a0 * h->a0);
+    a.op = OpR<R>{p->ops[0].kind, (R)p->ops[0].r, (R)p->ops[0].R1, (R)(p->ops[0].q2 * p->ops[0].q2)};
+    const int64_t H = g.nstd, N = g.nreal;
+    cudaStream_t s = p->stream;
+    R *ps = reinterpret_cast<R *>(psi);
+    R *t1 = reinterpret_cast<R *>(h->T1), *t2 = reinterpret_cast<R *>(h->T2);
+    pfc_status st;
+#define HYD_CALL(x) if ((st = (x)) != PFC_OK) return st
+    for (int64_t k = 0; k < nsteps; ++k) {
+        HYD_CALL(r2c_impl<R>(p, psi, h->Ps));
+        launch_hyd_real<R>(s, HYD_CUBE, N, ps, nullptr, t1);
+        HYD_CALL(r2c_impl<R>(p, t1, h->Ns));
+        for (int j = 0; j < h->ndim; ++j) {   // advection v . grad psi into T1
+            launch_hyd_spec<R>(s, HYD_DERIV, a, H, h->Hw, h->Ps, nullptr, j);
+            HYD_CALL(c2r_impl<R>(p, h->Hw, t2));
+            launch_hyd_real<R>(s, j == 0 ? HYD_MUL : HYD_FMA, N, reinterpret_cast<R *>(v) + (size_t)j * N, t2, t1);
+        }
+        HYD_CALL(r2c_impl<R>(p, t1, h->Fh));
+        launch_hyd_spec<R>(s, HYD_PSI, a, H, h->Ps, h->Ns, h->Fh, 0);
+        HYD_CALL(c2r_impl<R>(p, h->Ps, psi));
+        launch_hyd_real<R>(s, HYD_CUBE, N, ps, nullptr, t1);
+        HYD_CALL(r2c_impl<R>(p, t1, h->Ns));
+        launch_hyd_spec<R>(s, HYD_MU, a, H, h->Mu, h->Ns, h->Ps, 0);
+        for (int j = 0; j < h->ndim; ++j) {   // velocity component j
+            R *vj = reinterpret_cast<R *>(v) + (size_t)j * N;
+            launch_hyd_spec<R>(s, HYD_DERIV, a, H, h->Hw, h->Mu, nullptr, j);
+            HYD_CALL(c2r_impl<R>(p, h->Hw, t2));
+            launch_hyd_real<R>(s, HYD_MUL, N, ps, t2, t1);
+            HYD_CALL(r2c_impl<R>(p, t1, h->Fh));
+            HYD_CALL(r2c_impl<R>(p, vj, h->Vh));
+            launch_hyd_spec<R>(s, HYD_VEL, a, H, h->Vh, h->Fh, nullptr, j);
+            HYD_CALL(c2r_impl<R>(p, h->Vh, vj));
+        }
+    }
+#undef HYD_CALL
+    PFC_CUDA(cudaGetLastError());
+    return PFC_OK;
+}
+
+void hydro_free(pfc_hydro *h) {
+    if (h->p) pfc_plan_destroy(h->p);
+    cudaFree(h->Ps); cudaFree(h->Ns); cudaFree(h->Mu); cudaFree(h->Hw); cudaFree(h->Fh); cudaFree(h->Vh);
+    cudaFree(h->T1); cudaFree(h->T2);
+    delete h;
+}
+
 // Adjoint of one step: lam_out = A lam_next - 3 psi_n^2 B lam_next, *dr += <lam_next, d psi'/dr>.
 // Three-pass plans run the same chain with the middle pass between the row-pass form (in Y) and
 // the line form of each array.
@@ -1031,6 +1106,53 @@ pfc_status pfc_adjoint_segment(pfc_plan *p, const void *record, int64_t nsteps, 
     if (s != PFC_OK) return s;
     return p->prec == PFC_FP64 ? segment_impl<double>(p, record, nsteps, lam, dr)
                                : segment_impl<float>(p, record, nsteps, lam, dr);
+}
+
+pfc_status pfc_hydro_create(pfc_hydro **out, int ndim, const int64_t *dims, double dx, double dt,
+                            const pfc_op *op, double rho, double gamma, double a0, int precision, void *stream) {
+    if (!out || !op) return fail(PFC_ERR_INVALID_ARG, "null pointer argument");
+    if (!(rho > 0) || std::isnan(rho)) return fail(PFC_ERR_INVALID_ARG, "rho must be > 0 (inf allowed)");
+    if (!(gamma >= 0) || !std::isfinite(gamma) || !(a0 >= 0) || !std::isfinite(a0))
+        return fail(PFC_ERR_INVALID_ARG, "gamma and a0 must be finite and >= 0");
+    pfc_plan *p = nullptr;
+    pfc_status st = pfc_plan_create(&p, ndim, dims, dx, dt, op, 1, nullptr, precision, stream);
+    if (st != PFC_OK) return st;
+    pfc_hydro *h = new pfc_hydro();
+    h->p = p;
+    h->ndim = ndim;
+    h->rho = rho;
+    h->gamma = gamma;
+    h->a0 = a0;
+    const Geom &g = p->t.g;
+    const size_t hb = (size_t)g.nstd * vbytes(p), rb = (size_t)g.nreal * vbytes(p) / 2;
+    void **halves[6] = {&h->Ps, &h->Ns, &h->Mu, &h->Hw, &h->Fh, &h->Vh};
+    cudaError_t e = cudaSuccess;
+    for (void **b : halves)
+        if (e == cudaSuccess) e = cudaMalloc(b, hb);
+    if (e == cudaSuccess) e = cudaMalloc(&h->T1, rb);
+    if (e == cudaSuccess) e = cudaMalloc(&h->T2, rb);
+    if (e != cudaSuccess) {
+        hydro_free(h);
+        return fail(e == cudaErrorMemoryAllocation ? PFC_ERR_OUT_OF_MEMORY : PFC_ERR_CUDA,
+                    std::string("hydro allocation: ") + cudaGetErrorString(e));
+    }
+    *out = h;
+    return PFC_OK;
+}
+
+pfc_status pfc_hydro_step(pfc_hydro *h, void *psi, void *v, int64_t nsteps) {
+    if (!h || !plan_ok(h->p)) return fail(PFC_ERR_INVALID_ARG, "invalid hydro object");
+    if (!psi || !v) return fail(PFC_ERR_INVALID_ARG, "null array");
+    if (nsteps < 0) return fail(PFC_ERR_INVALID_ARG, "nsteps must be >= 0");
+    if (nsteps == 0) return PFC_OK;
+    return h->p->prec == PFC_FP64 ? hydro_impl<double>(h, psi, v, nsteps) : hydro_impl<float>(h, psi, v, nsteps);
+}
+
+pfc_status pfc_hydro_destroy(pfc_hydro *h) {
+    if (!h) return PFC_OK;
+    if (h->p) cudaStreamSynchronize(h->p->stream);
+    hydro_free(h);
+    return PFC_OK;
 }
 
 pfc_status pfc_sync(pfc_plan *p) {

@@ -6,6 +6,8 @@
 #include "pfc_reduce.cuh"
 #include "pfc_row_cluster.cuh"
 
+#include <algorithm>
+
 namespace pfc {
 
 template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
@@ -135,6 +137,25 @@ template <typename R> cudaError_t set_smem_adj2(size_t smem) {
 }
 
 template <typename R>
+void launch_hyd_spec(cudaStream_t s, int kind, const HydArgs<R> &a, int64_t n, void *x, const void *y,
+                     const void *z, int axis) {
+    using V = typename VT<R>::V;
+    V *xv = reinterpret_cast<V *>(x);
+    const V *yv = reinterpret_cast<const V *>(y), *zv = reinterpret_cast<const V *>(z);
+    const int blocks = (int)std::min<int64_t>(4 * 304, (n + 255) / 256);
+    if (kind == HYD_DERIV) k_hyd_spec<R, HYD_DERIV><<<blocks, 256, 0, s>>>(a, n, xv, yv, zv, axis);
+    else if (kind == HYD_PSI) k_hyd_spec<R, HYD_PSI><<<blocks, 256, 0, s>>>(a, n, xv, yv, zv, axis);
+    else if (kind == HYD_MU) k_hyd_spec<R, HYD_MU><<<blocks, 256, 0, s>>>(a, n, xv, yv, zv, axis);
+    else k_hyd_spec<R, HYD_VEL><<<blocks, 256, 0, s>>>(a, n, xv, yv, zv, axis);
+}
+template <typename R> void launch_hyd_real(cudaStream_t s, int kind, int64_t n, const R *p, const R *q, R *out) {
+    const int blocks = (int)std::min<int64_t>(4 * 304, (n + 255) / 256);
+    if (kind == HYD_CUBE) k_hyd_real<R, HYD_CUBE><<<blocks, 256, 0, s>>>(n, p, q, out);
+    else if (kind == HYD_FMA) k_hyd_real<R, HYD_FMA><<<blocks, 256, 0, s>>>(n, p, q, out);
+    else k_hyd_real<R, HYD_MUL><<<blocks, 256, 0, s>>>(n, p, q, out);
+}
+
+template <typename R>
 void launch_batch_mean(cudaStream_t s, const R *base, const int64_t *off, const int64_t *n,
                        int members, double *mean, int *status) {
     k_batch_mean<R><<<members, RED_THREADS, 0, s>>>(base, off, n, mean, status);
@@ -166,6 +187,9 @@ void launch_reduce_spec(cudaStream_t s, const Geom &g, OpDev op, double dx, cons
     template cudaError_t set_smem_onchip<R>(size_t);                                       \
     template void launch_row_adj2<R>(cudaStream_t, const Geom &, int, size_t, const RowArgs<R> &); \
     template cudaError_t set_smem_adj2<R>(size_t);                                         \
+    template void launch_hyd_spec<R>(cudaStream_t, int, const HydArgs<R> &, int64_t, void *, const void *, \
+                                     const void *, int);                                  \
+    template void launch_hyd_real<R>(cudaStream_t, int, int64_t, const R *, const R *, R *); \
     template void launch_batch_mean<R>(cudaStream_t, const R *, const int64_t *,           \
                                        const int64_t *, int, double *, int *);             \
     template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t,  \

@@ -12,6 +12,7 @@
 #include "pfc_line_v2.cuh"
 #include "pfc_onchip.cuh"
 #include "pfc_adjoint_row.cuh"
+#include "pfc_hydro.cuh"
 
 namespace pfc {
 
@@ -59,6 +60,12 @@ template <typename R> cudaError_t set_smem_onchip(size_t smem);
 template <typename R>
 void launch_row_adj2(cudaStream_t s, const Geom &g, int nt, size_t smem, const RowArgs<R> &a);
 template <typename R> cudaError_t set_smem_adj2(size_t smem);
+// pointwise kernels of the hydrodynamic step (pfc_hydro.cuh): spectral (standard half spectra of
+// n complex values) and real (n values)
+template <typename R>
+void launch_hyd_spec(cudaStream_t s, int kind, const HydArgs<R> &a, int64_t n, void *x, const void *y,
+                     const void *z, int axis);
+template <typename R> void launch_hyd_real(cudaStream_t s, int kind, int64_t n, const R *p, const R *q, R *out);
 // middle pass of a three-pass plan (g.R > 1): dir -1 forward, +1 inverse (pfc_mid.cuh)
 template <typename R> void launch_mid(const LaunchCfg &c, int dir, const MidArgs<R> &a);
 
@@ -102,6 +109,9 @@ template <typename R> cudaError_t set_smem_attrs_fixed(const LaunchCfg &c);
     extern template cudaError_t set_smem_onchip<R>(size_t);                                      \
     extern template void launch_row_adj2<R>(cudaStream_t, const Geom &, int, size_t, const RowArgs<R> &); \
     extern template cudaError_t set_smem_adj2<R>(size_t);                                        \
+    extern template void launch_hyd_spec<R>(cudaStream_t, int, const HydArgs<R> &, int64_t, void *, \
+                                            const void *, const void *, int);                    \
+    extern template void launch_hyd_real<R>(cudaStream_t, int, int64_t, const R *, const R *, R *); \
     extern template void launch_batch_mean<R>(cudaStream_t, const R *, const int64_t *,         \
                                               const int64_t *, int, double *, int *);           \
     extern template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t, \

@@ -81,6 +81,14 @@ def test_host_side_validation(lib):
     assert lib.pfc_batch_autotune(None, 4, 20, None) == 1
     assert lib.pfc_batch_info(None, None, 0, None) == 1
     assert lib.pfc_set_integrator(None, 2, 0.0) == 1
+    assert lib.pfc_hydro_step(None, None, None, 1) == 1
+    assert lib.pfc_hydro_destroy(None) == 0
+    h = ctypes.c_void_p()
+    dims = (ctypes.c_int64 * 2)(32, 32)
+    op = binding.make_op(0, -0.25)
+    assert lib.pfc_hydro_create(ctypes.byref(h), 2, dims, 0.785, 0.5, ctypes.byref(op), -1.0, 1.0, 1.0, 0, None) == 1
+    assert lib.pfc_hydro_create(ctypes.byref(h), 2, dims, 0.785, 0.5, ctypes.byref(op), 1.0, float("nan"), 1.0, 0,
+                                None) == 1
     assert lib.pfc_plan_destroy(None) == 0
 
 
