@@ -94,6 +94,11 @@ CONFIGS = {
                     "fused adjoint over it (pfc_adjoint_segment); rate in rollout steps (forward + adjoint) x points",
                kind="segment", dims=(256, 256, 256), prec="fp32", op=(0, -0.25, 0.0, 0.0), dt=0.5,
                inner=20, sweeps=14),
+    "h": dict(desc="hydrodynamic PFC 256^3 FP32-mixed (density and three velocity components), one-mode "
+                   "r=-0.25, dx=pi/4, dt=0.5, rho=1, Gamma=1, a0=2, psi0=-0.25+U[-0.1,0.1] (seed 91), "
+                   "v0=0.05 U[-1,1] (seeds 92-94); 2 steps per bench step (20 transforms of the grid a step)",
+              kind="hydro", dims=(256, 256, 256), prec="fp32", op=(0, -0.25, 0.0, 0.0), dt=0.5, inner=2,
+              sweeps=110),
     "3d64": dict(desc="3D two-mode 512^3 FP64 (three-pass schedule), as config 3; 4 time steps per bench step",
                  kind="plan", dims=(512, 512, 512), prec="fp64", op=(1, -0.3, 0.05, math.sqrt(4.0 / 3.0)),
                  dt=0.1, inner=4, sweeps=9),
@@ -154,6 +159,14 @@ def run_config(args):
         if c.get("autotune") and not args.no_autotune:
             extra["autotune"] = {"candidates": 6, "trial_steps": 8, "ms_per_step": obj.autotune(6, 8)}
         extra["plan"] = obj.info()
+    elif c["kind"] == "hydro":
+        shape = c["dims"]
+        obj = binding.Hydro(shape, DX, c["dt"], c["op"], rho=1.0, gamma=1.0, a0=2.0, precision=prec)
+        state = torch.from_numpy(inputs.uniform_state(shape, -0.25, 0.1, seed=91)).to(device=dev, dtype=dtype)
+        vel = torch.from_numpy(0.05 * np.stack([inputs.uniform_state(shape, 0.0, 1.0, seed=92 + j)
+                                                 for j in range(3)])).to(device=dev, dtype=dtype)
+        npts = state.numel()
+        run = lambda: obj.step(state, vel, c["inner"])
     elif c["kind"] == "largest":
         torch.cuda.empty_cache()
         n = largest_cube(torch.cuda.mem_get_info()[0])
@@ -494,11 +507,14 @@ def kernel_source_hash():
 
 
 def kernel_names(info):
-    """Names (as ncu prints them, without arguments) of the row and line kernels a plan runs."""
+    """Names (as ncu prints them, without arguments) of the row and line kernels a FP32 plan runs."""
     row = "k_row_cube_cl<float, 2, 11>" if info.get("row_cluster") == 2 else "k_row<float, ROW_CUBE>"
     ly = info["Qy"].bit_length() - 1
-    fixed = info["Qz"] == 1 and info["threads_line"] <= 512 and 6 <= ly <= 10
-    line = f"k_line<float, LINE_STEP, 512, {ly}, 0>" if fixed else "k_line<float, LINE_STEP>"
+    if info["W"] >= 2 and info["threads_line"] >= 64:   # the two-column update pass
+        line = f"k_line_v2<512, {ly}, 0>" if info["Qz"] == 1 and ly in (8, 9, 10) else "k_line_v2<512>"
+    else:
+        fixed = info["Qz"] == 1 and info["threads_line"] <= 512 and 6 <= ly <= 10
+        line = f"k_line<float, LINE_STEP, 512, {ly}, 0>" if fixed else "k_line<float, LINE_STEP>"
     return {"row": row, "line": line}
 
 
