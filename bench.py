@@ -102,6 +102,16 @@ CONFIGS = {
     "3d64": dict(desc="3D two-mode 512^3 FP64 (three-pass schedule), as config 3; 4 time steps per bench step",
                  kind="plan", dims=(512, 512, 512), prec="fp64", op=(1, -0.3, 0.05, math.sqrt(4.0 / 3.0)),
                  dt=0.1, inner=4, sweeps=9),
+    "750": dict(desc="3D one-mode 750^3 FP32-mixed (the paper's best single-GPU size; mixed-radix schedule, "
+                     "radices 2, 3, 5), dx=pi/4, dt=0.5, r=-0.25, psi0=-0.25+U[-0.01,0.01] (seed 6); "
+                     "4 time steps per bench step",
+                kind="plan", dims=(750, 750, 750), prec="fp32", op=(0, -0.25, 0.0, 0.0), dt=0.5, inner=4,
+                sweeps=11),
+    "1400": dict(desc="3D one-mode 1400^3 FP32-mixed (the paper's largest grid, 4 H100 there; mixed-radix "
+                      "schedule, radices 8, 7, 5), dx=pi/4, dt=0.5, r=-0.25, psi0=-0.25+U[-0.01,0.01] "
+                      "(torch generator, seed 8); 2 time steps per bench step",
+                 kind="plan", dims=(1400, 1400, 1400), prec="fp32", op=(0, -0.25, 0.0, 0.0), dt=0.5,
+                 inner=2, sweeps=11, device_draw=True),
     "L": dict(desc="the largest power-of-two 3D one-mode grid whose FP32-mixed plan and state fit the GPU's "
                    "free memory (2048^3 on a GB300), dx=pi/4, dt=0.5, r=-0.25, psi0=-0.25+U[-0.01,0.01] "
                    "(torch generator, seed 8), three-pass schedule; 3 time steps per bench step",
@@ -182,10 +192,12 @@ def run_config(args):
         shape = c["dims"]
         seed = {"1": 1, "3": 3, "3d64": 3}.get(args.config, 6)
         mean, amp = {"1": (-0.25, 0.01), "3": (-0.35, 0.02), "3d64": (-0.35, 0.02)}.get(args.config, (-0.25, 0.01))
-        psi0 = inputs.uniform_state(shape, mean, amp, seed=seed)
         obj = binding.Plan(shape, DX, c["dt"], [binding.make_op(*c["op"])], precision=prec)
-        state = torch.from_numpy(psi0).to(device=dev, dtype=dtype)
-        npts = psi0.size
+        if c.get("device_draw"):
+            state = seeded_uniform_state(shape, mean, amp, 8, dtype, dev)
+        else:
+            state = torch.from_numpy(inputs.uniform_state(shape, mean, amp, seed=seed)).to(device=dev, dtype=dtype)
+        npts = state.numel()
         if args.autotune and c["kind"] == "plan":
             extra["autotune"] = {"candidates": 8, "trial_steps": c["inner"],
                                  "ms_per_step": obj.autotune(8, c["inner"])}

@@ -14,8 +14,10 @@
  *
  * Conventions shared by every call:
  *   - dims are given slowest first, like a C array or a torch/numpy shape: 2D (ny, nx),
- *     3D (nz, ny, nx); x is contiguous. Every extent must be a power of two in [16, 4096],
- *     otherwise PFC_ERR_UNSUPPORTED.
+ *     3D (nz, ny, nx); x is contiguous. Every extent is a power of two in [16, 4096], or
+ *     the grid is a mixed-radix one: every extent a product of 2, 3, 5 and 7 in [8, 4096],
+ *     nx even and nx / 2 such a product too (the paper's 750^3, 900^3, 1400^3); otherwise
+ *     PFC_ERR_UNSUPPORTED.
  *   - Box length per axis is n dx; k = 2 pi m / (n dx) with m in FFT order.
  *   - Real arrays hold nfields fields back to back, each nz*ny*nx values; complex arrays
  *     are interleaved (re, im) with the half-spectrum shape (nz, ny, nx/2 + 1).
@@ -83,8 +85,13 @@ typedef struct pfc_plan pfc_plan;
  * grids (FP64 512^3, 3D grids from 1024^3 up) take the three-pass schedule: a middle pass takes
  * over a third part of the y/z transforms (9 sweeps a step). Two-field plans need the two-pass
  * schedule (UNSUPPORTED otherwise).
+ * Mixed-radix grids (extents not all powers of two) take one pass per axis instead, each line
+ * a Stockham transform of radices 2, 3, 4, 5, 7, 8 in shared memory (11 sweeps a step in 3D,
+ * 7 in 2D). They support one field and the semi-implicit step: pfc_step, the transforms,
+ * pfc_mass, pfc_energy, pfc_set_r, pfc_profile_steps and the hydrodynamic model; the adjoint,
+ * recorded segments, the other integrators and pfc_plan_autotune return UNSUPPORTED.
  * Allocates the plan's device scratch with cudaMalloc: 2 * nfields half spectra, and a third
- * for a three-pass plan.
+ * for a three-pass or mixed-radix plan.
  * Errors: INVALID_ARG, UNSUPPORTED, UNSTABLE_OPERATOR, OUT_OF_MEMORY, CUDA. */
 pfc_status pfc_plan_create(pfc_plan **out, int ndim, const int64_t *dims, double dx, double dt,
                            const pfc_op *ops, int nfields, const double *coupling,
@@ -184,6 +191,8 @@ pfc_status pfc_sync(pfc_plan *plan);
  *     row_cluster: blocks per cluster of the psi^3 row pass, 0 = none.
  *     Ry, Rz: the middle pass of the three-pass schedule (1, 1 = the two-pass schedule); the
  *     y length is Py Ry Qy and the z length Pz Rz Qz.
+ *     A mixed-radix plan reports Py = Pz = Qy = Qz = 0, W = the y pass' columns a block,
+ *     row_groups_per_cta = the x pass' rows a block, and the threads of those blocks.
  *   scratch_bytes = device bytes the plan owns. */
 pfc_status pfc_plan_info(pfc_plan *plan, int32_t *tiles, int64_t *scratch_bytes);
 
@@ -212,7 +221,9 @@ pfc_status pfc_plan_autotune(pfc_plan *plan, int max_candidates, int trial_steps
  * CUDA event on the plan's stream between consecutive kernel launches (no CUDA graph), then
  * synchronises and returns the summed event time per kernel kind in ms_out[5] (host):
  *   {row pass forming psi^3, line pass with the update, entry conversion, exit conversion,
- *    middle passes of a three-pass plan (0 for two-pass plans)}
+ *    middle passes of a three-pass plan (0 for two-pass plans)};
+ * on a mixed-radix plan {x pass forming psi^3, the y and z passes, entry, exit, the transforms
+ *    of the projection columns}
  * and the number of kernel launches in *launches (host). */
 pfc_status pfc_profile_steps(pfc_plan *plan, void *state, int64_t nsteps, double *ms_out,
                              int64_t *launches);

@@ -47,6 +47,14 @@ struct pfc_plan {
     int scheme = PFC_SEMI_IMPLICIT;   // time integrator (pfc_set_integrator)
     double stab = 0.0;            // its stabilisation constant S
     void *X2 = nullptr, *C2 = nullptr;   // the second time level of the second-order scheme
+    // mixed-radix plans (extents of 2, 3, 5, 7 that are not all powers of two): X holds S, Y the
+    // row-space work array, C the cube's transform, E the projection columns
+    bool mixed = false;
+    MrGeom mg{};
+    void *mtw = nullptr, *mtwx = nullptr, *E = nullptr;
+    int mr_rows = 1;              // x pass: rows (warps) a block
+    int mr_W[3] = {1, 1, 1};      // column passes: columns (warps) a block, per axis
+    int mr_wE[3] = {1, 1, 1};     // the same for the two projection columns
     void *A = nullptr;            // third half spectrum, allocated by the first adjoint call
     double *d_adjpart = nullptr;  // adjoint line-pass partial sums (one per block)
     double *d_mean = nullptr, *d_part = nullptr, *d_out = nullptr;
@@ -122,6 +130,132 @@ void launch_mid_m(const pfc_plan *p, int dir, const void *in, void *out, double 
     launch_mid<R>(cfg(p), dir, a);
 }
 bool three_pass(const pfc_plan *p) { return p->t.g.R > 1; }
+
+// ------------------------------------------------------------------------------------------
+// Mixed-radix plans (pfc_mixed.cuh): one pass per axis
+// ------------------------------------------------------------------------------------------
+template <typename R> void launch_means(pfc_plan *p, const void *state);
+
+template <typename R> MrArgs<R> mr_args(const pfc_plan *p) {
+    MrArgs<R> a{};
+    a.tw = reinterpret_cast<const typename VT<R>::V *>(p->mtw);
+    a.twx = reinterpret_cast<const typename VT<R>::V *>(p->mtwx);
+    a.scale = (R)1;
+    const double two_pi = 6.28318530717958647692528676655900576839;
+    const MrGeom &g = p->mg;
+    a.up.dt = (R)p->dt;
+    a.up.cx = (R)(two_pi / (g.nx * p->dx));
+    a.up.cy = (R)(two_pi / (g.ny * p->dx));
+    a.up.cz = (R)(two_pi / (g.nz * p->dx));
+    a.up.inv_halfN = (R)(1.0 / ((double)g.ny * g.nz * g.M));
+    a.up.op[0] = OpR<R>{p->ops[0].kind, (R)p->ops[0].r, (R)p->ops[0].R1, (R)(p->ops[0].q2 * p->ops[0].q2)};
+    return a;
+}
+// column pass along axis (1 y, 2 z) of a half spectrum of M + 1 columns
+template <typename R>
+void mr_col(const pfc_plan *p, int mode, int axis, const void *in, void *out, double scale) {
+    MrArgs<R> a = mr_args<R>(p);
+    a.scale = (R)scale;
+    launch_mr_col<R>(p->stream, mode, p->mg, a, axis, p->mr_W[axis], p->mg.M + 1, in, out);
+}
+template <typename R>
+void mr_row(const pfc_plan *p, int mode, const void *in, void *out, const double *mean, double scale) {
+    MrArgs<R> a = mr_args<R>(p);
+    a.scale = (R)scale;
+    a.mean = mean;
+    launch_mr_row<R>(p->stream, mode, p->mg, a, in, out, p->E, p->mr_rows);
+}
+// forward y (and z) of a half spectrum in place, the last pass scaled
+template <typename R> void mr_fwd_yz(const pfc_plan *p, void *x, double scale) {
+    const bool z = p->mg.nz > 1;
+    mr_col<R>(p, MR_COL_FWD, 1, x, x, z ? 1.0 : scale);
+    if (z) mr_col<R>(p, MR_COL_FWD, 2, x, x, scale);
+}
+// inverse z (and y) from in into out (unnormalised)
+template <typename R> void mr_inv_yz(const pfc_plan *p, const void *in, void *out) {
+    if (p->mg.nz > 1) {
+        mr_col<R>(p, MR_COL_INV, 2, in, out, 1.0);
+        mr_col<R>(p, MR_COL_INV, 1, out, out, 1.0);
+    } else {
+        mr_col<R>(p, MR_COL_INV, 1, in, out, 1.0);
+    }
+}
+// The mixed-radix step sequence; mk(kind) is called before each group of launches (the kinds of
+// pfc_profile_steps: 0 x pass, 1 y/z passes, 2 entry, 3 exit, 4 projection columns).
+template <typename R, typename Mark>
+void mixed_enqueue(pfc_plan *p, void *state, int64_t nsteps, Mark &&mk) {
+    const MrGeom &g = p->mg;
+    const double sc = 1.0 / ((double)g.ny * g.nz * g.M);
+    mk(2);
+    launch_means<R>(p, state);
+    // entry: S = F(psi - mean) / (ny nz M)
+    mr_row<R>(p, MR_ROW_FWD, state, p->X, p->d_mean, 1.0);
+    mr_fwd_yz<R>(p, p->X, sc);
+    // the projection columns E as a half spectrum of two columns
+    MrGeom ge = g;
+    ge.xs = 2;
+    MrArgs<R> ea = mr_args<R>(p);
+    for (int64_t s = 0; s < nsteps; ++s) {
+        mk(1);
+        mr_inv_yz<R>(p, p->X, p->Y);
+        mk(0);
+        mr_row<R>(p, MR_ROW_CUBE, p->Y, p->C, p->d_mean, 1.0);
+        mk(1);
+        if (g.nz > 1) mr_col<R>(p, MR_COL_FWD, 1, p->C, p->C, 1.0);
+        mk(4);
+        // Hermitian projection of the kx = 0 and nx/2 columns: F_yz of their real parts / (ny nz)
+        ea.scale = (R)(g.nz > 1 ? 1.0 : 1.0 / g.ny);
+        launch_mr_col<R>(p->stream, MR_COL_FWD, ge, ea, 1, p->mr_wE[1], 2, p->E, p->E);
+        if (g.nz > 1) {
+            ea.scale = (R)(1.0 / ((double)g.ny * g.nz));
+            launch_mr_col<R>(p->stream, MR_COL_FWD, ge, ea, 2, p->mr_wE[2], 2, p->E, p->E);
+        }
+        launch_mr_edges<R>(p->stream, g, p->E, p->X, 1.0);
+        mk(1);
+        mr_col<R>(p, MR_COL_UPDATE, g.nz > 1 ? 2 : 1, p->C, p->X, 1.0);
+    }
+    // exit
+    mk(3);
+    mr_inv_yz<R>(p, p->X, p->Y);
+    mr_row<R>(p, MR_ROW_INV, p->Y, state, p->d_mean, 1.0);
+}
+// launches of mixed_enqueue
+int64_t mixed_launches(const pfc_plan *p, int64_t nsteps) {
+    const bool z = p->mg.nz > 1;
+    return 3 + (z ? 2 : 1) + nsteps * (z ? 8 : 5) + (z ? 3 : 2);
+}
+template <typename R> pfc_status mixed_step_impl(pfc_plan *p, void *state, int64_t nsteps) {
+    mixed_enqueue<R>(p, state, nsteps, [](int) {});
+    PFC_CUDA(cudaGetLastError());
+    return PFC_OK;
+}
+template <typename R> pfc_status mixed_r2c_impl(pfc_plan *p, const void *in, void *out) {
+    mr_row<R>(p, MR_ROW_FWD, in, out, nullptr, 1.0);
+    mr_fwd_yz<R>(p, out, 1.0);
+    PFC_CUDA(cudaGetLastError());
+    return PFC_OK;
+}
+template <typename R> pfc_status mixed_c2r_impl(pfc_plan *p, const void *in, void *out) {
+    mr_inv_yz<R>(p, in, p->Y);
+    mr_row<R>(p, MR_ROW_INV, p->Y, out, nullptr, 1.0 / ((double)p->mg.ny * p->mg.nz * p->mg.M));
+    PFC_CUDA(cudaGetLastError());
+    return PFC_OK;
+}
+
+// radices of n in {8, 4, 2, 7, 5, 3}; false when n has another prime factor
+bool mr_factor(int n, std::vector<int> &rad) {
+    rad.clear();
+    while (n % 8 == 0) { rad.push_back(8); n /= 8; }
+    if (n % 4 == 0) { rad.push_back(4); n /= 4; }
+    if (n % 2 == 0) { rad.push_back(2); n /= 2; }
+    for (int r : {7, 5, 3})
+        while (n % r == 0) { rad.push_back(r); n /= r; }
+    return n == 1 && (int)rad.size() <= MR_MAXST;
+}
+bool mr_extent_ok(int64_t n) {
+    std::vector<int> r;
+    return n >= 8 && n <= 4096 && mr_factor((int)n, r);
+}
 template <typename R> void launch_line_m(const pfc_plan *p, int mode, const LineArgs<R> &a, int nf) {
     launch_line<R>(cfg(p), mode, a, nf);
 }
@@ -294,6 +428,7 @@ template <typename R> pfc_status run_steps(pfc_plan *p, int64_t nsteps) {
 }
 
 template <typename R> pfc_status step_impl(pfc_plan *p, void *state, int64_t nsteps) {
+    if (p->mixed) return mixed_step_impl<R>(p, state, nsteps);
     enqueue_entry<R>(p, state);
     PFC_CUDA(cudaGetLastError());
     pfc_status s = run_steps<R>(p, nsteps);
@@ -304,6 +439,7 @@ template <typename R> pfc_status step_impl(pfc_plan *p, void *state, int64_t nst
 }
 
 template <typename R> pfc_status r2c_impl(pfc_plan *p, const void *in, void *out) {
+    if (p->mixed) return mixed_r2c_impl<R>(p, in, out);
     RowArgs<R> ra = row_args<R>(p);
     ra.in = in;
     ra.out = p->X;
@@ -318,6 +454,7 @@ template <typename R> pfc_status r2c_impl(pfc_plan *p, const void *in, void *out
 }
 
 template <typename R> pfc_status c2r_impl(pfc_plan *p, const void *in, void *out) {
+    if (p->mixed) return mixed_c2r_impl<R>(p, in, out);
     const Geom &g = p->t.g;
     LineArgs<R> la = line_args<R>(p);
     la.x = p->X;
@@ -364,16 +501,21 @@ template <typename R> pfc_status energy_impl(pfc_plan *p, const void *state, dou
     // slots in d_out: [0, nf) spectral sums, [nf, 2nf) sum psi^4, [2nf] cross term
     for (int f = 0; f < p->nfields; ++f) {
         const R *x = reinterpret_cast<const R *>(state) + (size_t)f * g.nreal;
-        RowArgs<R> ra = row_args<R>(p);
-        ra.in = x;
-        ra.out = p->X;
-        ra.mean = p->d_mean + f;
-        launch_row_m<R>(p, ROW_FWD, ra, 1);
-        if (three_pass(p)) launch_mid_m<R>(p, -1, p->X, p->X, 1.0, false);
-        LineArgs<R> la = line_args<R>(p);
-        la.x = p->X;
-        la.std_out = p->C;
-        launch_line_m<R>(p, LINE_FWD, la, 1);
+        if (p->mixed) {
+            mr_row<R>(p, MR_ROW_FWD, x, p->C, p->d_mean + f, 1.0);
+            mr_fwd_yz<R>(p, p->C, 1.0);
+        } else {
+            RowArgs<R> ra = row_args<R>(p);
+            ra.in = x;
+            ra.out = p->X;
+            ra.mean = p->d_mean + f;
+            launch_row_m<R>(p, ROW_FWD, ra, 1);
+            if (three_pass(p)) launch_mid_m<R>(p, -1, p->X, p->X, 1.0, false);
+            LineArgs<R> la = line_args<R>(p);
+            la.x = p->X;
+            la.std_out = p->C;
+            launch_line_m<R>(p, LINE_FWD, la, 1);
+        }
         launch_reduce_spec<R>(p->stream, g, to_dev(p->ops[f]), p->dx, p->C, p->d_mean + f,
                               p->d_part, p->d_status);
         launch_finish(p->stream, p->d_part, RED_BLOCKS, 1.0, p->d_out + f);
@@ -569,6 +711,7 @@ bool adj2_geom(const pfc_plan *p, Geom &g, int &nt, size_t &smem) {
 }
 
 pfc_status segment_supported(const pfc_plan *p) {
+    if (p->mixed) return fail(PFC_ERR_UNSUPPORTED, "recorded segments are built for power-of-two grids");
     if (p->nfields != 1) return fail(PFC_ERR_UNSUPPORTED, "recorded segments are built for single-field plans");
     if (p->scheme != PFC_SEMI_IMPLICIT) return fail(PFC_ERR_UNSUPPORTED, "recorded segments follow the semi-implicit step");
     if (three_pass(p)) return fail(PFC_ERR_UNSUPPORTED, "recorded segments are built for two-pass plans");
@@ -686,20 +829,28 @@ pfc_status profile_impl(pfc_plan *p, void *state, int64_t nsteps, double *ms, in
     };
     int64_t nl = 0;
     const bool three = three_pass(p);
-    cudaError_t err = mark(2);
-    enqueue_entry<R>(p, state);
-    nl += 2 * p->nfields + 1 + (three ? 1 : 0);
-    auto mk = [&](int k) {
-        if (err == cudaSuccess) err = mark(k);
-    };
-    for (int64_t s = 0; s < nsteps && err == cudaSuccess; ++s) {
-        enqueue_step<R>(p, s, mk);
-        nl += 2 + (three ? 3 : 0);
+    cudaError_t err = cudaSuccess;
+    if (p->mixed) {
+        mixed_enqueue<R>(p, state, nsteps, [&](int k) {
+            if (err == cudaSuccess) err = mark(k);
+        });
+        nl = mixed_launches(p, nsteps);
+    } else {
+        err = mark(2);
+        enqueue_entry<R>(p, state);
+        nl += 2 * p->nfields + 1 + (three ? 1 : 0);
+        auto mk = [&](int k) {
+            if (err == cudaSuccess) err = mark(k);
+        };
+        for (int64_t s = 0; s < nsteps && err == cudaSuccess; ++s) {
+            enqueue_step<R>(p, s, mk);
+            nl += 2 + (three ? 3 : 0);
+        }
+        mk(3);
+        enqueue_exit<R>(p, final_state(p, nsteps), state);
+        nl += 1 + (three ? 1 : 0);
     }
-    mk(3);
-    enqueue_exit<R>(p, final_state(p, nsteps), state);
-    nl += 1 + (three ? 1 : 0);
-    mk(-1);
+    if (err == cudaSuccess) err = mark(-1);
     if (err == cudaSuccess) err = cudaGetLastError();
     if (err == cudaSuccess) err = cudaStreamSynchronize(p->stream);
     double acc[5] = {0, 0, 0, 0, 0};
@@ -836,6 +987,116 @@ size_t smem_optin() {
     return (size_t)optin;
 }
 
+// A mixed-radix plan (single field, the semi-implicit step): tables, work arrays, launch shapes.
+pfc_status mixed_plan_create(pfc_plan **out, int ndim, const int64_t d[3], double dx, double dt,
+                             const pfc_op *ops, int precision, void *stream) {
+    pfc_plan *p = new pfc_plan();
+    p->ndim = ndim;
+    p->nz = (int)d[0]; p->ny = (int)d[1]; p->nx = (int)d[2];
+    p->dx = dx; p->dt = dt;
+    p->ops[0] = ops[0];
+    p->nfields = 1;
+    p->prec = precision;
+    p->stream = reinterpret_cast<cudaStream_t>(stream);
+    p->mixed = true;
+    MrGeom &g = p->mg;
+    g.nx = p->nx; g.ny = p->ny; g.nz = p->nz; g.M = p->nx / 2; g.xs = g.M + 1; g.ndim = ndim;
+    g.nstd = (int64_t)g.ny * g.nz * g.xs;
+    g.nreal = (int64_t)g.nx * g.ny * g.nz;
+    // the plan geometry's fields the shared kernels (reductions) read
+    Geom &pg = p->t.g;
+    pg = Geom{};
+    pg.nx = g.nx; pg.ny = g.ny; pg.nz = g.nz; pg.M = g.M; pg.nreal = g.nreal; pg.nstd = g.nstd;
+    pg.Ry = pg.Rz = pg.R = 1;
+    const size_t vb = vbytes(p);
+    // tables: per axis the stage twiddles
+    std::vector<double> tw;
+    const int lens[3] = {g.M, g.ny, g.nz};
+    int optin = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        delete p;
+        return fail(PFC_ERR_CUDA, "device query failed");
+    }
+    // a block's shared memory: up to 100 KB (two blocks an SM), more only for one long line
+    const size_t budget = 100 * 1024;
+    size_t smem_col = 0;
+    for (int a = 0; a < 3; ++a) {
+        MrAxis &ax = g.ax[a];
+        ax.n = lens[a];
+        std::vector<int> rad;
+        if (ax.n > 1) mr_factor(ax.n, rad);
+        ax.nst = (int)rad.size();
+        int Ns = 1;
+        for (int s = 0; s < ax.nst; ++s) {
+            ax.radix[s] = rad[s];
+            ax.ns[s] = Ns;
+            ax.twoff[s] = (int)(tw.size() / 2);
+            for (int m = 0; m < rad[s]; ++m)
+                for (int k = 0; k < Ns; ++k) {
+                    double re, im;
+                    unit_root_fwd((int64_t)m * k, (int64_t)rad[s] * Ns, &re, &im);
+                    tw.push_back(re);
+                    tw.push_back(im);
+                }
+            Ns *= rad[s];
+        }
+        // launch shapes: one warp a line; as many lines a block as the budget holds (rows of
+        // 128 bytes in the column passes: 16 FP32 or 8 FP64 columns)
+        if (a == 0) {
+            int rows = 8;
+            while (rows > 1 && mr_row_smem(ax.n, rows, vb) > budget) rows /= 2;
+            p->mr_rows = rows;
+        } else if (ax.n > 1) {
+            int W = vb == 8 ? 16 : 8;
+            while (W > 1 && mr_col_smem(ax.n, W, vb) > budget) W /= 2;
+            p->mr_W[a] = W;
+            p->mr_wE[a] = mr_col_smem(ax.n, 2, vb) <= budget ? 2 : 1;
+            smem_col = std::max(smem_col, mr_col_smem(ax.n, std::max(W, p->mr_wE[a]), vb));
+        }
+    }
+    if (smem_col > (size_t)optin || mr_row_smem(g.M, p->mr_rows, vb) > (size_t)optin) {
+        delete p;
+        return fail(PFC_ERR_UNSUPPORTED, "a line of this grid does not fit shared memory");
+    }
+    std::vector<double> twx(2 * (size_t)g.nx);
+    for (int t = 0; t < g.nx; ++t) unit_root_fwd(t, g.nx, &twx[2 * t], &twx[2 * t + 1]);
+    auto cleanup = [&](cudaError_t err) {
+        pfc_plan_destroy(p);
+        return fail(err == cudaErrorMemoryAllocation ? PFC_ERR_OUT_OF_MEMORY : PFC_ERR_CUDA,
+                    std::string("plan allocation: ") + cudaGetErrorString(err));
+    };
+    const size_t half = (size_t)g.nstd * vb;
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->X, half)) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMalloc(&p->C, half)) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMalloc(&p->Y, half)) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMalloc(&p->E, 2 * (size_t)g.ny * g.nz * vb)) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMalloc(&p->mtw, tw.size() / 2 * vb)) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMalloc(&p->mtwx, twx.size() / 2 * vb)) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMalloc(&p->d_mean, 8 * sizeof(double))) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMalloc(&p->d_part, RED_BLOCKS * sizeof(double))) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMalloc(&p->d_out, 8 * sizeof(double))) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) return cleanup(e);
+    p->half_cap = p->y_cap = half;
+    p->scratch = 3 * half + 2 * (size_t)g.ny * g.nz * vb + (tw.size() + twx.size()) / 2 * vb +
+                 (16 + RED_BLOCKS) * sizeof(double) + sizeof(int);
+    auto upload = [&](void *dst, const std::vector<double> &src) {
+        if (p->prec == PFC_FP64) return cudaMemcpy(dst, src.data(), src.size() * 8, cudaMemcpyHostToDevice);
+        std::vector<float> f(src.begin(), src.end());
+        return cudaMemcpy(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice);
+    };
+    if ((e = upload(p->mtw, tw)) != cudaSuccess) return cleanup(e);
+    if ((e = upload(p->mtwx, twx)) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMemset(p->d_status, 0, sizeof(int))) != cudaSuccess) return cleanup(e);
+    if ((e = cudaMemset(p->d_mean, 0, 8 * sizeof(double))) != cudaSuccess) return cleanup(e);
+    const size_t smem_row = mr_row_smem(g.M, p->mr_rows, vb);
+    e = p->prec == PFC_FP64 ? set_smem_mr<double>(smem_row, smem_col) : set_smem_mr<float>(smem_row, smem_col);
+    if (e != cudaSuccess) return cleanup(e);
+    *out = p;
+    return PFC_OK;
+}
+
 }  // namespace
 
 pfc_status pfc::set_error(pfc_status s, const std::string &msg) {
@@ -882,11 +1143,17 @@ pfc_status pfc_plan_create(pfc_plan **out, int ndim, const int64_t *dims, double
     }
     int64_t d[3] = {1, 1, 1};   // (nz, ny, nx)
     for (int i = 0; i < ndim; ++i) d[3 - ndim + i] = dims[i];
+    bool all_pow2 = true, mixed_ok = d[2] % 2 == 0 && mr_extent_ok(d[2] / 2);
     for (int i = 3 - ndim; i < 3; ++i) {
         if (d[i] <= 0) return fail(PFC_ERR_INVALID_ARG, "dims must be positive");
-        if (!is_pow2(d[i]) || d[i] < 16 || d[i] > 4096)
-            return fail(PFC_ERR_UNSUPPORTED, "every extent must be a power of two in [16, 4096]");
+        all_pow2 = all_pow2 && is_pow2(d[i]) && d[i] >= 16 && d[i] <= 4096;
+        mixed_ok = mixed_ok && mr_extent_ok(d[i]);
     }
+    if (!all_pow2 && !mixed_ok)
+        return fail(PFC_ERR_UNSUPPORTED, "extents must be powers of two in [16, 4096], or products of 2, 3, 5 "
+                                         "and 7 in [8, 4096] with nx / 2 one too");
+    if (!all_pow2 && nfields != 1)
+        return fail(PFC_ERR_UNSUPPORTED, "two-field plans need power-of-two extents");
     double alpha = 0.0;
     if (nfields == 2 && coupling) alpha = coupling[1];
     const double kmax = M_PI / dx;
@@ -894,6 +1161,7 @@ pfc_status pfc_plan_create(pfc_plan **out, int ndim, const int64_t *dims, double
     if (min_implicit(ops, nfields, alpha, dt, k2max) <= 0.0)
         return fail(PFC_ERR_UNSTABLE_OPERATOR, "1 + dt k^2 Lk(k) is not positive on the grid");
 
+    if (!all_pow2) return mixed_plan_create(out, ndim, d, dx, dt, ops, precision, stream);
     pfc_plan *p = new pfc_plan();
     p->ndim = ndim;
     p->nz = (int)d[0]; p->ny = (int)d[1]; p->nx = (int)d[2];
@@ -964,6 +1232,11 @@ pfc_status pfc_plan_create(pfc_plan **out, int ndim, const int64_t *dims, double
 
 pfc_status pfc_plan_destroy(pfc_plan *p) {
     if (!p) return PFC_OK;
+    if (!p->destroyed && p->mixed) {
+        cudaStreamSynchronize(p->stream);
+        cudaFree(p->mtw); cudaFree(p->mtwx); cudaFree(p->E);
+        p->mtw = p->mtwx = p->E = nullptr;
+    }
     if (p->destroyed) return fail(PFC_ERR_INVALID_ARG, "plan already destroyed");
     cudaStreamSynchronize(p->stream);
     if (p->graph) cudaGraphExecDestroy(p->graph);
@@ -1012,6 +1285,7 @@ pfc_status pfc_step_adjoint(pfc_plan *p, const void *psi_n, const void *lam_next
                             double *dr) {
     if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
     if (!psi_n || !lam_next || !lam_out || !dr) return fail(PFC_ERR_INVALID_ARG, "null pointer");
+    if (p->mixed) return fail(PFC_ERR_UNSUPPORTED, "the adjoint step is built for power-of-two grids");
     return p->prec == PFC_FP64 ? adjoint_impl<double>(p, psi_n, lam_next, lam_out, dr)
                                : adjoint_impl<float>(p, psi_n, lam_next, lam_out, dr);
 }
@@ -1045,6 +1319,8 @@ pfc_status pfc_set_integrator(pfc_plan *p, int scheme, double S) {
     if (scheme != PFC_SEMI_IMPLICIT && scheme != PFC_STABILIZED && scheme != PFC_SBDF2)
         return fail(PFC_ERR_INVALID_ARG, "unknown integrator");
     if (!std::isfinite(S) || S < 0) return fail(PFC_ERR_INVALID_ARG, "S must be finite and >= 0");
+    if (scheme != PFC_SEMI_IMPLICIT && p->mixed)
+        return fail(PFC_ERR_UNSUPPORTED, "mixed-radix grids step with the semi-implicit scheme");
     if (scheme != PFC_SEMI_IMPLICIT && p->nfields != 1)
         return fail(PFC_ERR_UNSUPPORTED, "the alternative integrators are built for single-field plans");
     // the implicit factor of the scheme must stay positive: 1 + dt k^2 (Lk + S) (stabilised, Lk
@@ -1163,7 +1439,11 @@ pfc_status pfc_sync(pfc_plan *p) {
 pfc_status pfc_plan_info(pfc_plan *p, int32_t *tiles, int64_t *scratch_bytes) {
     if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
     const Geom &g = p->t.g;
-    if (tiles) {
+    if (tiles && p->mixed) {
+        // one pass per axis: Py = Pz = 0, W = the y pass' columns a block, gpc = the x pass' rows a block
+        const int32_t v[11] = {0, 0, 0, 0, p->mr_W[1], p->mr_rows, 32 * p->mr_rows, 32 * p->mr_W[1], 0, 1, 1};
+        std::memcpy(tiles, v, sizeof(v));
+    } else if (tiles) {
         const int32_t v[11] = {g.Py, g.Pz, g.Qy, g.Qz, g.W, g.gpc, p->t.nt_row, p->t.nt_line, p->t.row_cs,
                                g.Ry, g.Rz};
         std::memcpy(tiles, v, sizeof(v));
@@ -1176,6 +1456,7 @@ pfc_status pfc_plan_autotune(pfc_plan *p, int max_candidates, int trial_steps, c
                              double *best_ms_out) {
     if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
     if (max_candidates < 1 || trial_steps < 1) return fail(PFC_ERR_INVALID_ARG, "max_candidates and trial_steps must be >= 1");
+    if (p->mixed) return fail(PFC_ERR_UNSUPPORTED, "mixed-radix plans have one launch shape");
     const size_t smem_max = smem_optin();
     if (!smem_max) return fail(PFC_ERR_CUDA, "device query failed");
     const std::string key = tune_key(p);

@@ -156,6 +156,41 @@ template <typename R> void launch_hyd_real(cudaStream_t s, int kind, int64_t n, 
 }
 
 template <typename R>
+void launch_mr_row(cudaStream_t s, int mode, const MrGeom &g, const MrArgs<R> &a, const void *in, void *out,
+                   void *E, int rows_per_block) {
+    const int64_t rows = (int64_t)g.ny * g.nz;
+    const unsigned blocks = (unsigned)((rows + rows_per_block - 1) / rows_per_block);
+    const int threads = 32 * rows_per_block;
+    const size_t smem = mr_row_smem(g.M, rows_per_block, sizeof(typename VT<R>::V));
+    if (mode == MR_ROW_CUBE) k_mr_row<R, MR_ROW_CUBE><<<blocks, threads, smem, s>>>(g, a, in, out, E);
+    else if (mode == MR_ROW_FWD) k_mr_row<R, MR_ROW_FWD><<<blocks, threads, smem, s>>>(g, a, in, out, E);
+    else k_mr_row<R, MR_ROW_INV><<<blocks, threads, smem, s>>>(g, a, in, out, E);
+}
+template <typename R>
+void launch_mr_col(cudaStream_t s, int mode, const MrGeom &g, const MrArgs<R> &a, int axis, int W, int ncols,
+                   const void *in, void *out) {
+    const dim3 grid((ncols + W - 1) / W, axis == 1 ? g.nz : g.ny);
+    const size_t smem = mr_col_smem(g.ax[axis].n, W, sizeof(typename VT<R>::V));
+    if (mode == MR_COL_FWD) k_mr_col<R, MR_COL_FWD><<<grid, 32 * W, smem, s>>>(g, a, axis, ncols, in, out);
+    else if (mode == MR_COL_INV) k_mr_col<R, MR_COL_INV><<<grid, 32 * W, smem, s>>>(g, a, axis, ncols, in, out);
+    else k_mr_col<R, MR_COL_UPDATE><<<grid, 32 * W, smem, s>>>(g, a, axis, ncols, in, out);
+}
+template <typename R>
+void launch_mr_edges(cudaStream_t s, const MrGeom &g, const void *E, void *S, double scale) {
+    using V = typename VT<R>::V;
+    k_mr_edges<R><<<304, 256, 0, s>>>(g, reinterpret_cast<const V *>(E), reinterpret_cast<V *>(S), (R)scale);
+}
+template <typename R> cudaError_t set_smem_mr(size_t row, size_t col) {
+    cudaError_t e;
+    if ((e = allow_smem(k_mr_row<R, MR_ROW_CUBE>, row)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_mr_row<R, MR_ROW_FWD>, row)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_mr_row<R, MR_ROW_INV>, row)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_mr_col<R, MR_COL_FWD>, col)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_mr_col<R, MR_COL_INV>, col)) != cudaSuccess) return e;
+    return allow_smem(k_mr_col<R, MR_COL_UPDATE>, col);
+}
+
+template <typename R>
 void launch_batch_mean(cudaStream_t s, const R *base, const int64_t *off, const int64_t *n,
                        int members, double *mean, int *status) {
     k_batch_mean<R><<<members, RED_THREADS, 0, s>>>(base, off, n, mean, status);
@@ -190,6 +225,12 @@ void launch_reduce_spec(cudaStream_t s, const Geom &g, OpDev op, double dx, cons
     template void launch_hyd_spec<R>(cudaStream_t, int, const HydArgs<R> &, int64_t, void *, const void *, \
                                      const void *, int);                                  \
     template void launch_hyd_real<R>(cudaStream_t, int, int64_t, const R *, const R *, R *); \
+    template void launch_mr_row<R>(cudaStream_t, int, const MrGeom &, const MrArgs<R> &, const void *, void *, \
+                                   void *, int);                                            \
+    template void launch_mr_col<R>(cudaStream_t, int, const MrGeom &, const MrArgs<R> &, int, int, int,  \
+                                   const void *, void *);                                   \
+    template void launch_mr_edges<R>(cudaStream_t, const MrGeom &, const void *, void *, double); \
+    template cudaError_t set_smem_mr<R>(size_t, size_t);                                   \
     template void launch_batch_mean<R>(cudaStream_t, const R *, const int64_t *,           \
                                        const int64_t *, int, double *, int *);             \
     template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t,  \

@@ -13,6 +13,7 @@
 #include "pfc_onchip.cuh"
 #include "pfc_adjoint_row.cuh"
 #include "pfc_hydro.cuh"
+#include "pfc_mixed.cuh"
 
 namespace pfc {
 
@@ -66,6 +67,16 @@ template <typename R>
 void launch_hyd_spec(cudaStream_t s, int kind, const HydArgs<R> &a, int64_t n, void *x, const void *y,
                      const void *z, int axis);
 template <typename R> void launch_hyd_real(cudaStream_t s, int kind, int64_t n, const R *p, const R *q, R *out);
+// passes of the mixed-radix schedule (pfc_mixed.cuh)
+template <typename R>
+void launch_mr_row(cudaStream_t s, int mode, const MrGeom &g, const MrArgs<R> &a, const void *in, void *out,
+                   void *E, int rows_per_block);
+template <typename R>
+void launch_mr_col(cudaStream_t s, int mode, const MrGeom &g, const MrArgs<R> &a, int axis, int W, int ncols,
+                   const void *in, void *out);
+template <typename R>
+void launch_mr_edges(cudaStream_t s, const MrGeom &g, const void *E, void *S, double scale);
+template <typename R> cudaError_t set_smem_mr(size_t row, size_t col);
 // middle pass of a three-pass plan (g.R > 1): dir -1 forward, +1 inverse (pfc_mid.cuh)
 template <typename R> void launch_mid(const LaunchCfg &c, int dir, const MidArgs<R> &a);
 
@@ -112,6 +123,12 @@ template <typename R> cudaError_t set_smem_attrs_fixed(const LaunchCfg &c);
     extern template void launch_hyd_spec<R>(cudaStream_t, int, const HydArgs<R> &, int64_t, void *, \
                                             const void *, const void *, int);                    \
     extern template void launch_hyd_real<R>(cudaStream_t, int, int64_t, const R *, const R *, R *); \
+    extern template void launch_mr_row<R>(cudaStream_t, int, const MrGeom &, const MrArgs<R> &, const void *, \
+                                          void *, void *, int);                                  \
+    extern template void launch_mr_col<R>(cudaStream_t, int, const MrGeom &, const MrArgs<R> &, int, int, \
+                                          int, const void *, void *);                            \
+    extern template void launch_mr_edges<R>(cudaStream_t, const MrGeom &, const void *, void *, double); \
+    extern template cudaError_t set_smem_mr<R>(size_t, size_t);                                  \
     extern template void launch_batch_mean<R>(cudaStream_t, const R *, const int64_t *,         \
                                               const int64_t *, int, double *, int *);           \
     extern template void launch_reduce_real<R>(cudaStream_t, int, const R *, const R *, int64_t, \

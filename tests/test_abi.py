@@ -65,7 +65,11 @@ def test_host_side_validation(lib):
     assert _create(lib, (128, 128), dx=0.0) == 1                        # dx <= 0
     assert _create(lib, (128, 128), dt=-1.0) == 1                       # dt <= 0
     assert _create(lib, (128,)) == 1                                    # ndim 1
-    assert _create(lib, (100, 128)) == 2                                # not a power of two
+    assert _create(lib, (88, 128)) == 2                                 # 88 = 8 * 11
+    assert _create(lib, (128, 130)) == 2                                # nx / 2 = 65 = 5 * 13
+    assert _create(lib, (128, 12)) == 2                                 # nx / 2 below 8
+    assert _create(lib, (96, 96), ops=[binding.make_op(0, -0.25), binding.make_op(0, -0.25)],
+                   nfields=2, coupling=0.1) == 2                        # two fields, not powers of two
     assert _create(lib, (8192, 128)) == 2                               # too large
     assert _create(lib, (128, 128), nfields=3) == 2                     # nfields
     assert _create(lib, (128, 128), prec=7) == 1                        # precision
