@@ -242,14 +242,15 @@ template <typename R> pfc_status mixed_c2r_impl(pfc_plan *p, const void *in, voi
     return PFC_OK;
 }
 
-// radices of n in {8, 4, 2, 7, 5, 3}; false when n has another prime factor
+// radices of n, the odd ones first (7, 5, 3), then 8, 4, 2; false when n has another prime
+// factor
 bool mr_factor(int n, std::vector<int> &rad) {
     rad.clear();
+    for (int r : {7, 5, 3})
+        while (n % r == 0) { rad.push_back(r); n /= r; }
     while (n % 8 == 0) { rad.push_back(8); n /= 8; }
     if (n % 4 == 0) { rad.push_back(4); n /= 4; }
     if (n % 2 == 0) { rad.push_back(2); n /= 2; }
-    for (int r : {7, 5, 3})
-        while (n % r == 0) { rad.push_back(r); n /= r; }
     return n == 1 && (int)rad.size() <= MR_MAXST;
 }
 bool mr_extent_ok(int64_t n) {

@@ -14,9 +14,9 @@
 // m < r, multiplies by W_{r Ns}^{m (b mod Ns)}, and stores the r-point DFT at
 // (b - b mod Ns) r + b mod Ns + m Ns). One warp owns a line: the stages alternate between two
 // shared-memory buffers (out of place, a __syncwarp between stages), a lane takes butterflies
-// b = lane, lane + 32, ... one at a time, so a thread holds at most 8 values. Buffers are padded
-// by one slot every 32 (index i at i + i / 32): the stride-r stores of the first stages then hit
-// every bank. Twiddles are FP64-generated on the host (rounded once for FP32); the roots of the
+// b = lane, lane + 32, ... one at a time, so a thread holds at most 8 values. The odd radices
+// come first: the stride-r stores of the first stage (Ns = 1) then hit distinct banks, and once
+// Ns > 1 a warp's stores are runs of consecutive elements. Reads are always consecutive. Twiddles are FP64-generated on the host (rounded once for FP32); the roots of the
 // odd radices are constants of the small-DFT code.
 //
 // Global memory is read in batches: a thread issues MR_U loads before it stores any of them to
@@ -106,35 +106,37 @@ __device__ __forceinline__ void mr_dft(V (&x)[R]) {
     }
 }
 
-__host__ __device__ __forceinline__ int mr_pad(int i) { return i + (i >> 5); }
-// slots of a padded line buffer of n values
-__host__ __device__ __forceinline__ int mr_slots(int n) { return n + (n >> 5) + 1; }
 
-// one stage of radix R, src -> dst (padded buffers), the butterflies strided over the warp
+// one stage of radix R, src -> dst, the butterflies strided over the warp: butterfly
+// b = q Ns + k (lane, lane + 32, ...), with q and k stepped, not divided, from one b to the next
 template <int S, int R, typename V>
 __device__ __forceinline__ void mr_stage(const V *src, V *dst, const MrAxis &ax, int s, const V *tw, int lane) {
     const int nb = ax.n / R, Ns = ax.ns[s];
     const V *t = tw + ax.twoff[s];
-    const float inv = 1.0f / (float)Ns;
+    const int dq = 32 / Ns, dk = 32 - dq * Ns;
+    int q = lane / Ns, k = lane - q * Ns;
     for (int b = lane; b < nb; b += 32) {
         V v[R];
 #pragma unroll
-        for (int m = 0; m < R; ++m) v[m] = src[mr_pad(b + m * nb)];
-        // k = b mod Ns (the float quotient is exact or one off, corrected)
-        int k = b - (int)((float)b * inv) * Ns;
-        k = k >= Ns ? k - Ns : (k < 0 ? k + Ns : k);
+        for (int m = 0; m < R; ++m) v[m] = src[b + m * nb];
         if (Ns > 1) {
 #pragma unroll
             for (int m = 1; m < R; ++m) v[m] = ctw<S>(v[m], __ldg(&t[m * Ns + k]));
         }
         mr_dft<S, R>(v);
-        const int o = (b - k) * R + k;
+        V *d = dst + q * (R * Ns) + k;
 #pragma unroll
-        for (int m = 0; m < R; ++m) dst[mr_pad(o + m * Ns)] = v[m];
+        for (int m = 0; m < R; ++m) d[m * Ns] = v[m];
+        q += dq;
+        k += dk;
+        if (k >= Ns) {
+            k -= Ns;
+            ++q;
+        }
     }
 }
 
-// The transform of one line by one warp: input in buffer a (natural order, padded), b the other
+// The transform of one line by one warp: input in buffer a (natural order), b the other
 // buffer; returns the buffer that holds the result. Every lane of the warp calls it.
 template <int S, typename V>
 __device__ __forceinline__ V *mr_fft(V *a, V *b, const MrAxis &ax, const V *tw, int lane) {
@@ -159,7 +161,7 @@ enum { MR_ROW_CUBE = 0, MR_ROW_FWD = 1, MR_ROW_INV = 2 };
 
 constexpr int MR_U = 8;   // global loads a thread issues before it stores them to shared memory
 
-// buf[mr_pad(i)] = src[i], i < cnt, by the 32 lanes of a warp in batches of MR_U loads a lane
+// buf[i] = src[i], i < cnt, by the 32 lanes of a warp in batches of MR_U loads a lane
 template <typename V>
 __device__ __forceinline__ void mr_warp_load(V *buf, const V *src, int cnt, int lane) {
     for (int i0 = lane; i0 < cnt; i0 += 32 * MR_U) {
@@ -172,13 +174,13 @@ __device__ __forceinline__ void mr_warp_load(V *buf, const V *src, int cnt, int 
 #pragma unroll
         for (int u = 0; u < MR_U; ++u) {
             const int i = i0 + 32 * u;
-            if (i < cnt) buf[mr_pad(i)] = t[u];
+            if (i < cnt) buf[i] = t[u];
         }
     }
 }
 
-// The x pass: one warp a row (z, y), blockDim.x / 32 rows a block, two padded buffers of M + 1
-// values a row in shared memory.
+// The x pass: one warp a row (z, y), blockDim.x / 32 rows a block, two buffers of M + 1 values a
+// row in shared memory.
 //   MR_ROW_CUBE  in: rows of T (y/z in row space) -> out: C rows = F_x(psi^3 - mean^3); E gets the
 //                real parts of the kx = 0 and nx/2 bins (for the Hermitian projection)
 //   MR_ROW_FWD   in: real rows -> out: scale F_x(psi - mean)
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(256) k_mr_row(const __grid_constant__ MrGeom g
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;   // row index z ny + y
     if (r >= (int64_t)g.ny * g.nz) return;   // a whole warp; the kernel has no block barrier
-    const int M = g.M, L = mr_slots(M + 1);
+    const int M = g.M, L = (M + 1);
     V *A = reinterpret_cast<V *>(smraw) + (size_t)warp * 2 * L;
     V *B = A + L;
     const R mean = a.mean ? (R)a.mean[0] : (R)0;
@@ -202,8 +204,8 @@ __global__ void __launch_bounds__(256) k_mr_row(const __grid_constant__ MrGeom g
         mr_warp_load(A, reinterpret_cast<const V *>(in) + r * M, M, lane);
         __syncwarp();
         for (int i = lane; i < M; i += 32) {
-            const V v = A[mr_pad(i)];
-            A[mr_pad(i)] = V{v.x - mean, v.y - mean};
+            const V v = A[i];
+            A[i] = V{v.x - mean, v.y - mean};
         }
     } else {
         // the row's M + 1 bins into B, then the real-transform pre-processing B -> A
@@ -211,16 +213,16 @@ __global__ void __launch_bounds__(256) k_mr_row(const __grid_constant__ MrGeom g
         __syncwarp();
         if (MODE == MR_ROW_CUBE && lane < 2) {
             V *e = reinterpret_cast<V *>(E);
-            e[2 * r + lane] = V{B[mr_pad(lane ? M : 0)].x, (R)0};
+            e[2 * r + lane] = V{B[lane ? M : 0].x, (R)0};
         }
         for (int kk = lane; kk < npairs; kk += 32) {
             const bool k0 = kk == 0, self = 2 * kk == M;
             const int ca = kk, cb = k0 ? M : M - kk;
-            const V xa = B[mr_pad(ca)], xb = self ? xa : B[mr_pad(cb)];
+            const V xa = B[ca], xb = self ? xa : B[cb];
             V za, zb;
             c2r_pre_pair<V, R>(xa, xb, __ldg(&a.twx[ca]), k0, za, zb);
-            A[mr_pad(ca)] = za;
-            if (!k0 && !self) A[mr_pad(cb)] = zb;
+            A[ca] = za;
+            if (!k0 && !self) A[cb] = zb;
         }
     }
     __syncwarp();
@@ -232,8 +234,8 @@ __global__ void __launch_bounds__(256) k_mr_row(const __grid_constant__ MrGeom g
     if (MODE == MR_ROW_INV) {
         V *dst = reinterpret_cast<V *>(out) + r * M;
         for (int i = lane; i < M; i += 32) {
-            const V v = X[mr_pad(i)];
-            __stcg(reinterpret_cast<V *>(&dst[i]), V{(v.x + mean) * a.scale, (v.y + mean) * a.scale});
+            const V v = X[i];
+            __stcg(&dst[i], V{(v.x + mean) * a.scale, (v.y + mean) * a.scale});
         }
         return;
     }
@@ -241,8 +243,8 @@ __global__ void __launch_bounds__(256) k_mr_row(const __grid_constant__ MrGeom g
         // (v + mean)^3 - mean^3 with v = psi - mean
         const R c3 = (R)3 * mean * mean, b3 = (R)3 * mean;
         for (int i = lane; i < M; i += 32) {
-            const V v = X[mr_pad(i)];
-            X[mr_pad(i)] = V{v.x * (c3 + v.x * (b3 + v.x)), v.y * (c3 + v.y * (b3 + v.y))};
+            const V v = X[i];
+            X[i] = V{v.x * (c3 + v.x * (b3 + v.x)), v.y * (c3 + v.y * (b3 + v.y))};
         }
         __syncwarp();
     }
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(256) k_mr_row(const __grid_constant__ MrGeom g
     for (int kk = lane; kk < npairs; kk += 32) {
         const bool k0 = kk == 0, self = 2 * kk == M;
         const int ca = kk, cb = k0 ? M : M - kk;
-        const V za = Z[mr_pad(ca)], zb = (k0 || self) ? za : Z[mr_pad(cb)];
+        const V za = Z[ca], zb = (k0 || self) ? za : Z[cb];
         V xa, xb;
         r2c_post_pair<V, R>(za, zb, __ldg(&a.twx[ca]), k0, xa, xb);
         __stcg(&dst[ca], cscale(xa, sc));
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(256) k_mr_row(const __grid_constant__ MrGeom g
 }
 
 // column stride of the column pass' buffers (odd, so that a row of W columns hits W banks)
-__host__ __device__ __forceinline__ int mr_col_stride(int n) { return mr_slots(n) | 1; }
+__host__ __device__ __forceinline__ int mr_col_stride(int n) { return n | 1; }
 
 enum { MR_COL_FWD = 0, MR_COL_INV = 1, MR_COL_UPDATE = 2 };
 
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(512) k_mr_col(const __grid_constant__ MrGeom g
 #pragma unroll
         for (int u = 0; u < MR_U; ++u) {
             const int e = e0 + u * nt, i = e >> lW, w = e & (W - 1);
-            if (e < total) A[w * CS + mr_pad(i)] = t[u];
+            if (e < total) A[w * CS + i] = t[u];
         }
     }
     __syncthreads();
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(512) k_mr_col(const __grid_constant__ MrGeom g
         for (int u = 0; u < MR_U; ++u) {
             const int e = e0 + u * nt, i = e >> lW, w = e & (W - 1);
             if (e >= total || w >= wv) continue;
-            const V c = res[w * CS + mr_pad(i)];
+            const V c = res[w * CS + i];
             const int64_t idx = base0 + i * step + w;
             if (MODE != MR_COL_UPDATE) {
                 __stcg(&dst[idx], cscale(c, a.scale));
@@ -355,7 +357,7 @@ __global__ void k_mr_edges(const MrGeom g, const typename VT<R>::V *E, typename 
 }
 
 // shared-memory bytes of the x pass (rows a block) and of a column pass (W columns of length n)
-inline size_t mr_row_smem(int M, int rows, size_t vb) { return (size_t)rows * 2 * mr_slots(M + 1) * vb; }
+inline size_t mr_row_smem(int M, int rows, size_t vb) { return (size_t)rows * 2 * (M + 1) * vb; }
 inline size_t mr_col_smem(int n, int W, size_t vb) { return (size_t)W * 2 * mr_col_stride(n) * vb; }
 
 }  // namespace pfc
