@@ -76,8 +76,11 @@ CONFIGS = {
               dt=0.1, inner=10, sweeps=5),
     "4a": dict(desc="1024 batched 2D one-mode domains, nx, ny from {64,128,256,512}, r~U[-0.4,-0.1], "
                     "mean~U[-0.4,-0.2] (seed 4), noise 0.01, dt=0.5, FP32-mixed; 20 time steps per bench "
-                    "step (graph of per-size-class branches)",
+                    "step, tiles and schedule autotuned",
                kind="batch", prec="fp32", dt=0.5, inner=20, sweeps=5, autotune=True),
+    "4p": dict(desc="1024 batched 2D one-mode domains as config 4a, FP32-mixed; 20 time steps per bench step "
+                    "in one persistent cooperative launch (replayed as a one-node CUDA graph)",
+               kind="batch", prec="fp32", dt=0.5, inner=20, sweeps=5, schedule="persistent"),
     "4b": dict(desc="coupled density/composition pair 256^3 FP32-mixed, alpha=0.1, one-mode r=-0.25 "
                     "for both, means -0.25/-0.2, noise 0.01 (seeds 5, 6), dt=0.5; 10 time steps per "
                     "bench step", kind="pair", dims=(256, 256, 256), prec="fp32", dt=0.5, inner=10,
@@ -150,10 +153,16 @@ def run_config(args):
         state = torch.from_numpy(np.concatenate(parts)).to(device=dev, dtype=dtype)
         npts = state.numel()
         run = lambda: obj.step(state, c["inner"])
+        if c.get("schedule") == "persistent":
+            obj.set_schedule("persistent", threads=int(os.environ.get("PFC_BENCH_PB_THREADS", "256")),
+                             onchip_smem_max=int(os.environ.get("PFC_BENCH_PB_ONCHIP", "0")),
+                             onchip_block_share=float(os.environ.get("PFC_BENCH_PB_SHARE", "-1")))
+            extra["schedule"] = obj.schedule_info()
         if c.get("autotune") and not args.no_autotune:
             # tiles of every size class chosen by measurement (untimed)
             extra["autotune"] = {"candidates": 6, "trial_steps": 8,
                                  "ms_per_step_sum_of_classes": obj.autotune(6, 8)}
+            extra["schedule"] = obj.schedule_info()
         extra["classes"] = [[k[f] for f in ("ny", "nx", "members", "Py", "W", "gpc", "threads_line")]
                             for k in obj.info()]
         extra["classes_fields"] = ["ny", "nx", "members", "Py", "W", "gpc", "threads_line"]

@@ -285,7 +285,8 @@ const char *pfc_last_error(void);
 /* ---------------------------------------------------------------------------------- */
 /* Batched ensemble: many independent 2D one-mode domains of uneven sizes. Domains of    */
 /* one size form a class stepped by one launch per pass (a member index per block);      */
-/* every class is a branch of a CUDA graph captured once and replayed.                   */
+/* every class is a branch of a CUDA graph captured once and replayed; or the whole call */
+/* runs as one persistent launch (pfc_batch_set_schedule).                               */
 /* ---------------------------------------------------------------------------------- */
 typedef struct pfc_batch pfc_batch;
 
@@ -305,8 +306,11 @@ pfc_status pfc_batch_step(pfc_batch *batch, void *packed_state, int64_t nsteps);
 
 /* Autotune the tiling of every size class as pfc_plan_autotune does, each class timed alone on
  * trial_steps of its steps on zero fields; *best_ms_out (host, may be NULL) = the sum over
- * classes of the chosen ms per step. The step graph is captured again at the next
- * pfc_batch_step. Synchronises. Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+ * classes of the chosen ms per step. Then the schedule (pfc_batch_set_schedule): whole calls of
+ * trial_steps steps on a zero state with the graph schedule and the persistent one at 256 and
+ * 128 threads a block, the fastest kept (pfc_batch_schedule_info reports it). The step graph is
+ * captured again at the next pfc_batch_step. Synchronises. Errors: INVALID_ARG, UNSUPPORTED,
+ * CUDA. */
 pfc_status pfc_batch_autotune(pfc_batch *batch, int max_candidates, int trial_steps,
                               double *best_ms_out);
 
@@ -318,6 +322,48 @@ pfc_status pfc_batch_info(pfc_batch *batch, int32_t *classes_out, int max_classe
 
 /* Per-domain mass (mean), out_host[ndomains]. Synchronises. */
 pfc_status pfc_batch_mass(pfc_batch *batch, const void *packed_state, double *out_host);
+
+/* Schedules of pfc_batch_step.
+ * PFC_BATCH_GRAPH: per size class one launch per pass, the classes as branches of a CUDA
+ *   graph (above).
+ * PFC_BATCH_PERSISTENT: the whole call in one cooperative launch (all blocks resident),
+ *   replayed as a CUDA graph of that launch while the state pointer and nsteps stay the same.
+ *   The launch's blocks of `threads` (128, 256 or 512) threads split in two groups. Blocks of the
+ *   first group take on-chip members one at a time and run all their steps in shared memory:
+ *   classes with both extents <= 128 that have no tiling of the block size, and (when
+ *   onchip_smem_max > 0) those whose two half spectra take at most onchip_smem_max bytes. onchip_block_share in [0, 1] is the share of blocks in that group (< 0: the on-chip
+ *   members' share of grid points). The other blocks take the two-pass members' work items
+ *   (one row-pass block or one line-pass tile of one member each, the per-class launches'
+ *   block work) from one queue per phase, meeting at a grid barrier between the phases: the
+ *   means, the entry pass, nsteps x (psi^3 row pass, update pass), the exit pass. The shared
+ *   memory of every block is the largest the classes need, so fewer blocks fit an SM when an
+ *   on-chip class needs much. Every barrier wait is bounded (pfc_batch_set_wait_limit); a wait
+ *   that runs out ends the launch with PFC_ERR_TIMEOUT latched for pfc_batch_sync, and the
+ *   state is then undefined. The arithmetic per member is that of the plans (Eq. (6) and the
+ *   update of Listing 1 in the two-pass form), so both schedules agree to rounding.
+ * Setting a schedule synchronises the batch's stream and allocates what it needs; when it
+ * fails the batch keeps its schedule.
+ * Errors: INVALID_ARG, UNSUPPORTED (more than 36 size classes, or a class the launch cannot
+ * step), OUT_OF_MEMORY, CUDA. */
+enum { PFC_BATCH_GRAPH = 0, PFC_BATCH_PERSISTENT = 1 };
+pfc_status pfc_batch_set_schedule(pfc_batch *batch, int schedule, int threads,
+                                  int64_t onchip_smem_max, double onchip_block_share);
+
+/* info_out[10] (host) = {schedule, threads, blocks, on-chip blocks, shared memory bytes a block,
+ * captured as a graph (1) or launched directly (0), row items, line items, on-chip items,
+ * mean items} of the persistent schedule (zeros before it is first set up). */
+pfc_status pfc_batch_schedule_info(pfc_batch *batch, int64_t *info_out);
+
+/* Bound of every grid-barrier wait of the persistent launch, in seconds of SM clock (default
+ * 2 s; a phase takes well under a millisecond). extra_arrivals (normally 0) makes every
+ * barrier wait for that many blocks beyond those that exist, so that every wait runs out:
+ * an aid to test the timeout path without a device fault. Synchronises. */
+pfc_status pfc_batch_set_wait_limit(pfc_batch *batch, double seconds, int extra_arrivals);
+
+/* Synchronises the batch's stream and returns the latched device status (cleared on read):
+ * PFC_ERR_TIMEOUT when a persistent launch's barrier wait ran out, PFC_ERR_NONFINITE when a
+ * mean reduction met NaN or Inf, else PFC_OK. */
+pfc_status pfc_batch_sync(pfc_batch *batch);
 
 #ifdef __cplusplus
 }

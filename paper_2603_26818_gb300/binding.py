@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "PFC_OK", 1: "PFC_ERR_INVALID_ARG", 2: "PFC_ERR_UNSUPPORTED",
 PFC_FP64, PFC_FP32_MIXED = 0, 1
 PFC_ONE_MODE, PFC_TWO_MODE = 0, 1
 PFC_SEMI_IMPLICIT, PFC_STABILIZED, PFC_SBDF2 = 0, 1, 2
+PFC_BATCH_GRAPH, PFC_BATCH_PERSISTENT = 0, 1
 
 # every extern "C" symbol of include/pfc.h
 EXPORTS = ["pfc_plan_create", "pfc_plan_destroy", "pfc_step", "pfc_fft_r2c", "pfc_fft_c2r",
@@ -30,7 +31,8 @@ EXPORTS = ["pfc_plan_create", "pfc_plan_destroy", "pfc_step", "pfc_fft_r2c", "pf
            "pfc_set_integrator", "pfc_record_bytes", "pfc_step_record", "pfc_adjoint_segment",
            "pfc_hydro_create", "pfc_hydro_step", "pfc_hydro_destroy",
            "pfc_status_string", "pfc_last_error", "pfc_batch_create", "pfc_batch_destroy",
-           "pfc_batch_step", "pfc_batch_mass"]
+           "pfc_batch_step", "pfc_batch_mass", "pfc_batch_set_schedule", "pfc_batch_schedule_info",
+           "pfc_batch_set_wait_limit", "pfc_batch_sync"]
 
 
 class PfcError(RuntimeError):
@@ -87,6 +89,10 @@ def load_library(path: str = LIB_PATH):
         "pfc_batch_destroy": [vp],
         "pfc_batch_step": [vp, vp, i64],
         "pfc_batch_mass": [vp, vp, P(dbl)],
+        "pfc_batch_set_schedule": [vp, cint, cint, i64, dbl],
+        "pfc_batch_schedule_info": [vp, P(i64)],
+        "pfc_batch_set_wait_limit": [vp, dbl, cint],
+        "pfc_batch_sync": [vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -380,6 +386,30 @@ class Batch:
         check(lib.pfc_batch_info(self._h, buf, n.value, ctypes.byref(n)))
         keys = ["ny", "nx", "members", "Py", "W", "gpc", "threads_row", "threads_line", "Qy"]
         return [dict(zip(keys, list(buf[9 * i:9 * i + 9]))) for i in range(n.value)]
+
+    def set_schedule(self, schedule: str = "persistent", threads: int = 128, onchip_smem_max: int = 0,
+                     onchip_block_share: float = -1.0):
+        """pfc_batch_set_schedule: "graph" (per-class launches in graph branches) or "persistent"
+        (the whole call in one cooperative launch)."""
+        code = {"graph": PFC_BATCH_GRAPH, "persistent": PFC_BATCH_PERSISTENT}[schedule]
+        check(load_library().pfc_batch_set_schedule(self._h, code, int(threads), int(onchip_smem_max),
+                                                    float(onchip_block_share)))
+
+    def schedule_info(self):
+        """pfc_batch_schedule_info as a dict."""
+        buf = (ctypes.c_int64 * 10)()
+        check(load_library().pfc_batch_schedule_info(self._h, buf))
+        keys = ["schedule", "threads", "blocks", "onchip_blocks", "smem", "graph", "row_items",
+                "line_items", "onchip_items", "mean_items"]
+        return dict(zip(keys, list(buf)))
+
+    def set_wait_limit(self, seconds: float = 2.0, extra_arrivals: int = 0):
+        """pfc_batch_set_wait_limit: bound of the persistent launch's barrier waits."""
+        check(load_library().pfc_batch_set_wait_limit(self._h, float(seconds), int(extra_arrivals)))
+
+    def sync(self):
+        """pfc_batch_sync: raises PfcError with the latched device status (TIMEOUT, NONFINITE)."""
+        check(load_library().pfc_batch_sync(self._h))
 
     def mass(self, state: torch.Tensor):
         out = (ctypes.c_double * self.nd)()

@@ -13,8 +13,11 @@
 // graph. PFC_ONCHIP=0 keeps every class on the two-pass path (to compare the two).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
+#include <type_traits>
 
 #include "pfc_host.h"
 
@@ -36,7 +39,12 @@ struct BatchClass {
     size_t cap = 0;             // bytes allocated for each of X and C
     bool onchip = false;        // stepped in shared memory by k_onchip (no X, C)
     size_t smem_oc = 0;         // its shared memory per block
+    // persistent schedule: the class's tiling there (line tiles of the launch's block size) or
+    // on-chip stepping inside the launch
+    Tiles tp{};
+    bool p_onchip = false;
 };
+
 
 }  // namespace
 
@@ -56,6 +64,27 @@ struct pfc_batch {
     cudaEvent_t ev_fork = nullptr;
     std::vector<cudaEvent_t> ev_join;
     bool destroyed = false;
+    // persistent schedule (pfc_batch_set_schedule)
+    int sched = PFC_BATCH_GRAPH;
+    int p_nt = 128;                  // threads a block
+    size_t p_oc_max = 0;             // largest on-chip shared memory allowed in the launch
+    double p_oc_share = -1.0;        // share of the blocks for on-chip members (< 0: by points)
+    bool p_ready = false;            // tilings, items and arrays prepared
+    int p_grid = 0, p_oc_blocks = 0;
+    size_t p_smem = 0;
+    int n_mean = 0, n_row = 0, n_line = 0, n_oc = 0;
+    int2 *d_mean_items = nullptr, *d_oc_items = nullptr;
+    int4 *d_row_items = nullptr, *d_line_items = nullptr;
+    unsigned *d_sync = nullptr;
+    long long p_budget = 0;          // clock64 cycles a barrier wait may take
+    int p_extra = 0;
+    void *p_args = nullptr;          // PbArgs<R> of the launch (host copy)
+    cudaGraph_t p_graph = nullptr;
+    cudaGraphExec_t p_exec = nullptr;
+    const void *p_state = nullptr;   // the state and step count the graph was captured for
+    int64_t p_nsteps = -1;
+    bool p_graph_ok = true;          // false once capturing the launch failed (launched directly)
+    cudaStream_t p_cap = nullptr;
 };
 
 namespace {
@@ -130,7 +159,10 @@ template <typename R> pfc_status enqueue_steps(pfc_batch *b, cudaStream_t origin
     return PFC_OK;
 }
 
+template <typename R> pfc_status persist_step(pfc_batch *b, void *state, int64_t nsteps);
+
 template <typename R> pfc_status batch_step_impl(pfc_batch *b, void *state, int64_t nsteps) {
+    if (b->sched == PFC_BATCH_PERSISTENT) return persist_step<R>(b, state, nsteps);
     launch_batch_mean<R>(b->stream, reinterpret_cast<const R *>(state), b->d_off, b->d_n, b->nd,
                          b->d_mean, b->d_status);
     for (BatchClass &c : b->cls) {
@@ -211,6 +243,8 @@ template <typename R> pfc_status batch_step_impl(pfc_batch *b, void *state, int6
 
 // Autotune one class: time up to max_candidates tilings (the planner's order, its own choice
 // first) on trial_steps class steps of zero fields (a fixed point of the step), keep the fastest.
+template <typename R> void free_persist(pfc_batch *b);
+
 template <typename R>
 pfc_status tune_class(pfc_batch *b, BatchClass &c, int max_candidates, int trial_steps, size_t smem_max,
                       double *ms_out) {
@@ -247,6 +281,7 @@ pfc_status tune_class(pfc_batch *b, BatchClass &c, int max_candidates, int trial
             c.X = x;
             c.C = y;
             c.cap = need;
+            free_persist<R>(b);   // its launch arguments held the old arrays
         }
         if (e == cudaSuccess) e = cudaMemsetAsync(c.X, 0, c.cap, b->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(c.C, 0, c.cap, b->stream);
@@ -284,6 +319,355 @@ pfc_status tune_class(pfc_batch *b, BatchClass &c, int max_candidates, int trial
     return PFC_OK;
 }
 
+// ---- persistent schedule ----
+
+// Line tiles of exactly nt threads (Q W = 8 nt) for a class of the persistent launch: the
+// candidate the planner scores best among them (one-axis tiles, up to 128 columns).
+bool persist_tiles(Tiles &t, int nx, int ny, size_t vb, int nt, size_t smem_max, int members) {
+    const Geom g0 = grid_geom(nx, ny, 1);
+    long best = LONG_MIN;
+    TileChoice bc;
+    for (int Py = 1; Py <= 8; Py *= 2)
+        for (int W = 1; W <= 128; W *= 2) {
+            if (ny % Py || (int64_t)(ny / Py) * W != 8 * (int64_t)nt) continue;
+            const long sc = tile_score(g0, Py, 1, W, vb, 2, smem_max, false, ilog2(nt), 1, 1, 128);
+            if (sc > best) {
+                best = sc;
+                bc.Py = Py;
+                bc.Pz = 1;
+                bc.W = W;
+                bc.cluster = 0;
+            }
+        }
+    if (best == LONG_MIN) return false;
+    if (!plan_tiles_as(t, bc, nx, ny, 1, vb, 2, smem_max, members, 128)) return false;
+    t.g.ltab = BATCH_LTAB;
+    return t.nt_line == nt;
+}
+
+template <typename R> void free_persist(pfc_batch *b) {
+    if (b->p_exec) cudaGraphExecDestroy(b->p_exec);
+    if (b->p_graph) cudaGraphDestroy(b->p_graph);
+    b->p_exec = nullptr;
+    b->p_graph = nullptr;
+    b->p_state = nullptr;
+    b->p_nsteps = -1;
+    cudaFree(b->d_mean_items); cudaFree(b->d_oc_items); cudaFree(b->d_row_items); cudaFree(b->d_line_items);
+    b->d_mean_items = b->d_oc_items = nullptr;
+    b->d_row_items = b->d_line_items = nullptr;
+    delete reinterpret_cast<PbArgs<R> *>(b->p_args);
+    b->p_args = nullptr;
+    b->p_ready = false;
+}
+
+template <typename R> cudaError_t persist_occ(int nt, size_t smem, int *bps) {
+    return nt == 512   ? persist_occupancy<R, 512>(smem, bps)
+           : nt == 256 ? persist_occupancy<R, 256>(smem, bps)
+                       : persist_occupancy<R, 128>(smem, bps);
+}
+
+template <typename R> cudaError_t persist_launch(const pfc_batch *b, const PbArgs<R> &a, cudaStream_t s) {
+    return b->p_nt == 512   ? launch_batch_persist<R, 512>(a, b->p_grid, b->p_smem, s)
+           : b->p_nt == 256 ? launch_batch_persist<R, 256>(a, b->p_grid, b->p_smem, s)
+                            : launch_batch_persist<R, 128>(a, b->p_grid, b->p_smem, s);
+}
+
+// Tilings, class arrays, work items and launch shape of the persistent schedule.
+template <typename R> pfc_status persist_prepare(pfc_batch *b) {
+    using V = typename VT<R>::V;
+    free_persist<R>(b);
+    const size_t vb = sizeof(V);
+    int dev = 0, optin = 0, nsm = 0, clk_khz = 0;
+    PFC_BCUDA(cudaGetDevice(&dev));
+    PFC_BCUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    PFC_BCUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev) != cudaSuccess || clk_khz <= 0) clk_khz = 2000000;
+    // a barrier wait may take two seconds (a phase takes well under a millisecond)
+    if (b->p_budget <= 0) b->p_budget = (long long)clk_khz * 2000;
+    if (b->cls.size() > (size_t)PB_MAXC) return set_error(PFC_ERR_UNSUPPORTED, "too many size classes for one persistent launch");
+    const int nt = b->p_nt;
+    // Which classes run on chip: those with no tiling of the block size (both extents <= 128),
+    // and, when oc_max > 0, those whose two half spectra fit oc_max. (Inside this launch the
+    // on-chip body runs at the launch's register budget of 64 a thread, far below the 214 of its
+    // own kernel, and its spills make it slower than the two-pass items: on the 1024-domain
+    // ensemble, putting the 64 x 64 class on chip lowered the rate from 4.1e10 to 3.4e10.)
+    const size_t nclass = b->cls.size();
+    std::vector<Tiles> tl(nclass);
+    std::vector<char> tp_ok(nclass), oc_able(nclass);
+    std::vector<size_t> oc_smem(nclass);
+    size_t smem = 0;
+    for (size_t i = 0; i < nclass; ++i) {
+        BatchClass &c = b->cls[i];
+        oc_smem[i] = onchip_smem(c.ny, c.nx, vb);
+        oc_able[i] = c.ny <= ONCHIP_MAX && c.nx <= ONCHIP_MAX && oc_smem[i] <= (size_t)optin;
+        tp_ok[i] = persist_tiles(tl[i], c.nx, c.ny, vb, nt, (size_t)optin, (int)c.members.size());
+        if (!tp_ok[i] && !oc_able[i])
+            return set_error(PFC_ERR_UNSUPPORTED, "no tiling of a domain size fills the persistent launch's blocks");
+        c.p_onchip = !tp_ok[i];
+        smem = std::max(smem, c.p_onchip ? oc_smem[i] : std::max(tl[i].smem_row, tl[i].smem_line));
+    }
+    if (b->p_oc_max > 0) {
+        const size_t oc_max = std::min(b->p_oc_max, (size_t)optin);
+        for (size_t i = 0; i < nclass; ++i)
+            if (oc_able[i] && tp_ok[i] && oc_smem[i] <= oc_max) {
+                b->cls[i].p_onchip = true;
+                smem = std::max(smem, oc_smem[i]);
+            }
+    }
+    double pts_oc = 0, pts_tp = 0;
+    for (size_t i = 0; i < nclass; ++i) {
+        BatchClass &c = b->cls[i];
+        const int nm = (int)c.members.size();
+        if (c.p_onchip) {
+            pts_oc += (double)c.ny * c.nx * nm;
+            continue;
+        }
+        const Tiles &t = tl[i];
+        c.tp = t;
+        pts_tp += (double)c.ny * c.nx * nm;
+        const size_t need = (size_t)t.g.nhalf * vb * nm;
+        if (need > c.cap) {
+            void *x = nullptr, *y = nullptr;
+            PFC_BCUDA(cudaStreamSynchronize(b->stream));
+            PFC_BCUDA(cudaMalloc(&x, need));
+            if (cudaError_t e = cudaMalloc(&y, need); e != cudaSuccess) {
+                cudaFree(x);
+                return set_error(PFC_ERR_OUT_OF_MEMORY, std::string("persistent batch arrays: ") + cudaGetErrorString(e));
+            }
+            cudaFree(c.X);
+            cudaFree(c.C);
+            c.X = x;
+            c.C = y;
+            c.cap = need;
+            // the graph schedule's captured graph held the old arrays: captured again when used
+            if (b->graph) {
+                cudaGraphExecDestroy(b->graph);
+                b->graph = nullptr;
+            }
+        }
+    }
+    int bps = 0;
+    PFC_BCUDA(persist_occ<R>(nt, smem, &bps));
+    if (bps < 1) return set_error(PFC_ERR_UNSUPPORTED, "the persistent kernel does not fit an SM with this shared memory");
+
+    // classes and work items
+    auto *pa = new PbArgs<R>();
+    b->p_args = pa;
+    std::vector<std::pair<int64_t, int2>> mi, oi;
+    std::vector<std::pair<int64_t, int4>> ri, li;
+    const double two_pi = 6.28318530717958647692528676655900576839;
+    const V *tw = reinterpret_cast<const V *>(b->tw);
+    for (size_t ci = 0; ci < b->cls.size(); ++ci) {
+        BatchClass &c = b->cls[ci];
+        PbClass<R> &pc = pa->cls[ci];
+        const int nm = (int)c.members.size();
+        Geom g;
+        if (c.p_onchip) {
+            g = grid_geom(c.nx, c.ny, 1);
+            g.nreal = (int64_t)c.nx * c.ny;
+            g.ltab = BATCH_LTAB;
+        } else {
+            g = c.tp.g;
+        }
+        pc.g = g;
+        RowArgs<R> ra{};
+        ra.tw = tw;
+        ra.st = bstage<R>(b);
+        ra.mean = b->d_mean + c.cbase;
+        ra.moff = c.moff;
+        pc.fwd = pc.cube = pc.inv = ra;
+        pc.fwd.scale = (R)(1.0 / ((double)g.P * (double)g.M));
+        pc.cube.scale = pc.inv.scale = (R)1;
+        LineArgs<R> la{};
+        la.scale = (R)1;
+        la.st = bstage<R>(b);
+        la.up.dt = (R)b->dt;
+        la.up.cx = (R)(two_pi / (g.nx * b->dx));
+        la.up.cy = (R)(two_pi / (g.ny * b->dx));
+        la.up.cz = (R)(two_pi / (g.nz * b->dx));
+        la.up.inv_halfN = (R)(2.0 / (double)g.nreal);
+        la.up.op[0] = la.up.op[1] = OpR<R>{PFC_ONE_MODE, (R)0, (R)0, (R)0};
+        la.rmem = reinterpret_cast<const R *>(c.r);
+        if (c.p_onchip) {
+            pc.line = la;
+            for (int m = 0; m < nm; ++m) oi.push_back({(int64_t)c.ny * c.nx, int2{(int)ci, m}});
+            continue;
+        }
+        la.up.invQ = (R)(1.0 / g.Q);
+        la.x = c.X;
+        la.c = c.C;
+        pc.line = la;
+        pc.fwd.out = c.X;
+        pc.cube.in = c.X;
+        pc.cube.out = c.C;
+        pc.cube.proj = c.X;
+        pc.inv.in = c.X;
+        const int64_t rcost = (int64_t)g.gpc * g.P * (g.M + 1), lcost = (int64_t)g.Q * g.W;
+        for (int m = 0; m < nm; ++m) {
+            mi.push_back({g.nreal, int2{(int)ci, m}});
+            for (int bx = 0; bx < g.QR / g.gpc; ++bx) ri.push_back({rcost, int4{(int)ci, m, bx, 0}});
+            for (int kp = 0; kp < g.P * g.R; ++kp)
+                for (int cg = 0; cg < g.ncg; ++cg) li.push_back({lcost, int4{(int)ci, m, cg, kp}});
+        }
+    }
+    // largest first; equal costs keep class, member and block order
+    auto by_cost = [](const auto &x, const auto &y) { return x.first > y.first; };
+    std::stable_sort(mi.begin(), mi.end(), by_cost);
+    std::stable_sort(oi.begin(), oi.end(), by_cost);
+    std::stable_sort(ri.begin(), ri.end(), by_cost);
+    std::stable_sort(li.begin(), li.end(), by_cost);
+    auto upload = [&](auto &vec, auto *&dptr) -> cudaError_t {
+        using T = typename std::decay_t<decltype(vec)>::value_type::second_type;
+        std::vector<T> h;
+        for (auto &e : vec) h.push_back(e.second);
+        if (h.empty()) return cudaSuccess;
+        cudaError_t e = cudaMalloc(&dptr, h.size() * sizeof(T));
+        if (e == cudaSuccess) e = cudaMemcpy(dptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+        return e;
+    };
+    PFC_BCUDA(upload(mi, b->d_mean_items));
+    PFC_BCUDA(upload(oi, b->d_oc_items));
+    PFC_BCUDA(upload(ri, b->d_row_items));
+    PFC_BCUDA(upload(li, b->d_line_items));
+    if (!b->d_sync) PFC_BCUDA(cudaMalloc(&b->d_sync, PB_NSYNC * sizeof(unsigned)));
+    b->n_mean = (int)mi.size();
+    b->n_oc = (int)oi.size();
+    b->n_row = (int)ri.size();
+    b->n_line = (int)li.size();
+    b->p_smem = smem;
+    b->p_grid = nsm * bps;
+    int ocb = 0;
+    if (b->n_oc > 0) {
+        if (b->n_row == 0) {
+            ocb = std::min(b->p_grid, b->n_oc);
+        } else {
+            const double share = b->p_oc_share >= 0 ? b->p_oc_share : pts_oc / (pts_oc + pts_tp);
+            ocb = (int)std::lround(share * b->p_grid);
+            ocb = std::max(1, std::min(ocb, std::min(b->n_oc, b->p_grid - 1)));
+        }
+    }
+    b->p_oc_blocks = ocb;
+    pa->mean_items = b->d_mean_items;
+    pa->oc_items = b->d_oc_items;
+    pa->row_items = b->d_row_items;
+    pa->line_items = b->d_line_items;
+    pa->n_mean = b->n_mean;
+    pa->n_oc = b->n_oc;
+    pa->n_row = b->n_row;
+    pa->n_line = b->n_line;
+    pa->n_oc_blocks = ocb;
+    pa->sync = b->d_sync;
+    pa->status = b->d_status;
+    b->p_ready = true;
+    return PFC_OK;
+}
+
+// One pfc_batch_step on the persistent schedule: the sync words cleared, then the launch, as a
+// graph of those two nodes captured for this state and step count (replayed while they stay the
+// same), or directly when the launch could not be captured.
+template <typename R> pfc_status persist_step(pfc_batch *b, void *state, int64_t nsteps) {
+    if (!b->p_ready) {
+        pfc_status st = persist_prepare<R>(b);
+        if (st != PFC_OK) return st;
+    }
+    PbArgs<R> &pa = *reinterpret_cast<PbArgs<R> *>(b->p_args);
+    pa.state = state;
+    for (size_t ci = 0; ci < b->cls.size(); ++ci) {
+        pa.cls[ci].fwd.in = state;    // entry: the real state in, X' out
+        pa.cls[ci].inv.out = state;   // exit: X' in, the real state out
+    }
+    pa.nsteps = nsteps;
+    pa.budget = b->p_budget;
+    pa.extra = b->p_extra;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    PFC_BCUDA(cudaStreamIsCapturing(b->stream, &cs));
+    const bool direct = !b->p_graph_ok || cs != cudaStreamCaptureStatusNone;
+    if (!direct && (b->p_state != state || b->p_nsteps != nsteps || !b->p_exec)) {
+        if (b->p_exec) cudaGraphExecDestroy(b->p_exec);
+        if (b->p_graph) cudaGraphDestroy(b->p_graph);
+        b->p_exec = nullptr;
+        b->p_graph = nullptr;
+        if (!b->p_cap) PFC_BCUDA(cudaStreamCreateWithFlags(&b->p_cap, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCapture(b->p_cap, cudaStreamCaptureModeThreadLocal);
+        cudaError_t el = cudaSuccess;
+        if (e == cudaSuccess) {
+            el = cudaMemsetAsync(b->d_sync, 0, PB_NSYNC * sizeof(unsigned), b->p_cap);
+            if (el == cudaSuccess) el = persist_launch<R>(b, pa, b->p_cap);
+            e = cudaStreamEndCapture(b->p_cap, &b->p_graph);
+        }
+        if (e == cudaSuccess && el == cudaSuccess) e = cudaGraphInstantiate(&b->p_exec, b->p_graph, 0);
+        if (e != cudaSuccess || el != cudaSuccess) {
+            // not capturable here: launch directly from now on
+            cudaGetLastError();
+            if (b->p_graph) cudaGraphDestroy(b->p_graph);
+            b->p_graph = nullptr;
+            b->p_exec = nullptr;
+            b->p_graph_ok = false;
+        } else {
+            b->p_state = state;
+            b->p_nsteps = nsteps;
+        }
+    }
+    if (b->p_graph_ok && !direct) {
+        PFC_BCUDA(cudaGraphLaunch(b->p_exec, b->stream));
+    } else {
+        PFC_BCUDA(cudaMemsetAsync(b->d_sync, 0, PB_NSYNC * sizeof(unsigned), b->stream));
+        PFC_BCUDA(persist_launch<R>(b, pa, b->stream));
+    }
+    return PFC_OK;
+}
+
+// The schedule of pfc_batch_step chosen by measurement: whole calls of trial_steps (at least 20)
+// steps on a zero state (a fixed point of the step) with the graph schedule and the persistent one at 256
+// and 128 threads a block; the fastest is kept.
+template <typename R> pfc_status tune_schedule(pfc_batch *b, int trial_steps) {
+    trial_steps = std::max(trial_steps, 20);   // the graph schedule replays its graph from 16 steps
+    int64_t total = 0;
+    for (const BatchClass &c : b->cls) total += (int64_t)c.ny * c.nx * (int64_t)c.members.size();
+    void *tmp = nullptr;
+    PFC_BCUDA(cudaMalloc(&tmp, (size_t)total * sizeof(R)));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMemsetAsync(tmp, 0, (size_t)total * sizeof(R), b->stream);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int cand[3][2] = {{PFC_BATCH_GRAPH, 0}, {PFC_BATCH_PERSISTENT, 256}, {PFC_BATCH_PERSISTENT, 128}};
+    int best = -1;
+    double best_ms = 1e300;
+    pfc_status st = PFC_OK;
+    for (int i = 0; i < 3 && e == cudaSuccess && st == PFC_OK; ++i) {
+        b->sched = cand[i][0];
+        if (b->sched == PFC_BATCH_PERSISTENT) {
+            b->p_nt = cand[i][1];
+            b->p_oc_max = 0;
+            b->p_oc_share = -1.0;
+            if (persist_prepare<R>(b) != PFC_OK) continue;   // this block size cannot step the batch
+        }
+        if ((st = batch_step_impl<R>(b, tmp, trial_steps)) != PFC_OK) break;
+        float ms = 0.f;
+        e = cudaEventRecord(e0, b->stream);
+        if (e == cudaSuccess && (st = batch_step_impl<R>(b, tmp, trial_steps)) != PFC_OK) break;
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = i;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(b->stream);
+    cudaFree(tmp);
+    if (st != PFC_OK) return st;
+    if (e != cudaSuccess) return set_error(PFC_ERR_CUDA, std::string("batch schedule autotune: ") + cudaGetErrorString(e));
+    b->sched = cand[best][0];
+    if (b->sched == PFC_BATCH_PERSISTENT) {
+        b->p_nt = cand[best][1];
+        return persist_prepare<R>(b);
+    }
+    return PFC_OK;
+}
+
 void free_batch(pfc_batch *b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -295,6 +679,10 @@ void free_batch(pfc_batch *b) {
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     cudaFree(b->d_off); cudaFree(b->d_n); cudaFree(b->d_mean); cudaFree(b->d_status);
     cudaFree(b->tw); cudaFree(b->stw);
+    if (b->prec == PFC_FP64) free_persist<double>(b);
+    else free_persist<float>(b);
+    cudaFree(b->d_sync);
+    if (b->p_cap) cudaStreamDestroy(b->p_cap);
     delete b;
 }
 
@@ -475,6 +863,8 @@ pfc_status pfc_batch_autotune(pfc_batch *b, int max_candidates, int trial_steps,
         b->smem_line = std::max(b->smem_line, c.t.smem_line);
     }
     PFC_BCUDA(cudaStreamSynchronize(b->stream));
+    pfc_status st = b->prec == PFC_FP64 ? tune_schedule<double>(b, trial_steps) : tune_schedule<float>(b, trial_steps);
+    if (st != PFC_OK) return st;
     if (best_ms_out) *best_ms_out = total;
     return PFC_OK;
 }
@@ -491,6 +881,60 @@ pfc_status pfc_batch_info(pfc_batch *b, int32_t *classes_out, int max_classes, i
                               c.onchip ? 0 : c.t.g.Qy};
         std::memcpy(classes_out + 9 * i, v, sizeof(v));
     }
+    return PFC_OK;
+}
+
+pfc_status pfc_batch_set_schedule(pfc_batch *b, int schedule, int threads, int64_t onchip_smem_max,
+                                  double onchip_block_share) {
+    if (!b) return set_error(PFC_ERR_INVALID_ARG, "invalid batch");
+    if (schedule != PFC_BATCH_GRAPH && schedule != PFC_BATCH_PERSISTENT)
+        return set_error(PFC_ERR_INVALID_ARG, "unknown batch schedule");
+    if (schedule == PFC_BATCH_PERSISTENT && threads != 128 && threads != 256 && threads != 512)
+        return set_error(PFC_ERR_INVALID_ARG, "persistent blocks have 128, 256 or 512 threads");
+    if (onchip_smem_max < 0 || !(onchip_block_share <= 1.0) || std::isnan(onchip_block_share))
+        return set_error(PFC_ERR_INVALID_ARG, "bad on-chip limit or block share");
+    PFC_BCUDA(cudaStreamSynchronize(b->stream));
+    if (schedule == PFC_BATCH_GRAPH) {
+        b->sched = schedule;
+        return PFC_OK;
+    }
+    b->p_nt = threads;
+    b->p_oc_max = (size_t)onchip_smem_max;
+    b->p_oc_share = onchip_block_share;
+    const pfc_status st = b->prec == PFC_FP64 ? persist_prepare<double>(b) : persist_prepare<float>(b);
+    if (st == PFC_OK) b->sched = schedule;   // on failure the batch keeps its schedule
+    return st;
+}
+
+pfc_status pfc_batch_schedule_info(pfc_batch *b, int64_t *info_out) {
+    if (!b || !info_out) return set_error(PFC_ERR_INVALID_ARG, "null pointer argument");
+    const int64_t v[10] = {b->sched, b->p_nt, b->p_grid, b->p_oc_blocks, (int64_t)b->p_smem,
+                           b->p_graph_ok ? 1 : 0, b->n_row, b->n_line, b->n_oc, b->n_mean};
+    std::memcpy(info_out, v, sizeof(v));
+    return PFC_OK;
+}
+
+pfc_status pfc_batch_set_wait_limit(pfc_batch *b, double seconds, int extra_arrivals) {
+    if (!b) return set_error(PFC_ERR_INVALID_ARG, "invalid batch");
+    if (!(seconds > 0) || !(seconds <= 60) || extra_arrivals < 0 || extra_arrivals > 1024)
+        return set_error(PFC_ERR_INVALID_ARG, "wait limit must be in (0, 60] s and extra arrivals in [0, 1024]");
+    int dev = 0, clk_khz = 0;
+    PFC_BCUDA(cudaGetDevice(&dev));
+    if (cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev) != cudaSuccess || clk_khz <= 0) clk_khz = 2000000;
+    PFC_BCUDA(cudaStreamSynchronize(b->stream));
+    b->p_budget = (long long)((double)clk_khz * 1000.0 * seconds);
+    b->p_extra = extra_arrivals;
+    return PFC_OK;
+}
+
+pfc_status pfc_batch_sync(pfc_batch *b) {
+    if (!b) return set_error(PFC_ERR_INVALID_ARG, "invalid batch");
+    int st = 0;
+    PFC_BCUDA(cudaMemcpyAsync(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    PFC_BCUDA(cudaStreamSynchronize(b->stream));
+    if (st) PFC_BCUDA(cudaMemset(b->d_status, 0, sizeof(int)));
+    if (st & STATUS_TIMEOUT) return set_error(PFC_ERR_TIMEOUT, "a grid barrier of the persistent batch launch ran out of time");
+    if (st & STATUS_NONFINITE) return set_error(PFC_ERR_NONFINITE, "the state holds NaN or Inf");
     return PFC_OK;
 }
 

@@ -132,11 +132,13 @@ inline Geom grid_geom(int nx, int ny, int nz) {
 // the line tile is Q = ny nz / (P R) long. They cost 9 sweeps a step instead of 5, so the planner
 // takes them only for grids with no two-pass tiling; among them the same preferences apply,
 // then the smallest R.
+// max_w: the widest tile (16 for the per-pass launches; the persistent batch launch, whose line
+// tiles must fill its fixed block size, allows up to 128 columns).
 inline long tile_score(const Geom &g, int Py, int Pz, int W, size_t vb, int ntile, size_t smem_max,
-                       bool limit_w, int lnt_target = 8, int Ry = 1, int Rz = 1) {
+                       bool limit_w, int lnt_target = 8, int Ry = 1, int Rz = 1, int max_w = 16) {
     const int max_threads = vb == 8 ? 1024 : 512;   // line pass blocks
     const int ny = g.ny, nz = g.nz;
-    if (!is_pow2(Py) || Py > 8 || !is_pow2(Pz) || Pz > 8 || !is_pow2(W) || W > 16) return LONG_MIN;
+    if (!is_pow2(Py) || Py > 8 || !is_pow2(Pz) || Pz > 8 || !is_pow2(W) || W > max_w) return LONG_MIN;
     if (!is_pow2(Ry) || Ry > 8 || !is_pow2(Rz) || Rz > 8 || (nz == 1 && Rz > 1)) return LONG_MIN;
     const int three = Ry * Rz > 1;
     if ((Py > 1 && ny / Py < 8) || ny % (Py * Ry)) return LONG_MIN;
@@ -214,10 +216,10 @@ inline std::vector<TileChoice> tile_candidates(int nx, int ny, int nz, size_t vb
 // shared memory, and the clustered psi^3 row pass where one exists for the grid.
 // instances: grids of this shape stepped by the same launches (the members of a batch class)
 inline bool plan_tiles_as(Tiles &t, const TileChoice &c, int nx, int ny, int nz, size_t vb, int ntile,
-                          size_t smem_max, int instances = 1) {
+                          size_t smem_max, int instances = 1, int max_w = 16) {
     Geom g = grid_geom(nx, ny, nz);
     const int Ry = std::max(c.Ry, 1), Rz = std::max(c.Rz, 1);
-    if (tile_score(g, c.Py, c.Pz, c.W, vb, ntile, smem_max, false, 8, Ry, Rz) == LONG_MIN) return false;
+    if (tile_score(g, c.Py, c.Pz, c.W, vb, ntile, smem_max, false, 8, Ry, Rz, max_w) == LONG_MIN) return false;
     // row blocks of at most 512 threads: two blocks (64 registers a thread) fit an SM, so one
     // block's memory phases overlap the other's transforms (256^3 FP32 row pass 212 -> 162 us
     // against 1024-thread blocks)

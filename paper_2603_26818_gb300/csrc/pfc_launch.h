@@ -14,6 +14,7 @@
 #include "pfc_adjoint_row.cuh"
 #include "pfc_hydro.cuh"
 #include "pfc_mixed.cuh"
+#include "pfc_persist.cuh"
 
 namespace pfc {
 
@@ -77,6 +78,11 @@ void launch_mr_col(cudaStream_t s, int mode, const MrGeom &g, const MrArgs<R> &a
 template <typename R>
 void launch_mr_edges(cudaStream_t s, const MrGeom &g, const void *E, void *S, double scale);
 template <typename R> cudaError_t set_smem_mr(size_t row, size_t col);
+// the persistent batch kernel (pfc_persist.cuh), NT = 128, 256 or 512 threads a block: one
+// cooperative launch of grid blocks; persist_occupancy allows smem bytes and returns the blocks
+// that fit an SM
+template <typename R, int NT> cudaError_t launch_batch_persist(const PbArgs<R> &a, int grid, size_t smem, cudaStream_t s);
+template <typename R, int NT> cudaError_t persist_occupancy(size_t smem, int *blocks_per_sm);
 // middle pass of a three-pass plan (g.R > 1): dir -1 forward, +1 inverse (pfc_mid.cuh)
 template <typename R> void launch_mid(const LaunchCfg &c, int dir, const MidArgs<R> &a);
 
@@ -135,6 +141,16 @@ template <typename R> cudaError_t set_smem_attrs_fixed(const LaunchCfg &c);
                                                double *, int *);                                \
     extern template void launch_reduce_spec<R>(cudaStream_t, const Geom &, OpDev, double,       \
                                                const void *, const double *, double *, int *);
+#define PFC_DECLARE_PERSIST(R)                                                                     \
+    extern template cudaError_t launch_batch_persist<R, 128>(const PbArgs<R> &, int, size_t, cudaStream_t); \
+    extern template cudaError_t launch_batch_persist<R, 256>(const PbArgs<R> &, int, size_t, cudaStream_t); \
+    extern template cudaError_t launch_batch_persist<R, 512>(const PbArgs<R> &, int, size_t, cudaStream_t); \
+    extern template cudaError_t persist_occupancy<R, 128>(size_t, int *);                          \
+    extern template cudaError_t persist_occupancy<R, 256>(size_t, int *);                          \
+    extern template cudaError_t persist_occupancy<R, 512>(size_t, int *);
+PFC_DECLARE_PERSIST(float)
+PFC_DECLARE_PERSIST(double)
+#undef PFC_DECLARE_PERSIST
 PFC_DECLARE_LAUNCH(float)
 PFC_DECLARE_LAUNCH(double)
 #undef PFC_DECLARE_LAUNCH

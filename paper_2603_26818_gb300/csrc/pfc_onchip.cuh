@@ -40,15 +40,16 @@ __host__ __device__ inline size_t onchip_smem(int ny, int nx, size_t vb) {
     return (size_t)(2 * ny * rs + 2 * ny) * vb;
 }
 
+// The steps of one member by one block (any block size that is a multiple of 32 and at least
+// 2 ny / 8); k_onchip runs it as its own block, the persistent batch kernel once per on-chip item.
 template <typename R>
-__global__ void __launch_bounds__(ONCHIP_THREADS) k_onchip(const Geom g, const OnchipArgs<R> a) {
+__device__ __forceinline__ void onchip_body(const Geom &g, const OnchipArgs<R> &a, int member) {
     using V = typename VT<R>::V;
     extern __shared__ __align__(16) unsigned char smraw[];
     V *S0 = reinterpret_cast<V *>(smraw);
     V *S1 = S0 + g.ny * g.rs;
     V *E = S1 + g.ny * g.rs;   // two projection columns of ny values
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int member = blockIdx.x;
     const int M = g.M, lM = g.lM, hM = M >> 1, ny = g.ny, rs = g.rs;
     const R mean = (R)a.mean[member];
     V *field = reinterpret_cast<V *>(a.state) + a.moff[member] / 2;   // rows of M real pairs
@@ -197,6 +198,11 @@ __global__ void __launch_bounds__(ONCHIP_THREADS) k_onchip(const Geom g, const O
         const V v = S0[y * rs + row_swz(i)];
         field[(size_t)y * M + i] = V{v.x + mean, v.y + mean};
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(ONCHIP_THREADS) k_onchip(const Geom g, const OnchipArgs<R> a) {
+    onchip_body<R>(g, a, blockIdx.x);
 }
 
 }  // namespace pfc

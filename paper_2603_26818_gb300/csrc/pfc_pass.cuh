@@ -486,15 +486,16 @@ __device__ __forceinline__ void row_fft(V (&v)[8], V *sm, const RowAddr &ad, int
 }
 
 // LM > 0: the kernel only serves plans with M = 2^LM.
+// The body of one row-pass block (block index bx, field or batch member `field`); k_row runs it
+// as its own block, the persistent batch kernel once per work item.
 template <typename R, int MODE, int LM = 0>
-__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_row(const Geom g, const RowArgs<R> a) {
+__device__ __forceinline__ void row_body(const Geom &g, const RowArgs<R> &a, int bx, int field) {
     using V = typename VT<R>::V;
     extern __shared__ __align__(16) unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int field = blockIdx.y;
     const int P = g.P, rows = g.gpc * P, M = g.M, lM = g.lM;
-    const int grp0 = blockIdx.x * g.gpc;
+    const int grp0 = bx * g.gpc;
     const R mean = a.mean ? (R)a.mean[field] : (R)0;
     // smem: rows | split twiddles of this block's groups (gpc P) | saved edge values (2 gpc P)
     V *stw = sm + rows * g.rs;
@@ -599,6 +600,11 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_row(const Geom 
     }
 }
 
+template <typename R, int MODE, int LM = 0>
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_row(const Geom g, const RowArgs<R> a) {
+    row_body<R, MODE, LM>(g, a, blockIdx.x, blockIdx.y);
+}
+
 // ------------------------------------------------------------------------------------------
 // Line pass: one tile of Q = Qz Qy complex values x W columns per block, interleaved (w
 // fastest, one padding row after every 8 tile rows), block = Q W / 8 threads. y-transforms use
@@ -694,12 +700,13 @@ __device__ __forceinline__ void line_zfft(V (&v)[8], V *sm, const TileAddr &ad, 
 
 // LY > 0, LZ = 0: the kernel only serves plans with Qz = 1 and Qy = 2^LY; LY, LZ > 0: plans with
 // Qy = 2^LY and Qz = 2^LZ; LY = LZ = 0: any plan (lengths at run time).
-template <typename R, int MODE, int MAXT, int LY = 0, int LZ = 0>
-__global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1) k_line(const Geom g, const LineArgs<R> a) {
+// The body of one line-pass block (column group cg, split index kp, field or batch member);
+// k_line runs it as its own block, the persistent batch kernel once per work item.
+template <typename R, int MODE, int LY = 0, int LZ = 0>
+__device__ __forceinline__ void line_body(const Geom &g, const LineArgs<R> &a, int cg, int kp, int field) {
     using V = typename VT<R>::V;
     extern __shared__ __align__(16) unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
-    const int cg = blockIdx.x, kp = blockIdx.y, field = blockIdx.z;
     V *T = sm;
     V *Cs = sm + g.tsz;
     const LineMap mp = line_map(g, threadIdx.x);
@@ -824,6 +831,11 @@ __global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1)
 #pragma unroll
     for (int m = 0; m < 8; ++m)
         __stcg(&Xo[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)], cscale(vt[m], sc));
+}
+
+template <typename R, int MODE, int MAXT, int LY = 0, int LZ = 0>
+__global__ void __launch_bounds__(MAXT, (sizeof(R) == 4 && MAXT == 512) ? 2 : 1) k_line(const Geom g, const LineArgs<R> a) {
+    line_body<R, MODE, LY, LZ>(g, a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace pfc

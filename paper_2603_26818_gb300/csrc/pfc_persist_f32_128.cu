@@ -1,0 +1,6 @@
+// FP32-mixed instantiation of the persistent batch kernel (pfc_persist.cuh), 128-thread blocks.
+#include "pfc_persist_launch.cuh"
+
+namespace pfc {
+PFC_INSTANTIATE_PERSIST(float, 128)
+}  // namespace pfc
