@@ -360,6 +360,23 @@ pfc_status pfc_batch_schedule_info(pfc_batch *batch, int64_t *info_out);
  * an aid to test the timeout path without a device fault. Synchronises. */
 pfc_status pfc_batch_set_wait_limit(pfc_batch *batch, double seconds, int extra_arrivals);
 
+/* Attach a coupled density/composition pair (two conserved fields, the 2x2 per-mode implicit
+ * update of pfc_plan_create with nfields = 2) to the batch: it is stepped inside the batch's
+ * persistent launch, its row-pass items beside the domains' and its line items (both fields of
+ * a tile) beside theirs, with the batch's dx, dt and precision. ndim 2 or 3, dims slowest
+ * first, powers of two in [16, 512]; ops[2] the fields' operators; alpha the linear coupling.
+ * Sets the persistent schedule (with its current block size). After this, pfc_batch_step
+ * returns INVALID_ARG: use pfc_batch_step_with_pair. Synchronises and allocates two half
+ * spectra per field. Errors: INVALID_ARG (a pair already attached), UNSUPPORTED,
+ * UNSTABLE_OPERATOR, OUT_OF_MEMORY, CUDA. */
+pfc_status pfc_batch_attach_pair(pfc_batch *batch, int ndim, const int64_t *dims, const pfc_op *ops,
+                                 double alpha);
+
+/* Advance the domains (packed_state) and the attached pair (pair_state: device, real,
+ * [field][z][y][x], in place) by nsteps in one persistent launch. */
+pfc_status pfc_batch_step_with_pair(pfc_batch *batch, void *packed_state, void *pair_state,
+                                    int64_t nsteps);
+
 /* Synchronises the batch's stream and returns the latched device status (cleared on read):
  * PFC_ERR_TIMEOUT when a persistent launch's barrier wait ran out, PFC_ERR_NONFINITE when a
  * mean reduction met NaN or Inf, else PFC_OK. */

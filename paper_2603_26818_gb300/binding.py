@@ -32,7 +32,8 @@ EXPORTS = ["pfc_plan_create", "pfc_plan_destroy", "pfc_step", "pfc_fft_r2c", "pf
            "pfc_hydro_create", "pfc_hydro_step", "pfc_hydro_destroy",
            "pfc_status_string", "pfc_last_error", "pfc_batch_create", "pfc_batch_destroy",
            "pfc_batch_step", "pfc_batch_mass", "pfc_batch_set_schedule", "pfc_batch_schedule_info",
-           "pfc_batch_set_wait_limit", "pfc_batch_sync"]
+           "pfc_batch_set_wait_limit", "pfc_batch_sync", "pfc_batch_attach_pair",
+           "pfc_batch_step_with_pair"]
 
 
 class PfcError(RuntimeError):
@@ -93,6 +94,8 @@ def load_library(path: str = LIB_PATH):
         "pfc_batch_schedule_info": [vp, P(i64)],
         "pfc_batch_set_wait_limit": [vp, dbl, cint],
         "pfc_batch_sync": [vp],
+        "pfc_batch_attach_pair": [vp, cint, P(i64), P(pfc_op), dbl],
+        "pfc_batch_step_with_pair": [vp, vp, vp, i64],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -406,6 +409,24 @@ class Batch:
     def set_wait_limit(self, seconds: float = 2.0, extra_arrivals: int = 0):
         """pfc_batch_set_wait_limit: bound of the persistent launch's barrier waits."""
         check(load_library().pfc_batch_set_wait_limit(self._h, float(seconds), int(extra_arrivals)))
+
+    def attach_pair(self, shape, ops, alpha: float):
+        """pfc_batch_attach_pair: a coupled density/composition pair (shape slowest first; ops two
+        pfc_op from make_op) stepped inside the persistent launch."""
+        lib = load_library()
+        self.pair_shape = tuple(int(v) for v in shape)
+        dims = (ctypes.c_int64 * len(shape))(*self.pair_shape)
+        arr = (pfc_op * 2)(*ops)
+        check(lib.pfc_batch_attach_pair(self._h, len(shape), dims, arr, float(alpha)))
+
+    def step_with_pair(self, state: torch.Tensor, pair_state: torch.Tensor, nsteps: int = 1):
+        """pfc_batch_step_with_pair: pair_state is (2, *shape) in the batch's dtype."""
+        if tuple(pair_state.shape) != (2,) + self.pair_shape:
+            raise PfcError(1, f"pair state has shape {tuple(pair_state.shape)}, expected {(2,) + self.pair_shape}")
+        check(load_library().pfc_batch_step_with_pair(self._h, ctypes.c_void_p(self._ptr(state)),
+                                                      ctypes.c_void_p(_dev_ptr(pair_state, self.real_dtype, "pair state")),
+                                                      int(nsteps)))
+        return state, pair_state
 
     def sync(self):
         """pfc_batch_sync: raises PfcError with the latched device status (TIMEOUT, NONFINITE)."""

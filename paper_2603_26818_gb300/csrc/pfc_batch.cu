@@ -85,6 +85,18 @@ struct pfc_batch {
     int64_t p_nsteps = -1;
     bool p_graph_ok = true;          // false once capturing the launch failed (launched directly)
     cudaStream_t p_cap = nullptr;
+    const void *p_pair_state = nullptr;
+    // an attached coupled pair (pfc_batch_attach_pair), stepped inside the persistent launch
+    bool has_pair = false;
+    int pair_ndim = 0;
+    int pair_n[3] = {1, 1, 1};       // nx, ny, nz
+    pfc_op pair_ops[2]{};
+    double pair_alpha = 0;
+    Tiles pair_t{};
+    void *pair_X = nullptr, *pair_C = nullptr;
+    size_t pair_cap = 0;
+    int64_t *pair_moff = nullptr;    // device {0, N}: the fields' offsets in the pair's state
+    double *pair_mean = nullptr;     // device: the fields' FP64 means
 };
 
 namespace {
@@ -159,10 +171,10 @@ template <typename R> pfc_status enqueue_steps(pfc_batch *b, cudaStream_t origin
     return PFC_OK;
 }
 
-template <typename R> pfc_status persist_step(pfc_batch *b, void *state, int64_t nsteps);
+template <typename R> pfc_status persist_step(pfc_batch *b, void *state, int64_t nsteps, void *pair_state);
 
 template <typename R> pfc_status batch_step_impl(pfc_batch *b, void *state, int64_t nsteps) {
-    if (b->sched == PFC_BATCH_PERSISTENT) return persist_step<R>(b, state, nsteps);
+    if (b->sched == PFC_BATCH_PERSISTENT) return persist_step<R>(b, state, nsteps, nullptr);
     launch_batch_mean<R>(b->stream, reinterpret_cast<const R *>(state), b->d_off, b->d_n, b->nd,
                          b->d_mean, b->d_status);
     for (BatchClass &c : b->cls) {
@@ -323,25 +335,28 @@ pfc_status tune_class(pfc_batch *b, BatchClass &c, int max_candidates, int trial
 
 // Line tiles of exactly nt threads (Q W = 8 nt) for a class of the persistent launch: the
 // candidate the planner scores best among them (one-axis tiles, up to 128 columns).
-bool persist_tiles(Tiles &t, int nx, int ny, size_t vb, int nt, size_t smem_max, int members) {
-    const Geom g0 = grid_geom(nx, ny, 1);
+// ntile: line tiles in shared memory (2; 3 for the coupled pair's update).
+bool persist_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int nt, size_t smem_max, int members,
+                   int ntile, int ltab) {
+    const Geom g0 = grid_geom(nx, ny, nz);
     long best = LONG_MIN;
     TileChoice bc;
     for (int Py = 1; Py <= 8; Py *= 2)
-        for (int W = 1; W <= 128; W *= 2) {
-            if (ny % Py || (int64_t)(ny / Py) * W != 8 * (int64_t)nt) continue;
-            const long sc = tile_score(g0, Py, 1, W, vb, 2, smem_max, false, ilog2(nt), 1, 1, 128);
-            if (sc > best) {
-                best = sc;
-                bc.Py = Py;
-                bc.Pz = 1;
-                bc.W = W;
-                bc.cluster = 0;
+        for (int Pz = 1; Pz <= (nz > 1 ? 8 : 1); Pz *= 2)
+            for (int W = 1; W <= 128; W *= 2) {
+                if (ny % Py || nz % Pz || (int64_t)(ny / Py) * (nz / Pz) * W != 8 * (int64_t)nt) continue;
+                const long sc = tile_score(g0, Py, Pz, W, vb, ntile, smem_max, false, ilog2(nt), 1, 1, 128);
+                if (sc > best) {
+                    best = sc;
+                    bc.Py = Py;
+                    bc.Pz = Pz;
+                    bc.W = W;
+                    bc.cluster = 0;
+                }
             }
-        }
     if (best == LONG_MIN) return false;
-    if (!plan_tiles_as(t, bc, nx, ny, 1, vb, 2, smem_max, members, 128)) return false;
-    t.g.ltab = BATCH_LTAB;
+    if (!plan_tiles_as(t, bc, nx, ny, nz, vb, ntile, smem_max, members, 128)) return false;
+    t.g.ltab = ltab;
     return t.nt_line == nt;
 }
 
@@ -400,7 +415,7 @@ template <typename R> pfc_status persist_prepare(pfc_batch *b) {
         BatchClass &c = b->cls[i];
         oc_smem[i] = onchip_smem(c.ny, c.nx, vb);
         oc_able[i] = c.ny <= ONCHIP_MAX && c.nx <= ONCHIP_MAX && oc_smem[i] <= (size_t)optin;
-        tp_ok[i] = persist_tiles(tl[i], c.nx, c.ny, vb, nt, (size_t)optin, (int)c.members.size());
+        tp_ok[i] = persist_tiles(tl[i], c.nx, c.ny, 1, vb, nt, (size_t)optin, (int)c.members.size(), 2, BATCH_LTAB);
         if (!tp_ok[i] && !oc_able[i])
             return set_error(PFC_ERR_UNSUPPORTED, "no tiling of a domain size fills the persistent launch's blocks");
         c.p_onchip = !tp_ok[i];
@@ -445,6 +460,30 @@ template <typename R> pfc_status persist_prepare(pfc_batch *b) {
                 b->graph = nullptr;
             }
         }
+    }
+    // an attached coupled pair: its tiling (three line tiles for the 2x2 update) and arrays
+    if (b->has_pair) {
+        if (nclass + 1 > (size_t)PB_MAXC)
+            return set_error(PFC_ERR_UNSUPPORTED, "too many size classes for one persistent launch");
+        Tiles t;
+        if (!persist_tiles(t, b->pair_n[0], b->pair_n[1], b->pair_n[2], vb, nt, (size_t)optin, 2, 3, BATCH_LTAB))
+            return set_error(PFC_ERR_UNSUPPORTED, "no tiling of the coupled pair's grid fills the persistent launch's blocks");
+        b->pair_t = t;
+        smem = std::max(smem, std::max(t.smem_row, t.smem_line));
+        pts_tp += 2.0 * (double)t.g.nreal;
+        const size_t need = 2 * (size_t)t.g.nhalf * vb;
+        if (need > b->pair_cap) {
+            PFC_BCUDA(cudaStreamSynchronize(b->stream));
+            cudaFree(b->pair_X);
+            cudaFree(b->pair_C);
+            b->pair_X = b->pair_C = nullptr;
+            b->pair_cap = 0;
+            PFC_BCUDA(cudaMalloc(&b->pair_X, need));
+            PFC_BCUDA(cudaMalloc(&b->pair_C, need));
+            b->pair_cap = need;
+        }
+        const int64_t moff[2] = {0, t.g.nreal};
+        PFC_BCUDA(cudaMemcpy(b->pair_moff, moff, sizeof(moff), cudaMemcpyHostToDevice));
     }
     int bps = 0;
     PFC_BCUDA(persist_occ<R>(nt, smem, &bps));
@@ -510,6 +549,52 @@ template <typename R> pfc_status persist_prepare(pfc_batch *b) {
                 for (int cg = 0; cg < g.ncg; ++cg) li.push_back({lcost, int4{(int)ci, m, cg, kp}});
         }
     }
+    pa->pair_ci = -1;
+    if (b->has_pair) {
+        const int pci = (int)b->cls.size();
+        const Geom &g = b->pair_t.g;
+        PbClass<R> &pc = pa->cls[pci];
+        pc.g = g;
+        RowArgs<R> ra{};
+        ra.tw = tw;
+        ra.st = bstage<R>(b);
+        ra.mean = b->pair_mean;
+        ra.moff = b->pair_moff;
+        pc.fwd = pc.cube = pc.inv = ra;
+        pc.fwd.scale = (R)(1.0 / ((double)g.P * (double)g.M));
+        pc.cube.scale = pc.inv.scale = (R)1;
+        pc.fwd.out = b->pair_X;
+        pc.cube.in = b->pair_X;
+        pc.cube.out = b->pair_C;
+        pc.cube.proj = b->pair_X;
+        pc.inv.in = b->pair_X;
+        Step2Args<R> a2{};
+        a2.x0 = b->pair_X;
+        a2.x1 = reinterpret_cast<V *>(b->pair_X) + g.nhalf;
+        a2.c0 = b->pair_C;
+        a2.c1 = reinterpret_cast<const V *>(b->pair_C) + g.nhalf;
+        a2.alpha = (R)b->pair_alpha;
+        a2.up.dt = (R)b->dt;
+        a2.up.cx = (R)(two_pi / (g.nx * b->dx));
+        a2.up.cy = (R)(two_pi / (g.ny * b->dx));
+        a2.up.cz = (R)(two_pi / (g.nz * b->dx));
+        a2.up.invQ = (R)(1.0 / g.Q);
+        a2.up.inv_halfN = (R)(2.0 / (double)g.nreal);
+        for (int f = 0; f < 2; ++f) {
+            const pfc_op &o = b->pair_ops[f];
+            a2.up.op[f] = OpR<R>{o.kind, (R)o.r, (R)o.R1, (R)(o.q2 * o.q2)};
+        }
+        a2.st = bstage<R>(b);
+        pa->pair = a2;
+        pa->pair_ci = pci;
+        const int64_t rcost = (int64_t)g.gpc * g.P * (g.M + 1), lcost = 2 * (int64_t)g.Q * g.W;
+        for (int f = 0; f < 2; ++f) {
+            mi.push_back({g.nreal, int2{pci, f}});
+            for (int bx = 0; bx < g.QR / g.gpc; ++bx) ri.push_back({rcost, int4{pci, f, bx, 0}});
+        }
+        for (int kp = 0; kp < g.P * g.R; ++kp)
+            for (int cg = 0; cg < g.ncg; ++cg) li.push_back({lcost, int4{pci, 0, cg, kp}});
+    }
     // largest first; equal costs keep class, member and block order
     auto by_cost = [](const auto &x, const auto &y) { return x.first > y.first; };
     std::stable_sort(mi.begin(), mi.end(), by_cost);
@@ -565,7 +650,7 @@ template <typename R> pfc_status persist_prepare(pfc_batch *b) {
 // One pfc_batch_step on the persistent schedule: the sync words cleared, then the launch, as a
 // graph of those two nodes captured for this state and step count (replayed while they stay the
 // same), or directly when the launch could not be captured.
-template <typename R> pfc_status persist_step(pfc_batch *b, void *state, int64_t nsteps) {
+template <typename R> pfc_status persist_step(pfc_batch *b, void *state, int64_t nsteps, void *pair_state) {
     if (!b->p_ready) {
         pfc_status st = persist_prepare<R>(b);
         if (st != PFC_OK) return st;
@@ -576,13 +661,17 @@ template <typename R> pfc_status persist_step(pfc_batch *b, void *state, int64_t
         pa.cls[ci].fwd.in = state;    // entry: the real state in, X' out
         pa.cls[ci].inv.out = state;   // exit: X' in, the real state out
     }
+    if (pa.pair_ci >= 0) {
+        pa.cls[pa.pair_ci].fwd.in = pair_state;
+        pa.cls[pa.pair_ci].inv.out = pair_state;
+    }
     pa.nsteps = nsteps;
     pa.budget = b->p_budget;
     pa.extra = b->p_extra;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     PFC_BCUDA(cudaStreamIsCapturing(b->stream, &cs));
     const bool direct = !b->p_graph_ok || cs != cudaStreamCaptureStatusNone;
-    if (!direct && (b->p_state != state || b->p_nsteps != nsteps || !b->p_exec)) {
+    if (!direct && (b->p_state != state || b->p_pair_state != pair_state || b->p_nsteps != nsteps || !b->p_exec)) {
         if (b->p_exec) cudaGraphExecDestroy(b->p_exec);
         if (b->p_graph) cudaGraphDestroy(b->p_graph);
         b->p_exec = nullptr;
@@ -605,6 +694,7 @@ template <typename R> pfc_status persist_step(pfc_batch *b, void *state, int64_t
             b->p_graph_ok = false;
         } else {
             b->p_state = state;
+            b->p_pair_state = pair_state;
             b->p_nsteps = nsteps;
         }
     }
@@ -624,17 +714,24 @@ template <typename R> pfc_status tune_schedule(pfc_batch *b, int trial_steps) {
     trial_steps = std::max(trial_steps, 20);   // the graph schedule replays its graph from 16 steps
     int64_t total = 0;
     for (const BatchClass &c : b->cls) total += (int64_t)c.ny * c.nx * (int64_t)c.members.size();
+    const int64_t ptotal = b->has_pair ? 2 * (int64_t)b->pair_n[0] * b->pair_n[1] * b->pair_n[2] : 0;
     void *tmp = nullptr;
-    PFC_BCUDA(cudaMalloc(&tmp, (size_t)total * sizeof(R)));
+    PFC_BCUDA(cudaMalloc(&tmp, (size_t)(total + ptotal) * sizeof(R)));
+    void *ptmp = b->has_pair ? reinterpret_cast<R *>(tmp) + total : nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaMemsetAsync(tmp, 0, (size_t)total * sizeof(R), b->stream);
+    cudaError_t e = cudaMemsetAsync(tmp, 0, (size_t)(total + ptotal) * sizeof(R), b->stream);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const int cand[3][2] = {{PFC_BATCH_GRAPH, 0}, {PFC_BATCH_PERSISTENT, 256}, {PFC_BATCH_PERSISTENT, 128}};
     int best = -1;
     double best_ms = 1e300;
     pfc_status st = PFC_OK;
-    for (int i = 0; i < 3 && e == cudaSuccess && st == PFC_OK; ++i) {
+    // a call of the chosen schedule (a coupled pair attached: the persistent one only)
+    auto call = [&]() {
+        return b->sched == PFC_BATCH_PERSISTENT ? persist_step<R>(b, tmp, trial_steps, ptmp)
+                                                : batch_step_impl<R>(b, tmp, trial_steps);
+    };
+    for (int i = b->has_pair ? 1 : 0; i < 3 && e == cudaSuccess && st == PFC_OK; ++i) {
         b->sched = cand[i][0];
         if (b->sched == PFC_BATCH_PERSISTENT) {
             b->p_nt = cand[i][1];
@@ -642,10 +739,10 @@ template <typename R> pfc_status tune_schedule(pfc_batch *b, int trial_steps) {
             b->p_oc_share = -1.0;
             if (persist_prepare<R>(b) != PFC_OK) continue;   // this block size cannot step the batch
         }
-        if ((st = batch_step_impl<R>(b, tmp, trial_steps)) != PFC_OK) break;
+        if ((st = call()) != PFC_OK) break;
         float ms = 0.f;
         e = cudaEventRecord(e0, b->stream);
-        if (e == cudaSuccess && (st = batch_step_impl<R>(b, tmp, trial_steps)) != PFC_OK) break;
+        if (e == cudaSuccess && (st = call()) != PFC_OK) break;
         if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
@@ -660,6 +757,7 @@ template <typename R> pfc_status tune_schedule(pfc_batch *b, int trial_steps) {
     cudaFree(tmp);
     if (st != PFC_OK) return st;
     if (e != cudaSuccess) return set_error(PFC_ERR_CUDA, std::string("batch schedule autotune: ") + cudaGetErrorString(e));
+    if (best < 0) return set_error(PFC_ERR_UNSUPPORTED, "no persistent block size can step the batch");
     b->sched = cand[best][0];
     if (b->sched == PFC_BATCH_PERSISTENT) {
         b->p_nt = cand[best][1];
@@ -683,6 +781,7 @@ void free_batch(pfc_batch *b) {
     else free_persist<float>(b);
     cudaFree(b->d_sync);
     if (b->p_cap) cudaStreamDestroy(b->p_cap);
+    cudaFree(b->pair_X); cudaFree(b->pair_C); cudaFree(b->pair_moff); cudaFree(b->pair_mean);
     delete b;
 }
 
@@ -833,9 +932,59 @@ pfc_status pfc_batch_step(pfc_batch *b, void *packed_state, int64_t nsteps) {
     if (nsteps < 0) return set_error(PFC_ERR_INVALID_ARG, "nsteps must be >= 0");
     if ((reinterpret_cast<uintptr_t>(packed_state) & 15) != 0)
         return set_error(PFC_ERR_INVALID_ARG, "state must be 16-byte aligned");
+    if (b->has_pair) return set_error(PFC_ERR_INVALID_ARG, "the batch has a coupled pair: pfc_batch_step_with_pair");
     if (nsteps == 0) return PFC_OK;
     return b->prec == PFC_FP64 ? batch_step_impl<double>(b, packed_state, nsteps)
                                : batch_step_impl<float>(b, packed_state, nsteps);
+}
+
+pfc_status pfc_batch_attach_pair(pfc_batch *b, int ndim, const int64_t *dims, const pfc_op *ops, double alpha) {
+    if (!b || !dims || !ops) return set_error(PFC_ERR_INVALID_ARG, "null pointer argument");
+    if (b->has_pair) return set_error(PFC_ERR_INVALID_ARG, "the batch already has a coupled pair");
+    if (ndim != 2 && ndim != 3) return set_error(PFC_ERR_INVALID_ARG, "ndim must be 2 or 3");
+    int n[3] = {1, 1, 1};   // nx, ny, nz
+    for (int d = 0; d < ndim; ++d) {
+        const int64_t v = dims[ndim - 1 - d];
+        if (!is_pow2(v) || v < 16 || v > 512)
+            return set_error(PFC_ERR_UNSUPPORTED, "the pair's extents must be powers of two in [16, 512]");
+        n[d] = (int)v;
+    }
+    for (int f = 0; f < 2; ++f)
+        if ((ops[f].kind != PFC_ONE_MODE && ops[f].kind != PFC_TWO_MODE) || !std::isfinite(ops[f].r) ||
+            !std::isfinite(ops[f].R1) || !std::isfinite(ops[f].q2))
+            return set_error(PFC_ERR_INVALID_ARG, "bad operator");
+    if (!std::isfinite(alpha)) return set_error(PFC_ERR_INVALID_ARG, "alpha must be finite");
+    const double kmax = M_PI / b->dx;
+    if (min_implicit(ops, 2, alpha, b->dt, ndim * kmax * kmax) <= 0.0)
+        return set_error(PFC_ERR_UNSTABLE_OPERATOR, "the coupled implicit system is not positive definite for some k");
+    PFC_BCUDA(cudaStreamSynchronize(b->stream));
+    if (!b->pair_moff) PFC_BCUDA(cudaMalloc(&b->pair_moff, 2 * sizeof(int64_t)));
+    if (!b->pair_mean) PFC_BCUDA(cudaMalloc(&b->pair_mean, 2 * sizeof(double)));
+    b->has_pair = true;
+    b->pair_ndim = ndim;
+    for (int d = 0; d < 3; ++d) b->pair_n[d] = n[d];
+    b->pair_ops[0] = ops[0];
+    b->pair_ops[1] = ops[1];
+    b->pair_alpha = alpha;
+    const pfc_status st = b->prec == PFC_FP64 ? persist_prepare<double>(b) : persist_prepare<float>(b);
+    if (st != PFC_OK) {
+        b->has_pair = false;
+        return st;
+    }
+    b->sched = PFC_BATCH_PERSISTENT;
+    return PFC_OK;
+}
+
+pfc_status pfc_batch_step_with_pair(pfc_batch *b, void *packed_state, void *pair_state, int64_t nsteps) {
+    if (!b) return set_error(PFC_ERR_INVALID_ARG, "invalid batch");
+    if (!b->has_pair) return set_error(PFC_ERR_INVALID_ARG, "the batch has no coupled pair");
+    if (!packed_state || !pair_state) return set_error(PFC_ERR_INVALID_ARG, "null state");
+    if (nsteps < 0) return set_error(PFC_ERR_INVALID_ARG, "nsteps must be >= 0");
+    if ((reinterpret_cast<uintptr_t>(packed_state) & 15) != 0 || (reinterpret_cast<uintptr_t>(pair_state) & 15) != 0)
+        return set_error(PFC_ERR_INVALID_ARG, "states must be 16-byte aligned");
+    if (nsteps == 0) return PFC_OK;
+    return b->prec == PFC_FP64 ? persist_step<double>(b, packed_state, nsteps, pair_state)
+                               : persist_step<float>(b, packed_state, nsteps, pair_state);
 }
 
 pfc_status pfc_batch_autotune(pfc_batch *b, int max_candidates, int trial_steps, double *best_ms_out) {
@@ -895,6 +1044,7 @@ pfc_status pfc_batch_set_schedule(pfc_batch *b, int schedule, int threads, int64
         return set_error(PFC_ERR_INVALID_ARG, "bad on-chip limit or block share");
     PFC_BCUDA(cudaStreamSynchronize(b->stream));
     if (schedule == PFC_BATCH_GRAPH) {
+        if (b->has_pair) return set_error(PFC_ERR_INVALID_ARG, "a batch with a coupled pair runs the persistent schedule");
         b->sched = schedule;
         return PFC_OK;
     }

@@ -26,12 +26,13 @@ template <typename R> struct Step2Args {
 // Three tiles of shared memory: A keeps, per register slot of its owner thread, first N0 then
 // e1 and finally the solved c field; N holds N1; B is the transforms' workspace. Only one
 // register set is live at a time.
+// The body of one block (column group cg, split index kp); k_line_step2 runs it as its own
+// block, the persistent batch kernel once per work item.
 template <typename R>
-__global__ void __launch_bounds__(512, 1) k_line_step2(const Geom g, const Step2Args<R> a) {
+__device__ __forceinline__ void line_step2_body(const Geom &g, const Step2Args<R> &a, int cg, int kp) {
     using V = typename VT<R>::V;
     extern __shared__ __align__(16) unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
-    const int cg = blockIdx.x, kp = blockIdx.y;
     V *A = sm;
     V *B = sm + g.tsz;
     V *N = sm + 2 * g.tsz;
@@ -125,5 +126,10 @@ __global__ void __launch_bounds__(512, 1) k_line_step2(const Geom g, const Step2
     for (int m = 0; m < 8; ++m) __stcg(&X1[xprime_index(g, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)], v[m]);
 }
 #undef PFC_KSQ
+
+template <typename R>
+__global__ void __launch_bounds__(512, 1) k_line_step2(const Geom g, const Step2Args<R> a) {
+    line_step2_body<R>(g, a, blockIdx.x, blockIdx.y);
+}
 
 }  // namespace pfc

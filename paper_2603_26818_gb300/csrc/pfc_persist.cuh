@@ -7,7 +7,8 @@
 //     memory). A block takes one member at a time from a queue, computes its FP64 mean, then runs
 //     all nsteps steps of that member in shared memory (onchip_body). These blocks never wait on
 //     any other block.
-//   blocks [n_oc_blocks, grid): the two-pass members of every other class, phase by phase:
+//   blocks [n_oc_blocks, grid): the two-pass members of every other class (and the two fields
+//     of an attached coupled pair, whose line items take both fields of a tile), phase by phase:
 //     the FP64 means; the entry row pass (real state -> X'); nsteps times the psi^3 row pass and
 //     the update line pass (the two passes of the single-grid plans); the exit row pass (X' ->
 //     real state). Within a phase a block takes work items from the phase's queue (an atomic
@@ -29,6 +30,7 @@
 // of a phase is visible to every block in the phases after the barrier.
 #pragma once
 
+#include "pfc_coupled.cuh"
 #include "pfc_onchip.cuh"
 #include "pfc_pass.cuh"
 
@@ -58,6 +60,8 @@ template <typename R> struct PbArgs {
     int extra;
     int64_t nsteps;
     void *state;                 // packed real state of the batch (in/out)
+    int pair_ci;                 // class index of an attached coupled pair (-1: none); its
+    Step2Args<R> pair;           // members are its two fields, its line items the 2x2 update
     unsigned *sync;              // PB_NSYNC words
     int *status;
     long long budget;            // clock64 cycles a barrier wait may take
@@ -125,7 +129,7 @@ __device__ __forceinline__ int pb_take(unsigned *q, int *s_item) {
 // fixed order; sets STATUS_NONFINITE on NaN or Inf.
 template <typename R, int NT>
 __device__ __forceinline__ void pb_mean(const PbClass<R> &c, int m, const PbArgs<R> &a, double *sh) {
-    const R *x = reinterpret_cast<const R *>(a.state) + c.fwd.moff[m];
+    const R *x = reinterpret_cast<const R *>(c.fwd.in) + c.fwd.moff[m];
     const int64_t n = c.g.nreal;
     double acc = 0.0;
     bool bad = false;
@@ -180,6 +184,12 @@ __device__ __forceinline__ void pb_line(const PbClass<R> &c, int cg, int kp, int
     case 9: pb_line_t<R, 9>(c, cg, kp, m); return;
     default: pb_line_t<R, 0>(c, cg, kp, m); return;
     }
+}
+
+// an update item of an attached coupled pair: both fields of one tile
+template <typename R>
+__device__ __noinline__ void pb_line_pair(const PbClass<R> &c, const Step2Args<R> &a, int cg, int kp) {
+    line_step2_body<R>(c.g, a, cg, kp);
 }
 
 // entry and exit row passes
@@ -267,7 +277,8 @@ __global__ void __launch_bounds__(NT, PFC_PB_THREADS_PER_SM / NT) k_batch_persis
             const int it = pb_take(&q[phase % 3], &s_item);
             if (it >= a.n_line) break;
             const int4 w = a.line_items[it];
-            pb_line<R>(a.cls[w.x], w.z, w.w, w.y);
+            if (w.x == a.pair_ci) pb_line_pair<R>(a.cls[w.x], a.pair, w.z, w.w);
+            else pb_line<R>(a.cls[w.x], w.z, w.w, w.y);
             __syncthreads();
         }
         if (!next_phase()) return;

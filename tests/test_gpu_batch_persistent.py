@@ -193,3 +193,75 @@ def test_switching_schedules_keeps_the_graph_schedule_valid():
         ref = oracle.step(parts[d].reshape(ny, nx), DX, 0.5, (0, r, 0.0, 0.0), 52)
         assert rel(b.view(x, d).cpu().numpy(), ref) <= 1e-11
     b.close()
+
+
+@pytest.mark.parametrize("prec,tol,shape,opc,threads", [
+    ("fp64", 1e-11, (16, 32, 32), (1, -0.3, 0.05, math.sqrt(4.0 / 3.0)), 128),
+    ("fp32", 1e-5, (32, 32, 64), (0, -0.2, 0.0, 0.0), 256),
+    ("fp64", 1e-11, (64, 128), (0, -0.2, 0.0, 0.0), 256)])
+def test_coupled_pair_in_the_persistent_launch(prec, tol, shape, opc, threads):
+    """A coupled density/composition pair attached to a batch steps in the same launch as the
+    domains: the pair against the oracle's Cramer-rule step, the domains against the oracle, the
+    pair's masses conserved. dt = 0.5 for both (the pair takes the batch's dt)."""
+    from paper_2603_26818_gb300 import binding
+    opp, alpha, nsteps = (0, -0.25, 0.0, 0.0), 0.1, 8
+    draws = [(64, 64, -0.25, -0.25), (128, 256, -0.3, -0.3), (16, 16, -0.2, -0.3)]
+    b = _batch(draws, prec)
+    b.set_schedule("persistent", threads=threads)
+    b.attach_pair(shape, [binding.make_op(*opp), binding.make_op(*opc)], alpha)
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    x, parts = _state(draws, 900, dtype)
+    p0 = inputs.uniform_state(shape, -0.25, 0.05, seed=61)
+    c0 = inputs.uniform_state(shape, -0.2, 0.05, seed=62)
+    if prec == "fp32":
+        p0, c0 = p0.astype(np.float32).astype(np.float64), c0.astype(np.float32).astype(np.float64)
+    pair = torch.from_numpy(np.stack([p0, c0])).to(device="cuda", dtype=dtype)
+    with pytest.raises(binding.PfcError):
+        b.step(x, 1)   # a batch with a pair steps only with it
+    b.step_with_pair(x, pair, nsteps)
+    b.sync()
+    rp, rc = oracle.step2(p0, c0, DX, 0.5, opp, opc, alpha, nsteps)
+    got = pair.double().cpu().numpy()
+    assert rel(got[0], rp) <= tol and rel(got[1], rc) <= tol
+    assert abs(got[0].mean() - p0.mean()) <= 1e-6 * abs(p0.mean())
+    assert abs(got[1].mean() - c0.mean()) <= 1e-6 * abs(c0.mean())
+    for d, (ny, nx, r, m) in enumerate(draws):
+        ref = oracle.step(parts[d].reshape(ny, nx), DX, 0.5, (0, r, 0.0, 0.0), nsteps)
+        assert rel(b.view(x, d).double().cpu().numpy(), ref) <= (1e-12 if prec == "fp64" else 1e-5)
+    assert b.schedule_info()["schedule"] == 1
+    b.close()
+
+
+def test_coupled_pair_config_size_with_the_ensemble_autotuned():
+    """The ensemble workload with the coupled pair at 256^3 FP32 in one launch, the schedule's
+    block size autotuned: the pair against a standalone coupled plan from the same start
+    (1e-5 after 10 steps) and a sample of domains against the graph schedule."""
+    from paper_2603_26818_gb300 import binding
+    draws = inputs.batch_draws(1024, seed=4)
+    b = _batch(draws, "fp32")
+    ops = [binding.make_op(0, -0.25), binding.make_op(0, -0.25)]
+    b.attach_pair((256, 256, 256), ops, 0.1)
+    b.autotune(2, 4)
+    assert b.schedule_info()["schedule"] == 1
+    x, parts = _state(draws, 4000, torch.float32)
+    p0 = inputs.uniform_state((256, 256, 256), -0.25, 0.01, seed=5)
+    c0 = inputs.uniform_state((256, 256, 256), -0.2, 0.01, seed=6)
+    pair = torch.from_numpy(np.stack([p0, c0])).to(device="cuda", dtype=torch.float32)
+    ref = pair.clone()
+    b.step_with_pair(x, pair, 10)
+    b.sync()
+    pl = binding.Plan((256, 256, 256), DX, 0.5, ops, precision="fp32", coupling=0.1)
+    pl.step(ref, 10)
+    a, c = pair.double().cpu().numpy(), ref.double().cpu().numpy()
+    assert rel(a[0], c[0]) <= 1e-5 and rel(a[1], c[1]) <= 1e-5
+    bg = _batch(draws, "fp32")
+    y, _ = _state(draws, 4000, torch.float32)
+    bg.step(y, 10)
+    xs, ys = x.double().cpu().numpy(), y.double().cpu().numpy()
+    for d in range(0, 1024, 37):
+        ny, nx, r, m = draws[d]
+        o = bg.offsets[d]
+        assert rel(xs[o:o + ny * nx], ys[o:o + ny * nx]) <= 1e-5, d
+    b.close()
+    bg.close()
+    pl.close()
