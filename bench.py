@@ -81,6 +81,11 @@ CONFIGS = {
     "4p": dict(desc="1024 batched 2D one-mode domains as config 4a, FP32-mixed; 20 time steps per bench step "
                     "in one persistent cooperative launch (replayed as a one-node CUDA graph)",
                kind="batch", prec="fp32", dt=0.5, inner=20, sweeps=5, schedule="persistent"),
+    "4": dict(desc="config 4 in one persistent launch: the 1024 domains of config 4a and the coupled pair of "
+                   "config 4b (256^3, alpha=0.1) stepped together, FP32-mixed, dt=0.5; 20 time steps per bench step; "
+                   "rate in grid points of the domains plus grid points of the pair (both fields of a pair point "
+                   "counted once) per second; block size autotuned",
+              kind="batch", prec="fp32", dt=0.5, inner=20, sweeps=5, pair=(256, 256, 256), autotune=True),
     "4b": dict(desc="coupled density/composition pair 256^3 FP32-mixed, alpha=0.1, one-mode r=-0.25 "
                     "for both, means -0.25/-0.2, noise 0.01 (seeds 5, 6), dt=0.5; 10 time steps per "
                     "bench step", kind="pair", dims=(256, 256, 256), prec="fp32", dt=0.5, inner=10,
@@ -153,6 +158,16 @@ def run_config(args):
         state = torch.from_numpy(np.concatenate(parts)).to(device=dev, dtype=dtype)
         npts = state.numel()
         run = lambda: obj.step(state, c["inner"])
+        if c.get("pair"):
+            # the coupled pair of config 4b in the same persistent launch
+            shape = c["pair"]
+            p0 = inputs.uniform_state(shape, -0.25, 0.01, seed=5)
+            c0 = inputs.uniform_state(shape, -0.2, 0.01, seed=6)
+            obj.attach_pair(shape, [binding.make_op(0, -0.25), binding.make_op(0, -0.25)], 0.1)
+            pair_state = torch.from_numpy(np.stack([p0, c0])).to(device=dev, dtype=dtype)
+            extra["pair_points"] = int(p0.size)
+            extra["pair_grid"] = list(shape)
+            run = lambda: obj.step_with_pair(state, pair_state, c["inner"])
         if c.get("schedule") == "persistent":
             obj.set_schedule("persistent", threads=int(os.environ.get("PFC_BENCH_PB_THREADS", "256")),
                              onchip_smem_max=int(os.environ.get("PFC_BENCH_PB_ONCHIP", "0")),
@@ -251,8 +266,14 @@ def run_config(args):
     steps = args.steps * c["inner"]
     value = npts * steps / (total * 1e-3)
     bpp = c["sweeps"] * vb       # bytes per grid point per step (a half spectrum ~ N/2 complex)
+    step_bytes = bpp * npts
+    if "pair_points" in extra:
+        # the pair: 10 sweeps a step (row pass 2 x 2 fields, line pass reads 4 arrays, writes 2)
+        step_bytes += 10 * vb * extra["pair_points"]
+        npts += extra["pair_points"]
+        bpp = step_bytes / npts
     peak, peak_kind = hbm_peak()
-    gbs = bpp * npts * steps / (total * 1e-3) / 1e9
+    gbs = step_bytes * steps / (total * 1e-3) / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",

@@ -307,8 +307,9 @@ pfc_status pfc_batch_step(pfc_batch *batch, void *packed_state, int64_t nsteps);
 /* Autotune the tiling of every size class as pfc_plan_autotune does, each class timed alone on
  * trial_steps of its steps on zero fields; *best_ms_out (host, may be NULL) = the sum over
  * classes of the chosen ms per step. Then the schedule (pfc_batch_set_schedule): whole calls of
- * trial_steps steps on a zero state with the graph schedule and the persistent one at 256 and
- * 128 threads a block, the fastest kept (pfc_batch_schedule_info reports it). The step graph is
+ * trial_steps steps on a zero state with the graph schedule and the persistent one at 256,
+ * 128 and 512 threads a block (the persistent one only when a coupled pair is attached), the
+ * fastest kept (pfc_batch_schedule_info reports it). The step graph is
  * captured again at the next pfc_batch_step. Synchronises. Errors: INVALID_ARG, UNSUPPORTED,
  * CUDA. */
 pfc_status pfc_batch_autotune(pfc_batch *batch, int max_candidates, int trial_steps,

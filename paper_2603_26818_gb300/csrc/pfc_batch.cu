@@ -335,29 +335,39 @@ pfc_status tune_class(pfc_batch *b, BatchClass &c, int max_candidates, int trial
 
 // Line tiles of exactly nt threads (Q W = 8 nt) for a class of the persistent launch: the
 // candidate the planner scores best among them (one-axis tiles, up to 128 columns).
-// ntile: line tiles in shared memory (2; 3 for the coupled pair's update).
+// ntile: line tiles in shared memory (2; 3 for the coupled pair's update). Among the tilings,
+// those whose shared memory (the larger of the row and line pass) fits smem_pref come first,
+// then the planner's score: the launch's blocks all take the largest shared memory of any
+// class, so one greedy class would lower the blocks an SM holds for every class.
 bool persist_tiles(Tiles &t, int nx, int ny, int nz, size_t vb, int nt, size_t smem_max, int members,
-                   int ntile, int ltab) {
+                   int ntile, int ltab, size_t smem_pref) {
     const Geom g0 = grid_geom(nx, ny, nz);
+    bool found = false, best_fit = false;
     long best = LONG_MIN;
-    TileChoice bc;
     for (int Py = 1; Py <= 8; Py *= 2)
         for (int Pz = 1; Pz <= (nz > 1 ? 8 : 1); Pz *= 2)
             for (int W = 1; W <= 128; W *= 2) {
                 if (ny % Py || nz % Pz || (int64_t)(ny / Py) * (nz / Pz) * W != 8 * (int64_t)nt) continue;
                 const long sc = tile_score(g0, Py, Pz, W, vb, ntile, smem_max, false, ilog2(nt), 1, 1, 128);
-                if (sc > best) {
+                if (sc == LONG_MIN) continue;
+                TileChoice c;
+                c.Py = Py;
+                c.Pz = Pz;
+                c.W = W;
+                c.cluster = 0;
+                Tiles tc;
+                if (!plan_tiles_as(tc, c, nx, ny, nz, vb, ntile, smem_max, members, 128) || tc.nt_line != nt) continue;
+                const bool fit = std::max(tc.smem_row, tc.smem_line) <= smem_pref;
+                if (!found || (fit && !best_fit) || (fit == best_fit && sc > best)) {
+                    found = true;
+                    best_fit = fit;
                     best = sc;
-                    bc.Py = Py;
-                    bc.Pz = Pz;
-                    bc.W = W;
-                    bc.cluster = 0;
+                    t = tc;
                 }
             }
-    if (best == LONG_MIN) return false;
-    if (!plan_tiles_as(t, bc, nx, ny, nz, vb, ntile, smem_max, members, 128)) return false;
+    if (!found) return false;
     t.g.ltab = ltab;
-    return t.nt_line == nt;
+    return true;
 }
 
 template <typename R> void free_persist(pfc_batch *b) {
@@ -401,6 +411,12 @@ template <typename R> pfc_status persist_prepare(pfc_batch *b) {
     if (b->p_budget <= 0) b->p_budget = (long long)clk_khz * 2000;
     if (b->cls.size() > (size_t)PB_MAXC) return set_error(PFC_ERR_UNSUPPORTED, "too many size classes for one persistent launch");
     const int nt = b->p_nt;
+    // shared memory a block may take while four blocks fit an SM (the pass bodies' 16 named
+    // barriers a block allow at most four)
+    int smem_sm = 0;
+    PFC_BCUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    // (1 KB a block is reserved by the hardware, 8 B are the kernel's static shared memory)
+    const size_t smem_pref = (size_t)smem_sm / 4 > 1032 ? (size_t)smem_sm / 4 - 1032 : 0;
     // Which classes run on chip: those with no tiling of the block size (both extents <= 128),
     // and, when oc_max > 0, those whose two half spectra fit oc_max. (Inside this launch the
     // on-chip body runs at the launch's register budget of 64 a thread, far below the 214 of its
@@ -415,7 +431,8 @@ template <typename R> pfc_status persist_prepare(pfc_batch *b) {
         BatchClass &c = b->cls[i];
         oc_smem[i] = onchip_smem(c.ny, c.nx, vb);
         oc_able[i] = c.ny <= ONCHIP_MAX && c.nx <= ONCHIP_MAX && oc_smem[i] <= (size_t)optin;
-        tp_ok[i] = persist_tiles(tl[i], c.nx, c.ny, 1, vb, nt, (size_t)optin, (int)c.members.size(), 2, BATCH_LTAB);
+        tp_ok[i] = persist_tiles(tl[i], c.nx, c.ny, 1, vb, nt, (size_t)optin, (int)c.members.size(), 2, BATCH_LTAB,
+                                 smem_pref);
         if (!tp_ok[i] && !oc_able[i])
             return set_error(PFC_ERR_UNSUPPORTED, "no tiling of a domain size fills the persistent launch's blocks");
         c.p_onchip = !tp_ok[i];
@@ -466,7 +483,8 @@ template <typename R> pfc_status persist_prepare(pfc_batch *b) {
         if (nclass + 1 > (size_t)PB_MAXC)
             return set_error(PFC_ERR_UNSUPPORTED, "too many size classes for one persistent launch");
         Tiles t;
-        if (!persist_tiles(t, b->pair_n[0], b->pair_n[1], b->pair_n[2], vb, nt, (size_t)optin, 2, 3, BATCH_LTAB))
+        if (!persist_tiles(t, b->pair_n[0], b->pair_n[1], b->pair_n[2], vb, nt, (size_t)optin, 2, 3, BATCH_LTAB,
+                           smem_pref))
             return set_error(PFC_ERR_UNSUPPORTED, "no tiling of the coupled pair's grid fills the persistent launch's blocks");
         b->pair_t = t;
         smem = std::max(smem, std::max(t.smem_row, t.smem_line));
@@ -485,6 +503,7 @@ template <typename R> pfc_status persist_prepare(pfc_batch *b) {
         const int64_t moff[2] = {0, t.g.nreal};
         PFC_BCUDA(cudaMemcpy(b->pair_moff, moff, sizeof(moff), cudaMemcpyHostToDevice));
     }
+    smem = std::max(smem, (size_t)nt * sizeof(double));   // the mean reduction's buffer
     int bps = 0;
     PFC_BCUDA(persist_occ<R>(nt, smem, &bps));
     if (bps < 1) return set_error(PFC_ERR_UNSUPPORTED, "the persistent kernel does not fit an SM with this shared memory");
@@ -708,8 +727,8 @@ template <typename R> pfc_status persist_step(pfc_batch *b, void *state, int64_t
 }
 
 // The schedule of pfc_batch_step chosen by measurement: whole calls of trial_steps (at least 20)
-// steps on a zero state (a fixed point of the step) with the graph schedule and the persistent one at 256
-// and 128 threads a block; the fastest is kept.
+// steps on a zero state (a fixed point of the step) with the graph schedule and the persistent one at
+// 256, 128 and 512 threads a block; the fastest is kept.
 template <typename R> pfc_status tune_schedule(pfc_batch *b, int trial_steps) {
     trial_steps = std::max(trial_steps, 20);   // the graph schedule replays its graph from 16 steps
     int64_t total = 0;
@@ -722,7 +741,8 @@ template <typename R> pfc_status tune_schedule(pfc_batch *b, int trial_steps) {
     cudaError_t e = cudaMemsetAsync(tmp, 0, (size_t)(total + ptotal) * sizeof(R), b->stream);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    const int cand[3][2] = {{PFC_BATCH_GRAPH, 0}, {PFC_BATCH_PERSISTENT, 256}, {PFC_BATCH_PERSISTENT, 128}};
+    const int cand[4][2] = {{PFC_BATCH_GRAPH, 0}, {PFC_BATCH_PERSISTENT, 256}, {PFC_BATCH_PERSISTENT, 128},
+                            {PFC_BATCH_PERSISTENT, 512}};
     int best = -1;
     double best_ms = 1e300;
     pfc_status st = PFC_OK;
@@ -731,7 +751,7 @@ template <typename R> pfc_status tune_schedule(pfc_batch *b, int trial_steps) {
         return b->sched == PFC_BATCH_PERSISTENT ? persist_step<R>(b, tmp, trial_steps, ptmp)
                                                 : batch_step_impl<R>(b, tmp, trial_steps);
     };
-    for (int i = b->has_pair ? 1 : 0; i < 3 && e == cudaSuccess && st == PFC_OK; ++i) {
+    for (int i = b->has_pair ? 1 : 0; i < 4 && e == cudaSuccess && st == PFC_OK; ++i) {
         b->sched = cand[i][0];
         if (b->sched == PFC_BATCH_PERSISTENT) {
             b->p_nt = cand[i][1];

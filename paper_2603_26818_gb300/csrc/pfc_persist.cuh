@@ -222,7 +222,11 @@ template <typename R, int NT>
 __global__ void __launch_bounds__(NT, PFC_PB_THREADS_PER_SM / NT) k_batch_persist(const __grid_constant__ PbArgs<R> a) {
     __shared__ int s_item;
     __shared__ int s_flag;
-    __shared__ double s_red[NT];
+    // the mean reduction runs between work items: it takes the start of the dynamic shared
+    // memory (at least NT doubles: every item's tiles are larger), so the kernel's static shared
+    // memory stays at two words and four blocks of up to 55 KB fit an SM
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double *s_red = reinterpret_cast<double *>(smraw);
 
     if ((int)blockIdx.x < a.n_oc_blocks) {
         for (;;) {
