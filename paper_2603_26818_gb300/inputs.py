@@ -103,3 +103,25 @@ def batch_draws(n_domains: int, seed: int, sizes=(64, 128, 256, 512),
         m = mean_range[0] + (mean_range[1] - mean_range[0]) * u[d, 3]
         out.append((ny, nx, float(r), float(m)))
     return out
+
+
+def apfc_triad(k0: float = 1.0):
+    """The three reciprocal vectors of a 2D triangular lattice of wavenumber k0, (x, y)
+    components, 120 degrees apart and summing to zero."""
+    h = math.sqrt(3.0) / 2.0
+    return [(-h * k0, -0.5 * k0), (0.0, k0), (h * k0, -0.5 * k0)]
+
+
+def apfc_bcc(k0: float = 1.0):
+    """The six shortest reciprocal vectors of a BCC lattice of wavenumber k0 (the {110} family,
+    one of each +- pair), (x, y, z) components."""
+    s = k0 / math.sqrt(2.0)
+    return [(s, s, 0.0), (s, 0.0, s), (0.0, s, s), (s, -s, 0.0), (s, 0.0, -s), (0.0, s, -s)]
+
+
+def apfc_amplitudes(namp: int, shape, amplitude: float, noise_amp: float, seed: int):
+    """Complex amplitudes (namp, *shape): amplitude + noise_amp (U[-1, 1] + i U[-1, 1]) per
+    point (stream: real parts of every amplitude, then imaginary parts)."""
+    n = int(np.prod(shape))
+    u = uniform(seed, 2 * namp * n).reshape(2, namp, *shape)
+    return (amplitude + noise_amp * (2.0 * u[0] - 1.0)) + 1j * (noise_amp * (2.0 * u[1] - 1.0))
