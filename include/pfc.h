@@ -278,6 +278,37 @@ pfc_status pfc_hydro_create(pfc_hydro **out, int ndim, const int64_t *dims, doub
 pfc_status pfc_hydro_step(pfc_hydro *h, void *psi, void *v, int64_t nsteps);
 pfc_status pfc_hydro_destroy(pfc_hydro *h);
 
+/* ---------------------------------------------------------------------------------- */
+/* Amplitude-expansion PFC: the density psi = psibar + sum_j [eta_j exp(i k_j.r) + c.c.] */
+/* carried as namp complex amplitude fields. The paper names this model (multiphysics  */
+/* section) as a workload of tens of complex fields; its equations here are the        */
+/* projection of Eq. (6) with the energy of Eq. (5) onto the modes k_j.                */
+/* ---------------------------------------------------------------------------------- */
+typedef struct pfc_apfc pfc_apfc;
+
+/* ndim 2 or 3, dims slowest first (each in [8, 4096], prime factors 2, 3, 5, 7); dx, dt > 0;
+ * op the PFC operator L of Eq. (5); namp in [1, 16] amplitudes with reciprocal-lattice
+ * vectors kvecs[namp * ndim] (host, components x first); psibar the mean density (fixed).
+ * One step per amplitude j, every grid wavevector q (FFT order; the middle bin of an even axis
+ * is -n/2):
+ *   eta_hat_j <- (eta_hat_j - dt Q N_hat_j) / (1 + dt Q L(Q)),  Q = |k_j + q|^2,
+ * the update of Listing 1 at the shifted wavevector, with N_j the component of psi^3 at k_j:
+ * 3 psibar^2 eta_j plus the products of two (times 3 psibar) and three signed amplitudes whose
+ * vectors sum to k_j (found on the host, exact to 1e-9 relative; eta_{-m} = conj(eta_m)).
+ * Transforms are complex mixed-radix passes, one warp a line; a step is 7 sweeps of the
+ * amplitude fields in 2D, 11 in 3D. Allocates two copies of the amplitude fields and tables.
+ * Errors: INVALID_ARG, UNSUPPORTED, UNSTABLE_OPERATOR (1 + dt Q L(Q) <= 0 for some Q on the
+ * grid), OUT_OF_MEMORY, CUDA. */
+pfc_status pfc_apfc_create(pfc_apfc **out, int ndim, const int64_t *dims, double dx, double dt,
+                           const pfc_op *op, int namp, const double *kvecs, double psibar,
+                           int precision, void *stream);
+/* Advance eta (device, namp complex fields [amp][z][y][x], interleaved re/im in the
+ * precision's real type, 16-byte aligned) by nsteps, in place, stream ordered. */
+pfc_status pfc_apfc_step(pfc_apfc *h, void *eta, int64_t nsteps);
+/* *count_out (host) = the number of resonance terms over all amplitudes. Synchronises. */
+pfc_status pfc_apfc_resonances(pfc_apfc *h, int32_t *count_out);
+pfc_status pfc_apfc_destroy(pfc_apfc *h);
+
 /* Names of a status code and of the last error on this thread. Never NULL. */
 const char *pfc_status_string(pfc_status status);
 const char *pfc_last_error(void);

@@ -30,6 +30,7 @@ EXPORTS = ["pfc_plan_create", "pfc_plan_destroy", "pfc_step", "pfc_fft_r2c", "pf
            "pfc_batch_info",
            "pfc_set_integrator", "pfc_record_bytes", "pfc_step_record", "pfc_adjoint_segment",
            "pfc_hydro_create", "pfc_hydro_step", "pfc_hydro_destroy",
+           "pfc_apfc_create", "pfc_apfc_step", "pfc_apfc_resonances", "pfc_apfc_destroy",
            "pfc_status_string", "pfc_last_error", "pfc_batch_create", "pfc_batch_destroy",
            "pfc_batch_step", "pfc_batch_mass", "pfc_batch_set_schedule", "pfc_batch_schedule_info",
            "pfc_batch_set_wait_limit", "pfc_batch_sync", "pfc_batch_attach_pair",
@@ -75,6 +76,10 @@ def load_library(path: str = LIB_PATH):
         "pfc_set_integrator": [vp, cint, dbl],
         "pfc_record_bytes": [vp, i64, P(i64)],
         "pfc_hydro_create": [P(vp), cint, P(i64), dbl, dbl, P(pfc_op), dbl, dbl, dbl, cint, vp],
+        "pfc_apfc_create": [P(vp), cint, P(i64), dbl, dbl, P(pfc_op), cint, P(dbl), dbl, cint, vp],
+        "pfc_apfc_step": [vp, vp, i64],
+        "pfc_apfc_resonances": [vp, P(ctypes.c_int32)],
+        "pfc_apfc_destroy": [vp],
         "pfc_hydro_step": [vp, vp, vp, i64],
         "pfc_hydro_destroy": [vp],
         "pfc_step_record": [vp, vp, i64, vp],
@@ -329,6 +334,51 @@ class Hydro:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             check(load_library().pfc_hydro_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Apfc:
+    """A pfc_apfc: the amplitude-expansion PFC model, namp complex amplitude fields on one grid.
+
+    dims slowest first; kvecs a list of namp vectors (x first); eta a complex CUDA tensor of shape
+    (namp, *dims), complex64 for "fp32", complex128 for "fp64"."""
+
+    def __init__(self, dims, dx, dt, op, kvecs, psibar, precision="fp32", stream=None):
+        lib = load_library()
+        op = op if isinstance(op, pfc_op) else make_op(*op)
+        self.dims = tuple(int(d) for d in dims)
+        self.ndim = len(self.dims)
+        self.namp = len(kvecs)
+        self.dtype = torch.complex128 if precision == "fp64" else torch.complex64
+        flat = [float(c) for k in kvecs for c in list(k)[:self.ndim]]
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        check(lib.pfc_apfc_create(ctypes.byref(h), self.ndim, (ctypes.c_int64 * self.ndim)(*self.dims), float(dx),
+                                  float(dt), ctypes.byref(op), self.namp, (ctypes.c_double * len(flat))(*flat),
+                                  float(psibar), PFC_FP64 if precision == "fp64" else PFC_FP32_MIXED,
+                                  ctypes.c_void_p(_stream_handle(self._stream))))
+        self._h = h
+
+    def step(self, eta: torch.Tensor, nsteps: int = 1) -> torch.Tensor:
+        if tuple(eta.shape) != (self.namp,) + self.dims:
+            raise PfcError(1, f"eta must have shape {(self.namp,) + self.dims}")
+        check(load_library().pfc_apfc_step(self._h, ctypes.c_void_p(_dev_ptr(eta, self.dtype, "eta")), int(nsteps)))
+        return eta
+
+    def resonances(self) -> int:
+        n = ctypes.c_int32()
+        check(load_library().pfc_apfc_resonances(self._h, ctypes.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            check(load_library().pfc_apfc_destroy(self._h))
             self._h = None
 
     def __del__(self):

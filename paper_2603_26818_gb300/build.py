@@ -56,11 +56,11 @@ def _link(out, objs, extra):
 
 
 # translation units of libpfc.so: host plan logic, the kernels of each precision, and the
-# allocation-free step, the persistent batch kernel of each precision
+# allocation-free step, the persistent batch kernel of each precision, the amplitude-expansion model
 LIB_UNITS = ["pfc_api.cu", "pfc_batch.cu", "pfc_kern_f32.cu", "pfc_kern_f64.cu", "pfc_line_fixed_f32.cu",
              "pfc_line_fixed_f64.cu", "pfc_row_fixed_f32.cu", "pfc_row_fixed_f64.cu", "pfc_noalloc.cu",
              "pfc_persist_f32_128.cu", "pfc_persist_f32_256.cu", "pfc_persist_f32_512.cu",
-             "pfc_persist_f64_128.cu", "pfc_persist_f64_256.cu", "pfc_persist_f64_512.cu"]
+             "pfc_persist_f64_128.cu", "pfc_persist_f64_256.cu", "pfc_persist_f64_512.cu", "pfc_apfc.cu"]
 
 
 def build(force: bool = False) -> str:
