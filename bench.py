@@ -107,6 +107,11 @@ CONFIGS = {
                    "v0=0.05 U[-1,1] (seeds 92-94); 2 steps per bench step (20 transforms of the grid a step)",
               kind="hydro", dims=(256, 256, 256), prec="fp32", op=(0, -0.25, 0.0, 0.0), dt=0.5, inner=2,
               sweeps=110),
+    "af": dict(desc="amplitude-expansion PFC, 3D BCC set of six complex amplitudes at 256^3 FP32-mixed, "
+                    "one-mode r=-0.25, psibar=-0.2, dx=1.1, dt=0.4, eta=0.1+0.02(U[-1,1]+iU[-1,1]) (torch "
+                    "generator, seed 9); 10 steps per bench step; rate in grid points x amplitudes per second, "
+                    "11 sweeps of 8 B a step", kind="apfc", dims=(256, 256, 256), prec="fp32",
+               op=(0, -0.25, 0.0, 0.0), dt=0.4, inner=10, sweeps=22),
     "3d64": dict(desc="3D two-mode 512^3 FP64 (three-pass schedule), as config 3; 4 time steps per bench step",
                  kind="plan", dims=(512, 512, 512), prec="fp64", op=(1, -0.3, 0.05, math.sqrt(4.0 / 3.0)),
                  dt=0.1, inner=4, sweeps=9),
@@ -201,6 +206,20 @@ def run_config(args):
                                                  for j in range(3)])).to(device=dev, dtype=dtype)
         npts = state.numel()
         run = lambda: obj.step(state, vel, c["inner"])
+    elif c["kind"] == "apfc":
+        shape = c["dims"]
+        kv = inputs.apfc_bcc(1.0)
+        obj = binding.Apfc(shape, 1.1, c["dt"], c["op"], kv, -0.2, precision=prec)
+        g = torch.Generator(device=dev)
+        g.manual_seed(9)
+        re = 0.1 + 0.02 * (2 * torch.rand((len(kv),) + tuple(shape), generator=g, device=dev) - 1)
+        im = 0.02 * (2 * torch.rand((len(kv),) + tuple(shape), generator=g, device=dev) - 1)
+        state = torch.complex(re, im).to(torch.complex64 if prec == "fp32" else torch.complex128)
+        del re, im
+        npts = state.numel()
+        extra["amplitudes"] = len(kv)
+        extra["resonance_terms"] = obj.resonances()
+        run = lambda: obj.step(state, c["inner"])
     elif c["kind"] == "largest":
         torch.cuda.empty_cache()
         n = largest_cube(torch.cuda.mem_get_info()[0])
