@@ -384,6 +384,60 @@ def other_grids(torch, dev, flush):
     return out
 
 
+def other_workloads(torch, dev, flush):
+    """Rates of the other rows at their bench sizes, short timings (same discipline): the
+    1024-domain ensemble on the graph and the persistent schedule, the paper's 750^3 grid
+    (mixed radix) and the amplitude-expansion BCC set at 256^3."""
+    import numpy as np
+    from paper_2603_26818_gb300 import binding, inputs
+    peak, _ = hbm_peak()
+    out = {}
+    draws = inputs.batch_draws(1024, seed=4)
+    parts = [inputs.uniform_state((ny, nx), m, 0.01, seed=1000 + i).ravel() for i, (ny, nx, r, m) in enumerate(draws)]
+    x0 = torch.from_numpy(np.concatenate(parts)).to(device=dev, dtype=torch.float32)
+    for sched in ("graph", "persistent"):
+        b = binding.Batch([(d[0], d[1]) for d in draws], [d[2] for d in draws], DX, 0.5, precision="fp32")
+        if sched == "persistent":
+            b.set_schedule("persistent", threads=256)
+        x = x0.clone()
+        ms = time_plan(torch, b, x, 20, 3, 2, flush)
+        out[f"batch_1024_domains_{sched}"] = {
+            "grid_point_steps_per_s": x.numel() / (ms * 1e-3), "ms_per_time_step": ms,
+            "hbm_frac_at_20_B_per_pt": 20 * x.numel() / (ms * 1e-3) / 1e9 / peak,
+            "tiles": "planner" if sched == "graph" else b.schedule_info()}
+        b.close()
+        del x
+    del x0
+    torch.cuda.empty_cache()
+    shape = (750, 750, 750)
+    p = binding.Plan(shape, DX, 0.5, [binding.make_op(0, -0.25)], precision="fp32")
+    x = seeded_uniform_state(shape, -0.25, 0.01, 8, torch.float32, dev)
+    ms = time_plan(torch, p, x, 4, 2, 2, flush)
+    npts = 750 ** 3
+    out["mixed_radix_750cube_fp32"] = {"grid_point_steps_per_s": npts / (ms * 1e-3), "ms_per_time_step": ms,
+                                       "hbm_frac_at_44_B_per_pt": 44 * npts / (ms * 1e-3) / 1e9 / peak}
+    p.close()
+    del x
+    torch.cuda.empty_cache()
+    shape = (256, 256, 256)
+    kv = inputs.apfc_bcc(1.0)
+    a = binding.Apfc(shape, 1.1, 0.4, (0, -0.25, 0.0, 0.0), kv, -0.2, precision="fp32")
+    g = torch.Generator(device=dev)
+    g.manual_seed(9)
+    re = 0.1 + 0.02 * (2 * torch.rand((6,) + shape, generator=g, device=dev) - 1)
+    im = 0.02 * (2 * torch.rand((6,) + shape, generator=g, device=dev) - 1)
+    eta = torch.complex(re, im)
+    del re, im
+    ms = time_plan(torch, a, eta, 10, 3, 2, flush)
+    npts = eta.numel()
+    out["apfc_bcc6_256cube_fp32"] = {"amplitude_point_steps_per_s": npts / (ms * 1e-3), "ms_per_time_step": ms,
+                                     "hbm_frac_at_88_B_per_amplitude_point": 88 * npts / (ms * 1e-3) / 1e9 / peak}
+    a.close()
+    del eta
+    torch.cuda.empty_cache()
+    return out
+
+
 def precision_report(torch, dev):
     """FP32-mixed against the FP64 path, per workload: relative L2 errors after each workload's
     full length (the FP64 paths are pinned to the oracle by the test suite). Both runs start from
@@ -823,6 +877,7 @@ def run_ours(args):
         # the other grids' rates (512^3, the largest cube that fits) and the other workloads'
         # FP32-mixed precision
         extras["other_grids"] = other_grids(torch, dev, flush)
+        extras["other_workloads"] = other_workloads(torch, dev, flush)
         extras["precision_per_config"] = {"2_4096sq_polycrystal_1000_steps": extras["precision_1000_steps"],
                                           **precision_report(torch, dev)}
         # ALU view: the transform flops of a step (5 log2 N per point for one r2c and one c2r,
