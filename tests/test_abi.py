@@ -138,3 +138,39 @@ def test_noalloc_host_side_rejections(lib):
     assert b"24 MiB" in lib.pfc_last_error()
     assert _noalloc(lib, (128, 128, 128), prec=0) == 2
     assert _noalloc(lib, (128, 128), nsteps=0) == 0                      # no work, no device
+
+
+def _apfc(lib, dims, kv, op=(0, -0.25, 0.0, 0.0), namp=None, dx=1.0, dt=0.3, prec=1, psibar=-0.2):
+    from paper_2603_26818_gb300 import binding
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int64 * len(dims))(*dims)
+    o = binding.make_op(*op)
+    flat = [float(c) for k in kv for c in k]
+    k = (ctypes.c_double * max(len(flat), 1))(*flat)
+    n = len(kv) if namp is None else namp
+    return lib.pfc_apfc_create(ctypes.byref(h), len(dims), d, dx, dt, ctypes.byref(o), n, k, psibar, prec, None)
+
+
+def test_apfc_host_side_rejections(lib):
+    """pfc_apfc_create rejects bad arguments before any device call: INVALID_ARG (1) for a bad
+    ndim, amplitude count, spacing, step, precision or a non-finite vector; UNSUPPORTED (2) for
+    an extent outside [8, 4096] or with a prime factor other than 2, 3, 5, 7; UNSTABLE_OPERATOR
+    (3) when 1 + dt Q L(Q) <= 0 for some shifted wavevector on the grid."""
+    tri = [(-0.866, -0.5), (0.0, 1.0), (0.866, -0.5)]
+    assert _apfc(lib, (16,), [(1.0,)]) == 1
+    assert _apfc(lib, (16, 16, 16, 16), tri) == 1
+    assert _apfc(lib, (16, 16), tri, namp=0) == 1
+    assert _apfc(lib, (16, 16), [(1.0, 0.0)] * 17) == 1
+    assert _apfc(lib, (16, 16), tri, dx=0.0) == 1
+    assert _apfc(lib, (16, 16), tri, dt=-1.0) == 1
+    assert _apfc(lib, (16, 16), tri, prec=7) == 1
+    assert _apfc(lib, (16, 16), [(float("nan"), 0.0)] + tri[1:]) == 1
+    assert _apfc(lib, (16, 16), tri, psibar=float("inf")) == 1
+    assert _apfc(lib, (16, 11), tri) == 2      # prime 11
+    assert _apfc(lib, (4, 16), tri) == 2       # below 8
+    assert _apfc(lib, (16, 8192), tri) == 2    # above 4096
+    # r = -3: L(Q) = r + (1 - Q)^2 is negative near Q = 1 and dt Q |L| > 1 there
+    assert _apfc(lib, (16, 16), tri, op=(0, -3.0, 0.0, 0.0), dt=1.0) == 3
+    null = ctypes.c_void_p()
+    assert lib.pfc_apfc_step(None, null, 1) == 1
+    assert lib.pfc_apfc_destroy(None) == 0

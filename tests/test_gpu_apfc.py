@@ -38,9 +38,14 @@ def rel(a, b):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("shape,kind,psibar,op", [((48, 60), "triad", -0.3, OP1), ((30, 64), "triad", 0.1, OP2),
-                                                  ((12, 20, 18), "bcc", -0.2, OP1), ((16, 14, 10), "bcc", 0.15, OP2)])
+                                                  ((12, 20, 18), "bcc", -0.2, OP1), ((16, 14, 10), "bcc", 0.15, OP2),
+                                                  ((15, 21), "single", -0.1, OP1), ((8, 8, 8), "bcc", 0.0, OP1),
+                                                  ((14, 49), "pair", 0.2, OP2)])
 def test_apfc_matches_oracle(shape, kind, psibar, op, prec):
-    kv = inputs.apfc_triad(1.0) if kind == "triad" else inputs.apfc_bcc(1.0)
+    """Edge cases among them: odd extents (15 x 21, 7^2), the smallest extent (8), one amplitude
+    (no cross resonance), two opposite-free vectors (no resonance beyond the self terms)."""
+    kv = {"triad": inputs.apfc_triad(1.0), "bcc": inputs.apfc_bcc(1.0), "single": [(1.0, 0.0)],
+          "pair": [(1.0, 0.0), (0.0, 1.0)]}[kind]
     eta = _eta(len(kv), shape, 21, prec)
     m = _model(shape, kv, psibar, op, prec)
     x = torch.from_numpy(eta).to(device="cuda", dtype=m.dtype)
