@@ -171,9 +171,11 @@ void launch_mr_col(cudaStream_t s, int mode, const MrGeom &g, const MrArgs<R> &a
                    const void *in, void *out) {
     const dim3 grid((ncols + W - 1) / W, axis == 1 ? g.nz : g.ny);
     const size_t smem = mr_col_smem(g.ax[axis].n, W, sizeof(typename VT<R>::V));
-    if (mode == MR_COL_FWD) k_mr_col<R, MR_COL_FWD><<<grid, 32 * W, smem, s>>>(g, a, axis, ncols, in, out);
-    else if (mode == MR_COL_INV) k_mr_col<R, MR_COL_INV><<<grid, 32 * W, smem, s>>>(g, a, axis, ncols, in, out);
-    else k_mr_col<R, MR_COL_UPDATE><<<grid, 32 * W, smem, s>>>(g, a, axis, ncols, in, out);
+    const int G = mr_col_group(W);
+    const int nt = 32 * W * G;
+    if (mode == MR_COL_FWD) k_mr_col<R, MR_COL_FWD><<<grid, nt, smem, s>>>(g, a, axis, ncols, in, out, G);
+    else if (mode == MR_COL_INV) k_mr_col<R, MR_COL_INV><<<grid, nt, smem, s>>>(g, a, axis, ncols, in, out, G);
+    else k_mr_col<R, MR_COL_UPDATE><<<grid, nt, smem, s>>>(g, a, axis, ncols, in, out, G);
 }
 template <typename R>
 void launch_mr_edges(cudaStream_t s, const MrGeom &g, const void *E, void *S, double scale) {

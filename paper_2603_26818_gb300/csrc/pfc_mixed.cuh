@@ -24,6 +24,8 @@
 // HBM far from busy).
 #pragma once
 
+#include <cstdlib>
+
 #include "pfc_pass.cuh"
 
 namespace pfc {
@@ -107,15 +109,17 @@ __device__ __forceinline__ void mr_dft(V (&x)[R]) {
 }
 
 
-// one stage of radix R, src -> dst, the butterflies strided over the warp: butterfly
-// b = q Ns + k (lane, lane + 32, ...), with q and k stepped, not divided, from one b to the next
+// one stage of radix R, src -> dst, the butterflies strided over the T threads of the line:
+// butterfly b = q Ns + k (th, th + T, ...), with q and k stepped, not divided, from one b to the
+// next
 template <int S, int R, typename V>
-__device__ __forceinline__ void mr_stage(const V *src, V *dst, const MrAxis &ax, int s, const V *tw, int lane) {
+__device__ __forceinline__ void mr_stage(const V *src, V *dst, const MrAxis &ax, int s, const V *tw, int th,
+                                         int T) {
     const int nb = ax.n / R, Ns = ax.ns[s];
     const V *t = tw + ax.twoff[s];
-    const int dq = 32 / Ns, dk = 32 - dq * Ns;
-    int q = lane / Ns, k = lane - q * Ns;
-    for (int b = lane; b < nb; b += 32) {
+    const int dq = T / Ns, dk = T - dq * Ns;
+    int q = th / Ns, k = th - q * Ns;
+    for (int b = th; b < nb; b += T) {
         V v[R];
 #pragma unroll
         for (int m = 0; m < R; ++m) v[m] = src[b + m * nb];
@@ -136,25 +140,34 @@ __device__ __forceinline__ void mr_stage(const V *src, V *dst, const MrAxis &ax,
     }
 }
 
-// The transform of one line by one warp: input in buffer a (natural order), b the other
-// buffer; returns the buffer that holds the result. Every lane of the warp calls it.
+// The transform of one line by the T threads of a line group (th its thread index): input in
+// buffer a (natural order), b the other buffer; returns the buffer that holds the result. Every
+// thread of the group calls it. Between stages the group syncs on its warp (T = 32) or on the
+// named barrier bar_id over T threads.
 template <int S, typename V>
-__device__ __forceinline__ V *mr_fft(V *a, V *b, const MrAxis &ax, const V *tw, int lane) {
+__device__ __forceinline__ V *mr_fft_g(V *a, V *b, const MrAxis &ax, const V *tw, int th, int T, int bar_id) {
     for (int s = 0; s < ax.nst; ++s) {
         switch (ax.radix[s]) {
-            case 2: mr_stage<S, 2>(a, b, ax, s, tw, lane); break;
-            case 3: mr_stage<S, 3>(a, b, ax, s, tw, lane); break;
-            case 4: mr_stage<S, 4>(a, b, ax, s, tw, lane); break;
-            case 5: mr_stage<S, 5>(a, b, ax, s, tw, lane); break;
-            case 7: mr_stage<S, 7>(a, b, ax, s, tw, lane); break;
-            default: mr_stage<S, 8>(a, b, ax, s, tw, lane); break;
+            case 2: mr_stage<S, 2>(a, b, ax, s, tw, th, T); break;
+            case 3: mr_stage<S, 3>(a, b, ax, s, tw, th, T); break;
+            case 4: mr_stage<S, 4>(a, b, ax, s, tw, th, T); break;
+            case 5: mr_stage<S, 5>(a, b, ax, s, tw, th, T); break;
+            case 7: mr_stage<S, 7>(a, b, ax, s, tw, th, T); break;
+            default: mr_stage<S, 8>(a, b, ax, s, tw, th, T); break;
         }
-        __syncwarp();
+        if (T == 32) __syncwarp();
+        else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(T) : "memory");
         V *t = a;
         a = b;
         b = t;
     }
     return a;
+}
+
+// The transform of one line by one warp (lane its lane index).
+template <int S, typename V>
+__device__ __forceinline__ V *mr_fft(V *a, V *b, const MrAxis &ax, const V *tw, int lane) {
+    return mr_fft_g<S>(a, b, ax, tw, lane, 32, 0);
 }
 
 enum { MR_ROW_CUBE = 0, MR_ROW_FWD = 1, MR_ROW_INV = 2 };
@@ -268,21 +281,21 @@ __host__ __device__ __forceinline__ int mr_col_stride(int n) { return n | 1; }
 
 enum { MR_COL_FWD = 0, MR_COL_INV = 1, MR_COL_UPDATE = 2 };
 
-// A pass along axis (1 = y, 2 = z) on W = blockDim.x / 32 columns of the half spectrum, one warp
-// a column; grid = (column chunks, the other axis' extent). The block loads the W columns (rows
-// of W adjacent values, W vb bytes apiece) into the first buffer of each column, the warps
-// transform, the block stores.
+// A pass along axis (1 = y, 2 = z) on W = blockDim.x / (32 G) columns of the half spectrum, G
+// warps a column (synced on the column's named barrier 1 + c when G > 1); grid = (column chunks,
+// the other axis' extent). The block loads the W columns (rows of W adjacent values, W vb bytes
+// apiece) into the first buffer of each column, the column groups transform, the block stores.
 // MR_COL_FWD / MR_COL_INV: out = scale * transform(in) (in may equal out);
 // MR_COL_UPDATE (the last forward axis): C = forward(in), then
 // S <- (S - dt k^2 C inv_halfN) / (1 + dt k^2 Lk), S = 0 at k = 0 (out = S, read and written).
 template <typename R, int MODE>
 __global__ void __launch_bounds__(512) k_mr_col(const __grid_constant__ MrGeom g, const __grid_constant__ MrArgs<R> a,
-                                                int axis, int ncols, const void *in, void *out) {
+                                                int axis, int ncols, const void *in, void *out, int G) {
     using V = typename VT<R>::V;
     extern __shared__ __align__(16) unsigned char smraw[];
     const MrAxis &ax = g.ax[axis];
-    const int n = ax.n, tid = threadIdx.x, nt = blockDim.x, W = nt >> 5, lW = __ffs(W) - 1;
-    const int warp = tid >> 5, lane = tid & 31;
+    const int n = ax.n, tid = threadIdx.x, nt = blockDim.x, W = (nt >> 5) / G, lW = __ffs(W) - 1;
+    const int col = (tid >> 5) / G, th = tid - col * 32 * G;   // column of the thread, index in its group
     const int CS = mr_col_stride(n);
     V *A = reinterpret_cast<V *>(smraw);
     V *B = A + (size_t)W * CS;
@@ -308,9 +321,9 @@ __global__ void __launch_bounds__(512) k_mr_col(const __grid_constant__ MrGeom g
     }
     __syncthreads();
     const V *res;
-    if (MODE == MR_COL_INV) res = mr_fft<+1>(A + warp * CS, B + warp * CS, ax, a.tw, lane);
-    else res = mr_fft<-1>(A + warp * CS, B + warp * CS, ax, a.tw, lane);
-    res -= warp * CS;   // the same buffer for every column (the same number of stages)
+    if (MODE == MR_COL_INV) res = mr_fft_g<+1>(A + col * CS, B + col * CS, ax, a.tw, th, 32 * G, 1 + col);
+    else res = mr_fft_g<-1>(A + col * CS, B + col * CS, ax, a.tw, th, 32 * G, 1 + col);
+    res -= col * CS;   // the same buffer for every column (the same number of stages)
     __syncthreads();
     V *dst = reinterpret_cast<V *>(out);
     for (int e0 = tid; e0 < total; e0 += nt * MR_U) {
@@ -358,6 +371,19 @@ __global__ void k_mr_edges(const MrGeom g, const typename VT<R>::V *E, typename 
 
 // shared-memory bytes of the x pass (rows a block) and of a column pass (W columns of length n)
 inline size_t mr_row_smem(int M, int rows, size_t vb) { return (size_t)rows * 2 * (M + 1) * vb; }
+
+// Warps a column of a column pass of W columns: up to PFC_MR_G (1, 2 or 4; default 2) while the
+// block keeps at most 512 threads and every column has its own named barrier (W <= 15).
+inline int mr_col_group(int W) {
+    static const int want = [] {
+        const char *e = std::getenv("PFC_MR_G");
+        const int v = e ? std::atoi(e) : 2;
+        return v == 1 || v == 4 ? v : 2;
+    }();
+    int G = want;
+    while (G > 1 && (32 * W * G > 512 || W > 15)) G /= 2;
+    return G;
+}
 inline size_t mr_col_smem(int n, int W, size_t vb) { return (size_t)W * 2 * mr_col_stride(n) * vb; }
 
 }  // namespace pfc
