@@ -88,8 +88,9 @@ typedef struct pfc_plan pfc_plan;
  * Mixed-radix grids (extents not all powers of two) take one pass per axis instead, each line
  * a Stockham transform of radices 2, 3, 4, 5, 7, 8 in shared memory (11 sweeps a step in 3D,
  * 7 in 2D). They support one field and the semi-implicit step: pfc_step, the transforms,
- * pfc_mass, pfc_energy, pfc_set_r, pfc_profile_steps and the hydrodynamic model; the adjoint,
- * recorded segments, the other integrators and pfc_plan_autotune return UNSUPPORTED.
+ * pfc_mass, pfc_energy, pfc_set_r, pfc_profile_steps, pfc_plan_autotune (radix order and
+ * launch shapes) and the hydrodynamic model; the adjoint, recorded segments and the other
+ * integrators return UNSUPPORTED.
  * Allocates the plan's device scratch with cudaMalloc: 2 * nfields half spectra, and a third
  * for a three-pass or mixed-radix plan.
  * Errors: INVALID_ARG, UNSUPPORTED, UNSTABLE_OPERATOR, OUT_OF_MEMORY, CUDA. */
@@ -213,7 +214,11 @@ pfc_status pfc_plan_info(pfc_plan *plan, int32_t *tiles, int64_t *scratch_bytes)
  * Synchronises. Allocates a real array of the grid for the duration of the call, and larger
  * plan scratch when the chosen tiling pads kx further; the adjoint's third half spectrum is
  * released (the next pfc_step_adjoint allocates it again). Errors: INVALID_ARG,
- * OUT_OF_MEMORY, CUDA; on an error the planner's tiling is restored. */
+ * OUT_OF_MEMORY, CUDA; on an error the planner's tiling is restored.
+ * Mixed-radix plans: the candidates are the radix order of every axis (7, 5, 3 before 8, 4, 2,
+ * or after), one or two warps a line in the column passes and the x pass' rows a block (the
+ * current shape, half and twice), timed on the plan's step sequence of trial_steps steps of a
+ * zero field; cache_path is not used. The twiddle table is rebuilt for the radix order. */
 pfc_status pfc_plan_autotune(pfc_plan *plan, int max_candidates, int trial_steps,
                              const char *cache_path, double *best_ms_out);
 

@@ -53,7 +53,11 @@ struct pfc_plan {
     MrGeom mg{};
     void *mtw = nullptr, *mtwx = nullptr, *E = nullptr;
     int mr_rows = 1;              // x pass: rows (warps) a block
-    int mr_W[3] = {1, 1, 1};      // column passes: columns (warps) a block, per axis
+    int mr_W[3] = {1, 1, 1};      // column passes: columns a block, per axis
+    int mr_G = 2;                 // column passes: warps a column (capped per launch)
+    bool mr_even_first = false;   // radix order of every axis: 8, 4, 2 before 7, 5, 3
+    size_t mtw_cap = 0;           // bytes of the stage-twiddle table
+    size_t mr_smem_col = 0;       // shared memory of the column passes' largest launch
     int mr_wE[3] = {1, 1, 1};     // the same for the two projection columns
     void *A = nullptr;            // third half spectrum, allocated by the first adjoint call
     double *d_adjpart = nullptr;  // adjoint line-pass partial sums (one per block)
@@ -156,7 +160,8 @@ template <typename R>
 void mr_col(const pfc_plan *p, int mode, int axis, const void *in, void *out, double scale) {
     MrArgs<R> a = mr_args<R>(p);
     a.scale = (R)scale;
-    launch_mr_col<R>(p->stream, mode, p->mg, a, axis, p->mr_W[axis], p->mg.M + 1, in, out);
+    launch_mr_col<R>(p->stream, mode, p->mg, a, axis, p->mr_W[axis], p->mg.M + 1, in, out,
+                     mr_col_group(p->mr_W[axis], p->mr_G));
 }
 template <typename R>
 void mr_row(const pfc_plan *p, int mode, const void *in, void *out, const double *mean, double scale) {
@@ -205,10 +210,11 @@ void mixed_enqueue(pfc_plan *p, void *state, int64_t nsteps, Mark &&mk) {
         mk(4);
         // Hermitian projection of the kx = 0 and nx/2 columns: F_yz of their real parts / (ny nz)
         ea.scale = (R)(g.nz > 1 ? 1.0 : 1.0 / g.ny);
-        launch_mr_col<R>(p->stream, MR_COL_FWD, ge, ea, 1, p->mr_wE[1], 2, p->E, p->E);
+        launch_mr_col<R>(p->stream, MR_COL_FWD, ge, ea, 1, p->mr_wE[1], 2, p->E, p->E, mr_col_group(p->mr_wE[1], p->mr_G));
         if (g.nz > 1) {
             ea.scale = (R)(1.0 / ((double)g.ny * g.nz));
-            launch_mr_col<R>(p->stream, MR_COL_FWD, ge, ea, 2, p->mr_wE[2], 2, p->E, p->E);
+            launch_mr_col<R>(p->stream, MR_COL_FWD, ge, ea, 2, p->mr_wE[2], 2, p->E, p->E,
+                             mr_col_group(p->mr_wE[2], p->mr_G));
         }
         launch_mr_edges<R>(p->stream, g, p->E, p->X, 1.0);
         mk(1);
@@ -242,16 +248,46 @@ template <typename R> pfc_status mixed_c2r_impl(pfc_plan *p, const void *in, voi
     return PFC_OK;
 }
 
-// radices of n, the odd ones first (7, 5, 3), then 8, 4, 2; false when n has another prime
-// factor
-bool mr_factor(int n, std::vector<int> &rad) {
+// radices of n, the odd ones first (7, 5, 3), then 8, 4, 2 (even_first: the other way round);
+// false when n has another prime factor
+bool mr_factor(int n, std::vector<int> &rad, bool even_first = false) {
     rad.clear();
+    std::vector<int> odd, even;
     for (int r : {7, 5, 3})
-        while (n % r == 0) { rad.push_back(r); n /= r; }
-    while (n % 8 == 0) { rad.push_back(8); n /= 8; }
-    if (n % 4 == 0) { rad.push_back(4); n /= 4; }
-    if (n % 2 == 0) { rad.push_back(2); n /= 2; }
+        while (n % r == 0) { odd.push_back(r); n /= r; }
+    while (n % 8 == 0) { even.push_back(8); n /= 8; }
+    if (n % 4 == 0) { even.push_back(4); n /= 4; }
+    if (n % 2 == 0) { even.push_back(2); n /= 2; }
+    const std::vector<int> &a = even_first ? even : odd, &b = even_first ? odd : even;
+    rad.insert(rad.end(), a.begin(), a.end());
+    rad.insert(rad.end(), b.begin(), b.end());
     return n == 1 && (int)rad.size() <= MR_MAXST;
+}
+
+// The stage radices and twiddle offsets of the three axes of g (lengths already set) in the
+// given radix order, and the stage twiddles W_{r Ns}^{m k} they index (FP64, re/im pairs).
+void mr_axes(MrGeom &g, bool even_first, std::vector<double> &tw) {
+    tw.clear();
+    for (int a = 0; a < 3; ++a) {
+        MrAxis &ax = g.ax[a];
+        std::vector<int> rad;
+        if (ax.n > 1) mr_factor(ax.n, rad, even_first);
+        ax.nst = (int)rad.size();
+        int Ns = 1;
+        for (int s = 0; s < ax.nst; ++s) {
+            ax.radix[s] = rad[s];
+            ax.ns[s] = Ns;
+            ax.twoff[s] = (int)(tw.size() / 2);
+            for (int m = 0; m < rad[s]; ++m)
+                for (int k = 0; k < Ns; ++k) {
+                    double re, im;
+                    unit_root_fwd((int64_t)m * k, (int64_t)rad[s] * Ns, &re, &im);
+                    tw.push_back(re);
+                    tw.push_back(im);
+                }
+            Ns *= rad[s];
+        }
+    }
 }
 bool mr_extent_ok(int64_t n) {
     std::vector<int> r;
@@ -1022,26 +1058,10 @@ pfc_status mixed_plan_create(pfc_plan **out, int ndim, const int64_t d[3], doubl
     // a block's shared memory: up to 100 KB (two blocks an SM), more only for one long line
     const size_t budget = 100 * 1024;
     size_t smem_col = 0;
+    for (int a = 0; a < 3; ++a) g.ax[a].n = lens[a];
+    mr_axes(g, false, tw);
     for (int a = 0; a < 3; ++a) {
-        MrAxis &ax = g.ax[a];
-        ax.n = lens[a];
-        std::vector<int> rad;
-        if (ax.n > 1) mr_factor(ax.n, rad);
-        ax.nst = (int)rad.size();
-        int Ns = 1;
-        for (int s = 0; s < ax.nst; ++s) {
-            ax.radix[s] = rad[s];
-            ax.ns[s] = Ns;
-            ax.twoff[s] = (int)(tw.size() / 2);
-            for (int m = 0; m < rad[s]; ++m)
-                for (int k = 0; k < Ns; ++k) {
-                    double re, im;
-                    unit_root_fwd((int64_t)m * k, (int64_t)rad[s] * Ns, &re, &im);
-                    tw.push_back(re);
-                    tw.push_back(im);
-                }
-            Ns *= rad[s];
-        }
+        const MrAxis &ax = g.ax[a];
         // launch shapes: one warp a line; as many lines a block as the budget holds (rows of
         // 128 bytes in the column passes: 16 FP32 or 8 FP64 columns)
         if (a == 0) {
@@ -1094,7 +1114,106 @@ pfc_status mixed_plan_create(pfc_plan **out, int ndim, const int64_t d[3], doubl
     const size_t smem_row = mr_row_smem(g.M, p->mr_rows, vb);
     e = p->prec == PFC_FP64 ? set_smem_mr<double>(smem_row, smem_col) : set_smem_mr<float>(smem_row, smem_col);
     if (e != cudaSuccess) return cleanup(e);
+    p->mtw_cap = tw.size() / 2 * vb;
+    p->mr_smem_col = smem_col;
     *out = p;
+    return PFC_OK;
+}
+
+// A launch shape of a mixed-radix plan: the radix order of the axes, warps a column of the
+// column passes, rows a block of the x pass.
+struct MrShape {
+    bool even_first;
+    int G, rows;
+};
+
+// Switch a mixed-radix plan to shape c (its twiddle table rebuilt for the radix order).
+template <typename R> pfc_status mr_apply(pfc_plan *p, const MrShape &c) {
+    const size_t vb = vbytes(p);
+    MrGeom g = p->mg;
+    std::vector<double> tw;
+    mr_axes(g, c.even_first, tw);
+    const size_t need = tw.size() / 2 * vb;
+    PFC_CUDA(cudaStreamSynchronize(p->stream));
+    if (need > p->mtw_cap) {
+        void *t = nullptr;
+        PFC_CUDA(cudaMalloc(&t, need));
+        cudaFree(p->mtw);
+        p->mtw = t;
+        p->mtw_cap = need;
+    }
+    if (sizeof(R) == 8) {
+        PFC_CUDA(cudaMemcpy(p->mtw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> f(tw.begin(), tw.end());
+        PFC_CUDA(cudaMemcpy(p->mtw, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+    }
+    PFC_CUDA(set_smem_mr<R>(mr_row_smem(g.M, c.rows, vb), p->mr_smem_col));
+    p->mg = g;
+    p->mr_even_first = c.even_first;
+    p->mr_G = c.G;
+    p->mr_rows = c.rows;
+    return PFC_OK;
+}
+
+// The autotuner of mixed-radix plans: the radix order (odd radices first or last), one or two
+// warps a column in the column passes, and the x pass' rows a block, each timed on trial_steps
+// steps of a zero field (a fixed point of the step); the fastest is kept.
+template <typename R> pfc_status mr_autotune(pfc_plan *p, int max_candidates, int trial_steps, double *best_ms_out) {
+    const size_t vb = vbytes(p);
+    const MrShape cur{p->mr_even_first, p->mr_G, p->mr_rows};
+    std::vector<MrShape> cand{cur};
+    bool mixed_order = false;   // some axis has both odd and even radices
+    for (int a = 0; a < 3; ++a) {
+        bool odd = false, even = false;
+        for (int s = 0; s < p->mg.ax[a].nst; ++s) (p->mg.ax[a].radix[s] & 1 ? odd : even) = true;
+        mixed_order = mixed_order || (odd && even);
+    }
+    const size_t optin = smem_optin();
+    for (int ef = 0; ef < (mixed_order ? 2 : 1); ++ef)
+        for (int G : {2, 1})
+            for (int rows : {cur.rows, cur.rows / 2, cur.rows * 2}) {
+                // (the x pass runs at most 256 threads a block: its launch bounds)
+                if (rows < 1 || rows > 8 || mr_row_smem(p->mg.M, rows, vb) > optin) continue;
+                const MrShape c{ef != 0, G, rows};
+                bool dup = false;
+                for (const MrShape &d : cand) dup = dup || (d.even_first == c.even_first && d.G == c.G && d.rows == c.rows);
+                if (!dup) cand.push_back(c);
+            }
+    if ((int)cand.size() > max_candidates) cand.resize(max_candidates);
+    void *tmp = nullptr;
+    const size_t bytes = (size_t)p->mg.nreal * sizeof(R);
+    PFC_CUDA(cudaMalloc(&tmp, bytes));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMemsetAsync(tmp, 0, bytes, p->stream);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int best = 0;
+    double best_ms = 1e300;
+    pfc_status st = PFC_OK;
+    for (size_t i = 0; i < cand.size() && e == cudaSuccess && st == PFC_OK; ++i) {
+        if ((st = mr_apply<R>(p, cand[i])) != PFC_OK) break;
+        mixed_enqueue<R>(p, tmp, 1, [](int) {});
+        float ms = 0.f;
+        e = cudaEventRecord(e0, p->stream);
+        if (e == cudaSuccess) mixed_enqueue<R>(p, tmp, trial_steps, [](int) {});
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms / trial_steps < best_ms) {
+            best_ms = ms / trial_steps;
+            best = (int)i;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(p->stream);
+    cudaFree(tmp);
+    if (st != PFC_OK) return st;
+    if (e != cudaSuccess) return fail(PFC_ERR_CUDA, std::string("mixed-radix autotune: ") + cudaGetErrorString(e));
+    if ((st = mr_apply<R>(p, cand[best])) != PFC_OK) return st;
+    if (best_ms_out) *best_ms_out = best_ms;
     return PFC_OK;
 }
 
@@ -1457,7 +1576,9 @@ pfc_status pfc_plan_autotune(pfc_plan *p, int max_candidates, int trial_steps, c
                              double *best_ms_out) {
     if (!plan_ok(p)) return fail(PFC_ERR_INVALID_ARG, "invalid plan");
     if (max_candidates < 1 || trial_steps < 1) return fail(PFC_ERR_INVALID_ARG, "max_candidates and trial_steps must be >= 1");
-    if (p->mixed) return fail(PFC_ERR_UNSUPPORTED, "mixed-radix plans have one launch shape");
+    if (p->mixed)
+        return p->prec == PFC_FP64 ? mr_autotune<double>(p, max_candidates, trial_steps, best_ms_out)
+                                   : mr_autotune<float>(p, max_candidates, trial_steps, best_ms_out);
     const size_t smem_max = smem_optin();
     if (!smem_max) return fail(PFC_ERR_CUDA, "device query failed");
     const std::string key = tune_key(p);

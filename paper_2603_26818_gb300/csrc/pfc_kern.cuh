@@ -168,10 +168,9 @@ void launch_mr_row(cudaStream_t s, int mode, const MrGeom &g, const MrArgs<R> &a
 }
 template <typename R>
 void launch_mr_col(cudaStream_t s, int mode, const MrGeom &g, const MrArgs<R> &a, int axis, int W, int ncols,
-                   const void *in, void *out) {
+                   const void *in, void *out, int G) {
     const dim3 grid((ncols + W - 1) / W, axis == 1 ? g.nz : g.ny);
     const size_t smem = mr_col_smem(g.ax[axis].n, W, sizeof(typename VT<R>::V));
-    const int G = mr_col_group(W);
     const int nt = 32 * W * G;
     if (mode == MR_COL_FWD) k_mr_col<R, MR_COL_FWD><<<grid, nt, smem, s>>>(g, a, axis, ncols, in, out, G);
     else if (mode == MR_COL_INV) k_mr_col<R, MR_COL_INV><<<grid, nt, smem, s>>>(g, a, axis, ncols, in, out, G);
@@ -230,7 +229,7 @@ void launch_reduce_spec(cudaStream_t s, const Geom &g, OpDev op, double dx, cons
     template void launch_mr_row<R>(cudaStream_t, int, const MrGeom &, const MrArgs<R> &, const void *, void *, \
                                    void *, int);                                            \
     template void launch_mr_col<R>(cudaStream_t, int, const MrGeom &, const MrArgs<R> &, int, int, int,  \
-                                   const void *, void *);                                   \
+                                   const void *, void *, int);                              \
     template void launch_mr_edges<R>(cudaStream_t, const MrGeom &, const void *, void *, double); \
     template cudaError_t set_smem_mr<R>(size_t, size_t);                                   \
     template void launch_batch_mean<R>(cudaStream_t, const R *, const int64_t *,           \

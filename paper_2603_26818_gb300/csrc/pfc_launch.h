@@ -74,7 +74,7 @@ void launch_mr_row(cudaStream_t s, int mode, const MrGeom &g, const MrArgs<R> &a
                    void *E, int rows_per_block);
 template <typename R>
 void launch_mr_col(cudaStream_t s, int mode, const MrGeom &g, const MrArgs<R> &a, int axis, int W, int ncols,
-                   const void *in, void *out);
+                   const void *in, void *out, int G);
 template <typename R>
 void launch_mr_edges(cudaStream_t s, const MrGeom &g, const void *E, void *S, double scale);
 template <typename R> cudaError_t set_smem_mr(size_t row, size_t col);
@@ -132,7 +132,7 @@ template <typename R> cudaError_t set_smem_attrs_fixed(const LaunchCfg &c);
     extern template void launch_mr_row<R>(cudaStream_t, int, const MrGeom &, const MrArgs<R> &, const void *, \
                                           void *, void *, int);                                  \
     extern template void launch_mr_col<R>(cudaStream_t, int, const MrGeom &, const MrArgs<R> &, int, int, \
-                                          int, const void *, void *);                            \
+                                          int, const void *, void *, int);                       \
     extern template void launch_mr_edges<R>(cudaStream_t, const MrGeom &, const void *, void *, double); \
     extern template cudaError_t set_smem_mr<R>(size_t, size_t);                                  \
     extern template void launch_batch_mean<R>(cudaStream_t, const R *, const int64_t *,         \

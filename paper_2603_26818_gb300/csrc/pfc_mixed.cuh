@@ -24,8 +24,6 @@
 // HBM far from busy).
 #pragma once
 
-#include <cstdlib>
-
 #include "pfc_pass.cuh"
 
 namespace pfc {
@@ -371,19 +369,14 @@ __global__ void k_mr_edges(const MrGeom g, const typename VT<R>::V *E, typename 
 
 // shared-memory bytes of the x pass (rows a block) and of a column pass (W columns of length n)
 inline size_t mr_row_smem(int M, int rows, size_t vb) { return (size_t)rows * 2 * (M + 1) * vb; }
+inline size_t mr_col_smem(int n, int W, size_t vb) { return (size_t)W * 2 * mr_col_stride(n) * vb; }
 
-// Warps a column of a column pass of W columns: up to PFC_MR_G (1, 2 or 4; default 2) while the
-// block keeps at most 512 threads and every column has its own named barrier (W <= 15).
-inline int mr_col_group(int W) {
-    static const int want = [] {
-        const char *e = std::getenv("PFC_MR_G");
-        const int v = e ? std::atoi(e) : 2;
-        return v == 1 || v == 4 ? v : 2;
-    }();
-    int G = want;
+// Warps a column of a column pass of W columns: up to want (1, 2 or 4) while the block keeps at
+// most 512 threads and every column has its own named barrier (W <= 15).
+inline int mr_col_group(int W, int want) {
+    int G = want == 4 ? 4 : want == 1 ? 1 : 2;
     while (G > 1 && (32 * W * G > 512 || W > 15)) G /= 2;
     return G;
 }
-inline size_t mr_col_smem(int n, int W, size_t vb) { return (size_t)W * 2 * mr_col_stride(n) * vb; }
 
 }  // namespace pfc

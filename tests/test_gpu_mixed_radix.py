@@ -10,7 +10,8 @@ naive DFT and numpy.fft):
   * one and twenty semi-implicit steps (FP64 1e-12 / 1e-11, FP32 2e-6 / 1e-5), the carried mass
     and the energy;
   * the hydrodynamic step, which runs on the plan's transforms;
-  * the calls built for power-of-two grids only, which report UNSUPPORTED.
+  * the calls built for power-of-two grids only, which report UNSUPPORTED;
+  * the autotuner's radix orders and launch shapes, against the oracle after tuning.
 At the paper's 750^3 (FP32-mixed) the oracle cannot step the grid in a test's time; there:
   * a field repeating a 150^3 block is stepped exactly like the block on the 150^3 grid, which
     the oracle steps;
@@ -143,8 +144,6 @@ def test_mixed_unsupported_calls():
     with pytest.raises(b.PfcError, match="UNSUPPORTED"):
         p.step_adjoint(x, x, lam, dr)
     with pytest.raises(b.PfcError, match="UNSUPPORTED"):
-        p.autotune(4, 2)
-    with pytest.raises(b.PfcError, match="UNSUPPORTED"):
         b.Plan((30, 42), DX, 0.5, [b.make_op(*ONE), b.make_op(*ONE)], precision="fp64", coupling=0.1)
     # the plan is still usable; the per-pass profile runs the same steps
     psi0 = x.cpu().numpy()
@@ -208,3 +207,24 @@ def test_750cube_fp32_forward_bins_from_the_definition():
         # FP32 rounding of a transform of 4.2e8 values: relative to the field's norm
         scale = math.sqrt(float((host * host).sum()))
         assert abs(g - acc) <= 1e-5 * scale, (kz, ky, kx, g, acc)
+
+
+def test_mixed_radix_autotune_keeps_parity():
+    """pfc_plan_autotune on a mixed-radix plan (radix order, warps a column, rows a block): the
+    autotuned plan against the oracle, FP64, 2D and 3D, and a 750-point line plan in FP32."""
+    import math
+    from paper_2603_26818_gb300 import binding, inputs
+    import oracle
+    for shape, prec, tol in (((60, 90), "fp64", 1e-11), ((24, 30, 36), "fp64", 1e-11), ((12, 750), "fp32", 1e-5)):
+        psi0 = inputs.uniform_state(shape, -0.25, 0.01, seed=77)
+        if prec == "fp32":
+            psi0 = psi0.astype(np.float32).astype(np.float64)
+        p = binding.Plan(shape, math.pi / 4, 0.5, [binding.make_op(0, -0.25)], precision=prec)
+        ms = p.autotune(8, 3)
+        assert ms > 0
+        x = torch.from_numpy(psi0).to(device="cuda", dtype=torch.float64 if prec == "fp64" else torch.float32)
+        p.step(x, 6)
+        ref = oracle.step(psi0, math.pi / 4, 0.5, (0, -0.25, 0.0, 0.0), 6)
+        got = x.double().cpu().numpy()
+        assert float(np.linalg.norm(got - ref) / np.linalg.norm(ref)) <= tol
+        p.close()
