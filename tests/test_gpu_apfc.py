@@ -2,7 +2,7 @@
 test_oracle_apfc.py): a 2D triangular triad and a 3D BCC set of six amplitudes, one- and
 two-mode operators, FP64 (1e-11 after 5 steps) and FP32-mixed (1e-5), mixed-radix extents, the
 middle (negative-frequency) bin, the resonance count; at a full size the oracle on a 1024^2
-triad and translation covariance (a property at any size) on a 192^3 BCC set.
+triad and translation covariance (a property at any size) on the bench's 256^3 BCC set.
 """
 import math
 
@@ -84,10 +84,11 @@ def test_apfc_1024sq_triad_fp32_matches_oracle():
     m.close()
 
 
-def test_apfc_192cube_bcc_translation_covariance_fp32():
-    """Translating the density by u multiplies eta_j by exp(i k_j . u); the step commutes with it
-    (both orders from the same FP32 start, 3 steps, 1e-5)."""
-    shape, kv = (192, 192, 192), inputs.apfc_bcc(1.0)
+def test_apfc_256cube_bcc_translation_covariance_fp32():
+    """At the bench's size and launch configuration (BCC, 256^3, dx 1.1, dt 0.4): translating the
+    density by u multiplies eta_j by exp(i k_j . u); the step commutes with it (both orders from
+    the same FP32 start, 3 steps, 1e-5)."""
+    shape, kv = (256, 256, 256), inputs.apfc_bcc(1.0)
     g = torch.Generator(device="cuda")
     g.manual_seed(5)
     x = (0.1 + 0.02 * (2 * torch.rand((6,) + shape, generator=g, device="cuda", dtype=torch.float32) - 1)).to(torch.complex64)

@@ -180,6 +180,33 @@ def test_750cube_fp32_tiled_block_matches_oracle():
     assert math.sqrt(err2 / ref2) <= 2e-6
 
 
+def test_1400cube_fp32_tiled_block_matches_oracle():
+    """The paper's largest grid, 1400^3 (radices 8, 7, 5, 5 per axis), in FP32-mixed: a field
+    that repeats a 175^3 block (175 = 5^2 7) eight times per axis is stepped exactly like the
+    block on the 175^3 grid, which the oracle steps; one step, one-mode operator as config 1400."""
+    big, small, dt, nsteps = 1400, 175, 0.5, 1
+    op = (0, -0.25, 0.0, 0.0)
+    sm_shape = (small,) * 3
+    psi_s = inputs.uniform_state(sm_shape, -0.25, 0.01, seed=53).astype(np.float32).astype(np.float64)
+    ref_s = oracle.step(psi_s, DX, dt, op, nsteps)
+    reps = big // small
+    p = plan((big,) * 3, op, "fp32", dt)
+    x = torch.from_numpy(psi_s).to(device="cuda", dtype=torch.float32).repeat(reps, reps, reps)
+    p.step(x, nsteps)
+    torch.cuda.synchronize()
+    p.close()
+    tgt = torch.from_numpy(ref_s).to(device="cuda", dtype=torch.float64).repeat(1, reps, reps)
+    err2 = ref2 = 0.0
+    for z0 in range(0, big, small):
+        d = x[z0:z0 + small].double() - tgt
+        err2 += float((d * d).sum())
+        ref2 += float((tgt * tgt).sum())
+        del d
+    del x, tgt
+    torch.cuda.empty_cache()
+    assert math.sqrt(err2 / ref2) <= 2e-6
+
+
 def test_750cube_fp32_forward_bins_from_the_definition():
     """X[kz, ky, kx] = sum_z e^{-2 pi i kz z / n} sum_y e^{-2 pi i ky y / n} sum_x e^{-2 pi i kx x / n}
     psi[z, y, x], summed one axis at a time in FP64 on the host (the FP32 field as given)."""
