@@ -104,18 +104,32 @@ __global__ void __launch_bounds__(512) k_ap_row_nl(const __grid_constant__ ApGeo
         const V *Xs = rowbase + (odd ? n : 0);   // amplitude j's real-space row at Xs + j 2n
         const size_t js = 2 * (size_t)n;
         const int t0 = a.term_beg[f], t1 = a.term_beg[f + 1];
-        for (int i = lane; i < n; i += 32) {
-            const V e = X[i];
-            V acc = V{a.c1 * e.x, a.c1 * e.y};
+        // four points a lane at a time (i0, i0 + 32, ...): one read of each term for the four
+        constexpr int PU = 4;
+        for (int i0 = lane; i0 < n; i0 += 32 * PU) {
+            int ii[PU];
+            V acc[PU];
+#pragma unroll
+            for (int u = 0; u < PU; ++u) {
+                const int i = i0 + 32 * u;
+                ii[u] = i < n ? i : n - 1;   // past the end: a valid point, not stored
+                const V e = X[ii[u]];
+                acc[u] = V{a.c1 * e.x, a.c1 * e.y};
+            }
             for (int t = t0; t < t1; ++t) {
                 const int4 tm = __ldg(&a.terms[t]);
-                V p = ap_mul(ap_mode(Xs, js, tm.x, i), ap_mode(Xs, js, tm.y, i));
-                if (tm.z != 0) p = ap_mul(p, ap_mode(Xs, js, tm.z, i));
                 const R c = __ldg(&a.coef[t]);
-                acc.x += c * p.x;
-                acc.y += c * p.y;
+#pragma unroll
+                for (int u = 0; u < PU; ++u) {
+                    V p = ap_mul(ap_mode(Xs, js, tm.x, ii[u]), ap_mode(Xs, js, tm.y, ii[u]));
+                    if (tm.z != 0) p = ap_mul(p, ap_mode(Xs, js, tm.z, ii[u]));
+                    acc[u].x += c * p.x;
+                    acc[u].y += c * p.y;
+                }
             }
-            Y[i] = acc;
+#pragma unroll
+            for (int u = 0; u < PU; ++u)
+                if (i0 + 32 * u < n) Y[i0 + 32 * u] = acc[u];
         }
     }
     __syncthreads();
