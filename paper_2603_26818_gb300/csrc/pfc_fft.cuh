@@ -28,6 +28,37 @@ struct __align__(16) cf2 {
     float2 a, b;
 };
 
+// L2 eviction priority of the C' stream of a step: the psi^3 row pass writes C' with priority
+// to stay in L2 (evict_last) for the update pass of the same step, which reads it for the last
+// time (evict_first). PFC_L2_HINTS=0 at compile time gives plain .cg accesses (to compare).
+#ifndef PFC_L2_HINTS
+#define PFC_L2_HINTS 1
+#endif
+__device__ __forceinline__ void st_keep_l2(float2 *p, float2 v) {
+#if PFC_L2_HINTS
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol)
+                 : "memory");
+#else
+    __stcg(p, v);
+#endif
+}
+__device__ __forceinline__ float4 ld_last_use_l2(const float4 *p) {
+#if PFC_L2_HINTS
+    unsigned long long pol;
+    float4 r;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("ld.global.cg.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(p), "l"(pol)
+                 : "memory");
+    return r;
+#else
+    return __ldcg(p);
+#endif
+}
+
 // scalar type and twiddle (table element) type of a transform element type
 template <typename V> struct ElemOf;
 template <> struct ElemOf<float2> { using R = float; using Tw = float2; };

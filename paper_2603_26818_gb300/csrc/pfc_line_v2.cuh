@@ -60,7 +60,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_line_v2(const Geom g, const Geom gv
         V vc[8];
         const V *C = reinterpret_cast<const V *>(a.c) + foff;
 #pragma unroll
-        for (int m = 0; m < 8; ++m) vc[m] = ldcg2(&C[xprime_index(gv, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)]);
+        for (int m = 0; m < 8; ++m) {
+            const float4 t = ld_last_use_l2(reinterpret_cast<const float4 *>(
+                &C[xprime_index(gv, kp, cg, mp.zq, mp.jy + m * mp.ny8, mp.w)]));
+            vc[m] = cf2{float2{t.x, t.y}, float2{t.z, t.w}};
+        }
         line_yfft<-1, LY>(vc, Cs, ady, gv, mp.jy, true, false, a.st);
         if (two_axes) line_zfft<-1, LZ>(vc, Cs, adz, gv, mp.jz, false, false, a.st);
     }

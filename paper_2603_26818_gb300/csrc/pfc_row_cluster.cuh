@@ -158,8 +158,13 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(512, 2)
                 for (int yy = 0; yy < ROWCL_PY; ++yy) {
                     const V t = stw[yy];
                     V *dst = out + (size_t)(yy * g.QR + grp) * g.xs;
-                    __stcg(&dst[ca], cscale(cmul(va[yy], t), a.scale));
-                    if (cb != ca) __stcg(&dst[cb], cscale(cmul(vb[yy], t), a.scale));
+                    if constexpr (sizeof(R) == 4) {
+                        st_keep_l2(&dst[ca], cscale(cmul(va[yy], t), a.scale));
+                        if (cb != ca) st_keep_l2(&dst[cb], cscale(cmul(vb[yy], t), a.scale));
+                    } else {
+                        __stcg(&dst[ca], cscale(cmul(va[yy], t), a.scale));
+                        if (cb != ca) __stcg(&dst[cb], cscale(cmul(vb[yy], t), a.scale));
+                    }
                 }
             }
         }
