@@ -229,40 +229,42 @@ __device__ void row_phase_a(const Geom &g, typename VT<R>::V *sm, const typename
 // real-transform pre-processing; rows end physical (z_p, y_p). FROM_GLOBAL (Pz == 1) reads X'
 // and applies the y twiddle; otherwise reads smem left by phase A. When edge is set, the real
 // parts of the kx = 0 and kx = M columns are saved there for the projection.
-template <typename R, bool FROM_GLOBAL>
+// PY > 0: the plan's Py fixed at compile time (the unused register slots drop out).
+template <typename R, bool FROM_GLOBAL, int PY = 0>
 __device__ __forceinline__ void row_pair_b(const Geom &g, typename VT<R>::V *sm, R *edge,
                                            const typename VT<R>::V *X, int gi, int grp, int zp,
                                            int ca, int cb, bool k0,
                                            const typename VT<R>::V *__restrict__ tw,
                                            const typename VT<R>::V *stw, typename VT<R>::V *proj) {
     using V = typename VT<R>::V;
-    const int P = g.P;
+    const int P = PY > 0 ? PY : g.P;   // (PY > 0 only with Pz == 1)
+    const int Py = PY > 0 ? PY : g.Py;
     V a[8], b[8];
 #pragma unroll
     for (int yy = 0; yy < 8; ++yy) {
-        if (yy < g.Py) {
+        if (yy < Py) {
             if (FROM_GLOBAL) {
                 const V *src = X + (size_t)(yy * g.QR + grp) * g.xs;
                 const V w = stw[gi * P + yy];
                 a[yy] = ctw<+1>(__ldcg(&src[ca]), w);
                 b[yy] = ctw<+1>(__ldcg(&src[cb]), w);
             } else {
-                const int row = gi * P + zp * g.Py + yy;
+                const int row = gi * P + zp * Py + yy;
                 a[yy] = sm[row * g.rs + row_swz(ca)];
                 b[yy] = sm[row * g.rs + row_swz(cb)];
             }
         }
     }
-    dft_small<+1>(a, g.Py);
-    dft_small<+1>(b, g.Py);
+    dft_small<+1>(a, Py);
+    dft_small<+1>(b, Py);
     const V w = __ldg(&tw[ca << (g.ltab - g.lnx)]);
 #pragma unroll
     for (int yy = 0; yy < 8; ++yy) {
-        if (yy < g.Py) {
-            const int row = gi * P + zp * g.Py + yy;
+        if (yy < Py) {
+            const int row = gi * P + zp * Py + yy;
             if (edge && k0) {
-                edge[(gi * 2) * P + zp * g.Py + yy] = a[yy].x;
-                edge[(gi * 2 + 1) * P + zp * g.Py + yy] = b[yy].x;
+                edge[(gi * 2) * P + zp * Py + yy] = a[yy].x;
+                edge[(gi * 2 + 1) * P + zp * Py + yy] = b[yy].x;
             }
             V za, zb;
             c2r_pre_pair<V, R>(a[yy], b[yy], w, k0, za, zb);
@@ -279,12 +281,12 @@ __device__ __forceinline__ void row_pair_b(const Geom &g, typename VT<R>::V *sm,
             a[yy].y = (R)0;
             b[yy].y = (R)0;
         }
-        dft_small<-1>(a, g.Py);
-        dft_small<-1>(b, g.Py);
+        dft_small<-1>(a, Py);
+        dft_small<-1>(b, Py);
         const R invP = (R)1 / (R)P;
 #pragma unroll
         for (int yy = 0; yy < 8; ++yy) {
-            if (yy < g.Py) {
+            if (yy < Py) {
                 V *dst = proj + (size_t)(yy * g.QR + grp) * g.xs;
                 dst[0] = cscale(cmul(a[yy], stw[gi * P + yy]), invP);
                 dst[g.M] = cscale(cmul(b[yy], stw[gi * P + yy]), invP);
@@ -297,7 +299,7 @@ __device__ __forceinline__ void row_pair_b(const Geom &g, typename VT<R>::V *sm,
 // real-transform pre-processing; rows end physical (z_p, y_p). FROM_GLOBAL (Pz == 1) reads X'
 // and applies the y twiddle; otherwise reads smem left by phase A. When edge is set, the real
 // parts of the kx = 0 and kx = M columns are saved there for the projection.
-template <typename R, bool FROM_GLOBAL>
+template <typename R, bool FROM_GLOBAL, int PY = 0>
 __device__ void row_phase_b(const Geom &g, typename VT<R>::V *sm, R *edge,
                             const typename VT<R>::V *X, int grp0,
                             const typename VT<R>::V *__restrict__ tw,
@@ -315,7 +317,7 @@ __device__ void row_phase_b(const Geom &g, typename VT<R>::V *sm, R *edge,
         for (int pp = 0; pp < npass; ++pp) {
             const bool k0 = kk == 0 && pp == 0;
             const int ca = pp ? hM : kk, cb = pp ? hM : (kk == 0 ? M : M - kk);
-            row_pair_b<R, FROM_GLOBAL>(g, sm, k0 ? edge : nullptr, X, gi, grp, zp, ca, cb, k0, tw, stw, proj);
+            row_pair_b<R, FROM_GLOBAL, PY>(g, sm, k0 ? edge : nullptr, X, gi, grp, zp, ca, cb, k0, tw, stw, proj);
         }
     }
 }
@@ -366,37 +368,38 @@ __device__ void project_edge_columns_par(const Geom &g, const R *edge, int grp0,
     }
 }
 
-template <typename R>
+template <typename R, int PY = 0>
 __device__ __forceinline__ void row_pair_d(const Geom &g, typename VT<R>::V *sm,
                                            typename VT<R>::V *out, int gi, int grp, int zp,
                                            int ca, int cb, bool k0,
                                            const typename VT<R>::V *__restrict__ tw,
                                            const typename VT<R>::V *stw, R scale) {
     using V = typename VT<R>::V;
-    const int P = g.P;
+    const int P = PY > 0 ? PY : g.P;   // (PY > 0 only with Pz == 1)
+    const int Py = PY > 0 ? PY : g.Py;
     const V w = __ldg(&tw[ca << (g.ltab - g.lnx)]);
     V a[8], b[8];
 #pragma unroll
     for (int yy = 0; yy < 8; ++yy) {
-        if (yy < g.Py) {
-            const int row = gi * P + zp * g.Py + yy;
+        if (yy < Py) {
+            const int row = gi * P + zp * Py + yy;
             const V za = sm[row * g.rs + row_swz(ca)];
             const V zb = (k0 || cb == ca) ? za : sm[row * g.rs + row_swz(cb)];
             r2c_post_pair<V, R>(za, zb, w, k0, a[yy], b[yy]);
         }
     }
-    dft_small<-1>(a, g.Py);
-    dft_small<-1>(b, g.Py);
+    dft_small<-1>(a, Py);
+    dft_small<-1>(b, Py);
 #pragma unroll
     for (int yy = 0; yy < 8; ++yy) {
-        if (yy < g.Py) {
+        if (yy < Py) {
             if (g.Pz == 1) {
                 const V t = stw[gi * P + yy];
                 V *dst = out + (size_t)(yy * g.QR + grp) * g.xs;
                 __stcg(&dst[ca], cscale(cmul(a[yy], t), scale));
                 if (cb != ca) __stcg(&dst[cb], cscale(cmul(b[yy], t), scale));
             } else {
-                const int row = gi * P + zp * g.Py + yy;
+                const int row = gi * P + zp * Py + yy;
                 sm[row * g.rs + row_swz(ca)] = a[yy];
                 if (cb != ca) sm[row * g.rs + row_swz(cb)] = b[yy];
             }
@@ -407,7 +410,7 @@ __device__ __forceinline__ void row_pair_d(const Geom &g, typename VT<R>::V *sm,
 // Phase D: real-transform post-processing of the pair (kk, M - kk) of the Py rows of (gi, z_p),
 // then the y-part forward. With Pz == 1 it applies the y twiddle and the scale and writes X'
 // rows (k_py Q + grp) of out; otherwise it writes smem rows (z_p, k_py) for phase E.
-template <typename R>
+template <typename R, int PY = 0>
 __device__ void row_phase_d(const Geom &g, typename VT<R>::V *sm, typename VT<R>::V *out,
                             int grp0, const typename VT<R>::V *__restrict__ tw,
                             const typename VT<R>::V *stw, R scale) {
@@ -422,7 +425,7 @@ __device__ void row_phase_d(const Geom &g, typename VT<R>::V *sm, typename VT<R>
         for (int pp = 0; pp < npass; ++pp) {
             const bool k0 = kk == 0 && pp == 0;
             const int ca = pp ? hM : kk, cb = pp ? hM : (kk == 0 ? M : M - kk);
-            row_pair_d<R>(g, sm, out, gi, grp, zp, ca, cb, k0, tw, stw, scale);
+            row_pair_d<R, PY>(g, sm, out, gi, grp, zp, ca, cb, k0, tw, stw, scale);
         }
     }
 }
@@ -488,7 +491,8 @@ __device__ __forceinline__ void row_fft(V (&v)[8], V *sm, const RowAddr &ad, int
 // LM > 0: the kernel only serves plans with M = 2^LM.
 // The body of one row-pass block (block index bx, field or batch member `field`); k_row runs it
 // as its own block, the persistent batch kernel once per work item.
-template <typename R, int MODE, int LM = 0>
+// PY > 0: only for plans with Pz == 1 and Py == PY.
+template <typename R, int MODE, int LM = 0, int PY = 0>
 __device__ __forceinline__ void row_body(const Geom &g, const RowArgs<R> &a, int bx, int field) {
     using V = typename VT<R>::V;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -530,7 +534,7 @@ __device__ __forceinline__ void row_body(const Geom &g, const RowArgs<R> &a, int
             __syncthreads();
             row_phase_b<R, false>(g, sm, ed, X, grp0, a.tw, stw, nullptr);
         } else {
-            row_phase_b<R, true>(g, sm, nullptr, X, grp0, a.tw, stw, pw);
+            row_phase_b<R, true, PY>(g, sm, nullptr, X, grp0, a.tw, stw, pw);
         }
     }
     __syncthreads();
@@ -586,7 +590,7 @@ __device__ __forceinline__ void row_body(const Geom &g, const RowArgs<R> &a, int
     __syncthreads();
     if (MODE == ROW_CUBE || MODE == ROW_FWD) {
         V *out = reinterpret_cast<V *>(a.out) + (size_t)field * g.nhalf;
-        row_phase_d<R>(g, sm, out, grp0, a.tw, stw, a.scale);
+        row_phase_d<R, PY>(g, sm, out, grp0, a.tw, stw, a.scale);
         if (g.Pz > 1) {
             __syncthreads();
             row_phase_e<R>(g, sm, out, grp0, stw, a.scale);
@@ -600,9 +604,9 @@ __device__ __forceinline__ void row_body(const Geom &g, const RowArgs<R> &a, int
     }
 }
 
-template <typename R, int MODE, int LM = 0>
+template <typename R, int MODE, int LM = 0, int PY = 0>
 __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_row(const Geom g, const RowArgs<R> a) {
-    row_body<R, MODE, LM>(g, a, blockIdx.x, blockIdx.y);
+    row_body<R, MODE, LM, PY>(g, a, blockIdx.x, blockIdx.y);
 }
 
 // ------------------------------------------------------------------------------------------
