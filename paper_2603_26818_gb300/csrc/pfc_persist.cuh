@@ -154,18 +154,34 @@ __device__ __forceinline__ void pb_mean(const PbClass<R> &c, int m, const PbArgs
 // gets the register allocation of its own kernel (at most 64 registers a thread), instead of one
 // allocation for the union of all bodies (which spilled heavily).
 
-// A psi^3 row-pass item: the row length fixed at compile time for M = 2^5 .. 2^8.
-template <typename R, int LM>
+// A psi^3 row-pass item: the row length fixed at compile time for M = 2^5 .. 2^8, and for the
+// FP32 2D classes (Pz = 1) Py too (as the per-class launches do).
+template <typename R, int LM, int PY = 0>
 __device__ __noinline__ void pb_row_cube_t(const PbClass<R> &c, int bx, int m) {
-    row_body<R, ROW_CUBE, LM>(c.g, c.cube, bx, m);
+    row_body<R, ROW_CUBE, LM, PY>(c.g, c.cube, bx, m);
+}
+template <typename R, int LM>
+__device__ __forceinline__ void pb_row_cube_py(const PbClass<R> &c, int bx, int m) {
+    if constexpr (sizeof(R) == 4) {
+        if (c.g.Pz == 1) {
+            switch (c.g.Py) {
+            case 1: pb_row_cube_t<R, LM, 1>(c, bx, m); return;
+            case 2: pb_row_cube_t<R, LM, 2>(c, bx, m); return;
+            case 4: pb_row_cube_t<R, LM, 4>(c, bx, m); return;
+            case 8: pb_row_cube_t<R, LM, 8>(c, bx, m); return;
+            default: break;
+            }
+        }
+    }
+    pb_row_cube_t<R, LM>(c, bx, m);
 }
 template <typename R>
 __device__ __forceinline__ void pb_row_cube(const PbClass<R> &c, int bx, int m) {
     switch (c.g.lM) {
-    case 5: pb_row_cube_t<R, 5>(c, bx, m); return;
-    case 6: pb_row_cube_t<R, 6>(c, bx, m); return;
-    case 7: pb_row_cube_t<R, 7>(c, bx, m); return;
-    case 8: pb_row_cube_t<R, 8>(c, bx, m); return;
+    case 5: pb_row_cube_py<R, 5>(c, bx, m); return;
+    case 6: pb_row_cube_py<R, 6>(c, bx, m); return;
+    case 7: pb_row_cube_py<R, 7>(c, bx, m); return;
+    case 8: pb_row_cube_py<R, 8>(c, bx, m); return;
     default: pb_row_cube_t<R, 0>(c, bx, m); return;
     }
 }
